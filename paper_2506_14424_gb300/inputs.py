@@ -1,0 +1,68 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds no arithmetic of the method itself: only random draws and
+the closed-form synthetic fields the workloads are built from. Every generator
+takes an explicit seed and uses numpy's ``default_rng``.
+
+* ``uniform_vector``  - U(-1, 1) DoF vectors (operator-apply inputs).
+* ``sinker``          - random sphere centres U(0.1, 0.9)^3 for the piecewise
+                        "sinker" viscosity field (radius 0.1, 8 spheres).
+* ``fourier_modes`` / ``fourier_field`` - a divergence-free velocity
+                        u(x) = sum_m c_m cos(2 pi k_m . x + phi_m) with integer
+                        wave vectors k_m (components in -3..3, k_m != 0),
+                        c_m = (k_m x a_m) / |k_m x a_m|, a_m ~ N(0, I),
+                        phi_m ~ U(0, 2 pi): unit amplitude per mode and
+                        exactly divergence-free because c_m . k_m = 0.
+"""
+import numpy as np
+
+
+def uniform_vector(n, seed):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=int(n))
+
+
+def sinker(seed, count=8, radius=0.1, nu_max=1e4, nu_matrix=1.0):
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(0.1, 0.9, size=(count, 3))
+    return {'law': 'sinker', 'centers': centers, 'radius': float(radius),
+            'nu_max': float(nu_max), 'nu_matrix': float(nu_matrix)}
+
+
+def carreau_blood_like():
+    """Carreau-Yasuda parameters of the 32^3 throughput workload."""
+    return {'law': 'carreau', 'eta0': 1.0, 'eta_inf': 1e-3, 'kappa': 1.0, 'lam': 1.0,
+            'a': 2.0, 'b': 0.5}
+
+
+def fourier_modes(seed, count=8, kmax=3):
+    rng = np.random.default_rng(seed)
+    ks, cs, phis = [], [], []
+    while len(ks) < count:
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        if not np.any(k):
+            continue
+        a = rng.standard_normal(3)
+        c = np.cross(k.astype(np.float64), a)
+        norm = np.linalg.norm(c)
+        if norm < 1e-12:
+            continue
+        ks.append(k.astype(np.float64))
+        cs.append(c / norm)
+        phis.append(rng.uniform(0.0, 2.0 * np.pi))
+    return np.array(ks), np.array(cs), np.array(phis)
+
+
+def fourier_field(points, modes):
+    """Evaluate the Fourier velocity at points (P, 3) -> (P, 3)."""
+    ks, cs, phis = modes
+    pts = np.asarray(points, dtype=np.float64)
+    arg = 2.0 * np.pi * pts @ ks.T + phis          # (P, m)
+    return np.cos(arg) @ cs
+
+
+def fourier_field_gradient(points, modes):
+    """d u_i / d x_j of ``fourier_field`` (P, 3, 3), for input checks."""
+    ks, cs, phis = modes
+    pts = np.asarray(points, dtype=np.float64)
+    arg = 2.0 * np.pi * pts @ ks.T + phis
+    return -2.0 * np.pi * np.einsum('pm,mi,mj->pij', np.sin(arg), cs, ks)
