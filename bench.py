@@ -1,0 +1,353 @@
+"""Benchmark of the SIPG viscous operator apply (and the solver around it) on GB300.
+
+Workload (the throughput configuration): unit cube, 32^3 affine hexahedra,
+velocity degree k = 3 (6,291,456 DoFs), Carreau-Yasuda viscosity (eta0 = 1,
+eta_inf = 1e-3, lambda = 1, a = 2, b = 0.5) evaluated from the gradient of a
+seeded divergence-free Fourier velocity (8 modes); one step = one FP64 apply
+y = A_visc(nu) x through the C ABI. Inputs exceed L2: four rotating x/y vector
+pairs (403 MB) plus the stored viscosity (42 MB).
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+(explicit element matrices) on a bounded sample of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS, K_U = 32, 3
+METRIC = "GDoF/s of SIPG viscous op apply"
+WORKLOAD = "box 32^3 affine hexes, k=3 velocity (6,291,456 DoFs), Carreau-Yasuda nu from Fourier field"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="skip the extra solve / precision lines")
+    p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ shared input
+def cfg2_velocity(node_points):
+    from paper_2506_14424_gb300 import inputs
+    modes = inputs.fourier_modes(1)
+    C = N_CELLS ** 3
+    u = inputs.fourier_field(node_points.reshape(-1, 3), modes)
+    return u.reshape(C, -1, 3).transpose(0, 2, 1).reshape(-1)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if still valid."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p)).get(kernel_key)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    src = open(os.path.join(ROOT, "paper_2506_14424_gb300", "csrc", rec["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
+# FP64 peak of this machine's GB300: own FMA-chain micro-benchmark.
+FP64_PEAK_TFLOPS = 1.01
+# Algorithmic flops per DoF of the k=3 viscous apply (minimal sum-factorised count).
+FLOP_PER_DOF = 250.0
+
+
+def algorithmic_bytes(n_dofs, cells, n):
+    return 16.0 * n_dofs + 8.0 * (cells * n ** 3 + 6 * cells * n ** 2)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_14424_gb300 import Context, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U)
+    n = ctx.n_dofs("viscous")
+    u = torch.tensor(cfg2_velocity(ctx.node_points("viscous", 0)), device="cuda")
+    ctx.set_viscosity(inputs.carreau_blood_like(), u)
+    del u
+    pairs = 4
+    xs = [torch.tensor(inputs.uniform_vector(n, seed=100 + i), device="cuda") for i in range(pairs)]
+    ys = [torch.empty_like(xs[0]) for _ in range(pairs)]
+    for i in range(args.warmup):
+        ctx.apply("viscous", xs[i % pairs], ys[i % pairs])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        ctx.apply("viscous", xs[i % pairs], ys[i % pairs])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        dist.barrier()
+    ms_step = ms / args.steps
+    value = n * args.steps * world / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    xh = np.ascontiguousarray(inputs.uniform_vector(n, seed=200))
+    for _ in range(2):
+        ctx.apply_host("viscous", xh)
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(e2e_steps):
+        ctx.apply_host("viscous", xh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    C = N_CELLS ** 3
+    nb = K_U + 1
+    alg_bytes = algorithmic_bytes(n, C, nb)
+    flops = FLOP_PER_DOF * n
+    achieved_tflops = flops / (ms_step * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic_record("apply_kernel<4,3,double>"),
+            "peak_source": "measured FP64 FMA rate (own micro-benchmark), MEASURED_PEAKS.json has no FP64 figure",
+            "hbm_achieved_gbs": alg_bytes / (ms_step * 1e-3) / 1e9,
+            "hbm_peak_gbs": peaks().get("hbm_gbs", 6686.1),
+            "hbm_frac": alg_bytes / (ms_step * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6686.1),
+            "algorithmic_bytes_per_launch": alg_bytes, "algorithmic_flops_per_launch": flops}
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = gpu_extras(ctx, xs, ys, stream)
+    line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": [N_CELLS] * 3, "k_u": K_U, "n_dofs": n,
+                       "l2": "inputs larger than L2: 4 rotating x/y pairs (403 MB) + 42 MB stored nu",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roof}
+    if rank == 0:
+        line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(sample_cells=1024)
+        line["extras"] = extras
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_apply(ctx, op, x, y, reps, stream, warm=3):
+    import torch
+    for _ in range(warm):
+        ctx.apply(op, x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.apply(op, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def gpu_extras(ctx, xs, ys, stream):
+    import numpy as np
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+
+    out = {}
+    n = ctx.n_dofs("viscous")
+    x32, y32 = xs[0].float(), ys[0].float()
+    ms = time_apply(ctx, "viscous", x32, y32, 20, stream)
+    out["viscous_f32_apply"] = {"ms": ms, "gdofs": n / ms / 1e6}
+    npr = ctx.n_dofs("poisson")
+    xp = torch.tensor(inputs.uniform_vector(npr, seed=300), device="cuda")
+    yp = torch.empty_like(xp)
+    ms = time_apply(ctx, "poisson", xp, yp, 50, stream)
+    out["poisson_f64_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr}
+    # mixed-precision vs all-FP64 multigrid solve, 16^3 cells, k = 4, sinker viscosity
+    solves = []
+    sink = inputs.sinker(seed=2, count=8, radius=0.1, nu_max=1.0)
+    for contrast in (1.0, 1e2, 1e4, 1e6):
+        sink["nu_max"] = contrast
+        row = {"contrast": contrast}
+        for prec in ("f32", "f64"):
+            c3 = Context(16, 16, 16, 4, mg_precision=prec)
+            c3.set_viscosity(sink)
+            nn = c3.n_dofs("viscous")
+            ustar = torch.tensor(inputs.uniform_vector(nn, seed=3), device="cuda")
+            b = c3.apply("viscous", ustar)
+            _, st = c3.solve("viscous", b, rtol=1e-8, precond="mg", maxit=300, check=False)
+            x, st = c3.solve("viscous", b, rtol=1e-8, precond="mg", maxit=300, check=False)
+            err = (torch.linalg.norm(x - ustar) / torch.linalg.norm(ustar)).item()
+            row[prec] = {"seconds": st["seconds"], "iterations": st["iterations"],
+                         "rel_residual": st["rel_residual"], "status": st["status"], "rel_error_vs_ustar": err}
+            c3.close()
+        row["mixed_speedup"] = row["f64"]["seconds"] / row["f32"]["seconds"]
+        solves.append(row)
+    out["cfg3_mg_solves_16cubed_k4"] = solves
+    return out
+
+
+# ------------------------------------------------------------- CPU oracle
+def _oracle_chunk(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle.mesh import BoxMesh
+    from oracle.sipg import SIPG
+    cells, seed = args
+    mesh = BoxMesh(N_CELLS, N_CELLS, N_CELLS)
+    S = SIPG(mesh, K_U, 3)
+    from paper_2506_14424_gb300 import inputs
+    need = set(cells)
+    for e in cells:
+        for f in range(6):
+            nb = mesh.neighbor(e, f)
+            if nb is not None:
+                need.add(nb)
+    # velocity on the needed cells only (same Fourier field as the GPU arm)
+    u = np.zeros((mesh.n_cells, 3, S.n ** 3))
+    modes = inputs.fourier_modes(1)
+    for e in need:
+        u[e] = inputs.fourier_field(S.node_points(e), modes).T
+    nc, nf = S.viscosity_at_points(inputs.carreau_blood_like(), u.reshape(-1), cells=sorted(need))
+    x = np.random.default_rng(seed).uniform(-1, 1, S.n_dofs)
+    t0 = time.perf_counter()
+    S.apply(x, nc, nf, cells=cells)
+    return time.perf_counter() - t0, len(cells) * S.n_dofs_cell
+
+
+def cpu_baseline(sample_cells=1024, workers=None):
+    """The oracle as it stands, timed on this host's cores on a sample of cells."""
+    import multiprocessing as mp
+    import numpy as np
+    workers = workers or os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    cells = rng.choice(N_CELLS ** 3, size=sample_cells, replace=False)
+    chunks = [(sorted(int(c) for c in ch), 9) for ch in np.array_split(cells, workers)]
+    ctxm = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctxm.Pool(workers) as pool:
+        res = pool.map(_oracle_chunk, chunks)
+    wall = time.perf_counter() - t0
+    dofs = sum(r[1] for r in res)
+    busy = max(r[0] for r in res)
+    return {"value": dofs / busy / 1e9, "unit": "GDoF/s", "cores": workers, "kind": "oracle",
+            "sample": f"{sample_cells} random cells of the 32^3 k=3 apply (rows of y), explicit element "
+                      f"blocks rebuilt per cell, {workers} spawn workers; value = DoFs / slowest worker's "
+                      f"apply time ({busy:.1f} s; wall incl. setup {wall:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sample = 256
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sample_cells=sample)
+        if i >= args.warmup:
+            times.append(cb)
+    value = statistics.mean(t["value"] for t in times)
+    ms_step = 1e3 * sample * 3 * (K_U + 1) ** 3 / (value * 1e9)
+    line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "cells": [N_CELLS] * 3, "k_u": K_U},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "kind": "oracle", "cores": times[0]["cores"],
+                             "sample": times[0]["sample"]},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,210 @@
+/*
+ * sipg.h - C ABI of libsipg, a GB300 (sm_103a) implementation of the
+ * matrix-free SIPG discontinuous Galerkin operators of arXiv 2506.14424
+ * ("Higher-order discontinuous Galerkin splitting schemes for fluids with
+ * variable viscosity") and of the CG / hp-multigrid solver around them.
+ *
+ * Conventions
+ *  - Every call returns int: SIPG_OK (0), SIPG_PENDING (1) or a negative
+ *    SIPG_ERR_* code. sipg_last_error() returns the message of the last
+ *    failing call on a context. No C++ exception crosses this boundary.
+ *  - "device" pointers are CUDA global-memory pointers of the current device
+ *    (for example torch.empty(..., device='cuda').data_ptr()); "host"
+ *    pointers are ordinary CPU memory. The caller owns every buffer passed
+ *    in; the library owns the context, the mesh hierarchy, the viscosity
+ *    storage, the multigrid levels and its workspaces. Nothing is freed
+ *    across the boundary.
+ *  - All work is ordered on the stream given to sipg_create (a cudaStream_t
+ *    passed as void*, 0 = legacy default stream). Calls marked (sync) block
+ *    until their work is done; the others are asynchronous.
+ *  - Vector layout (shared with every test): DoF index
+ *      ((cell * ncomp + c) * n + iz) * n * n + iy * n + ix,  n = k + 1,
+ *    cells lexicographic with x fastest, nodes = k+1 Gauss-Lobatto points per
+ *    direction on each cell. ncomp = 3 for velocity, 1 for pressure.
+ *  - Quadrature: k+1 Gauss-Legendre points per direction in cells and on
+ *    faces (Sec. 5 of the paper: as many quadrature as support points).
+ */
+#ifndef SIPG_H
+#define SIPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  SIPG_OK = 0,
+  SIPG_PENDING = 1,
+  SIPG_ERR_INVALID = -1,   /* bad argument, size or option */
+  SIPG_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  SIPG_ERR_NOMEM = -3,     /* allocation or HBM budget exceeded */
+  SIPG_ERR_MAXIT = -4,     /* solver hit its iteration limit */
+  SIPG_ERR_BREAKDOWN = -5, /* CG breakdown: p^T A p <= 0 */
+  SIPG_ERR_NAN = -6,       /* NaN or Inf met in a residual */
+  SIPG_ERR_TIMEOUT = -7,   /* a bounded wait ran out */
+  SIPG_ERR_STATE = -8      /* call out of order (e.g. solve before viscosity) */
+};
+
+enum { SIPG_BC_DIRICHLET = 0, SIPG_BC_NEUMANN = 1 };
+enum { SIPG_OP_VISCOUS = 0, SIPG_OP_POISSON = 1 };
+enum { SIPG_F64 = 0, SIPG_F32 = 1 };
+enum { SIPG_FACE_NU_MAX = 0, SIPG_FACE_NU_ARITH = 1, SIPG_FACE_NU_HARMONIC = 2 };
+enum { SIPG_LAW_CONSTANT = 0, SIPG_LAW_ANALYTIC = 1, SIPG_LAW_SINKER = 2, SIPG_LAW_CARREAU = 3 };
+enum { SIPG_PRECOND_NONE = 0, SIPG_PRECOND_JACOBI = 1, SIPG_PRECOND_MG = 2 };
+
+typedef struct sipg_ctx sipg_ctx;
+
+/* Box mesh [0,lx]x[0,ly]x[0,lz] cut into nx*ny*nz affine hexahedra (Sec. 5).
+ * Boundary types per box face in the order -x,+x,-y,+y,-z,+z; the pressure
+ * types apply to the Poisson operator (Dirichlet velocity walls normally go
+ * with Neumann pressure walls, Sec. 3.2). */
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz;
+  int bc_velocity[6];
+  int bc_pressure[6];
+} sipg_mesh_desc;
+
+/* Discretisation and solver options. Zero-initialised fields take the
+ * defaults in brackets (sipg_default_opts fills them in explicitly).
+ *  k_u            velocity degree, 2..5 (pressure degree k_u - 1) [3]
+ *  penalty_factor C_IP of tau = C_IP (k+1)^2 max(Lambda-,Lambda+) nubar;
+ *                 the paper takes tau "from Hillewaert 2013" without
+ *                 printing it (Sec. 5.1, 5.2) [1.0]
+ *  face_nu        nubar on a face point: SIPG_FACE_NU_* [MAX]
+ *  mg_precision   arithmetic of the multigrid V-cycle, SIPG_F32 / SIPG_F64
+ *                 (the paper: single precision, Sec. 5.4) [F32]
+ *  cheb_degree    Chebyshev-Jacobi smoother degree [3]
+ *  cheb_range     lmax / lmin of the smoother interval [20]
+ *  cheb_lmax_factor  safety factor on the Lanczos estimate [1.2]
+ *  lanczos_steps  Lanczos steps of the eigenvalue estimate [15]
+ *  coarse_max_dofs   direct solve below this many unknowns (Sec. 5.4) [2000]
+ *  seed           seed of the Lanczos start vector [0] */
+typedef struct {
+  int k_u;
+  double penalty_factor;
+  int face_nu;
+  int mg_precision;
+  int cheb_degree;
+  double cheb_range;
+  double cheb_lmax_factor;
+  int lanczos_steps;
+  int coarse_max_dofs;
+  uint64_t seed;
+} sipg_opts;
+
+/* Viscosity field (Eq. viscosity_general and Sec. 2).
+ *  CONSTANT  nu
+ *  ANALYTIC  nu(x) = 1 + 9 sin^2(pi x) sin^2(pi y) sin^2(pi z)
+ *  SINKER    n_spheres spheres (centers: HOST array of 3*n_spheres doubles,
+ *            copied during the call), radius, nu_max inside, nu_matrix
+ *            outside; projected onto one constant per cell (element-local L2
+ *            projection with the cell's Gauss rule)
+ *  CARREAU   eta(gdot) = eta_inf + (eta0 - eta_inf) (kappa + (lambda gdot)^a)^((b-1)/a),
+ *            gdot = sqrt(2 eps(u):eps(u)) of the linearization velocity */
+typedef struct {
+  int law;
+  double nu;
+  int n_spheres;
+  const double* centers;
+  double radius, nu_max, nu_matrix;
+  double eta0, eta_inf, kappa, lambda, a, b;
+} sipg_rheology;
+
+typedef struct {
+  double rtol;      /* relative residual target ||b - A x|| <= rtol ||b|| [1e-8] */
+  double atol;      /* absolute residual target [0] */
+  int maxit;        /* iteration limit [500] */
+  int precond;      /* SIPG_PRECOND_* [MG] */
+  double mass_coeff;/* m of the operator m M + A (viscous step, gamma0/dt) [0] */
+} sipg_solve_opts;
+
+typedef struct {
+  int iterations;
+  double rel_residual;   /* final ||r|| / ||b|| (recomputed, not recursive) */
+  double seconds;        /* wall time of the solve (host clock, sync) */
+  int status;            /* SIPG_OK or SIPG_ERR_* */
+} sipg_solve_stats;
+
+/* Fill *o with the defaults listed above. */
+void sipg_default_opts(sipg_opts* o);
+
+/* Create a context on the current CUDA device. Builds the multigrid level
+ * hierarchies of both operators (p-levels k -> 2 -> 1 of the velocity,
+ * k_p -> ... -> 1 of the pressure, then h-levels until fewer than
+ * coarse_max_dofs unknowns or an odd cell count, Sec. 5.4) and allocates
+ * their storage. Errors: SIPG_ERR_INVALID for k_u outside 2..5, non-positive
+ * sizes or bad boundary types; SIPG_ERR_NOMEM when the device is full. */
+int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts, void* stream, sipg_ctx** out);
+int sipg_destroy(sipg_ctx* ctx);
+const char* sipg_last_error(const sipg_ctx* ctx);
+
+/* Sizes: DoFs of a level's vector (level 0 = the fine space) and the level
+ * count of an operator's hierarchy. */
+int sipg_num_levels(const sipg_ctx* ctx, int op, int* n_levels);
+int sipg_level_info(const sipg_ctx* ctx, int op, int level, int* cells_xyz /*3*/, int* degree,
+                    int64_t* n_dofs);
+
+/* Evaluate the viscosity at the cell and face quadrature points of every
+ * multigrid level (Eq. viscosity_pointwise; Sec. 5.4: nu is stored at the
+ * integration points of each level and refreshed through the transfer
+ * operators when the linearization changes), then rebuild the inverse
+ * diagonals, the Chebyshev eigenvalue estimates and the coarse-level inverse
+ * of BOTH operators. u_lin: DEVICE FP64 velocity vector of the fine level,
+ * required for CARREAU, ignored otherwise. (sync) */
+int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const double* u_lin);
+
+/* y = (mass_coeff M + A) x on the fine level of operator op (A_visc of
+ * Eq. viscous_term_weak, or the SIPG Laplacian of Eq. pressure_step_weak).
+ * prec SIPG_F64: x, y DEVICE double*; SIPG_F32: DEVICE float*.
+ * x and y must not overlap. */
+int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double mass_coeff);
+
+/* Same as sipg_apply with FP64 HOST buffers: copies x to the device, applies,
+ * copies y back (sync). */
+int sipg_apply_host(sipg_ctx* ctx, int op, const double* x_host, double* y_host, double mass_coeff);
+
+/* Level-operator apply on multigrid level `level` (level 0 = fine). */
+int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, const void* x, void* y,
+                     double mass_coeff);
+
+/* Solve (mass_coeff M + A) x = b with FP64 CG (Sec. 5.4), preconditioned by
+ * nothing, the FP64 Jacobi diagonal, or the hp-multigrid V-cycle whose
+ * arithmetic is opts.mg_precision. b, x: DEVICE double*; x holds the initial
+ * guess on entry and the solution on return. For the all-Neumann Poisson
+ * operator, b and the iterates are kept mean-free (Sec. 3.2: the pressure is
+ * fixed up to a constant). (sync) */
+int sipg_solve(sipg_ctx* ctx, int op, const double* b, double* x, const sipg_solve_opts* so,
+               sipg_solve_stats* stats);
+
+/* ------------------------------------------------ multigrid pieces (tests) */
+/* Copy the stored viscosity of a level to DEVICE buffers: nu_cell
+ * [cells][n^3] and nu_face [cells][6][n^2] (the cell's own side of each face;
+ * faces -x,+x,-y,+y,-z,+z; face point a + n b over the face's tangential
+ * directions in increasing order). */
+int sipg_get_viscosity(const sipg_ctx* ctx, int level, double* nu_cell, double* nu_face);
+/* FP64 inverse diagonal of a level operator (with mass_coeff of the last
+ * set_viscosity / solve call: 0 unless a solve set it) into a DEVICE buffer. */
+int sipg_get_inverse_diagonal(const sipg_ctx* ctx, int op, int level, double* out);
+/* Largest eigenvalue estimate of D^-1 A on a level (before the 1.2 factor). */
+int sipg_get_lmax_estimate(const sipg_ctx* ctx, int op, int level, double* lmax);
+/* Prolongate level+1 -> level (dir = +1) or restrict level -> level+1
+ * (dir = -1, the transpose). DEVICE buffers of precision prec. */
+int sipg_transfer(sipg_ctx* ctx, int op, int level, int dir, int prec, const void* in, void* out);
+/* One Chebyshev-Jacobi smoother application on a level: x <- S(x, b),
+ * DEVICE buffers of precision prec, x updated in place. */
+int sipg_smooth(sipg_ctx* ctx, int op, int level, int prec, const void* b, void* x);
+/* One V-cycle x = V(b) from a zero initial guess, FP64 DEVICE buffers on
+ * level 0 (internally in opts.mg_precision). */
+int sipg_vcycle(sipg_ctx* ctx, int op, const double* b, double* x);
+/* Physical coordinates of the Gauss-Lobatto nodes of a level into a HOST
+ * buffer [cells][n^3][3] (for building interpolated input fields). */
+int sipg_node_points(const sipg_ctx* ctx, int op, int level, double* xyz_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIPG_H */

@@ -21,6 +21,14 @@ Readings (the paper does not print these details):
 * Linearization velocity on a coarse level = interpolation of the fine field
   at the coarse Gauss-Lobatto nodes; a coarse node on an interface between
   two children is taken from the child with the lower index.
+* Viscosity on the levels (Sec. 5.4: the quadrature-point data of all levels
+  is updated through the transfer operators): the analytic field is evaluated
+  at each level's points; Carreau-Yasuda from the interpolated velocity; the
+  cellwise-constant sphere field is carried down by the transfer of
+  piecewise constants - the same value on a p-level, the mean of the eight
+  children on an h-level (its L2 projection). Re-evaluating the sphere field
+  with each level's coarser Gauss rule instead gives levels that disagree and
+  a V-cycle that stalls at high contrast (a test keeps that comparison).
 Pinned in tests: prolongation reproduces coarse polynomials exactly;
 restriction equals the transpose; the smoother's error propagation equals the
 closed-form scaled Chebyshev polynomial on eigenvectors. The V-cycle as a whole
@@ -112,6 +120,33 @@ def interpolate_down_h(u_fine, mesh_fine, mesh_coarse, k, ncomp):
                     w = np.einsum('z,y,x->zyx', L[jz], L[jy], L[jx])
                     out[ec, :, jz, jy, jx] = np.einsum('czyx,zyx->c', Ufine[ef], w)
     return out.reshape(-1)
+
+
+def level_viscosity(levels, rheology, u=None):
+    """[(nu_cell, nu_face)] per level (fine to coarse), per the readings above."""
+    from .sipg import SIPG
+    out, discs, u_l = [], [], u
+    for l, (m, k) in enumerate(levels):
+        S = SIPG(m, k, 3)
+        if l > 0:
+            Fm, Fk = levels[l - 1]
+            if rheology['law'] == 'carreau':
+                u_l = (interpolate_down_p(u_l, m, Fk, k, 3) if Fm.n_cells == m.n_cells
+                       else interpolate_down_h(u_l, Fm, m, k, 3))
+            if rheology['law'] == 'sinker' and rheology.get('projection', 'cell') == 'cell':
+                fine = out[-1][0][:, 0]
+                if Fm.n_cells == m.n_cells:
+                    v = fine.copy()
+                else:
+                    v = np.zeros(m.n_cells)
+                    for ef in range(Fm.n_cells):
+                        i, j, kk = Fm.cell_ijk(ef)
+                        v[m.cell_index((i // 2, j // 2, kk // 2))] += fine[ef] / 8.0
+                out.append((np.repeat(v[:, None], S.nq ** 3, 1),
+                            np.repeat(v[:, None, None], 6, 1).repeat(S.nq ** 2, 2)))
+                continue
+        out.append(S.viscosity_at_points(rheology, u_l))
+    return out
 
 
 def inverse_diagonal(A):

@@ -138,11 +138,12 @@ class SIPG:
         return V, G
 
     # ------------------------------------------------------------- viscosity
-    def viscosity_at_points(self, rheology, u=None):
+    def viscosity_at_points(self, rheology, u=None, cells=None):
         """nu_cell (C, nq^3) and nu_face (C, 6, nq^2) per Eq. (viscosity_pointwise).
 
         For the Carreau-Yasuda law the gradient of the DoF vector u is taken on
-        each side from that side's own cell (face values differ per side)."""
+        each side from that side's own cell (face values differ per side).
+        ``cells`` restricts the evaluation to a subset (others stay zero)."""
         C = self.mesh.n_cells
         nq3, nq2 = self.nq ** 3, self.nq ** 2
         nu_cell = np.zeros((C, nq3))
@@ -150,7 +151,7 @@ class SIPG:
         needs_u = rheology['law'] == 'carreau'
         if needs_u and u is None:
             raise ValueError("Carreau-Yasuda viscosity needs the velocity vector")
-        for e in range(C):
+        for e in (range(C) if cells is None else cells):
             ue = None
             if needs_u:
                 ue = np.asarray(u).reshape(C, 3, self.n ** 3)[e]

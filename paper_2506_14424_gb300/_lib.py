@@ -1,0 +1,103 @@
+"""ctypes binding of libsipg (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts Python
+arguments to the C structs of ``include/sipg.h`` and passes device pointers of
+caller-owned torch tensors through. It never falls back to a CPU path: if the
+shared library is missing or fails to load, it raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsipg.so")
+
+SIPG_OK, SIPG_PENDING = 0, 1
+ERRORS = {-1: "SIPG_ERR_INVALID", -2: "SIPG_ERR_CUDA", -3: "SIPG_ERR_NOMEM", -4: "SIPG_ERR_MAXIT",
+          -5: "SIPG_ERR_BREAKDOWN", -6: "SIPG_ERR_NAN", -7: "SIPG_ERR_TIMEOUT", -8: "SIPG_ERR_STATE"}
+OP = {"viscous": 0, "poisson": 1}
+PREC = {"f64": 0, "f32": 1}
+LAW = {"constant": 0, "analytic": 1, "sinker": 2, "carreau": 3}
+PRECOND = {"none": 0, "jacobi": 1, "mg": 2}
+FACE_NU = {"max": 0, "arith": 1, "harmonic": 2}
+BC = {"D": 0, "N": 1}
+
+# Every symbol declared in include/sipg.h (checked by the CPU test suite).
+EXPORTS = [
+    "sipg_default_opts", "sipg_create", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
+    "sipg_level_info", "sipg_set_viscosity", "sipg_apply", "sipg_apply_host", "sipg_level_apply",
+    "sipg_solve", "sipg_get_viscosity", "sipg_get_inverse_diagonal", "sipg_get_lmax_estimate",
+    "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points",
+]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("bc_velocity", ctypes.c_int * 6), ("bc_pressure", ctypes.c_int * 6)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("k_u", ctypes.c_int), ("penalty_factor", ctypes.c_double), ("face_nu", ctypes.c_int),
+                ("mg_precision", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_range", ctypes.c_double),
+                ("cheb_lmax_factor", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
+                ("coarse_max_dofs", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class Rheology(ctypes.Structure):
+    _fields_ = [("law", ctypes.c_int), ("nu", ctypes.c_double), ("n_spheres", ctypes.c_int),
+                ("centers", ctypes.POINTER(ctypes.c_double)), ("radius", ctypes.c_double),
+                ("nu_max", ctypes.c_double), ("nu_matrix", ctypes.c_double), ("eta0", ctypes.c_double),
+                ("eta_inf", ctypes.c_double), ("kappa", ctypes.c_double), ("lam", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("precond", ctypes.c_int), ("mass_coeff", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libsipg.so (raises OSError/RuntimeError if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libsipg is not built ({p} missing): run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "sipg_default_opts": (None, [P(Opts)]),
+        "sipg_create": (i, [P(MeshDesc), P(Opts), vp, P(vp)]),
+        "sipg_destroy": (i, [vp]),
+        "sipg_last_error": (ctypes.c_char_p, [vp]),
+        "sipg_num_levels": (i, [vp, i, P(i)]),
+        "sipg_level_info": (i, [vp, i, i, P(ctypes.c_int * 3), P(i), P(i64)]),
+        "sipg_set_viscosity": (i, [vp, P(Rheology), vp]),
+        "sipg_apply": (i, [vp, i, i, vp, vp, d]),
+        "sipg_apply_host": (i, [vp, i, vp, vp, d]),
+        "sipg_level_apply": (i, [vp, i, i, i, vp, vp, d]),
+        "sipg_solve": (i, [vp, i, vp, vp, P(SolveOpts), P(SolveStats)]),
+        "sipg_get_viscosity": (i, [vp, i, vp, vp]),
+        "sipg_get_inverse_diagonal": (i, [vp, i, i, vp]),
+        "sipg_get_lmax_estimate": (i, [vp, i, i, P(d)]),
+        "sipg_transfer": (i, [vp, i, i, i, i, vp, vp]),
+        "sipg_smooth": (i, [vp, i, i, i, vp, vp]),
+        "sipg_vcycle": (i, [vp, i, vp, vp]),
+        "sipg_node_points": (i, [vp, i, i, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,209 @@
+"""Python face of libsipg: a thin wrapper over the C ABI of ``include/sipg.h``.
+
+PyTorch supplies device memory and the stream; every step of the operator,
+viscosity and solver path runs in the library's CUDA kernels. Function names
+follow the C calls (``sipg_apply`` -> ``Context.apply`` and so on).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class SipgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{L.ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda(t, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+
+
+def rheology_struct(rh):
+    r = L.Rheology()
+    r.law = L.LAW[rh['law']]
+    keep = None
+    if rh['law'] == 'constant':
+        r.nu = float(rh['nu'])
+    elif rh['law'] == 'sinker':
+        c = np.ascontiguousarray(np.asarray(rh['centers'], dtype=np.float64).reshape(-1))
+        keep = c
+        r.n_spheres = len(c) // 3
+        r.centers = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.radius, r.nu_max, r.nu_matrix = float(rh['radius']), float(rh['nu_max']), float(rh['nu_matrix'])
+    elif rh['law'] == 'carreau':
+        r.eta0, r.eta_inf, r.kappa = float(rh['eta0']), float(rh['eta_inf']), float(rh['kappa'])
+        r.lam, r.a, r.b = float(rh['lam']), float(rh['a']), float(rh['b'])
+    return r, keep
+
+
+class Context:
+    """One mesh, degree and multigrid hierarchy on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
+                 penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
+                 cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, stream=None):
+        self._lib = L.load()
+        m = L.MeshDesc()
+        m.nx, m.ny, m.nz = int(nx), int(ny), int(nz)
+        m.lx, m.ly, m.lz = (float(v) for v in extent)
+        for i in range(6):
+            m.bc_velocity[i] = L.BC[bc_velocity[i]]
+            m.bc_pressure[i] = L.BC[bc_pressure[i]]
+        o = L.Opts()
+        o.k_u = int(k_u)
+        o.penalty_factor = float(penalty_factor)
+        o.face_nu = L.FACE_NU[face_nu]
+        o.mg_precision = L.PREC[mg_precision]
+        o.cheb_degree = int(cheb_degree)
+        o.cheb_range = float(cheb_range)
+        o.cheb_lmax_factor = float(cheb_lmax_factor)
+        o.lanczos_steps = int(lanczos_steps)
+        o.coarse_max_dofs = int(coarse_max_dofs)
+        o.seed = int(seed)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = self._lib.sipg_create(ctypes.byref(m), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.byref(h))
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, "sipg_create failed (see stderr)")
+        self._h = h
+        self.k_u = int(k_u)
+        self.cells = (int(nx), int(ny), int(nz))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sipg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, self._lib.sipg_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- sizes
+    def num_levels(self, op="viscous"):
+        n = ctypes.c_int()
+        self._check(self._lib.sipg_num_levels(self._h, L.OP[op], ctypes.byref(n)))
+        return n.value
+
+    def level_info(self, op="viscous", level=0):
+        cells = (ctypes.c_int * 3)()
+        k = ctypes.c_int()
+        nd = ctypes.c_int64()
+        self._check(self._lib.sipg_level_info(self._h, L.OP[op], level, ctypes.byref(cells), ctypes.byref(k),
+                                              ctypes.byref(nd)))
+        return tuple(cells), k.value, nd.value
+
+    def n_dofs(self, op="viscous", level=0):
+        return self.level_info(op, level)[2]
+
+    # ------------------------------------------------------------ viscosity
+    def set_viscosity(self, rheology, u_lin=None):
+        r, keep = rheology_struct(rheology)
+        if u_lin is not None:
+            _need_cuda(u_lin, torch.float64)
+        self._check(self._lib.sipg_set_viscosity(self._h, ctypes.byref(r), _ptr(u_lin)))
+        del keep
+
+    def get_viscosity(self, level=0):
+        (nx, ny, nz), k, _ = self.level_info("viscous", level)
+        n = k + 1
+        C = nx * ny * nz
+        dev = torch.device("cuda")
+        nc = torch.empty(C * n ** 3, dtype=torch.float64, device=dev)
+        nf = torch.empty(C * 6 * n * n, dtype=torch.float64, device=dev)
+        self._check(self._lib.sipg_get_viscosity(self._h, level, _ptr(nc), _ptr(nf)))
+        return nc.view(C, n ** 3), nf.view(C, 6, n * n)
+
+    # ---------------------------------------------------------------- apply
+    def apply(self, op, x, y=None, mass=0.0, level=0):
+        _need_cuda(x)
+        prec = L.PREC["f64" if x.dtype == torch.float64 else "f32"]
+        if y is None:
+            y = torch.empty_like(x)
+        _need_cuda(y, x.dtype)
+        if x.numel() != self.n_dofs(op, level) or y.numel() != x.numel():
+            raise ValueError("vector size does not match the level")
+        self._check(self._lib.sipg_level_apply(self._h, L.OP[op], level, prec, _ptr(x), _ptr(y), float(mass)))
+        return y
+
+    def apply_host(self, op, x, mass=0.0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if x.size != self.n_dofs(op):
+            raise ValueError("vector size does not match the fine level")
+        y = np.empty_like(x)
+        self._check(self._lib.sipg_apply_host(self._h, L.OP[op], x.ctypes.data_as(ctypes.c_void_p),
+                                              y.ctypes.data_as(ctypes.c_void_p), float(mass)))
+        return y
+
+    # ---------------------------------------------------------------- solve
+    def solve(self, op, b, x=None, rtol=1e-8, atol=0.0, maxit=500, precond="mg", mass=0.0, check=True):
+        _need_cuda(b, torch.float64)
+        if x is None:
+            x = torch.zeros_like(b)
+        _need_cuda(x, torch.float64)
+        so = L.SolveOpts(float(rtol), float(atol), int(maxit), L.PRECOND[precond], float(mass))
+        st = L.SolveStats()
+        rc = self._lib.sipg_solve(self._h, L.OP[op], _ptr(b), _ptr(x), ctypes.byref(so), ctypes.byref(st))
+        stats = {"iterations": st.iterations, "rel_residual": st.rel_residual, "seconds": st.seconds,
+                 "status": st.status}
+        if check and rc != L.SIPG_OK:
+            raise SipgError(rc, self._lib.sipg_last_error(self._h).decode())
+        return x, stats
+
+    # ------------------------------------------------------- multigrid bits
+    def inverse_diagonal(self, op="viscous", level=0):
+        out = torch.empty(self.n_dofs(op, level), dtype=torch.float64, device="cuda")
+        self._check(self._lib.sipg_get_inverse_diagonal(self._h, L.OP[op], level, _ptr(out)))
+        return out
+
+    def lmax_estimate(self, op="viscous", level=0):
+        v = ctypes.c_double()
+        self._check(self._lib.sipg_get_lmax_estimate(self._h, L.OP[op], level, ctypes.byref(v)))
+        return v.value
+
+    def transfer(self, op, level, direction, x):
+        _need_cuda(x)
+        prec = L.PREC["f64" if x.dtype == torch.float64 else "f32"]
+        n_out = self.n_dofs(op, level if direction > 0 else level + 1)
+        out = torch.empty(n_out, dtype=x.dtype, device=x.device)
+        self._check(self._lib.sipg_transfer(self._h, L.OP[op], level, int(direction), prec, _ptr(x), _ptr(out)))
+        return out
+
+    def smooth(self, op, level, b, x):
+        _need_cuda(b)
+        _need_cuda(x, b.dtype)
+        prec = L.PREC["f64" if b.dtype == torch.float64 else "f32"]
+        self._check(self._lib.sipg_smooth(self._h, L.OP[op], level, prec, _ptr(b), _ptr(x)))
+        return x
+
+    def vcycle(self, op, b):
+        _need_cuda(b, torch.float64)
+        x = torch.empty_like(b)
+        self._check(self._lib.sipg_vcycle(self._h, L.OP[op], _ptr(b), _ptr(x)))
+        return x
+
+    def node_points(self, op="viscous", level=0):
+        (nx, ny, nz), k, _ = self.level_info(op, level)
+        n = k + 1
+        out = np.empty((nx * ny * nz, n ** 3, 3))
+        self._check(self._lib.sipg_node_points(self._h, L.OP[op], level, out.ctypes.data_as(ctypes.c_void_p)))
+        return out

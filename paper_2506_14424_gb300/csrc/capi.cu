@@ -1,0 +1,533 @@
+// libsipg C ABI: context, level hierarchy, viscosity update, operator apply,
+// FP64 CG with a Chebyshev-smoothed hp-multigrid V-cycle (Sec. 5.4 of the
+// paper: CG for the pressure and viscous steps; multigrid that lowers the
+// degree, then coarsens the mesh; Chebyshev-accelerated Jacobi smoothing with
+// precomputed inverse diagonals; single-precision preconditioner with a
+// double-precision direct solve below 2000 unknowns).
+#include "../../include/sipg.h"
+#include "ctx.h"
+#include "kernels.cuh"
+#include "tables.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace sipg;
+
+#define CK(expr)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess) return ctx->fail(SIPG_ERR_CUDA, #expr, e_);        \
+  } while (0)
+
+int sipg_ctx::fail(int code, const char* what, cudaError_t e) {
+  char buf[512];
+  if (e != cudaSuccess)
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  else
+    snprintf(buf, sizeof buf, "%s", what);
+  err = buf;
+  return code;
+}
+
+namespace {
+
+template <typename T>
+T* dalloc(int64_t n, cudaError_t* e) {
+  void* p = nullptr;
+  *e = cudaMalloc(&p, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  if (*e == cudaSuccess) *e = cudaMemset(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  return (T*)p;
+}
+
+bool valid_bc(const int* bc) {
+  for (int i = 0; i < 6; ++i)
+    if (bc[i] != SIPG_BC_DIRICHLET && bc[i] != SIPG_BC_NEUMANN) return false;
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ construction
+int sipg_ctx::build_hierarchy(int op) {
+  Hier& H = hier[op];
+  H.op = op;
+  H.ncomp = op == SIPG_OP_VISCOUS ? 3 : 1;
+  const int k0 = op == SIPG_OP_VISCOUS ? opts.k_u : opts.k_u - 1;
+  const int* bc = op == SIPG_OP_VISCOUS ? mesh.bc_velocity : mesh.bc_pressure;
+  std::vector<int> ks{k0};
+  if (k0 > 2) ks.push_back(2);
+  if (k0 > 1) ks.push_back(1);
+  int nx = mesh.nx, ny = mesh.ny, nz = mesh.nz;
+  auto make_level = [&](int k, int lnx, int lny, int lnz) {
+    Level L{};
+    L.k = k;
+    L.n = k + 1;
+    L.g.nx = lnx;
+    L.g.ny = lny;
+    L.g.nz = lnz;
+    L.g.ncells = lnx * lny * lnz;
+    L.g.h[0] = mesh.lx / lnx;
+    L.g.h[1] = mesh.ly / lny;
+    L.g.h[2] = mesh.lz / lnz;
+    for (int i = 0; i < 6; ++i) L.g.bc[i] = bc[i];
+    L.g.cip = opts.penalty_factor;
+    L.g.face_nu = opts.face_nu;
+    L.ndofs = (int64_t)L.g.ncells * H.ncomp * L.n * L.n * L.n;
+    return L;
+  };
+  H.L.clear();
+  for (int k : ks) H.L.push_back(make_level(k, nx, ny, nz));
+  while (H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
+    nx /= 2;
+    ny /= 2;
+    nz /= 2;
+    H.L.push_back(make_level(H.L.back().k, nx, ny, nz));
+  }
+  for (size_t l = 0; l + 1 < H.L.size(); ++l) {
+    Level& F = H.L[l];
+    Level& C = H.L[l + 1];
+    if (C.g.ncells == F.g.ncells) {
+      F.next_kind = 1;
+      F.tt = make_p_transfer(F.n, C.n);
+      F.interp = make_p_interp_down(F.n, C.n);
+    } else {
+      F.next_kind = 2;
+      F.tt = make_h_transfer(F.n);
+      F.interp = make_h_interp_down(F.n, F.child);
+    }
+  }
+  H.singular = true;  // all-Neumann operator: constants (Poisson) / rigid modes (viscous)
+  for (int i = 0; i < 6; ++i)
+    if (bc[i] == SIPG_BC_DIRICHLET) H.singular = false;
+  // storage
+  cudaError_t e = cudaSuccess;
+  for (size_t l = 0; l < H.L.size(); ++l) {
+    Level& L = H.L[l];
+    const int64_t C = L.g.ncells, n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
+    if (op == SIPG_OP_VISCOUS) {
+      L.nu_cell64 = dalloc<double>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_face64 = dalloc<double>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_cell32 = dalloc<float>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_face32 = dalloc<float>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      if (l > 0) { L.ulin = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc ulin", e); }
+    }
+    L.diag64 = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    L.dinv64 = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    L.dinv32 = dalloc<float>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    for (int p = 0; p < 2; ++p) {
+      const size_t es = p == 0 ? sizeof(double) : sizeof(float);
+      for (int v = 0; v < 4; ++v) {
+        void* ptr = nullptr;
+        e = cudaMalloc(&ptr, es * (size_t)L.ndofs);
+        if (e == cudaSuccess) e = cudaMemset(ptr, 0, es * (size_t)L.ndofs);
+        if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
+        L.w[p][v] = ptr;
+      }
+    }
+  }
+  Level& Cl = H.L.back();
+  Cl.N = (int)Cl.ndofs;
+  if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
+  Cl.Ainv = dalloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  Cl.Atmp = dalloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  // CG vectors on level 0
+  for (int v = 0; v < 5; ++v) {
+    H.cg[v] = dalloc<double>(H.L[0].ndofs, &e);
+    if (e) return fail(SIPG_ERR_NOMEM, "alloc cg", e);
+  }
+  return SIPG_OK;
+}
+
+sipg_ctx::~sipg_ctx() {
+  for (Hier& H : hier) {
+    for (Level& L : H.L) {
+      cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
+      cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32);
+      for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
+      cudaFree(L.Ainv); cudaFree(L.Atmp);
+    }
+    for (double*& p : H.cg) cudaFree(p);
+  }
+  cudaFree(partials); cudaFree(dscal); cudaFree(dflag); cudaFree(host_x); cudaFree(host_y);
+  if (hscal) cudaFreeHost(hscal);
+}
+
+extern "C" void sipg_default_opts(sipg_opts* o) {
+  std::memset(o, 0, sizeof *o);
+  o->k_u = 3;
+  o->penalty_factor = 1.0;
+  o->face_nu = SIPG_FACE_NU_MAX;
+  o->mg_precision = SIPG_F32;
+  o->cheb_degree = 3;
+  o->cheb_range = 20.0;
+  o->cheb_lmax_factor = 1.2;
+  o->lanczos_steps = 15;
+  o->coarse_max_dofs = 2000;
+  o->seed = 0;
+}
+
+extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in, void* stream, sipg_ctx** out) {
+  if (!out || !mesh) return SIPG_ERR_INVALID;
+  *out = nullptr;
+  sipg_opts o;
+  sipg_default_opts(&o);
+  if (opts_in) {
+    o = *opts_in;
+    sipg_opts d;
+    sipg_default_opts(&d);
+    if (o.penalty_factor == 0) o.penalty_factor = d.penalty_factor;
+    if (o.cheb_degree == 0) o.cheb_degree = d.cheb_degree;
+    if (o.cheb_range == 0) o.cheb_range = d.cheb_range;
+    if (o.cheb_lmax_factor == 0) o.cheb_lmax_factor = d.cheb_lmax_factor;
+    if (o.lanczos_steps == 0) o.lanczos_steps = d.lanczos_steps;
+    if (o.coarse_max_dofs == 0) o.coarse_max_dofs = d.coarse_max_dofs;
+    if (o.k_u == 0) o.k_u = d.k_u;
+  }
+  if (o.k_u < 2 || o.k_u > 5) return SIPG_ERR_INVALID;
+  if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0 || !(mesh->lx > 0) || !(mesh->ly > 0) || !(mesh->lz > 0))
+    return SIPG_ERR_INVALID;
+  if ((int64_t)mesh->nx * mesh->ny * mesh->nz > (int64_t)1 << 28) return SIPG_ERR_INVALID;
+  if (!valid_bc(mesh->bc_velocity) || !valid_bc(mesh->bc_pressure)) return SIPG_ERR_INVALID;
+  if (o.mg_precision != SIPG_F32 && o.mg_precision != SIPG_F64) return SIPG_ERR_INVALID;
+  if (o.face_nu < 0 || o.face_nu > 2 || o.cheb_degree < 1 || o.lanczos_steps < 2) return SIPG_ERR_INVALID;
+  sipg_ctx* ctx = new sipg_ctx();
+  ctx->mesh = *mesh;
+  ctx->opts = o;
+  ctx->st = (cudaStream_t)stream;
+  for (int n = 2; n <= kMaxN; ++n) ctx->tabs[n] = make_tab(n);
+  cudaError_t e = cudaSuccess;
+  int rc = SIPG_OK;
+  for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);
+  if (rc == SIPG_OK) {
+    ctx->partials = dalloc<double>(kDotBlocks, &e);
+    if (!e) ctx->dscal = dalloc<double>(16, &e);
+    if (!e) ctx->dflag = dalloc<int>(4, &e);
+    if (!e) e = cudaMallocHost(&ctx->hscal, 16 * sizeof(double));
+    if (e) rc = ctx->fail(SIPG_ERR_NOMEM, "alloc scalars", e);
+  }
+  if (rc == SIPG_OK) rc = ctx->setup_operator(SIPG_OP_POISSON, 0.0);  // no viscosity needed
+  if (rc != SIPG_OK) {
+    fprintf(stderr, "sipg_create: %s\n", ctx->err.c_str());
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return SIPG_OK;
+}
+
+extern "C" int sipg_destroy(sipg_ctx* ctx) {
+  if (!ctx) return SIPG_ERR_INVALID;
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+  return SIPG_OK;
+}
+
+extern "C" const char* sipg_last_error(const sipg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int sipg_num_levels(const sipg_ctx* ctx, int op, int* n) {
+  if (!ctx || (op != 0 && op != 1) || !n) return SIPG_ERR_INVALID;
+  *n = (int)ctx->hier[op].L.size();
+  return SIPG_OK;
+}
+
+extern "C" int sipg_level_info(const sipg_ctx* ctx, int op, int level, int* cells, int* degree, int64_t* ndofs) {
+  if (!ctx || (op != 0 && op != 1)) return SIPG_ERR_INVALID;
+  const Hier& H = ctx->hier[op];
+  if (level < 0 || level >= (int)H.L.size()) return SIPG_ERR_INVALID;
+  const Level& L = H.L[level];
+  if (cells) { cells[0] = L.g.nx; cells[1] = L.g.ny; cells[2] = L.g.nz; }
+  if (degree) *degree = L.k;
+  if (ndofs) *ndofs = L.ndofs;
+  return SIPG_OK;
+}
+
+// ------------------------------------------------------------ level pieces
+template <typename T>
+int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
+  sipg_ctx* ctx = this;
+  const Hier& H = hier[op];
+  const Level& L = H.L[l];
+  const T* nc = nullptr;
+  const T* nf = nullptr;
+  if (op == SIPG_OP_VISCOUS) {
+    if constexpr (sizeof(T) == 8) { nc = (const T*)L.nu_cell64; nf = (const T*)L.nu_face64; }
+    else { nc = (const T*)L.nu_cell32; nf = (const T*)L.nu_face32; }
+  }
+  CK((launch_apply<T>(L.n, H.ncomp, L.g, tabs[L.n], x, y, nc, nf, T(mass), 1, st)));
+  return SIPG_OK;
+}
+
+int sipg_ctx::dot(int64_t n, const double* a, const double* b, double* out_host) {
+  sipg_ctx* ctx = this;
+  CK(launch_dot(n, a, b, partials, dscal, st));
+  CK(cudaMemcpyAsync(hscal, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out_host = hscal[0];
+  return SIPG_OK;
+}
+
+// remove the mean (Euclidean projection onto the complement of constants)
+int sipg_ctx::project_mean(int64_t n, double* v) {
+  sipg_ctx* ctx = this;
+  CK(launch_sum(n, v, partials, dscal + 1, st));
+  CK(launch_add_const(n, dscal + 1, -1.0 / (double)n, v, st));
+  return SIPG_OK;
+}
+
+// Largest eigenvalue of a symmetric tridiagonal matrix by bisection on the
+// Sturm sequence count.
+static double tridiag_lmax(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      q = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
+  sipg_ctx* ctx = this;
+  Hier& H = hier[op];
+  Level& L = H.L[l];
+  const double* nc = op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr;
+  const double* nf = op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr;
+  CK(launch_diagonal(L.n, H.ncomp, L.g, tabs[L.n], nc, nf, mass, L.diag64, st));
+  CK(launch_reciprocal(L.ndofs, L.diag64, L.dinv64, st));
+  CK((launch_cast<double, float>(L.ndofs, L.dinv64, L.dinv32, st)));
+  if (l + 1 == (int)H.L.size()) return SIPG_OK;
+  // Lanczos on D^-1/2 A D^-1/2 with FP64 level applies
+  double* q = (double*)L.w[0][0];
+  double* qp = (double*)L.w[0][1];
+  double* w = (double*)L.w[0][2];
+  double* t = (double*)L.w[0][3];
+  const int64_t n = L.ndofs;
+  CK(launch_random(n, opts.seed + 7919ull * (uint64_t)(l + 1) + 104729ull * (uint64_t)op, q, st));
+  if (H.singular && op == SIPG_OP_POISSON) { int rc = project_mean(n, q); if (rc) return rc; }
+  double nrm;
+  int rc = dot(n, q, q, &nrm);
+  if (rc) return rc;
+  CK(launch_scale(n, 1.0 / std::sqrt(nrm), q, q, st));
+  CK(launch_fill<double>(n, 0.0, qp, st));
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int j = 0; j < opts.lanczos_steps; ++j) {
+    // w = s A (s q) - beta q_prev, s = sqrt(dinv)
+    CK((launch_cast<double, double>(n, L.dinv64, t, st)));
+    sqrt_inplace(n, t);
+    CK(launch_mul(n, t, q, w, st));
+    rc = level_apply<double>(op, l, w, t, mass);
+    if (rc) return rc;
+    CK((launch_cast<double, double>(n, L.dinv64, w, st)));
+    sqrt_inplace(n, w);
+    CK(launch_mul(n, w, t, w, st));
+    if (j > 0) CK(launch_add_scaled_f64(n, -beta, qp, w, st));
+    double alpha;
+    rc = dot(n, q, w, &alpha);
+    if (rc) return rc;
+    CK(launch_add_scaled_f64(n, -alpha, q, w, st));
+    double bb;
+    rc = dot(n, w, w, &bb);
+    if (rc) return rc;
+    al.push_back(alpha);
+    beta = std::sqrt(bb);
+    if (!(beta > 1e-300) || j + 1 == opts.lanczos_steps) break;
+    be.push_back(beta);
+    std::swap(q, qp);  // qp <- old q
+    CK(launch_scale(n, 1.0 / beta, w, q, st));
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  L.lmax = tridiag_lmax(al, be);
+  // leave the work vectors zeroed for later use
+  for (int v = 0; v < 4; ++v) CK(cudaMemsetAsync(L.w[0][v], 0, sizeof(double) * (size_t)n, st));
+  return SIPG_OK;
+}
+
+void sipg_ctx::sqrt_inplace(int64_t n, double* v) {
+  // dinv >= 0 for an SPD operator; reuse the reciprocal + scale kernels is not
+  // enough, so a dedicated elementwise sqrt lives in the vector helpers.
+  launch_sqrt(n, v, st);
+}
+
+int sipg_ctx::setup_coarse(int op, double mass) {
+  sipg_ctx* ctx = this;
+  Hier& H = hier[op];
+  Level& C = H.L.back();
+  const int N = C.N;
+  const int l = (int)H.L.size() - 1;
+  if (H.singular && op == SIPG_OP_VISCOUS && mass == 0.0) return SIPG_OK;  // rigid modes: no inverse
+  // columns of the operator: apply to all unit vectors in one batched launch
+  CK(launch_unit_columns(N, 0, N, C.Atmp, st));
+  const double* nc = op == SIPG_OP_VISCOUS ? C.nu_cell64 : nullptr;
+  const double* nf = op == SIPG_OP_VISCOUS ? C.nu_face64 : nullptr;
+  CK((launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, N, st)));
+  (void)l;
+  // column j of A is stored contiguously: that is A^T row-major = A (symmetric)
+  if (H.singular && op == SIPG_OP_POISSON && mass == 0.0) {
+    // constant null space: A + c 1 1^T is SPD and solves A x = b for mean-free b
+    // scale c from the mean diagonal, so that c 1^T 1 is of the operator's size
+    CK(launch_sum(N, C.diag64, partials, dscal + 2, st));
+    CK(cudaMemcpyAsync(hscal, dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double mean_diag = hscal[0] / N;
+    CK(launch_add_rank1(N, mean_diag / N, C.Ainv, st));
+  }
+  // Gauss-Jordan inverse, ping-pong between Ainv and Atmp
+  double* A = C.Ainv;
+  double* B = C.Atmp;
+  for (int k = 0; k < N; ++k) {
+    CK(launch_gj_step(N, k, A, B, st));
+    std::swap(A, B);
+  }
+  if (A != C.Ainv) CK(cudaMemcpyAsync(C.Ainv, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
+  return SIPG_OK;
+}
+
+int sipg_ctx::setup_operator(int op, double mass) {
+  sipg_ctx* ctx = this;
+  Hier& H = hier[op];
+  for (size_t l = 0; l < H.L.size(); ++l) {
+    int rc = setup_level_smoother(op, (int)l, mass);
+    if (rc) return rc;
+  }
+  int rc = setup_coarse(op, mass);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st));
+  H.setup_mass = mass;
+  H.ready = true;
+  return SIPG_OK;
+}
+
+// ------------------------------------------------------------ viscosity
+extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const double* u_lin) {
+  if (!ctx || !rh) return SIPG_ERR_INVALID;
+  RheologyDev r{};
+  r.law = rh->law;
+  switch (rh->law) {
+    case SIPG_LAW_CONSTANT:
+      if (!(rh->nu > 0)) return ctx->fail(SIPG_ERR_INVALID, "constant viscosity must be positive");
+      r.nu = rh->nu;
+      break;
+    case SIPG_LAW_ANALYTIC:
+      break;
+    case SIPG_LAW_SINKER:
+      if (rh->n_spheres < 0 || rh->n_spheres > 64 || (rh->n_spheres > 0 && !rh->centers))
+        return ctx->fail(SIPG_ERR_INVALID, "sinker: 0..64 spheres with a host centre array");
+      if (!(rh->nu_max > 0) || !(rh->nu_matrix > 0)) return ctx->fail(SIPG_ERR_INVALID, "sinker viscosities must be positive");
+      r.n_spheres = rh->n_spheres;
+      std::memcpy(r.centers, rh->centers, sizeof(double) * 3 * rh->n_spheres);
+      r.radius = rh->radius;
+      r.nu_max = rh->nu_max;
+      r.nu_matrix = rh->nu_matrix;
+      break;
+    case SIPG_LAW_CARREAU:
+      if (!u_lin) return ctx->fail(SIPG_ERR_INVALID, "Carreau-Yasuda viscosity needs the linearization velocity");
+      if (!(rh->eta0 > 0) || !(rh->eta_inf >= 0) || !(rh->a > 0))
+        return ctx->fail(SIPG_ERR_INVALID, "Carreau-Yasuda parameters out of range");
+      r.eta0 = rh->eta0; r.eta_inf = rh->eta_inf; r.kappa = rh->kappa; r.lambda = rh->lambda;
+      r.a = rh->a; r.b = rh->b;
+      break;
+    default:
+      return ctx->fail(SIPG_ERR_INVALID, "unknown viscosity law");
+  }
+  Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+  for (size_t l = 0; l < H.L.size(); ++l) {
+    Level& L = H.L[l];
+    const double* u = nullptr;
+    if (r.law == SIPG_LAW_CARREAU) {
+      if (l == 0) {
+        u = u_lin;
+      } else {
+        Level& F = H.L[l - 1];
+        const double* uf = l == 1 ? u_lin : F.ulin;
+        cudaError_t e = F.next_kind == 1
+                            ? launch_p_interp_down(F.n, L.n, 3, L.g.ncells, F.interp, uf, L.ulin, ctx->st)
+                            : launch_h_interp_down(L.n, 3, F.g, L.g, F.interp, F.child, uf, L.ulin, ctx->st);
+        if (e) return ctx->fail(SIPG_ERR_CUDA, "interpolate linearization velocity", e);
+        u = L.ulin;
+      }
+    }
+    cudaError_t e;
+    if (r.law == SIPG_LAW_SINKER && l > 0) {
+      // cellwise-constant field: carried down by the transfer of piecewise constants
+      const Level& F = H.L[l - 1];
+      e = launch_cell_nu_transfer(F.g, L.g, F.next_kind, F.n, L.n, F.nu_cell64, L.nu_cell64, L.nu_face64, ctx->st);
+    } else {
+      e = launch_viscosity(L.n, L.g, ctx->tabs[L.n], r, u, L.nu_cell64, L.nu_face64, ctx->st);
+    }
+    if (e) return ctx->fail(SIPG_ERR_CUDA, "viscosity kernel", e);
+    const int64_t n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
+    e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, ctx->st);
+    if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, ctx->st);
+    if (e) return ctx->fail(SIPG_ERR_CUDA, "viscosity cast", e);
+  }
+  ctx->have_nu = true;
+  return ctx->setup_operator(SIPG_OP_VISCOUS, 0.0);
+}
+
+// ------------------------------------------------------------ apply
+static int check_op(sipg_ctx* ctx, int op) {
+  if (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) return ctx->fail(SIPG_ERR_INVALID, "unknown operator");
+  if (op == SIPG_OP_VISCOUS && !ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
+  return SIPG_OK;
+}
+
+extern "C" int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, const void* x, void* y, double mass) {
+  if (!ctx) return SIPG_ERR_INVALID;
+  int rc = check_op(ctx, op);
+  if (rc) return rc;
+  if (level < 0 || level >= (int)ctx->hier[op].L.size() || !x || !y || x == y)
+    return ctx->fail(SIPG_ERR_INVALID, "bad level or buffers");
+  if (prec == SIPG_F64) return ctx->level_apply<double>(op, level, (const double*)x, (double*)y, mass);
+  if (prec == SIPG_F32) return ctx->level_apply<float>(op, level, (const float*)x, (float*)y, mass);
+  return ctx->fail(SIPG_ERR_INVALID, "bad precision");
+}
+
+extern "C" int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double mass) {
+  return sipg_level_apply(ctx, op, 0, prec, x, y, mass);
+}
+
+extern "C" int sipg_apply_host(sipg_ctx* ctx, int op, const double* xh, double* yh, double mass) {
+  if (!ctx || !xh || !yh) return SIPG_ERR_INVALID;
+  int rc = check_op(ctx, op);
+  if (rc) return rc;
+  const int64_t n = ctx->hier[op].L[0].ndofs;
+  if (ctx->host_n < n) {
+    cudaFree(ctx->host_x);
+    cudaFree(ctx->host_y);
+    ctx->host_x = ctx->host_y = nullptr;
+    ctx->host_n = 0;
+    CK(cudaMalloc(&ctx->host_x, sizeof(double) * n));
+    CK(cudaMalloc(&ctx->host_y, sizeof(double) * n));
+    ctx->host_n = n;
+  }
+  CK(cudaMemcpyAsync(ctx->host_x, xh, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  rc = ctx->level_apply<double>(op, 0, ctx->host_x, ctx->host_y, mass);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(yh, ctx->host_y, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return SIPG_OK;
+}
+
+template int sipg_ctx::level_apply<double>(int, int, const double*, double*, double);
+template int sipg_ctx::level_apply<float>(int, int, const float*, float*, double);

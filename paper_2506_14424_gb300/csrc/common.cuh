@@ -1,0 +1,67 @@
+// Shared definitions of the libsipg CUDA sources (device side and host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace sipg {
+
+constexpr int kMaxN = 6;  // n = k + 1, degrees 1..5
+
+// 1D tables of one degree, passed to kernels by value (lives in the
+// kernel-parameter constant bank) and copied to shared memory on entry.
+//  S[q*n + j]  = l_j(g_q): Lagrange basis on the n Gauss-Lobatto nodes at the
+//                n Gauss-Legendre points (nodal values -> quadrature values)
+//  Dg[q*n + p] = l'_p(g_q) for the Lagrange basis on the Gauss points
+//                (collocation derivative at the quadrature points)
+//  DS[q*n + j] = l'_j(g_q): derivative of the Gauss-Lobatto basis at Gauss points
+//  dS0[j], dS1[j] = l'_j(0), l'_j(1): normal derivative at the cell faces
+//  gw, gp       = Gauss weights / points on [0, 1];  gll = Gauss-Lobatto nodes
+struct Tab {
+  int n;
+  double S[kMaxN * kMaxN];
+  double Dg[kMaxN * kMaxN];
+  double DS[kMaxN * kMaxN];
+  double dS0[kMaxN], dS1[kMaxN];
+  double gw[kMaxN], gp[kMaxN], gll[kMaxN];
+};
+
+// Embedding matrices of the transfers (prolongation = interpolation of the
+// coarse polynomial at the fine Gauss-Lobatto nodes), row-major [nf][nc].
+struct TransferTab {
+  int nf, nc;
+  double E[kMaxN * kMaxN];      // p-transfer, or h-transfer child 0
+  double E1[kMaxN * kMaxN];     // h-transfer child 1
+};
+
+// Geometry and discretisation of one level, passed by value to kernels.
+struct LevelGeom {
+  int nx, ny, nz;
+  int ncells;
+  double h[3];
+  int bc[6];        // 0 = Dirichlet, 1 = Neumann, per box face -x,+x,-y,+y,-z,+z
+  double cip;       // penalty factor C_IP
+  int face_nu;      // 0 max, 1 arithmetic, 2 harmonic
+};
+
+__host__ __device__ inline int cell_neighbor(const LevelGeom& g, int e, int f) {
+  const int d = f >> 1, s = f & 1;
+  int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  ijk[d] += s ? 1 : -1;
+  if (ijk[d] < 0 || ijk[d] >= dims[d]) return -1;
+  return (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+}
+
+// Penalty geometry factor Lambda_e = sum_f w_f |f| / |Omega_e| with w_f = 1/2
+// on interior and 1 on boundary faces (box cells: |f| / |Omega_e| = 1 / h_d).
+__host__ __device__ inline double penalty_lambda(const LevelGeom& g, int e) {
+  double lam = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    const double w = cell_neighbor(g, e, f) >= 0 ? 0.5 : 1.0;
+    lam += w / g.h[f >> 1];
+  }
+  return lam;
+}
+
+}  // namespace sipg

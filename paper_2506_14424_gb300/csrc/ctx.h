@@ -1,0 +1,79 @@
+// Host-side state of a libsipg context.
+#pragma once
+#include "../../include/sipg.h"
+#include "common.cuh"
+
+#include <string>
+#include <vector>
+
+namespace sipg {
+
+struct Level {
+  LevelGeom g{};
+  int k = 0, n = 0;
+  int64_t ndofs = 0;
+  int next_kind = 0;         // transfer to level+1: 1 = p (degree), 2 = h (mesh)
+  TransferTab tt{};          // prolongation tables toward level+1
+  TransferTab interp{};      // downward interpolation of the linearization velocity
+  int child[kMaxN] = {0};    // h: child of each coarse node (ties to child 0)
+  double *nu_cell64 = nullptr, *nu_face64 = nullptr;
+  float *nu_cell32 = nullptr, *nu_face32 = nullptr;
+  double* ulin = nullptr;    // linearization velocity on this level (l > 0)
+  double* diag64 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double lmax = 0.0;         // Lanczos estimate of lambda_max(D^-1 A)
+  void* w[2][4] = {{nullptr}};  // [prec F64/F32][b, x, t, d]
+  int N = 0;                 // coarsest level: dense size
+  double* Ainv = nullptr;    // coarsest level: FP64 inverse (row-major)
+  double* Atmp = nullptr;
+};
+
+struct Hier {
+  int op = 0, ncomp = 0;
+  bool singular = false;
+  bool ready = false;
+  double setup_mass = 0.0;
+  std::vector<Level> L;
+  double* cg[5] = {nullptr};  // r, z, p, q, tmp (level 0, FP64)
+};
+
+}  // namespace sipg
+
+struct sipg_ctx {
+  sipg_mesh_desc mesh{};
+  sipg_opts opts{};
+  cudaStream_t st = nullptr;
+  sipg::Tab tabs[sipg::kMaxN + 1]{};
+  sipg::Hier hier[2];
+  bool have_nu = false;
+  std::string err;
+  double* partials = nullptr;
+  double* dscal = nullptr;
+  int* dflag = nullptr;
+  double* hscal = nullptr;  // pinned
+  double* host_x = nullptr;
+  double* host_y = nullptr;
+  int64_t host_n = 0;
+
+  ~sipg_ctx();
+  int fail(int code, const char* what, cudaError_t e = cudaSuccess);
+  int build_hierarchy(int op);
+  int setup_level_smoother(int op, int l, double mass);
+  int setup_coarse(int op, double mass);
+  int setup_operator(int op, double mass);
+  template <typename T>
+  int level_apply(int op, int l, const T* x, T* y, double mass);
+  int dot(int64_t n, const double* a, const double* b, double* out_host);
+  int project_mean(int64_t n, double* v);
+  void sqrt_inplace(int64_t n, double* v);
+  template <typename T>
+  int smooth(int op, int l, bool x_zero, double mass);
+  template <typename T>
+  int transfer(int op, int l, int dir, const T* in, T* out);
+  template <typename T>
+  int vcycle(int op, int l, double mass);
+  int coarse_solve64(int op);
+  int precondition(int op, int kind, const double* r, double* z, double mass);
+  int solve(int op, const double* b, double* x, const sipg_solve_opts* so, sipg_solve_stats* stats);
+};

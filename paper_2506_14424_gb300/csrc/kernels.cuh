@@ -1,0 +1,73 @@
+// Declarations of the kernel launchers shared by the host-side sources.
+#pragma once
+#include "common.cuh"
+
+namespace sipg {
+
+// ---- operator apply (operator.cuh instantiations)
+template <typename T>
+cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, const T* x, T* y,
+                         const T* nu_cell, const T* nu_face, T mass, int nbatch, cudaStream_t st);
+
+// ---- viscosity (viscosity.cu)
+struct RheologyDev {
+  int law;  // 0 constant, 1 analytic, 2 sinker, 3 carreau
+  double nu;
+  int n_spheres;
+  double centers[3 * 64];
+  double radius, nu_max, nu_matrix;
+  double eta0, eta_inf, kappa, lambda, a, b;
+};
+cudaError_t launch_viscosity(int n, const LevelGeom& g, const Tab& tab, const RheologyDev& rh,
+                             const double* u, double* nu_cell, double* nu_face, cudaStream_t st);
+cudaError_t launch_cell_nu_transfer(const LevelGeom& fine, const LevelGeom& coarse, int kind, int nf, int nc,
+                                    const double* fine_cell, double* nu_cell, double* nu_face, cudaStream_t st);
+
+// ---- multigrid and vector kernels (mg.cu)
+cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
+                            const double* nu_face, double mass, double* diag, cudaStream_t st);
+template <typename T>
+cudaError_t launch_p_transfer(int nf, int nc, int ncomp, int ncells, const TransferTab& tt, int dir,
+                              const T* in, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_h_transfer(int n, int ncomp, const LevelGeom& fine, const LevelGeom& coarse,
+                              const TransferTab& tt, int dir, const T* in, T* out, cudaStream_t st);
+cudaError_t launch_p_interp_down(int nf, int nc, int ncomp, int ncells, const TransferTab& tt,
+                                 const double* in, double* out, cudaStream_t st);
+cudaError_t launch_h_interp_down(int n, int ncomp, const LevelGeom& fine, const LevelGeom& coarse,
+                                 const TransferTab& tt, const int* child, const double* in,
+                                 double* out, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t st);  // y = a x + b y
+template <typename T>
+cudaError_t launch_sub(int64_t n, const T* b, const T* t, T* r, cudaStream_t st);  // r = b - t
+// Chebyshev step: d = c1 d + c2 dinv (b - t); x += d (x = d when first with zero guess)
+template <typename T>
+cudaError_t launch_cheb(int64_t n, T c1, T c2, const T* dinv, const T* b, const T* t, T* d, T* x,
+                        bool x_zero, cudaStream_t st);
+template <typename S, typename D>
+cudaError_t launch_cast(int64_t n, const S* in, D* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill(int64_t n, T v, T* out, cudaStream_t st);
+cudaError_t launch_add_scaled_f64(int64_t n, double a, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t st);
+cudaError_t launch_reciprocal(int64_t n, const double* a, double* out, cudaStream_t st);
+cudaError_t launch_scale(int64_t n, double a, const double* x, double* y, cudaStream_t st);  // y = a x
+cudaError_t launch_sqrt(int64_t n, double* v, cudaStream_t st);
+cudaError_t launch_random(int64_t n, uint64_t seed, double* out, cudaStream_t st);
+// deterministic dot product into dev_out[0] (partials: >= kDotBlocks doubles)
+constexpr int kDotBlocks = 304;
+cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials, double* dev_out,
+                       cudaStream_t st);
+cudaError_t launch_sum(int64_t n, const double* a, double* partials, double* dev_out, cudaStream_t st);
+cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, double* y, cudaStream_t st);
+cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st);
+// dense FP64 helpers for the coarse level
+cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st);
+cudaError_t launch_gj_step(int N, int k, const double* A, double* B, cudaStream_t st);
+cudaError_t launch_gemv(int N, const double* M, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_add_rank1(int N, double c, double* M, cudaStream_t st);
+cudaError_t launch_node_points(int n, const LevelGeom& g, const Tab& tab, double* xyz, cudaStream_t st);
+
+}  // namespace sipg

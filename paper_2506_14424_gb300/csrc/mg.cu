@@ -1,0 +1,553 @@
+// Multigrid and Krylov building blocks: operator diagonal, p/h transfers,
+// Chebyshev and CG vector updates, deterministic reductions and the dense FP64
+// coarse-level helpers (Sec. 5.4 of the paper).
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace sipg {
+
+namespace {
+constexpr int kBS = 256;
+inline int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + kBS - 1) / kBS, 152 * 16); }
+}  // namespace
+
+// ---------------------------------------------------------------- diagonal
+// Diagonal of (m M + A) for DoF (c, i) of a cell: the cell integral of the
+// test function against itself plus the own-side face terms (trial = test on
+// the own side, zero neighbour state on interior faces, mirror state on
+// Dirichlet faces). With n = sigma e_d and phi the scalar shape function:
+//  viscous cell:  sum_q W nu (|grad phi|^2 + (d_c phi)^2) + m W phi^2
+//  viscous face:  interior  -nu sigma phi d_d phi (1 + delta_cd) + tau phi^2 (1 + delta_cd)
+//                 Dirichlet 2 x the same with tau of the wall
+//  Poisson cell:  sum_q W |grad phi|^2 + m W phi^2
+//  Poisson face:  interior  -sigma phi d_d phi + tau phi^2;  Dirichlet 2 x the same
+template <int N, int NC>
+__global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__ nu_cell,
+                                const double* __restrict__ nu_face, double mass, double* __restrict__ diag) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.ncells * NC * N3) return;
+  const int e = (int)(idx / (NC * N3));
+  const int rem = (int)(idx % (NC * N3));
+  const int c = rem / N3, r = rem % N3;
+  const int ii[3] = {r % N, (r / N) % N, r / N2};
+  const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+  const double detJ = g.h[0] * g.h[1] * g.h[2];
+  double acc = 0.0;
+  for (int q = 0; q < N3; ++q) {
+    const int qq[3] = {q % N, (q / N) % N, q / N2};
+    double val = 1.0, gr[3];
+    for (int l = 0; l < 3; ++l) val *= tab.S[qq[l] * N + ii[l]];
+    for (int l = 0; l < 3; ++l) {
+      double p = ih[l];
+      for (int m = 0; m < 3; ++m) p *= (m == l ? tab.DS[qq[m] * N + ii[m]] : tab.S[qq[m] * N + ii[m]]);
+      gr[l] = p;
+    }
+    const double W = tab.gw[qq[0]] * tab.gw[qq[1]] * tab.gw[qq[2]] * detJ;
+    const double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    if (NC == 3)
+      acc += W * nu_cell[(size_t)e * N3 + q] * (g2 + gr[c] * gr[c]);
+    else
+      acc += W * g2;
+    acc += mass * W * val * val;
+  }
+  double lam_e = penalty_lambda(g, e);
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] == 1) continue;
+    const int layer = s ? N - 1 : 0;
+    const double sigma = s ? 1.0 : -1.0;
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
+    const double* dS = s ? tab.dS1 : tab.dS0;
+    const double on_face = ii[d] == layer ? 1.0 : 0.0;
+    const double area = g.h[t1] * g.h[t2];
+    const double mirror = nb >= 0 ? 1.0 : 2.0;
+    for (int p = 0; p < N2; ++p) {
+      const int a = p % N, b = p / N;
+      const double st = tab.S[a * N + ii[t1]] * tab.S[b * N + ii[t2]];
+      const double phi = on_face * st;
+      const double dd = dS[ii[d]] * st * ih[d];
+      const double W = tab.gw[a] * tab.gw[b] * area;
+      if (NC == 3) {
+        const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
+        const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p] : num;
+        double nub = num > nup ? num : nup;
+        if (g.face_nu == 1) nub = 0.5 * (num + nup);
+        if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
+        const double tau = g.cip * N * N * lam * nub;
+        const double fac = c == d ? 2.0 : 1.0;
+        acc += mirror * W * fac * (-num * sigma * phi * dd + tau * phi * phi);
+      } else {
+        const double tau = g.cip * N * N * lam;
+        acc += mirror * W * (-sigma * phi * dd + tau * phi * phi);
+      }
+    }
+  }
+  diag[idx] = acc;
+}
+
+cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
+                            const double* nu_face, double mass, double* diag, cudaStream_t st) {
+  const int64_t total = (int64_t)g.ncells * ncomp * n * n * n;
+  const int blocks = (int)((total + 127) / 128);
+  if (blocks == 0) return cudaSuccess;
+#define SIPG_DIAG(NN)                                                                             \
+  case NN:                                                                                        \
+    if (ncomp == 3)                                                                               \
+      diagonal_kernel<NN, 3><<<blocks, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);       \
+    else                                                                                          \
+      diagonal_kernel<NN, 1><<<blocks, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);       \
+    break;
+  switch (n) {
+    SIPG_DIAG(2) SIPG_DIAG(3) SIPG_DIAG(4) SIPG_DIAG(5) SIPG_DIAG(6)
+    default: return cudaErrorInvalidValue;
+  }
+#undef SIPG_DIAG
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- transfers
+// p-transfer on one cell and component: fine = (E x E x E) coarse with
+// E[i*nc + j] = l^coarse_j(xi^fine_i) (prolongation, dir +1), or the
+// transpose (restriction, dir -1). One thread per output value.
+template <typename T>
+__global__ void p_transfer_kernel(int nf, int nc, int ntens, TransferTab tt, int dir, const T* __restrict__ in,
+                                  T* __restrict__ out) {
+  const int nin = dir > 0 ? nc : nf, nout = dir > 0 ? nf : nc;
+  const int in3 = nin * nin * nin, out3 = nout * nout * nout;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ntens * out3) return;
+  const int t = (int)(idx / out3), r = (int)(idx % out3);
+  const int o[3] = {r % nout, (r / nout) % nout, r / (nout * nout)};
+  const T* src = in + (size_t)t * in3;
+  T acc = T(0);
+  for (int k = 0; k < nin; ++k) {
+    const double ez = dir > 0 ? tt.E[o[2] * nc + k] : tt.E[k * nc + o[2]];
+    for (int j = 0; j < nin; ++j) {
+      const double ey = dir > 0 ? tt.E[o[1] * nc + j] : tt.E[j * nc + o[1]];
+      for (int i = 0; i < nin; ++i) {
+        const double ex = dir > 0 ? tt.E[o[0] * nc + i] : tt.E[i * nc + o[0]];
+        acc += T(ex * ey * ez) * src[(k * nin + j) * nin + i];
+      }
+    }
+  }
+  out[idx] = acc;
+}
+
+template <typename T>
+cudaError_t launch_p_transfer(int nf, int nc, int ncomp, int ncells, const TransferTab& tt, int dir,
+                              const T* in, T* out, cudaStream_t st) {
+  const int nout = dir > 0 ? nf : nc;
+  const int64_t total = (int64_t)ncells * ncomp * nout * nout * nout;
+  const int blocks = (int)((total + kBS - 1) / kBS);
+  if (blocks == 0) return cudaSuccess;
+  p_transfer_kernel<T><<<blocks, kBS, 0, st>>>(nf, nc, ncells * ncomp, tt, dir, in, out);
+  return cudaGetLastError();
+}
+
+// h-transfer: coarse cell -> its 8 children on the once-refined mesh; child
+// (cx, cy, cz) uses E_c[i*n + j] = l_j((xi_i + c)/2). Prolongation: one thread
+// per fine value; restriction: one thread per coarse value summing its children.
+template <typename T>
+__global__ void h_prolong_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coarse, TransferTab tt,
+                                 const T* __restrict__ in, T* __restrict__ out) {
+  const int n3 = n * n * n;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)fine.ncells * ncomp * n3) return;
+  const int ef = (int)(idx / (ncomp * n3));
+  const int rem = (int)(idx % (ncomp * n3));
+  const int comp = rem / n3, r = rem % n3;
+  const int fx = ef % fine.nx, fy = (ef / fine.nx) % fine.ny, fz = ef / (fine.nx * fine.ny);
+  const int ec = ((fz / 2) * coarse.ny + fy / 2) * coarse.nx + fx / 2;
+  const double* Ex = (fx & 1) ? tt.E1 : tt.E;
+  const double* Ey = (fy & 1) ? tt.E1 : tt.E;
+  const double* Ez = (fz & 1) ? tt.E1 : tt.E;
+  const int o[3] = {r % n, (r / n) % n, r / (n * n)};
+  const T* src = in + ((size_t)ec * ncomp + comp) * n3;
+  T acc = T(0);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i)
+        acc += T(Ex[o[0] * n + i] * Ey[o[1] * n + j] * Ez[o[2] * n + k]) * src[(k * n + j) * n + i];
+  out[idx] = acc;
+}
+
+template <typename T>
+__global__ void h_restrict_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coarse, TransferTab tt,
+                                  const T* __restrict__ in, T* __restrict__ out) {
+  const int n3 = n * n * n;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)coarse.ncells * ncomp * n3) return;
+  const int ec = (int)(idx / (ncomp * n3));
+  const int rem = (int)(idx % (ncomp * n3));
+  const int comp = rem / n3, r = rem % n3;
+  const int cx = ec % coarse.nx, cy = (ec / coarse.nx) % coarse.ny, cz = ec / (coarse.nx * coarse.ny);
+  const int o[3] = {r % n, (r / n) % n, r / (n * n)};
+  T acc = T(0);
+  for (int ch = 0; ch < 8; ++ch) {
+    const int bx = ch & 1, by = (ch >> 1) & 1, bz = ch >> 2;
+    const int ef = ((2 * cz + bz) * fine.ny + 2 * cy + by) * fine.nx + 2 * cx + bx;
+    const double* Ex = bx ? tt.E1 : tt.E;
+    const double* Ey = by ? tt.E1 : tt.E;
+    const double* Ez = bz ? tt.E1 : tt.E;
+    const T* src = in + ((size_t)ef * ncomp + comp) * n3;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i)
+          acc += T(Ex[i * n + o[0]] * Ey[j * n + o[1]] * Ez[k * n + o[2]]) * src[(k * n + j) * n + i];
+  }
+  out[idx] = acc;
+}
+
+template <typename T>
+cudaError_t launch_h_transfer(int n, int ncomp, const LevelGeom& fine, const LevelGeom& coarse,
+                              const TransferTab& tt, int dir, const T* in, T* out, cudaStream_t st) {
+  const int64_t total = (int64_t)(dir > 0 ? fine.ncells : coarse.ncells) * ncomp * n * n * n;
+  const int blocks = (int)((total + kBS - 1) / kBS);
+  if (blocks == 0) return cudaSuccess;
+  if (dir > 0)
+    h_prolong_kernel<T><<<blocks, kBS, 0, st>>>(n, ncomp, fine, coarse, tt, in, out);
+  else
+    h_restrict_kernel<T><<<blocks, kBS, 0, st>>>(n, ncomp, fine, coarse, tt, in, out);
+  return cudaGetLastError();
+}
+
+// Downward interpolation of the linearization velocity (nodal values of the
+// fine function at the coarse nodes).
+__global__ void p_interp_down_kernel(int nf, int nc, int ntens, TransferTab tt, const double* __restrict__ in,
+                                     double* __restrict__ out) {
+  const int f3 = nf * nf * nf, c3 = nc * nc * nc;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ntens * c3) return;
+  const int t = (int)(idx / c3), r = (int)(idx % c3);
+  const int o[3] = {r % nc, (r / nc) % nc, r / (nc * nc)};
+  const double* src = in + (size_t)t * f3;
+  double acc = 0.0;
+  for (int k = 0; k < nf; ++k)
+    for (int j = 0; j < nf; ++j)
+      for (int i = 0; i < nf; ++i)
+        acc += tt.E[o[0] * nf + i] * tt.E[o[1] * nf + j] * tt.E[o[2] * nf + k] * src[(k * nf + j) * nf + i];
+  out[idx] = acc;
+}
+
+cudaError_t launch_p_interp_down(int nf, int nc, int ncomp, int ncells, const TransferTab& tt,
+                                 const double* in, double* out, cudaStream_t st) {
+  const int64_t total = (int64_t)ncells * ncomp * nc * nc * nc;
+  const int blocks = (int)((total + kBS - 1) / kBS);
+  if (blocks == 0) return cudaSuccess;
+  p_interp_down_kernel<<<blocks, kBS, 0, st>>>(nf, nc, ncells * ncomp, tt, in, out);
+  return cudaGetLastError();
+}
+
+struct ChildMap { int c[kMaxN]; };
+
+__global__ void h_interp_down_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coarse, TransferTab tt,
+                                     ChildMap cm, const double* __restrict__ in, double* __restrict__ out) {
+  const int n3 = n * n * n;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)coarse.ncells * ncomp * n3) return;
+  const int ec = (int)(idx / (ncomp * n3));
+  const int rem = (int)(idx % (ncomp * n3));
+  const int comp = rem / n3, r = rem % n3;
+  const int cx = ec % coarse.nx, cy = (ec / coarse.nx) % coarse.ny, cz = ec / (coarse.nx * coarse.ny);
+  const int o[3] = {r % n, (r / n) % n, r / (n * n)};
+  const int ef = ((2 * cz + cm.c[o[2]]) * fine.ny + 2 * cy + cm.c[o[1]]) * fine.nx + 2 * cx + cm.c[o[0]];
+  const double* src = in + ((size_t)ef * ncomp + comp) * n3;
+  double acc = 0.0;
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i)
+        acc += tt.E[o[0] * n + i] * tt.E[o[1] * n + j] * tt.E[o[2] * n + k] * src[(k * n + j) * n + i];
+  out[idx] = acc;
+}
+
+cudaError_t launch_h_interp_down(int n, int ncomp, const LevelGeom& fine, const LevelGeom& coarse,
+                                 const TransferTab& tt, const int* child, const double* in, double* out,
+                                 cudaStream_t st) {
+  ChildMap cm{};
+  for (int i = 0; i < n; ++i) cm.c[i] = child[i];
+  const int64_t total = (int64_t)coarse.ncells * ncomp * n * n * n;
+  const int blocks = (int)((total + kBS - 1) / kBS);
+  if (blocks == 0) return cudaSuccess;
+  h_interp_down_kernel<<<blocks, kBS, 0, st>>>(n, ncomp, fine, coarse, tt, cm, in, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ vector updates
+template <typename T>
+__global__ void axpby_kernel(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+template <typename T>
+cudaError_t launch_axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  axpby_kernel<T><<<blocks_for(n), kBS, 0, st>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void sub_kernel(int64_t n, const T* __restrict__ b, const T* __restrict__ t, T* __restrict__ r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - t[i];
+}
+template <typename T>
+cudaError_t launch_sub(int64_t n, const T* b, const T* t, T* r, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  sub_kernel<T><<<blocks_for(n), kBS, 0, st>>>(n, b, t, r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void cheb_kernel(int64_t n, T c1, T c2, const T* __restrict__ dinv, const T* __restrict__ b,
+                            const T* __restrict__ t, T* __restrict__ d, T* __restrict__ x, bool first_zero) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T r = t ? b[i] - t[i] : b[i];
+    const T dn = (first_zero ? T(0) : c1 * d[i]) + c2 * dinv[i] * r;
+    d[i] = dn;
+    x[i] = first_zero ? dn : x[i] + dn;
+  }
+}
+template <typename T>
+cudaError_t launch_cheb(int64_t n, T c1, T c2, const T* dinv, const T* b, const T* t, T* d, T* x, bool x_zero,
+                        cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  cheb_kernel<T><<<blocks_for(n), kBS, 0, st>>>(n, c1, c2, dinv, b, t, d, x, x_zero);
+  return cudaGetLastError();
+}
+
+template <typename S, typename D>
+__global__ void cast_kernel(int64_t n, const S* __restrict__ in, D* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = D(in[i]);
+}
+template <typename S, typename D>
+cudaError_t launch_cast(int64_t n, const S* in, D* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  cast_kernel<S, D><<<blocks_for(n), kBS, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void fill_kernel(int64_t n, T v, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v;
+}
+template <typename T>
+cudaError_t launch_fill(int64_t n, T v, T* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  fill_kernel<T><<<blocks_for(n), kBS, 0, st>>>(n, v, out);
+  return cudaGetLastError();
+}
+
+__global__ void add_scaled_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+cudaError_t launch_add_scaled_f64(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  add_scaled_kernel<<<blocks_for(n), kBS, 0, st>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+
+__global__ void mul_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i];
+}
+cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  mul_kernel<<<blocks_for(n), kBS, 0, st>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+__global__ void reciprocal_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 1.0 / a[i];
+}
+cudaError_t launch_reciprocal(int64_t n, const double* a, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  reciprocal_kernel<<<blocks_for(n), kBS, 0, st>>>(n, a, out);
+  return cudaGetLastError();
+}
+__global__ void scale_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+cudaError_t launch_scale(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  scale_kernel<<<blocks_for(n), kBS, 0, st>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+
+__global__ void sqrt_kernel(int64_t n, double* v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = sqrt(v[i]);
+}
+cudaError_t launch_sqrt(int64_t n, double* v, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  sqrt_kernel<<<blocks_for(n), kBS, 0, st>>>(n, v);
+  return cudaGetLastError();
+}
+
+// Counter-based uniform(-1, 1) numbers (splitmix64 of seed + index).
+__global__ void random_kernel(int64_t n, uint64_t seed, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    out[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+  }
+}
+cudaError_t launch_random(int64_t n, uint64_t seed, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  random_kernel<<<blocks_for(n), kBS, 0, st>>>(n, seed, out);
+  return cudaGetLastError();
+}
+
+// Deterministic reductions: fixed grid, fixed per-thread order, tree in shared.
+template <bool DOT>
+__global__ void partial_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                               double* __restrict__ partials) {
+  __shared__ double red[kBS];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kBS + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kBS)
+    s += DOT ? a[i] * b[i] : a[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kBS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+__global__ void final_kernel(const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double red[512];
+  red[threadIdx.x] = threadIdx.x < kDotBlocks ? partials[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int w = 256; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials, double* dev_out,
+                       cudaStream_t st) {
+  partial_kernel<true><<<kDotBlocks, kBS, 0, st>>>(n, a, b, partials);
+  final_kernel<<<1, 512, 0, st>>>(partials, dev_out);
+  return cudaGetLastError();
+}
+cudaError_t launch_sum(int64_t n, const double* a, double* partials, double* dev_out, cudaStream_t st) {
+  partial_kernel<false><<<kDotBlocks, kBS, 0, st>>>(n, a, nullptr, partials);
+  final_kernel<<<1, 512, 0, st>>>(partials, dev_out);
+  return cudaGetLastError();
+}
+
+// y += scale * c[0] (c on the device), used for mean removal.
+__global__ void add_const_kernel(int64_t n, const double* __restrict__ c, double scale, double* __restrict__ y) {
+  const double v = scale * c[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += v;
+}
+cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, double* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  add_const_kernel<<<blocks_for(n), kBS, 0, st>>>(n, dev_c, scale, y);
+  return cudaGetLastError();
+}
+
+__global__ void finite_kernel(int64_t n, const double* __restrict__ a, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) *flag = 1;
+}
+cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  finite_kernel<<<blocks_for(n), kBS, 0, st>>>(n, a, flag);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- dense coarse
+// Columns j0 .. j0+ncols-1 of the N x N identity, stored column-major.
+__global__ void unit_columns_kernel(int N, int j0, int ncols, double* out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * ncols) return;
+  const int col = (int)(idx / N), row = (int)(idx % N);
+  out[idx] = row == j0 + col ? 1.0 : 0.0;
+}
+cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st) {
+  const int64_t total = (int64_t)N * ncols;
+  unit_columns_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, j0, ncols, out);
+  return cudaGetLastError();
+}
+
+// One in-place-equivalent Gauss-Jordan step (pivot k) from A into B (both
+// N x N row-major): the inverse of an SPD matrix after N steps, no pivoting.
+__global__ void gj_step_kernel(int N, int k, const double* __restrict__ A, double* __restrict__ B) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * N) return;
+  const int i = (int)(idx / N), j = (int)(idx % N);
+  const double p = A[(size_t)k * N + k];
+  double v;
+  if (i == k && j == k)
+    v = 1.0 / p;
+  else if (i == k)
+    v = A[(size_t)k * N + j] / p;
+  else if (j == k)
+    v = -A[(size_t)i * N + k] / p;
+  else
+    v = A[idx] - A[(size_t)i * N + k] * A[(size_t)k * N + j] / p;
+  B[idx] = v;
+}
+cudaError_t launch_gj_step(int N, int k, const double* A, double* B, cudaStream_t st) {
+  const int64_t total = (int64_t)N * N;
+  gj_step_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, k, A, B);
+  return cudaGetLastError();
+}
+
+// y = M x, M row-major N x N: one warp per row.
+__global__ void gemv_kernel(int N, const double* __restrict__ M, const double* __restrict__ x, double* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) s += M[(size_t)row * N + j] * x[j];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) y[row] = s;
+}
+cudaError_t launch_gemv(int N, const double* M, const double* x, double* y, cudaStream_t st) {
+  gemv_kernel<<<(N + 7) / 8, 256, 0, st>>>(N, M, x, y);
+  return cudaGetLastError();
+}
+
+__global__ void add_rank1_kernel(int N, double c, double* M) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx < (int64_t)N * N) M[idx] += c;
+}
+cudaError_t launch_add_rank1(int N, double c, double* M, cudaStream_t st) {
+  const int64_t total = (int64_t)N * N;
+  add_rank1_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, c, M);
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+#define SIPG_INST(T)                                                                                      \
+  template cudaError_t launch_p_transfer<T>(int, int, int, int, const TransferTab&, int, const T*, T*,   \
+                                            cudaStream_t);                                              \
+  template cudaError_t launch_h_transfer<T>(int, int, const LevelGeom&, const LevelGeom&,                \
+                                            const TransferTab&, int, const T*, T*, cudaStream_t);        \
+  template cudaError_t launch_axpby<T>(int64_t, T, const T*, T, T*, cudaStream_t);                       \
+  template cudaError_t launch_sub<T>(int64_t, const T*, const T*, T*, cudaStream_t);                     \
+  template cudaError_t launch_cheb<T>(int64_t, T, T, const T*, const T*, const T*, T*, T*, bool,         \
+                                      cudaStream_t);                                                     \
+  template cudaError_t launch_fill<T>(int64_t, T, T*, cudaStream_t);
+SIPG_INST(double)
+SIPG_INST(float)
+#undef SIPG_INST
+template cudaError_t launch_cast<double, float>(int64_t, const double*, float*, cudaStream_t);
+template cudaError_t launch_cast<float, double>(int64_t, const float*, double*, cudaStream_t);
+template cudaError_t launch_cast<double, double>(int64_t, const double*, double*, cudaStream_t);
+
+}  // namespace sipg

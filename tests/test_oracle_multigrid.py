@@ -110,3 +110,31 @@ def test_vcycle_preconditioned_cg_converges_fast():
     assert hist[-1] <= 1e-8 and it <= 25, it
     x_ref = solvers.cholesky_solve(mats[0], b)
     assert np.abs(x - x_ref).max() <= 1e-6 * np.abs(x_ref).max()
+
+
+def _sinker_vcycle_iterations(levels_visc):
+    mats, Ps = [], []
+    for l, ((m, k), nu) in enumerate(levels_visc):
+        S = SIPG(m, k, 3)
+        mats.append(S.assemble(*nu))
+        if l > 0:
+            pm, pk = levels_visc[l - 1][0]
+            Ps.append(mg.prolongation_p(m, pk, k, 3) if pm.n_cells == m.n_cells else mg.prolongation_h(pm, m, k, 3))
+    lmax = [1.2 * mg.lanczos_lmax(A, 1.0 / A.diagonal(), np.random.default_rng(0).uniform(-1, 1, A.shape[0]), 15)
+            for A in mats[:-1]]
+    V = mg.VCycle(mats, Ps, 3, lmax)
+    b = mats[0] @ np.random.default_rng(1).uniform(-1, 1, mats[0].shape[0])
+    return solvers.pcg(mats[0], b, precond=V, rtol=1e-8, maxit=150)[1]
+
+
+def test_transferred_sinker_viscosity_keeps_vcycle_robust():
+    """Finding behind the viscosity-transfer reading: at contrast 1e4 the V-cycle
+    with transferred cell values converges in a few dozen CG iterations, with
+    per-level re-evaluation it stalls."""
+    from paper_2506_14424_gb300 import inputs
+    rheo = inputs.sinker(seed=2, count=8, radius=0.2, nu_max=1e4)
+    levels = mg.level_sequence(BoxMesh(4, 4, 4), 2, 3, coarse_threshold=200)
+    transferred = mg.level_viscosity(levels, rheo)
+    reevaluated = [SIPG(m, k, 3).viscosity_at_points(rheo) for m, k in levels]
+    assert _sinker_vcycle_iterations(list(zip(levels, transferred))) <= 35
+    assert _sinker_vcycle_iterations(list(zip(levels, reevaluated))) >= 100
