@@ -220,14 +220,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def time_apply(ctx, op, x, y, reps, stream, warm=3):
+def time_apply(ctx, op, x, y, reps, stream, warm=3, arith=None):
     import torch
     for _ in range(warm):
-        ctx.apply(op, x, y)
+        ctx.apply(op, x, y, arith=arith)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        ctx.apply(op, x, y)
+        ctx.apply(op, x, y, arith=arith)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
@@ -241,6 +241,10 @@ def gpu_extras(ctx, xs, ys, stream):
 
     out = {}
     n = ctx.n_dofs("viscous")
+    ms = time_apply(ctx, "viscous", xs[0], ys[0], 20, stream, arith="f64ff")
+    yref = ctx.apply("viscous", xs[0])
+    diff = ((ys[0] - yref).abs().max() / yref.abs().max()).item()
+    out["viscous_f64ff_apply"] = {"ms": ms, "gdofs": n / ms / 1e6, "rel_diff_vs_f64": diff}
     x32, y32 = xs[0].float(), ys[0].float()
     ms = time_apply(ctx, "viscous", x32, y32, 20, stream)
     out["viscous_f32_apply"] = {"ms": ms, "gdofs": n / ms / 1e6}
@@ -249,6 +253,8 @@ def gpu_extras(ctx, xs, ys, stream):
     yp = torch.empty_like(xp)
     ms = time_apply(ctx, "poisson", xp, yp, 50, stream)
     out["poisson_f64_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr}
+    ms = time_apply(ctx, "poisson", xp, yp, 50, stream, arith="f64ff")
+    out["poisson_f64ff_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr}
     # mixed-precision vs all-FP64 multigrid solve, 16^3 cells, k = 4, sinker viscosity
     solves = []
     sink = inputs.sinker(seed=2, count=8, radius=0.1, nu_max=1.0)

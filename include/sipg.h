@@ -50,7 +50,11 @@ enum {
 
 enum { SIPG_BC_DIRICHLET = 0, SIPG_BC_NEUMANN = 1 };
 enum { SIPG_OP_VISCOUS = 0, SIPG_OP_POISSON = 1 };
-enum { SIPG_F64 = 0, SIPG_F32 = 1 };
+/* Arithmetic of an apply: SIPG_F64 native binary64; SIPG_F32 binary32;
+ * SIPG_F64_FF binary64 storage with float-float arithmetic (each value an
+ * unevaluated sum of two binary32 numbers, ~48-bit significand), which runs on
+ * the FP32 pipe and matches the FP64 result to ~1e-14 relative. */
+enum { SIPG_F64 = 0, SIPG_F32 = 1, SIPG_F64_FF = 2 };
 enum { SIPG_FACE_NU_MAX = 0, SIPG_FACE_NU_ARITH = 1, SIPG_FACE_NU_HARMONIC = 2 };
 enum { SIPG_LAW_CONSTANT = 0, SIPG_LAW_ANALYTIC = 1, SIPG_LAW_SINKER = 2, SIPG_LAW_CARREAU = 3 };
 enum { SIPG_PRECOND_NONE = 0, SIPG_PRECOND_JACOBI = 1, SIPG_PRECOND_MG = 2 };
@@ -82,7 +86,8 @@ typedef struct {
  *  cheb_lmax_factor  safety factor on the Lanczos estimate [1.2]
  *  lanczos_steps  Lanczos steps of the eigenvalue estimate [15]
  *  coarse_max_dofs   direct solve below this many unknowns (Sec. 5.4) [2000]
- *  seed           seed of the Lanczos start vector [0] */
+ *  seed           seed of the Lanczos start vector [0]
+ *  krylov_arith   arithmetic of the outer CG's operator applies [F64] */
 typedef struct {
   int k_u;
   double penalty_factor;
@@ -94,6 +99,8 @@ typedef struct {
   int lanczos_steps;
   int coarse_max_dofs;
   uint64_t seed;
+  int krylov_arith;  /* arithmetic of the FP64 operator applies inside CG:
+                        SIPG_F64 or SIPG_F64_FF [F64] */
 } sipg_opts;
 
 /* Viscosity field (Eq. viscosity_general and Sec. 2).
@@ -159,7 +166,7 @@ int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const double* u_l
 
 /* y = (mass_coeff M + A) x on the fine level of operator op (A_visc of
  * Eq. viscous_term_weak, or the SIPG Laplacian of Eq. pressure_step_weak).
- * prec SIPG_F64: x, y DEVICE double*; SIPG_F32: DEVICE float*.
+ * prec SIPG_F64 or SIPG_F64_FF: x, y DEVICE double*; SIPG_F32: DEVICE float*.
  * x and y must not overlap. */
 int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double mass_coeff);
 

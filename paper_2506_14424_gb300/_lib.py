@@ -15,7 +15,7 @@ SIPG_OK, SIPG_PENDING = 0, 1
 ERRORS = {-1: "SIPG_ERR_INVALID", -2: "SIPG_ERR_CUDA", -3: "SIPG_ERR_NOMEM", -4: "SIPG_ERR_MAXIT",
           -5: "SIPG_ERR_BREAKDOWN", -6: "SIPG_ERR_NAN", -7: "SIPG_ERR_TIMEOUT", -8: "SIPG_ERR_STATE"}
 OP = {"viscous": 0, "poisson": 1}
-PREC = {"f64": 0, "f32": 1}
+PREC = {"f64": 0, "f32": 1, "f64ff": 2}
 LAW = {"constant": 0, "analytic": 1, "sinker": 2, "carreau": 3}
 PRECOND = {"none": 0, "jacobi": 1, "mg": 2}
 FACE_NU = {"max": 0, "arith": 1, "harmonic": 2}
@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("k_u", ctypes.c_int), ("penalty_factor", ctypes.c_double), ("face_nu", ctypes.c_int),
                 ("mg_precision", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_range", ctypes.c_double),
                 ("cheb_lmax_factor", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
-                ("coarse_max_dofs", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("coarse_max_dofs", ctypes.c_int), ("seed", ctypes.c_uint64), ("krylov_arith", ctypes.c_int)]
 
 
 class Rheology(ctypes.Structure):

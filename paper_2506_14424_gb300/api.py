@@ -54,7 +54,8 @@ class Context:
 
     def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
                  penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
-                 cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, stream=None):
+                 cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, krylov_arith="f64",
+                 stream=None):
         self._lib = L.load()
         m = L.MeshDesc()
         m.nx, m.ny, m.nz = int(nx), int(ny), int(nz)
@@ -73,6 +74,7 @@ class Context:
         o.lanczos_steps = int(lanczos_steps)
         o.coarse_max_dofs = int(coarse_max_dofs)
         o.seed = int(seed)
+        o.krylov_arith = L.PREC[krylov_arith]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = self._lib.sipg_create(ctypes.byref(m), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),
@@ -134,9 +136,12 @@ class Context:
         return nc.view(C, n ** 3), nf.view(C, 6, n * n)
 
     # ---------------------------------------------------------------- apply
-    def apply(self, op, x, y=None, mass=0.0, level=0):
+    def apply(self, op, x, y=None, mass=0.0, level=0, arith=None):
+        """y = (mass M + A) x; arith 'f64' (default for double), 'f64ff' or 'f32'."""
         _need_cuda(x)
-        prec = L.PREC["f64" if x.dtype == torch.float64 else "f32"]
+        prec = L.PREC[arith or ("f64" if x.dtype == torch.float64 else "f32")]
+        if (prec == L.PREC["f32"]) != (x.dtype == torch.float32):
+            raise TypeError("f32 arithmetic needs float32 vectors, f64/f64ff need float64")
         if y is None:
             y = torch.empty_like(x)
         _need_cuda(y, x.dtype)

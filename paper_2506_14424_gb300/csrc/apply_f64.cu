@@ -1,7 +1,10 @@
 // FP64 instantiations of the fused cell + face SIPG operator kernel.
 #include "apply_dispatch.cuh"
 namespace sipg {
-template cudaError_t launch_apply<double>(int, int, const LevelGeom&, const Tab&, const double*, double*,
-                                          const double*, const double*, double, int,
-                                          cudaStream_t);
+template <>
+cudaError_t launch_apply<double>(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
+                                 const double* nu_cell, const double* nu_face, double mass, int nbatch,
+                                 cudaStream_t st) {
+  return launch_apply_t<double, double>(n, ncomp, g, tab, x, y, nu_cell, nu_face, mass, nbatch, st);
 }
+}  // namespace sipg

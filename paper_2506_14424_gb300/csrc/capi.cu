@@ -74,6 +74,7 @@ int sipg_ctx::build_hierarchy(int op) {
     L.g.h[0] = mesh.lx / lnx;
     L.g.h[1] = mesh.ly / lny;
     L.g.h[2] = mesh.lz / lnz;
+    for (int d = 0; d < 3; ++d) L.g.ih[d] = 1.0 / L.g.h[d];
     for (int i = 0; i < 6; ++i) L.g.bc[i] = bc[i];
     L.g.cip = opts.penalty_factor;
     L.g.face_nu = opts.face_nu;
@@ -195,6 +196,7 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (!valid_bc(mesh->bc_velocity) || !valid_bc(mesh->bc_pressure)) return SIPG_ERR_INVALID;
   if (o.mg_precision != SIPG_F32 && o.mg_precision != SIPG_F64) return SIPG_ERR_INVALID;
   if (o.face_nu < 0 || o.face_nu > 2 || o.cheb_degree < 1 || o.lanczos_steps < 2) return SIPG_ERR_INVALID;
+  if (o.krylov_arith != SIPG_F64 && o.krylov_arith != SIPG_F64_FF) return SIPG_ERR_INVALID;
   sipg_ctx* ctx = new sipg_ctx();
   ctx->mesh = *mesh;
   ctx->opts = o;
@@ -260,6 +262,21 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
   }
   CK((launch_apply<T>(L.n, H.ncomp, L.g, tabs[L.n], x, y, nc, nf, T(mass), 1, st)));
   return SIPG_OK;
+}
+
+int sipg_ctx::level_apply_ff(int op, int l, const double* x, double* y, double mass) {
+  sipg_ctx* ctx = this;
+  const Hier& H = hier[op];
+  const Level& L = H.L[l];
+  const double* nc = op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr;
+  const double* nf = op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr;
+  CK(launch_apply_ff(L.n, H.ncomp, L.g, tabs[L.n], x, y, nc, nf, mass, 1, st));
+  return SIPG_OK;
+}
+
+int sipg_ctx::krylov_apply(int op, const double* x, double* y, double mass) {
+  return opts.krylov_arith == SIPG_F64_FF ? level_apply_ff(op, 0, x, y, mass)
+                                          : level_apply<double>(op, 0, x, y, mass);
 }
 
 int sipg_ctx::dot(int64_t n, const double* a, const double* b, double* out_host) {
@@ -396,7 +413,7 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   double* A = C.Ainv;
   double* B = C.Atmp;
   for (int k = 0; k < N; ++k) {
-    CK(launch_gj_step(N, k, A, B, st));
+    CK(launch_gj_step(N, k, A, B, dscal + 8, st));
     std::swap(A, B);
   }
   if (A != C.Ainv) CK(cudaMemcpyAsync(C.Ainv, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
@@ -500,6 +517,7 @@ extern "C" int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, cons
     return ctx->fail(SIPG_ERR_INVALID, "bad level or buffers");
   if (prec == SIPG_F64) return ctx->level_apply<double>(op, level, (const double*)x, (double*)y, mass);
   if (prec == SIPG_F32) return ctx->level_apply<float>(op, level, (const float*)x, (float*)y, mass);
+  if (prec == SIPG_F64_FF) return ctx->level_apply_ff(op, level, (const double*)x, (double*)y, mass);
   return ctx->fail(SIPG_ERR_INVALID, "bad precision");
 }
 
@@ -522,7 +540,7 @@ extern "C" int sipg_apply_host(sipg_ctx* ctx, int op, const double* xh, double* 
     ctx->host_n = n;
   }
   CK(cudaMemcpyAsync(ctx->host_x, xh, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
-  rc = ctx->level_apply<double>(op, 0, ctx->host_x, ctx->host_y, mass);
+  rc = ctx->krylov_apply(op, ctx->host_x, ctx->host_y, mass);
   if (rc) return rc;
   CK(cudaMemcpyAsync(yh, ctx->host_y, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));

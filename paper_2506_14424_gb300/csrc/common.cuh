@@ -39,6 +39,7 @@ struct LevelGeom {
   int nx, ny, nz;
   int ncells;
   double h[3];
+  double ih[3];     // 1 / h, precomputed on the host (no FP64 division on the device)
   int bc[6];        // 0 = Dirichlet, 1 = Neumann, per box face -x,+x,-y,+y,-z,+z
   double cip;       // penalty factor C_IP
   int face_nu;      // 0 max, 1 arithmetic, 2 harmonic
@@ -59,7 +60,7 @@ __host__ __device__ inline double penalty_lambda(const LevelGeom& g, int e) {
   double lam = 0.0;
   for (int f = 0; f < 6; ++f) {
     const double w = cell_neighbor(g, e, f) >= 0 ? 0.5 : 1.0;
-    lam += w / g.h[f >> 1];
+    lam += w * g.ih[f >> 1];
   }
   return lam;
 }

@@ -64,6 +64,8 @@ struct sipg_ctx {
   int setup_operator(int op, double mass);
   template <typename T>
   int level_apply(int op, int l, const T* x, T* y, double mass);
+  int level_apply_ff(int op, int l, const double* x, double* y, double mass);
+  int krylov_apply(int op, const double* x, double* y, double mass);
   int dot(int64_t n, const double* a, const double* b, double* out_host);
   int project_mean(int64_t n, double* v);
   void sqrt_inplace(int64_t n, double* v);

@@ -8,6 +8,9 @@ namespace sipg {
 template <typename T>
 cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, const T* x, T* y,
                          const T* nu_cell, const T* nu_face, T mass, int nbatch, cudaStream_t st);
+// FP64-accurate apply with float-float arithmetic (double storage)
+cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
+                            const double* nu_cell, const double* nu_face, double mass, int nbatch, cudaStream_t st);
 
 // ---- viscosity (viscosity.cu)
 struct RheologyDev {
@@ -65,7 +68,7 @@ cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, doubl
 cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st);
 // dense FP64 helpers for the coarse level
 cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st);
-cudaError_t launch_gj_step(int N, int k, const double* A, double* B, cudaStream_t st);
+cudaError_t launch_gj_step(int N, int k, const double* A, double* B, double* recip, cudaStream_t st);
 cudaError_t launch_gemv(int N, const double* M, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_add_rank1(int N, double c, double* M, cudaStream_t st);
 cudaError_t launch_node_points(int n, const LevelGeom& g, const Tab& tab, double* xyz, cudaStream_t st);

@@ -32,7 +32,7 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
   const int rem = (int)(idx % (NC * N3));
   const int c = rem / N3, r = rem % N3;
   const int ii[3] = {r % N, (r / N) % N, r / N2};
-  const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+  const double ih[3] = {g.ih[0], g.ih[1], g.ih[2]};
   const double detJ = g.h[0] * g.h[1] * g.h[2];
   double acc = 0.0;
   for (int q = 0; q < N3; ++q) {
@@ -483,27 +483,33 @@ cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStrea
   return cudaGetLastError();
 }
 
-// One in-place-equivalent Gauss-Jordan step (pivot k) from A into B (both
-// N x N row-major): the inverse of an SPD matrix after N steps, no pivoting.
-__global__ void gj_step_kernel(int N, int k, const double* __restrict__ A, double* __restrict__ B) {
+// One Gauss-Jordan step (pivot k) from A into B (both N x N row-major): the
+// inverse of an SPD matrix after N steps, no pivoting. recip[k & 1] holds
+// 1 / A[k][k]; the thread that writes the next pivot B[k+1][k+1] stores its
+// reciprocal in recip[(k + 1) & 1], so no thread divides per element.
+__global__ void gj_step_kernel(int N, int k, const double* __restrict__ A, double* __restrict__ B,
+                               double* __restrict__ recip) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)N * N) return;
   const int i = (int)(idx / N), j = (int)(idx % N);
-  const double p = A[(size_t)k * N + k];
+  const double rp = recip[k & 1];
   double v;
   if (i == k && j == k)
-    v = 1.0 / p;
+    v = rp;
   else if (i == k)
-    v = A[(size_t)k * N + j] / p;
+    v = A[(size_t)k * N + j] * rp;
   else if (j == k)
-    v = -A[(size_t)i * N + k] / p;
+    v = -A[(size_t)i * N + k] * rp;
   else
-    v = A[idx] - A[(size_t)i * N + k] * A[(size_t)k * N + j] / p;
+    v = A[idx] - A[(size_t)i * N + k] * (A[(size_t)k * N + j] * rp);
   B[idx] = v;
+  if (i == k + 1 && j == k + 1) recip[(k + 1) & 1] = 1.0 / v;
 }
-cudaError_t launch_gj_step(int N, int k, const double* A, double* B, cudaStream_t st) {
+__global__ void recip_first_kernel(const double* A, double* recip) { recip[0] = 1.0 / A[0]; }
+cudaError_t launch_gj_step(int N, int k, const double* A, double* B, double* recip, cudaStream_t st) {
+  if (k == 0) recip_first_kernel<<<1, 1, 0, st>>>(A, recip);
   const int64_t total = (int64_t)N * N;
-  gj_step_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, k, A, B);
+  gj_step_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, k, A, B, recip);
   return cudaGetLastError();
 }
 

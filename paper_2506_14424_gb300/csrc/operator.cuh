@@ -31,12 +31,13 @@
 // cooperatively by the CTA's threads.
 #pragma once
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace sipg {
 
 template <typename T>
 __device__ __forceinline__ T nubar_of(int mode, T a, T b) {
-  if (mode == 1) return T(0.5) * (a + b);
+  if (mode == 1) return T(0.5f) * (a + b);
   if (mode == 2) return T(2) * a * b / (a + b);
   return a > b ? a : b;
 }
@@ -52,10 +53,10 @@ __device__ __forceinline__ void sweep3(const T* __restrict__ in, T* __restrict__
     const int t = idx / N3, r = idx - t * N3;
     const int o = (r / STR) % N;
     const T* base = in + t * N3 + (r - o * STR);
-    T s = T(0);
+    Acc<T> acc;
 #pragma unroll
-    for (int j = 0; j < N; ++j) s += (TR ? M[j * N + o] : M[o * N + j]) * base[j * STR];
-    out[idx] = ACC ? out[idx] + s : s;
+    for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], base[j * STR]);
+    out[idx] = ACC ? out[idx] + acc.get() : acc.get();
   }
 }
 
@@ -69,10 +70,10 @@ __device__ __forceinline__ void sweep2(const T* __restrict__ in, T* __restrict__
     const int t = idx / N2, r = idx - t * N2;
     const int o = (r / STR) % N;
     const T* base = in + t * N2 + (r - o * STR);
-    T s = T(0);
+    Acc<T> acc;
 #pragma unroll
-    for (int j = 0; j < N; ++j) s += (TR ? M[j * N + o] : M[o * N + j]) * base[j * STR];
-    out[idx] = ACC ? out[idx] + s : s;
+    for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], base[j * STR]);
+    out[idx] = ACC ? out[idx] + acc.get() : acc.get();
   }
 }
 
@@ -103,23 +104,26 @@ __host__ __device__ constexpr int op_smem_elems() {
 template <int N, typename T>
 __device__ __forceinline__ void load_tables(const Tab& tab, T* S, T* Dg, T* dS0, T* dS1, T* gw) {
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    S[i] = T(tab.S[i]);
-    Dg[i] = T(tab.Dg[i]);
+    S[i] = from_double<T>(tab.S[i]);
+    Dg[i] = from_double<T>(tab.Dg[i]);
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    dS0[i] = T(tab.dS0[i]);
-    dS1[i] = T(tab.dS1[i]);
-    gw[i] = T(tab.gw[i]);
+    dS0[i] = from_double<T>(tab.dS0[i]);
+    dS1[i] = from_double<T>(tab.dS1[i]);
+    gw[i] = from_double<T>(tab.gw[i]);
   }
 }
 
 // y = (m M + A) x on the cells [blockIdx.x*CPB, ...) of a level.
 // NC = 3: viscous operator (nu_cell [C][N^3], nu_face [C][6][N^2]);
 // NC = 1: Poisson operator (nu pointers unused).
-template <int N, int NC, typename T>
+// TS is the storage type of x, y and nu; T the arithmetic type (double,
+// float, or ff = float-float with double storage).
+template <int N, int NC, typename TS, typename T>
 __global__ void __launch_bounds__(OpCfg<N>::NT)
-apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
-             const T* __restrict__ nu_cell, const T* __restrict__ nu_face, T mass, int64_t batch_stride) {
+apply_kernel(LevelGeom g, Tab tab, const TS* __restrict__ x, TS* __restrict__ y,
+             const TS* __restrict__ nu_cell, const TS* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
+  const T mass = from_double<T>(mass_d);
   constexpr int N2 = N * N, N3 = N * N * N, CPB = OpCfg<N>::CPB;
   // blockIdx.y selects one of several vectors applied in the same launch
   x += (int64_t)blockIdx.y * batch_stride;
@@ -149,7 +153,7 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
   const int ncell = min(CPB, g.ncells - cell0);
   const int nt = ncell * NC;
   const size_t base0 = (size_t)cell0 * NC * N3;
-  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) Xs[i] = x[base0 + i];
+  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) Xs[i] = load_as<T>(x[base0 + i]);
   __syncthreads();
 
   // ---- cell term: values at Gauss points, then the collocation gradient
@@ -163,9 +167,8 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
   sweep3<N, 1, false, false>(U, B2, Dg, nt);
   sweep3<N, 2, false, false>(U, B3, Dg, nt);
   __syncthreads();
-  const T h0 = T(g.h[0]), h1 = T(g.h[1]), h2 = T(g.h[2]);
-  const T ih[3] = {T(1) / h0, T(1) / h1, T(1) / h2};
-  const T detJ = h0 * h1 * h2;
+  const T ih[3] = {from_double<T>(g.ih[0]), from_double<T>(g.ih[1]), from_double<T>(g.ih[2])};
+  const T detJ = from_double<T>(g.h[0] * g.h[1] * g.h[2]);
   for (int i = threadIdx.x; i < ncell * N3; i += blockDim.x) {
     const int c = i / N3, q = i - c * N3;
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
@@ -177,12 +180,12 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
       for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l) G[k][l] = Bl[l][(c * 3 + k) * N3 + q] * ih[l];
-      const T nu2W = T(2) * nu_cell[(size_t)(cell0 + c) * N3 + q] * W;
+      const T nu2W = T(2) * load_as<T>(nu_cell[(size_t)(cell0 + c) * N3 + q]) * W;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
 #pragma unroll
         for (int l = 0; l < 3; ++l)
-          Bl[l][(c * 3 + k) * N3 + q] = nu2W * T(0.5) * (G[k][l] + G[l][k]) * ih[l];
+          Bl[l][(c * 3 + k) * N3 + q] = nu2W * T(0.5f) * (G[k][l] + G[l][k]) * ih[l];
         U[(c * 3 + k) * N3 + q] *= mass * W;
       }
     } else {
@@ -204,7 +207,6 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
   __syncthreads();
 
   // ---- face terms, one face direction/side at a time
-  const T kp1sq = T(N * N);
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     const int fo = f ^ 1;
@@ -221,19 +223,19 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
       const int e = cell0 + c;
       const int off0 = face_node<N>(d, 0, a, b);
       const T* xs = Xs + t * N3 + off0;
-      T dn = T(0);
+      Acc<T> dn;
 #pragma unroll
-      for (int j = 0; j < N; ++j) dn += dS[j] * xs[j * std_];
+      for (int j = 0; j < N; ++j) dn.add(dS[j], xs[j * std_]);
       sV[i] = xs[layer * std_];
-      sN[i] = dn;
+      sN[i] = dn.get();
       const int nb = cell_neighbor(g, e, f);
       if (nb >= 0) {
-        const T* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
-        T dnn = T(0);
+        const TS* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
+        Acc<T> dnn;
 #pragma unroll
-        for (int j = 0; j < N; ++j) dnn += dSn[j] * xn[j * std_];
-        pV[i] = xn[layer_nb * std_];
-        pN[i] = dnn;
+        for (int j = 0; j < N; ++j) dnn.add(dSn[j], load_as<T>(xn[j * std_]));
+        pV[i] = load_as<T>(xn[layer_nb * std_]);
+        pN[i] = dnn.get();
       } else {
         pV[i] = T(0);
         pN[i] = T(0);
@@ -258,7 +260,7 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
     // numerical flux at the face quadrature points
     const T nsign = s ? T(1) : T(-1);
     const T ihd = ih[d], iht1 = ih[t1], iht2 = ih[t2];
-    const T area = T(g.h[t1]) * T(g.h[t2]);
+    const T area = from_double<T>(g.h[t1] * g.h[t2]);
     for (int i = threadIdx.x; i < ncell * N2; i += blockDim.x) {
       const int c = i / N2, p = i - c * N2;
       const int a = p % N, b = p / N;
@@ -273,13 +275,14 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
         continue;
       }
       const T W = gw[a] * gw[b] * area;
-      const T lam_m = T(penalty_lambda(g, e));
-      const T lam_p = nb >= 0 ? T(penalty_lambda(g, nb)) : lam_m;
-      const T lam = lam_m > lam_p ? lam_m : lam_p;
+      const double lam_md = penalty_lambda(g, e);
+      const double lam_pd = nb >= 0 ? penalty_lambda(g, nb) : lam_md;
+      // C_IP (k+1)^2 max(Lambda-, Lambda+): geometry only, formed in FP64 once
+      const T pen = from_double<T>(g.cip * double(N * N) * (lam_md > lam_pd ? lam_md : lam_pd));
       if constexpr (NC == 3) {
-        const T num = nu_face[((size_t)e * 6 + f) * N2 + p];
-        const T nup = nb >= 0 ? nu_face[((size_t)nb * 6 + fo) * N2 + p] : num;
-        const T tau = T(g.cip) * kp1sq * lam * nubar_of<T>(g.face_nu, num, nup);
+        const T num = load_as<T>(nu_face[((size_t)e * 6 + f) * N2 + p]);
+        const T nup = nb >= 0 ? load_as<T>(nu_face[((size_t)nb * 6 + fo) * N2 + p]) : num;
+        const T tau = pen * nubar_of<T>(g.face_nu, num, nup);
         T um[3], up[3], Gm[3][3], Gp[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -310,15 +313,15 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
         // (A + A^T) n with A = (nu^- G^- + nu^+ G^+)/2 and n = nsign e_d
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const T Akd = T(0.5) * (num * Gm[k][d] + nup * Gp[k][d]);
-          const T Adk = T(0.5) * (num * Gm[d][k] + nup * Gp[d][k]);
+          const T Akd = T(0.5f) * (num * Gm[k][d] + nup * Gp[k][d]);
+          const T Adk = T(0.5f) * (num * Gm[d][k] + nup * Gp[d][k]);
           const T nk = k == d ? nsign : T(0);
           const T P = -((Akd + Adk) * nsign - tau * (jmp[k] + nk * jn));
           // test-gradient coefficient Q = -nu^- sym(jump (x) n)
           // Q[k][l] = -nu^- (jmp_k n_l + n_k jmp_l) / 2
-          const T Qkd = -num * T(0.5) * (jmp[k] * nsign + nk * jmp[d]);
-          const T Qkt1 = -num * T(0.5) * (k == d ? nsign * jmp[t1] : T(0));
-          const T Qkt2 = -num * T(0.5) * (k == d ? nsign * jmp[t2] : T(0));
+          const T Qkd = -num * T(0.5f) * (jmp[k] * nsign + nk * jmp[d]);
+          const T Qkt1 = -num * T(0.5f) * (k == d ? nsign * jmp[t1] : T(0));
+          const T Qkt2 = -num * T(0.5f) * (k == d ? nsign * jmp[t2] : T(0));
           const int j = (c * 3 + k) * N2 + p;
           gV[j] = W * P;
           gN[j] = W * Qkd * ihd;
@@ -326,7 +329,7 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
           gT2[j] = W * Qkt2 * iht2;
         }
       } else {
-        const T tau = T(g.cip) * kp1sq * lam;
+        const T tau = pen;
         const int j = c * N2 + p;
         const T pm = gV[j];
         const T dnm = gN[j] * ihd;
@@ -340,8 +343,8 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
         }
         const T jmp = pm - pp;
         // -grad q . n jump/2 - q ({{dp/dx_d}} n_d - tau jump)
-        gV[j] = -W * (T(0.5) * (dnm + dnp) * nsign - tau * jmp);
-        gN[j] = -W * T(0.5) * jmp * nsign * ihd;
+        gV[j] = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
+        gN[j] = -W * T(0.5f) * jmp * nsign * ihd;
         gT1[j] = T(0);
         gT2[j] = T(0);
       }
@@ -369,7 +372,7 @@ apply_kernel(LevelGeom g, Tab tab, const T* __restrict__ x, T* __restrict__ y,
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = B3[i];
+  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(B3[i]);
 }
 
 }  // namespace sipg

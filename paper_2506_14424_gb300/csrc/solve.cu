@@ -159,7 +159,7 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
   const bool proj = H.singular && op == SIPG_OP_POISSON;
   CK(cudaMemcpyAsync(bb, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (proj) { int rc = project_mean(n, bb); if (rc) return rc; }
-  int rc = level_apply<double>(op, 0, x, q, so.mass_coeff);
+  int rc = krylov_apply(op, x, q, so.mass_coeff);
   if (rc) return rc;
   CK(launch_sub<double>(n, bb, q, r, st));
   if (proj) { rc = project_mean(n, r); if (rc) return rc; }
@@ -177,7 +177,7 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
     if ((rc = dot(n, r, z, &rz))) return rc;
     while (true) {
       if (it >= so.maxit) { status = SIPG_ERR_MAXIT; break; }
-      if ((rc = level_apply<double>(op, 0, p, q, so.mass_coeff))) return rc;
+      if ((rc = krylov_apply(op, p, q, so.mass_coeff))) return rc;
       double pq;
       if ((rc = dot(n, p, q, &pq))) return rc;
       if (!std::isfinite(pq)) { status = SIPG_ERR_NAN; break; }
@@ -199,7 +199,7 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
     }
   }
   // true residual of the returned iterate
-  if ((rc = level_apply<double>(op, 0, x, q, so.mass_coeff))) return rc;
+  if ((rc = krylov_apply(op, x, q, so.mass_coeff))) return rc;
   CK(launch_sub<double>(n, bb, q, r, st));
   if (proj) { if ((rc = project_mean(n, r))) return rc; }
   if ((rc = dot(n, r, r, &rr))) return rc;

@@ -105,7 +105,7 @@ __global__ void viscosity_carreau_kernel(LevelGeom g, Tab tab, RheologyDev rh, c
   sweep3<N, 1, false, false>(U, B2, Dg, 3);
   sweep3<N, 2, false, false>(U, B3, Dg, 3);
   __syncthreads();
-  const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+  const double ih[3] = {g.ih[0], g.ih[1], g.ih[2]};
   for (int q = threadIdx.x; q < N3; q += blockDim.x) {
     double G[3][3];
     const double* Bl[3] = {B1, B2, B3};

@@ -34,35 +34,37 @@ def _dev(x, dtype=torch.float64):
 
 CASES = [
     # dims, k, velocity bc, rheology
-    ((5, 3, 2), 2, "DDDDDD", {'law': 'analytic'}),
-    ((3, 4, 3), 3, "DNDDND", {'law': 'analytic'}),
-    ((2, 3, 2), 4, "DDDDDD", {'law': 'constant', 'nu': 0.3}),
-    ((2, 2, 3), 5, "NDDNDD", {'law': 'analytic'}),
+    ((7, 5, 2), 2, "DDDDDD", {'law': 'analytic'}),           # 70 cells: 3 CTAs of 32, ragged
+    ((3, 4, 3), 3, "DNDDND", {'law': 'analytic'}),           # 36 cells: 5 CTAs of 8, ragged
+    ((3, 1, 1), 4, "DDDDDD", {'law': 'constant', 'nu': 0.3}),  # 3 cells: 2 CTAs of 2, ragged
+    ((1, 1, 3), 5, "NDDNDD", {'law': 'analytic'}),
     ((1, 1, 1), 2, "DDDDDD", {'law': 'analytic'}),
 ]
 
 
+@pytest.mark.parametrize("arith", ["f64", "f64ff"])
 @pytest.mark.parametrize("dims,k,bc,rheo", CASES)
-def test_viscous_apply_f64_matches_oracle(dims, k, bc, rheo):
+def test_viscous_apply_f64_matches_oracle(dims, k, bc, rheo, arith):
     ctx = Context(*dims, k, bc_velocity=bc)
     ctx.set_viscosity(rheo)
     S = SIPG(BoxMesh(*dims, bc=_bc(bc)), k, 3)
     nu = S.viscosity_at_points(rheo)
     x = inputs.uniform_vector(S.n_dofs, seed=11)
-    y = ctx.apply('viscous', _dev(x)).cpu().numpy()
+    y = ctx.apply('viscous', _dev(x), arith=arith).cpu().numpy()
     assert _rel(y, S.apply(x, *nu)) <= TOL64
     # mass term of the viscous-step operator (gamma0/dt) M + A
-    y = ctx.apply('viscous', _dev(x), mass=37.5).cpu().numpy()
+    y = ctx.apply('viscous', _dev(x), mass=37.5, arith=arith).cpu().numpy()
     assert _rel(y, S.apply(x, *nu, mass=37.5)) <= TOL64
 
 
+@pytest.mark.parametrize("arith", ["f64", "f64ff"])
 @pytest.mark.parametrize("dims,k,bc", [((5, 3, 2), 1, "NNNNNN"), ((3, 2, 4), 2, "DDNNDD"),
                                        ((2, 3, 2), 3, "DDDDDD"), ((2, 2, 2), 4, "NNNNNN")])
-def test_poisson_apply_f64_matches_oracle(dims, k, bc):
+def test_poisson_apply_f64_matches_oracle(dims, k, bc, arith):
     ctx = Context(*dims, k + 1, bc_pressure=bc)
     P = SIPG(BoxMesh(*dims, bc=_bc(bc)), k, 1)
     x = inputs.uniform_vector(P.n_dofs, seed=12)
-    y = ctx.apply('poisson', _dev(x)).cpu().numpy()
+    y = ctx.apply('poisson', _dev(x), arith=arith).cpu().numpy()
     assert _rel(y, P.apply(x)) <= TOL64
 
 
@@ -103,12 +105,13 @@ def test_viscosity_at_points_matches_oracle(rheo_name):
     assert _rel(y, S.apply(x, rc, rf)) <= TOL64
 
 
-def test_apply_is_deterministic():
+@pytest.mark.parametrize("arith", ["f64", "f64ff"])
+def test_apply_is_deterministic(arith):
     ctx = Context(6, 5, 4, 3)
     ctx.set_viscosity({'law': 'analytic'})
     x = _dev(inputs.uniform_vector(ctx.n_dofs(), seed=15))
-    y1 = ctx.apply('viscous', x)
-    y2 = ctx.apply('viscous', x)
+    y1 = ctx.apply('viscous', x, arith=arith)
+    y2 = ctx.apply('viscous', x, arith=arith)
     assert torch.equal(y1, y2)
 
 
@@ -145,6 +148,9 @@ def test_cfg2_full_size_sampled_rows():
     ctx.set_viscosity(rheo, _dev(u))
     x = inputs.uniform_vector(ctx.n_dofs(), seed=19)
     y = ctx.apply('viscous', _dev(x)).cpu().numpy().reshape(mesh.n_cells, -1)
+    yff = ctx.apply('viscous', _dev(x), arith='f64ff').cpu().numpy().reshape(mesh.n_cells, -1)
+    # float-float against native FP64 over the whole vector
+    assert _rel(yff, y) <= TOL64
     rng = np.random.default_rng(20)
     cells = sorted(set([0, N - 1, N * N * N - 1, (N // 2) * (N * N + N + 1)] +
                        list(rng.integers(0, N ** 3, 12))))
@@ -158,6 +164,7 @@ def test_cfg2_full_size_sampled_rows():
     nc_ref, nf_ref = S.viscosity_at_points(rheo, u, cells=sorted(need))
     y_ref = S.apply(x, nc_ref, nf_ref, cells=cells)
     assert _rel(y[cells], y_ref) <= TOL64
+    assert _rel(yff[cells], y_ref) <= TOL64
     nc, nf = ctx.get_viscosity(0)
     assert _rel(nc.cpu().numpy()[cells], nc_ref[cells]) <= 1e-13
     assert _rel(nf.cpu().numpy()[cells], nf_ref[cells]) <= 1e-13

@@ -60,7 +60,7 @@ def _oracle_hierarchy(ctx, op, rheo, bc, mass=0.0, u=None):
 
 @pytest.mark.parametrize("op", ["viscous", "poisson"])
 def test_transfers_match_oracle(op):
-    ctx = Context(4, 4, 2, 4, coarse_max_dofs=100)
+    ctx = Context(4, 2, 2, 4, coarse_max_dofs=100)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     _, Ps, _ = _oracle_hierarchy(ctx, op, rheo, "DDDDDD" if op == "viscous" else "NNNNNN")
@@ -202,6 +202,18 @@ def test_poisson_mg_solve_singular():
     xg = x.cpu().numpy()
     assert np.linalg.norm(b - A @ xg) <= 1e-8 * (1 + 1e-6) * np.linalg.norm(b)
     assert abs(xg.mean()) < 1e-10 * np.abs(xg).max()
+
+
+def test_krylov_float_float_solve_matches_oracle():
+    dims, k = (4, 4, 2), 3
+    rheo = inputs.sinker(seed=2, count=8, radius=0.2, nu_max=1e2)
+    ctx = Context(*dims, k, coarse_max_dofs=300, krylov_arith="f64ff")
+    ctx.set_viscosity(rheo)
+    S = SIPG(BoxMesh(*dims), k, 3)
+    A = S.assemble(*S.viscosity_at_points(rheo))
+    b = A @ inputs.uniform_vector(S.n_dofs, seed=83)
+    x, st = ctx.solve("viscous", _dev(b), rtol=1e-10, precond="mg")
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-10 * (1 + 1e-6) * np.linalg.norm(b)
 
 
 def test_viscous_step_operator_mass_solve():
