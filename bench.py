@@ -35,6 +35,8 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip the extra solve / precision lines")
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    p.add_argument("--arith", default="f64", choices=["f64", "f64ff"],
+                   help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
     return p.parse_args()
 
 
@@ -154,7 +156,7 @@ def run_gpu(args):
     xs = [torch.tensor(inputs.uniform_vector(n, seed=100 + i), device="cuda") for i in range(pairs)]
     ys = [torch.empty_like(xs[0]) for _ in range(pairs)]
     for i in range(args.warmup):
-        ctx.apply("viscous", xs[i % pairs], ys[i % pairs])
+        ctx.apply("viscous", xs[i % pairs], ys[i % pairs], arith=args.arith)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -165,7 +167,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e0.record(stream)
     for i in range(args.steps):
-        ctx.apply("viscous", xs[i % pairs], ys[i % pairs])
+        ctx.apply("viscous", xs[i % pairs], ys[i % pairs], arith=args.arith)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -206,8 +208,9 @@ def run_gpu(args):
         extras = gpu_extras(ctx, xs, ys, stream)
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": [N_CELLS] * 3, "k_u": K_U, "n_dofs": n,
+            "vs_baseline": None, "dtype": "f64" if args.arith == "f64" else "f32x2 (float-float, FP64-accurate)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": [N_CELLS] * 3, "k_u": K_U, "n_dofs": n, "arith": args.arith,
                        "l2": "inputs larger than L2: 4 rotating x/y pairs (403 MB) + 42 MB stored nu",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roof}

@@ -5,34 +5,58 @@
 
 namespace sipg {
 
-template <int N, int NC, typename TS, typename TC>
-cudaError_t launch_apply_n(const LevelGeom& g, const Tab& tab, const TS* x, TS* y, const TS* nu_cell,
-                           const TS* nu_face, double mass, int nbatch, cudaStream_t st) {
-  constexpr int CPB = OpCfg<N>::CPB;
-  static_assert(sizeof(TC) == sizeof(TS) || sizeof(TC) == 8, "compute type width");
+// Host conversion of the FP64 tables to the kernel's arithmetic type (the
+// float-float split is exact: hi = RN(d), lo = RN(d - hi)).
+template <typename T>
+inline T host_from_double(double d) { return T(d); }
+template <>
+inline ff host_from_double<ff>(double d) {
+  const float h = (float)d;
+  return ff(h, (float)(d - (double)h));
+}
+
+template <typename T>
+CTab<T> make_ctab(const Tab& t) {
+  CTab<T> c{};
+  for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    c.S[i] = host_from_double<T>(t.S[i]);
+    c.Dg[i] = host_from_double<T>(t.Dg[i]);
+  }
+  for (int i = 0; i < kMaxN; ++i) {
+    c.dS0[i] = host_from_double<T>(t.dS0[i]);
+    c.dS1[i] = host_from_double<T>(t.dS1[i]);
+    c.gw[i] = host_from_double<T>(t.gw[i]);
+  }
+  return c;
+}
+
+template <int N, int NC, typename TS, typename TN, typename TC>
+cudaError_t launch_apply_n(const LevelGeom& g, const Tab& tab, const TS* x, TS* y, const TN* nu_cell,
+                           const TN* nu_face, double mass, int nbatch, cudaStream_t st) {
+  using Cfg = OpCfg<N, NC>;
   const size_t smem = sizeof(TC) * op_smem_elems<N, NC>();
   static bool attr_set = false;  // per instantiation, per process (single device)
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, NC, TS, TC>,
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, NC, TS, TN, TC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int grid = (g.ncells + CPB - 1) / CPB;
+  const int grid = (g.ncells + Cfg::CPB - 1) / Cfg::CPB;
   if (grid == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
-  apply_kernel<N, NC, TS, TC><<<dim3(grid, nbatch), OpCfg<N>::NT, smem, st>>>(g, tab, x, y, nu_cell, nu_face,
-                                                                              mass, stride);
+  apply_kernel<N, NC, TS, TN, TC><<<dim3(grid, nbatch), Cfg::NT, smem, st>>>(g, make_ctab<TC>(tab), x, y, nu_cell,
+                                                                             nu_face, mass, stride);
   return cudaGetLastError();
 }
 
-template <typename TS, typename TC>
+template <typename TS, typename TN, typename TC>
 cudaError_t launch_apply_t(int n, int ncomp, const LevelGeom& g, const Tab& tab, const TS* x, TS* y,
-                           const TS* nu_cell, const TS* nu_face, double mass, int nbatch, cudaStream_t st) {
-#define SIPG_CASE(NN)                                                                                   \
-  case NN:                                                                                              \
-    return ncomp == 3 ? launch_apply_n<NN, 3, TS, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st) \
-                      : launch_apply_n<NN, 1, TS, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st);
+                           const TN* nu_cell, const TN* nu_face, double mass, int nbatch, cudaStream_t st) {
+#define SIPG_CASE(NN)                                                                                       \
+  case NN:                                                                                                  \
+    return ncomp == 3 ? launch_apply_n<NN, 3, TS, TN, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st) \
+                      : launch_apply_n<NN, 1, TS, TN, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st);
   switch (n) {
     SIPG_CASE(2)
     SIPG_CASE(3)

@@ -115,6 +115,10 @@ int sipg_ctx::build_hierarchy(int op) {
       L.nu_face64 = dalloc<double>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
       L.nu_cell32 = dalloc<float>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
       L.nu_face32 = dalloc<float>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      if (l == 0) {
+        L.nu_cellff = dalloc<float2>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+        L.nu_faceff = dalloc<float2>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      }
       if (l > 0) { L.ulin = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc ulin", e); }
     }
     L.diag64 = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
@@ -148,6 +152,7 @@ sipg_ctx::~sipg_ctx() {
   for (Hier& H : hier) {
     for (Level& L : H.L) {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
+      cudaFree(L.nu_cellff); cudaFree(L.nu_faceff);
       cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32);
       for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
       cudaFree(L.Ainv); cudaFree(L.Atmp);
@@ -268,8 +273,9 @@ int sipg_ctx::level_apply_ff(int op, int l, const double* x, double* y, double m
   sipg_ctx* ctx = this;
   const Hier& H = hier[op];
   const Level& L = H.L[l];
-  const double* nc = op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr;
-  const double* nf = op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr;
+  if (op == SIPG_OP_VISCOUS && !L.nu_cellff) return fail(SIPG_ERR_INVALID, "float-float apply on level 0 only");
+  const float2* nc = op == SIPG_OP_VISCOUS ? L.nu_cellff : nullptr;
+  const float2* nf = op == SIPG_OP_VISCOUS ? L.nu_faceff : nullptr;
   CK(launch_apply_ff(L.n, H.ncomp, L.g, tabs[L.n], x, y, nc, nf, mass, 1, st));
   return SIPG_OK;
 }
@@ -496,6 +502,8 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
     const int64_t n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
     e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, ctx->st);
     if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, ctx->st);
+    if (!e && L.nu_cellff) e = launch_split_ff(L.g.ncells * n3, L.nu_cell64, L.nu_cellff, ctx->st);
+    if (!e && L.nu_faceff) e = launch_split_ff(L.g.ncells * 6 * n2, L.nu_face64, L.nu_faceff, ctx->st);
     if (e) return ctx->fail(SIPG_ERR_CUDA, "viscosity cast", e);
   }
   ctx->have_nu = true;

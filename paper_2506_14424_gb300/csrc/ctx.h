@@ -18,6 +18,7 @@ struct Level {
   int child[kMaxN] = {0};    // h: child of each coarse node (ties to child 0)
   double *nu_cell64 = nullptr, *nu_face64 = nullptr;
   float *nu_cell32 = nullptr, *nu_face32 = nullptr;
+  float2 *nu_cellff = nullptr, *nu_faceff = nullptr;  // (hi, lo) split for float-float
   double* ulin = nullptr;    // linearization velocity on this level (l > 0)
   double* diag64 = nullptr;
   double* dinv64 = nullptr;

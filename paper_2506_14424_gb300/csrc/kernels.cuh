@@ -9,8 +9,10 @@ template <typename T>
 cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, const T* x, T* y,
                          const T* nu_cell, const T* nu_face, T mass, int nbatch, cudaStream_t st);
 // FP64-accurate apply with float-float arithmetic (double storage)
+// (nu given as (hi, lo) float pairs, see launch_split_ff)
 cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
-                            const double* nu_cell, const double* nu_face, double mass, int nbatch, cudaStream_t st);
+                            const float2* nu_cell, const float2* nu_face, double mass, int nbatch, cudaStream_t st);
+cudaError_t launch_split_ff(int64_t n, const double* in, float2* out, cudaStream_t st);
 
 // ---- viscosity (viscosity.cu)
 struct RheologyDev {

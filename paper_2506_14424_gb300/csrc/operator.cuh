@@ -35,6 +35,15 @@
 
 namespace sipg {
 
+// 1D tables in the arithmetic type of a kernel (kernel parameter: compile-time
+// indices become constant-bank operands, no shared-memory traffic).
+template <typename T>
+struct CTab {
+  T S[kMaxN * kMaxN];
+  T Dg[kMaxN * kMaxN];
+  T dS0[kMaxN], dS1[kMaxN], gw[kMaxN];
+};
+
 template <typename T>
 __device__ __forceinline__ T nubar_of(int mode, T a, T b) {
   if (mode == 1) return T(0.5f) * (a + b);
@@ -44,36 +53,49 @@ __device__ __forceinline__ T nubar_of(int mode, T a, T b) {
 
 // out[t][.. o ..] (+)= sum_j M(o, j) in[t][.. j ..] along direction DIR of
 // N^3 tensors (x fastest); M(o, j) = M[o*N + j], or M[j*N + o] if TR.
+// One thread per 1D line: the N inputs are loaded once into registers, the
+// N x N matrix comes from the kernel-parameter bank, N outputs are stored.
 template <int N, int DIR, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void sweep3(const T* __restrict__ in, T* __restrict__ out,
-                                       const T* __restrict__ M, int ntens) {
-  constexpr int N3 = N * N * N;
-  constexpr int STR = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
-  for (int idx = threadIdx.x; idx < ntens * N3; idx += blockDim.x) {
-    const int t = idx / N3, r = idx - t * N3;
-    const int o = (r / STR) % N;
-    const T* base = in + t * N3 + (r - o * STR);
-    Acc<T> acc;
+__device__ __forceinline__ void sweep3(const T* __restrict__ in, T* __restrict__ out, const T* M, int ntens) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int STR = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
+  for (int line = threadIdx.x; line < ntens * N2; line += blockDim.x) {
+    const int t = line / N2, r = line - t * N2;
+    // r enumerates the two other coordinates, the lower one fastest
+    const int off = t * N3 + (DIR == 0 ? r * N : (DIR == 1 ? (r % N) + (r / N) * N2 : r));
+    T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], base[j * STR]);
-    out[idx] = ACC ? out[idx] + acc.get() : acc.get();
+    for (int j = 0; j < N; ++j) v[j] = in[off + j * STR];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      Acc<T> acc;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], v[j]);
+      T* dst = out + off + o * STR;
+      *dst = ACC ? *dst + acc.get() : acc.get();
+    }
   }
 }
 
 // Same on N^2 face tensors (a fastest): DIR 0 along a, 1 along b.
 template <int N, int DIR, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void sweep2(const T* __restrict__ in, T* __restrict__ out,
-                                       const T* __restrict__ M, int ntens) {
+__device__ __forceinline__ void sweep2(const T* __restrict__ in, T* __restrict__ out, const T* M, int ntens) {
   constexpr int N2 = N * N;
   constexpr int STR = DIR == 0 ? 1 : N;
-  for (int idx = threadIdx.x; idx < ntens * N2; idx += blockDim.x) {
-    const int t = idx / N2, r = idx - t * N2;
-    const int o = (r / STR) % N;
-    const T* base = in + t * N2 + (r - o * STR);
-    Acc<T> acc;
+  for (int line = threadIdx.x; line < ntens * N; line += blockDim.x) {
+    const int t = line / N, r = line - t * N;
+    const int off = t * N2 + (DIR == 0 ? r * N : r);
+    T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], base[j * STR]);
-    out[idx] = ACC ? out[idx] + acc.get() : acc.get();
+    for (int j = 0; j < N; ++j) v[j] = in[off + j * STR];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      Acc<T> acc;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], v[j]);
+      T* dst = out + off + o * STR;
+      *dst = ACC ? *dst + acc.get() : acc.get();
+    }
   }
 }
 
@@ -89,66 +111,372 @@ __device__ __forceinline__ int face_node(int d, int layer, int a, int b) {
 template <int N>
 __device__ __forceinline__ int dir_stride(int d) { return d == 0 ? 1 : (d == 1 ? N : N * N); }
 
-// Cells per CTA and threads per CTA of the operator kernels.
-template <int N> struct OpCfg {
-  static constexpr int CPB = N == 2 ? 32 : (N == 3 ? 8 : (N == 4 ? 4 : 2));
-  static constexpr int NT = 256;
+// Cells per CTA and threads per CTA of the operator kernels: about 100 1D
+// lines per sweep (one thread each), so that a CTA is a few warps and many
+// independent CTAs share an SM (their barriers overlap).
+template <int N, int NC> struct OpCfg {
+  static constexpr int CPB = NC == 3 ? (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : (N == 5 ? 2 : 1))))
+                                     : (N == 2 ? 32 : (N == 3 ? 12 : (N == 4 ? 8 : (N == 5 ? 4 : 3))));
+  static constexpr int LINES = CPB * NC * N * N;
+  static constexpr int NT = ((LINES + 31) / 32) * 32;
 };
 
-// Shared-memory footprint (in elements of T) of apply_kernel.
+// Shared-memory layout per cell (elements of T): staged x, the y accumulator,
+// and a work region used by the cell phase (3 tensors) and then by the face
+// phase (16 face slots: 8 per side of one direction).
+template <int N, int NC>
+__host__ __device__ constexpr int op_work_elems() {
+  return (3 * NC * N * N * N > 16 * NC * N * N) ? 3 * NC * N * N * N : 16 * NC * N * N;
+}
 template <int N, int NC>
 __host__ __device__ constexpr int op_smem_elems() {
-  return 3 * N * N + 4 * N + OpCfg<N>::CPB * (5 * NC * N * N * N + 16 * NC * N * N);
+  return 4 * N + 2 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
 }
 
 template <int N, typename T>
-__device__ __forceinline__ void load_tables(const Tab& tab, T* S, T* Dg, T* dS0, T* dS1, T* gw) {
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    S[i] = from_double<T>(tab.S[i]);
-    Dg[i] = from_double<T>(tab.Dg[i]);
-  }
+__device__ __forceinline__ void load_tables(const CTab<T>& ct, T* dS0, T* dS1, T* gw) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    dS0[i] = from_double<T>(tab.dS0[i]);
-    dS1[i] = from_double<T>(tab.dS1[i]);
-    gw[i] = from_double<T>(tab.gw[i]);
+    dS0[i] = ct.dS0[i];
+    dS1[i] = ct.dS1[i];
+    gw[i] = ct.gw[i];
   }
+}
+
+// Numerical flux at the quadrature points of both faces of direction D of the
+// CTA's cells. Per side s, slots F[s*8 + .] of FS elements hold on entry:
+//   0 own trace gV, 1 own normal derivative gN, 2 neighbour trace gVp,
+//   3 neighbour normal derivative gNp, 4 own d/dxi_t2 gT2, 5 own d/dxi_t1 gT1,
+//   6 neighbour d/dxi_t2, 7 neighbour d/dxi_t1   (reference coordinates)
+// and on exit slots 0, 1, 5, 4 hold the coefficients of the test value, of
+// the normal test derivative and of the two tangential test derivatives.
+// pen[s*CPB + c] = C_IP (k+1)^2 max(Lambda-, Lambda+).
+template <int N, int NC, int D, typename TN, typename T>
+__device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, int ncell, int FS, int CPB,
+                                               const T* ih, const T* gw, const T* pen,
+                                               const TN* __restrict__ nu_face, T* F) {
+  constexpr int N2 = N * N;
+  constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+  const T ihd = ih[D], iht1 = ih[T1], iht2 = ih[T2];
+  const T area = from_double<T>(g.h[T1] * g.h[T2]);
+  for (int i = threadIdx.x; i < 2 * ncell * N2; i += blockDim.x) {
+    const int s = i / (ncell * N2);
+    const int rem = i - s * ncell * N2;
+    const int c = rem / N2, p = rem - c * N2;
+    const int a = p % N, b = p / N;
+    const int e = cell0 + c;
+    const int f = 2 * D + s;
+    const int nb = cell_neighbor(g, e, f);
+    T* gV = F + (s * 8 + 0) * FS;
+    T* gN = F + (s * 8 + 1) * FS;
+    const T* gVp = F + (s * 8 + 2) * FS;
+    const T* gNp = F + (s * 8 + 3) * FS;
+    T* gT2 = F + (s * 8 + 4) * FS;
+    T* gT1 = F + (s * 8 + 5) * FS;
+    const T* gT2p = F + (s * 8 + 6) * FS;
+    const T* gT1p = F + (s * 8 + 7) * FS;
+    if (nb < 0 && g.bc[f] == 1) {  // homogeneous Neumann: no face term
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const int j = (c * NC + k) * N2 + p;
+        gV[j] = T(0); gN[j] = T(0); gT1[j] = T(0); gT2[j] = T(0);
+      }
+      continue;
+    }
+    const T nsign = s ? T(1) : T(-1);
+    const T W = gw[a] * gw[b] * area;
+    const T pe = pen[s * CPB + c];
+    if constexpr (NC == 3) {
+      const T num = load_as<T>(nu_face[((size_t)e * 6 + f) * N2 + p]);
+      const T nup = nb >= 0 ? load_as<T>(nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p]) : num;
+      const T tau = pe * nubar_of<T>(g.face_nu, num, nup);
+      // gradients in physical coordinates: G[k][l] = d u_k / d x_l
+      T um[3], up[3], Gm[3][3], Gp[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int j = (c * 3 + k) * N2 + p;
+        um[k] = gV[j];
+        Gm[k][D] = gN[j] * ihd;
+        Gm[k][T1] = gT1[j] * iht1;
+        Gm[k][T2] = gT2[j] * iht2;
+        if (nb >= 0) {
+          up[k] = gVp[j];
+          Gp[k][D] = gNp[j] * ihd;
+          Gp[k][T1] = gT1p[j] * iht1;
+          Gp[k][T2] = gT2p[j] * iht2;
+        } else {  // Dirichlet mirror: u+ = -u-, grad u+ = grad u-
+          up[k] = -um[k];
+          Gp[k][D] = Gm[k][D];
+          Gp[k][T1] = Gm[k][T1];
+          Gp[k][T2] = Gm[k][T2];
+        }
+      }
+      T jmp[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) jmp[k] = um[k] - up[k];
+      const T jn = jmp[D] * nsign;
+      const T hq = -num * T(0.5f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // value coefficient P = -[(A + A^T) n - tau ([u] + n ([u].n))],
+        // A = (nu- grad u- + nu+ grad u+)/2, n = nsign e_D
+        const T Akd = T(0.5f) * (num * Gm[k][D] + nup * Gp[k][D]);
+        const T Adk = T(0.5f) * (num * Gm[D][k] + nup * Gp[D][k]);
+        const T pen_k = k == D ? jmp[k] + nsign * jn : jmp[k];
+        const T P = tau * pen_k - (Akd + Adk) * nsign;
+        // test-gradient coefficient Q = -nu- sym([u] (x) n):
+        // Q[k][l] = -nu- (jmp_k n_l + n_k jmp_l) / 2
+        const T Qkd = k == D ? hq * (T(2) * jmp[D] * nsign) : hq * (jmp[k] * nsign);
+        const int j = (c * 3 + k) * N2 + p;
+        gV[j] = W * P;
+        gN[j] = W * Qkd * ihd;
+        gT1[j] = k == D ? W * (hq * (nsign * jmp[T1])) * iht1 : T(0);
+        gT2[j] = k == D ? W * (hq * (nsign * jmp[T2])) * iht2 : T(0);
+      }
+    } else {
+      const T tau = pe;
+      const int j = c * N2 + p;
+      const T pm = gV[j];
+      const T dnm = gN[j] * ihd;
+      T pp, dnp;
+      if (nb >= 0) {
+        pp = gVp[j];
+        dnp = gNp[j] * ihd;
+      } else {
+        pp = -pm;
+        dnp = dnm;
+      }
+      const T jmp = pm - pp;
+      // -grad q . n jump/2 - q ({{dp/dx_d}} n_d - tau jump)
+      gV[j] = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
+      gN[j] = -W * T(0.5f) * jmp * nsign * ihd;
+      gT1[j] = T(0);
+      gT2[j] = T(0);
+    }
+  }
+}
+
+// 1D contraction of one line held in registers: out[o] = sum_j M(o, j) v[j]
+template <int N, bool TR, typename T>
+__device__ __forceinline__ T line_dot(const T* M, const T* v, int o) {
+  Acc<T> acc;
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], v[j]);
+  return acc.get();
+}
+
+// Face terms of direction D (both sides) added to Y.
+template <int N, int NC, int D, typename TS, typename TN, typename T>
+__device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct, int cell0, int ncell, int CPB,
+                                          const TS* __restrict__ x, const TN* __restrict__ nu_face,
+                                          const T* Xs, T* Y, T* F, T* pen, const T* ih, const T* gw,
+                                          const T* dS0, const T* dS1) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int STD = D == 0 ? 1 : (D == 1 ? N : N2);
+  const int nt = ncell * NC;
+  const int FS = CPB * NC * N2;
+  const T* S = ct.S;
+  const T* Dg = ct.Dg;
+  // (A) traces and normal derivatives at the face Gauss-Lobatto nodes of both
+  // sides (neighbour data straight from global memory); penalty per cell/side
+  for (int i = threadIdx.x; i < 2 * nt * N2; i += blockDim.x) {
+    const int s = i / (nt * N2);
+    const int rem = i - s * nt * N2;
+    const int t = rem / N2, p = rem - t * N2;
+    const int c = t / NC, comp = t - c * NC;
+    const int e = cell0 + c;
+    const int off0 = face_node<N>(D, 0, p % N, p / N);
+    const T* dS = s ? dS1 : dS0;
+    const T* dSn = s ? dS0 : dS1;
+    const T* xs = Xs + t * N3 + off0;
+    Acc<T> dn;
+#pragma unroll
+    for (int j = 0; j < N; ++j) dn.add(dS[j], xs[j * STD]);
+    T* Fs = F + s * 8 * FS;
+    Fs[rem] = xs[(s ? N - 1 : 0) * STD];
+    Fs[FS + rem] = dn.get();
+    const int nb = cell_neighbor(g, e, 2 * D + s);
+    if (nb >= 0) {
+      const TS* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
+      T v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = load_as<T>(xn[j * STD]);
+      Acc<T> dnn;
+#pragma unroll
+      for (int j = 0; j < N; ++j) dnn.add(dSn[j], v[j]);
+      Fs[2 * FS + rem] = v[s ? 0 : N - 1];
+      Fs[3 * FS + rem] = dnn.get();
+    } else {
+      Fs[2 * FS + rem] = T(0);
+      Fs[3 * FS + rem] = T(0);
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * ncell; i += blockDim.x) {
+    const int s = i / ncell, c = i - s * ncell;
+    const int e = cell0 + c;
+    const int nb = cell_neighbor(g, e, 2 * D + s);
+    const double lm = penalty_lambda(g, e);
+    const double lp = nb >= 0 ? penalty_lambda(g, nb) : lm;
+    pen[s * CPB + c] = from_double<T>(g.cip * double(N * N) * (lm > lp ? lm : lp));
+  }
+  __syncthreads();
+  // (B) interpolate the four node quantities of each side along a
+  for (int line = threadIdx.x; line < 2 * 4 * nt * N; line += blockDim.x) {
+    const int s = line / (4 * nt * N);
+    const int rem = line - s * 4 * nt * N;
+    const int q = rem / (nt * N), lt = rem - q * nt * N;
+    const int t = lt / N, r = lt - t * N;
+    const T* in = F + (s * 8 + q) * FS + t * N2 + r * N;
+    T* out = F + (s * 8 + 4 + q) * FS + t * N2 + r * N;
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = in[j];
+#pragma unroll
+    for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(S, v, o);
+  }
+  __syncthreads();
+  // (C) along b: values at the face Gauss points and their b-derivatives
+  for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
+    const int s = line / (nt * N);
+    const int lt = line - s * nt * N;
+    const int t = lt / N, r = lt - t * N;
+    T* Fs = F + s * 8 * FS + t * N2 + r;
+    T v4[N], v5[N], v6[N], v7[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      v4[j] = Fs[4 * FS + j * N];
+      v5[j] = Fs[5 * FS + j * N];
+      v6[j] = Fs[6 * FS + j * N];
+      v7[j] = Fs[7 * FS + j * N];
+    }
+    T gv[N], gvp[N];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      gv[o] = line_dot<N, false>(S, v4, o);
+      gvp[o] = line_dot<N, false>(S, v6, o);
+      Fs[0 * FS + o * N] = gv[o];
+      Fs[1 * FS + o * N] = line_dot<N, false>(S, v5, o);
+      Fs[2 * FS + o * N] = gvp[o];
+      Fs[3 * FS + o * N] = line_dot<N, false>(S, v7, o);
+    }
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      Fs[4 * FS + o * N] = line_dot<N, false>(Dg, gv, o);
+      Fs[6 * FS + o * N] = line_dot<N, false>(Dg, gvp, o);
+    }
+  }
+  __syncthreads();
+  // (D) along a: tangential a-derivatives of the own and neighbour traces
+  for (int line = threadIdx.x; line < 2 * 2 * nt * N; line += blockDim.x) {
+    const int s = line / (2 * nt * N);
+    const int rem = line - s * 2 * nt * N;
+    const int q = rem / (nt * N), lt = rem - q * nt * N;  // q = 0 own, 1 neighbour
+    const int t = lt / N, r = lt - t * N;
+    const T* in = F + (s * 8 + 2 * q) * FS + t * N2 + r * N;
+    T* out = F + (s * 8 + 5 + 2 * q) * FS + t * N2 + r * N;
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = in[j];
+#pragma unroll
+    for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(Dg, v, o);
+  }
+  __syncthreads();
+  // (E) numerical flux
+  face_flux_pair<N, NC, D, TN, T>(g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
+  __syncthreads();
+  // (F) test side, along a: slot 2 = gV + Dg_a^T gT1
+  for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
+    const int s = line / (nt * N);
+    const int lt = line - s * nt * N;
+    const int t = lt / N, r = lt - t * N;
+    T* Fs = F + s * 8 * FS + t * N2 + r * N;
+    T g5[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) g5[j] = Fs[5 * FS + j];
+#pragma unroll
+    for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o] + line_dot<N, true>(Dg, g5, o);
+  }
+  __syncthreads();
+  // (G) along b: slot 6 = S_b^T (slot 2 + Dg_b^T gT2), slot 7 = S_b^T gN
+  for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
+    const int s = line / (nt * N);
+    const int lt = line - s * nt * N;
+    const int t = lt / N, r = lt - t * N;
+    T* Fs = F + s * 8 * FS + t * N2 + r;
+    T w[N], g4[N], g1[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      g4[j] = Fs[4 * FS + j * N];
+      g1[j] = Fs[1 * FS + j * N];
+    }
+#pragma unroll
+    for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N] + line_dot<N, true>(Dg, g4, o);
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      Fs[6 * FS + o * N] = line_dot<N, true>(S, w, o);
+      Fs[7 * FS + o * N] = line_dot<N, true>(S, g1, o);
+    }
+  }
+  __syncthreads();
+  // (H) along a: node coefficients, slot 0 (value) and slot 1 (normal)
+  for (int line = threadIdx.x; line < 2 * 2 * nt * N; line += blockDim.x) {
+    const int s = line / (2 * nt * N);
+    const int rem = line - s * 2 * nt * N;
+    const int q = rem / (nt * N), lt = rem - q * nt * N;
+    const int t = lt / N, r = lt - t * N;
+    const T* in = F + (s * 8 + 6 + q) * FS + t * N2 + r * N;
+    T* out = F + (s * 8 + q) * FS + t * N2 + r * N;
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = in[j];
+#pragma unroll
+    for (int o = 0; o < N; ++o) out[o] = line_dot<N, true>(S, v, o);
+  }
+  __syncthreads();
+  // (I) scatter onto the cell nodes: value on the face layer, normal
+  // derivative spread along D, both sides
+  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) {
+    const int t = i / N3, r = i - t * N3;
+    const int ix = r % N, iy = (r / N) % N, iz = r / N2;
+    const int id = D == 0 ? ix : (D == 1 ? iy : iz);
+    const int fp = t * N2 + (D == 0 ? iy : ix) + N * (D == 2 ? iy : iz);
+    T v = dS0[id] * F[1 * FS + fp] + dS1[id] * F[9 * FS + fp];
+    if (id == 0) v += F[fp];
+    if (id == N - 1) v += F[8 * FS + fp];
+    Y[i] += v;
+  }
+  __syncthreads();
 }
 
 // y = (m M + A) x on the cells [blockIdx.x*CPB, ...) of a level.
 // NC = 3: viscous operator (nu_cell [C][N^3], nu_face [C][6][N^2]);
 // NC = 1: Poisson operator (nu pointers unused).
-// TS is the storage type of x, y and nu; T the arithmetic type (double,
-// float, or ff = float-float with double storage).
-template <int N, int NC, typename TS, typename T>
-__global__ void __launch_bounds__(OpCfg<N>::NT)
-apply_kernel(LevelGeom g, Tab tab, const TS* __restrict__ x, TS* __restrict__ y,
-             const TS* __restrict__ nu_cell, const TS* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
-  const T mass = from_double<T>(mass_d);
-  constexpr int N2 = N * N, N3 = N * N * N, CPB = OpCfg<N>::CPB;
+// TS is the storage type of x and y, TN that of nu, T the arithmetic type
+// (double, float, or ff = float-float with double x/y and pre-split nu).
+template <int N, int NC, typename TS, typename TN, typename T>
+__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
+apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
+             const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
+  constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
   // blockIdx.y selects one of several vectors applied in the same launch
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  T* S = sm;
-  T* Dg = S + N2;
-  T* dS0 = Dg + N2;
+  T* dS0 = sm;
   T* dS1 = dS0 + N;
   T* gw = dS1 + N;
-  T* buf = sm + 3 * N2 + 4 * N;
-  T* Xs = buf;
-  T* U = Xs + CPB * NC * N3;
-  T* B1 = U + CPB * NC * N3;
-  T* B2 = B1 + CPB * NC * N3;
-  T* B3 = B2 + CPB * NC * N3;
-  T* F = B3 + CPB * NC * N3;  // 16 face slots of CPB*NC*N2
-  const int FS = CPB * NC * N2;
-  T *sV = F, *sN = F + FS, *pV = F + 2 * FS, *pN = F + 3 * FS;
-  T *T1 = F + 4 * FS, *T2 = F + 5 * FS, *T3 = F + 6 * FS, *T4 = F + 7 * FS;
-  T *gV = F + 8 * FS, *gN = F + 9 * FS, *gT1 = F + 10 * FS, *gT2 = F + 11 * FS;
-  T *gVp = F + 12 * FS, *gNp = F + 13 * FS, *gT1p = F + 14 * FS, *gT2p = F + 15 * FS;
+  T* pen = gw + 2 * N;             // 2 * CPB
+  T* Xs = pen + 2 * CPB;           // CPB * NC * N3
+  T* Y = Xs + CPB * NC * N3;       // CPB * NC * N3
+  T* Wk = Y + CPB * NC * N3;       // CPB * op_work_elems
+  T* W0 = Wk;
+  T* W1 = Wk + CPB * NC * N3;
+  T* W2 = Wk + 2 * CPB * NC * N3;
+  const T* S = ct.S;
+  const T* Dg = ct.Dg;
 
-  load_tables<N>(tab, S, Dg, dS0, dS1, gw);
+  load_tables<N>(ct, dS0, dS1, gw);
+  const T mass = from_double<T>(mass_d);
   const int cell0 = blockIdx.x * CPB;
   const int ncell = min(CPB, g.ncells - cell0);
   const int nt = ncell * NC;
@@ -156,16 +484,29 @@ apply_kernel(LevelGeom g, Tab tab, const TS* __restrict__ x, TS* __restrict__ y,
   for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) Xs[i] = load_as<T>(x[base0 + i]);
   __syncthreads();
 
-  // ---- cell term: values at Gauss points, then the collocation gradient
-  sweep3<N, 0, false, false>(Xs, B1, S, nt);
+  // ---- cell term: nodes -> Gauss points along x, y; the z pass also forms
+  // the collocation z-derivative
+  sweep3<N, 0, false, false>(Xs, W1, S, nt);
   __syncthreads();
-  sweep3<N, 1, false, false>(B1, B2, S, nt);
+  sweep3<N, 1, false, false>(W1, W2, S, nt);
   __syncthreads();
-  sweep3<N, 2, false, false>(B2, U, S, nt);
+  for (int line = threadIdx.x; line < nt * N2; line += blockDim.x) {
+    const int t = line / N2, r = line - t * N2;
+    const int off = t * N3 + r;
+    T v[N], u[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = W2[off + j * N2];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      u[o] = line_dot<N, false>(S, v, o);
+      W0[off + o * N2] = u[o];
+    }
+#pragma unroll
+    for (int o = 0; o < N; ++o) Y[off + o * N2] = line_dot<N, false>(Dg, u, o);  // d/dz (Y free until the end)
+  }
   __syncthreads();
-  sweep3<N, 0, false, false>(U, B1, Dg, nt);
-  sweep3<N, 1, false, false>(U, B2, Dg, nt);
-  sweep3<N, 2, false, false>(U, B3, Dg, nt);
+  sweep3<N, 0, false, false>(W0, W1, Dg, nt);
+  sweep3<N, 1, false, false>(W0, W2, Dg, nt);
   __syncthreads();
   const T ih[3] = {from_double<T>(g.ih[0]), from_double<T>(g.ih[1]), from_double<T>(g.ih[2])};
   const T detJ = from_double<T>(g.h[0] * g.h[1] * g.h[2]);
@@ -173,7 +514,7 @@ apply_kernel(LevelGeom g, Tab tab, const TS* __restrict__ x, TS* __restrict__ y,
     const int c = i / N3, q = i - c * N3;
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
     const T W = gw[qx] * gw[qy] * gw[qz] * detJ;
-    T* Bl[3] = {B1, B2, B3};
+    T* Bl[3] = {W1, W2, Y};
     if constexpr (NC == 3) {
       T G[3][3];
 #pragma unroll
@@ -186,193 +527,42 @@ apply_kernel(LevelGeom g, Tab tab, const TS* __restrict__ x, TS* __restrict__ y,
 #pragma unroll
         for (int l = 0; l < 3; ++l)
           Bl[l][(c * 3 + k) * N3 + q] = nu2W * T(0.5f) * (G[k][l] + G[l][k]) * ih[l];
-        U[(c * 3 + k) * N3 + q] *= mass * W;
+        W0[(c * 3 + k) * N3 + q] *= mass * W;
       }
     } else {
 #pragma unroll
       for (int l = 0; l < 3; ++l) Bl[l][c * N3 + q] = Bl[l][c * N3 + q] * ih[l] * W * ih[l];
-      U[c * N3 + q] *= mass * W;
+      W0[c * N3 + q] *= mass * W;
     }
   }
   __syncthreads();
-  sweep3<N, 0, true, true>(B1, U, Dg, nt);
-  sweep3<N, 1, true, true>(B2, U, Dg, nt);
-  sweep3<N, 2, true, true>(B3, U, Dg, nt);
+  // transposed: W0 += Dx^T W1 + Dy^T W2 + Dz^T Y, then S^T in z (fused), y, x
+  sweep3<N, 0, true, true>(W1, W0, Dg, nt);
   __syncthreads();
-  sweep3<N, 2, true, false>(U, B1, S, nt);
+  sweep3<N, 1, true, true>(W2, W0, Dg, nt);
   __syncthreads();
-  sweep3<N, 1, true, false>(B1, B2, S, nt);
+  for (int line = threadIdx.x; line < nt * N2; line += blockDim.x) {
+    const int t = line / N2, r = line - t * N2;
+    const int off = t * N3 + r;
+    T v[N], z[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) z[j] = Y[off + j * N2];
+#pragma unroll
+    for (int o = 0; o < N; ++o) v[o] = W0[off + o * N2] + line_dot<N, true>(Dg, z, o);
+#pragma unroll
+    for (int o = 0; o < N; ++o) W1[off + o * N2] = line_dot<N, true>(S, v, o);
+  }
   __syncthreads();
-  sweep3<N, 0, true, false>(B2, B3, S, nt);  // B3 = cell contribution to y
+  sweep3<N, 1, true, false>(W1, W2, S, nt);
+  __syncthreads();
+  sweep3<N, 0, true, false>(W2, Y, S, nt);  // Y = cell contribution to y
   __syncthreads();
 
-  // ---- face terms, one face direction/side at a time
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, s = f & 1;
-    const int fo = f ^ 1;
-    const int layer = s ? N - 1 : 0, layer_nb = s ? 0 : N - 1;
-    const T* dS = s ? dS1 : dS0;
-    const T* dSn = s ? dS0 : dS1;
-    const int std_ = dir_stride<N>(d);
-    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    // traces and normal derivatives at the face Gauss-Lobatto nodes
-    for (int i = threadIdx.x; i < nt * N2; i += blockDim.x) {
-      const int t = i / N2, p = i - t * N2;
-      const int a = p % N, b = p / N;
-      const int c = t / NC, comp = t - c * NC;
-      const int e = cell0 + c;
-      const int off0 = face_node<N>(d, 0, a, b);
-      const T* xs = Xs + t * N3 + off0;
-      Acc<T> dn;
-#pragma unroll
-      for (int j = 0; j < N; ++j) dn.add(dS[j], xs[j * std_]);
-      sV[i] = xs[layer * std_];
-      sN[i] = dn.get();
-      const int nb = cell_neighbor(g, e, f);
-      if (nb >= 0) {
-        const TS* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
-        Acc<T> dnn;
-#pragma unroll
-        for (int j = 0; j < N; ++j) dnn.add(dSn[j], load_as<T>(xn[j * std_]));
-        pV[i] = load_as<T>(xn[layer_nb * std_]);
-        pN[i] = dnn.get();
-      } else {
-        pV[i] = T(0);
-        pN[i] = T(0);
-      }
-    }
-    __syncthreads();
-    sweep2<N, 0, false, false>(sV, T1, S, nt);
-    sweep2<N, 0, false, false>(sN, T2, S, nt);
-    sweep2<N, 0, false, false>(pV, T3, S, nt);
-    sweep2<N, 0, false, false>(pN, T4, S, nt);
-    __syncthreads();
-    sweep2<N, 1, false, false>(T1, gV, S, nt);
-    sweep2<N, 1, false, false>(T2, gN, S, nt);
-    sweep2<N, 1, false, false>(T3, gVp, S, nt);
-    sweep2<N, 1, false, false>(T4, gNp, S, nt);
-    __syncthreads();
-    sweep2<N, 0, false, false>(gV, gT1, Dg, nt);
-    sweep2<N, 1, false, false>(gV, gT2, Dg, nt);
-    sweep2<N, 0, false, false>(gVp, gT1p, Dg, nt);
-    sweep2<N, 1, false, false>(gVp, gT2p, Dg, nt);
-    __syncthreads();
-    // numerical flux at the face quadrature points
-    const T nsign = s ? T(1) : T(-1);
-    const T ihd = ih[d], iht1 = ih[t1], iht2 = ih[t2];
-    const T area = from_double<T>(g.h[t1] * g.h[t2]);
-    for (int i = threadIdx.x; i < ncell * N2; i += blockDim.x) {
-      const int c = i / N2, p = i - c * N2;
-      const int a = p % N, b = p / N;
-      const int e = cell0 + c;
-      const int nb = cell_neighbor(g, e, f);
-      const bool neumann = nb < 0 && g.bc[f] == 1;
-      if (neumann) {
-        for (int k = 0; k < NC; ++k) {
-          const int j = (c * NC + k) * N2 + p;
-          gV[j] = T(0); gN[j] = T(0); gT1[j] = T(0); gT2[j] = T(0);
-        }
-        continue;
-      }
-      const T W = gw[a] * gw[b] * area;
-      const double lam_md = penalty_lambda(g, e);
-      const double lam_pd = nb >= 0 ? penalty_lambda(g, nb) : lam_md;
-      // C_IP (k+1)^2 max(Lambda-, Lambda+): geometry only, formed in FP64 once
-      const T pen = from_double<T>(g.cip * double(N * N) * (lam_md > lam_pd ? lam_md : lam_pd));
-      if constexpr (NC == 3) {
-        const T num = load_as<T>(nu_face[((size_t)e * 6 + f) * N2 + p]);
-        const T nup = nb >= 0 ? load_as<T>(nu_face[((size_t)nb * 6 + fo) * N2 + p]) : num;
-        const T tau = pen * nubar_of<T>(g.face_nu, num, nup);
-        T um[3], up[3], Gm[3][3], Gp[3][3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int j = (c * 3 + k) * N2 + p;
-          um[k] = gV[j];
-          Gm[k][d] = gN[j] * ihd;
-          Gm[k][t1] = gT1[j] * iht1;
-          Gm[k][t2] = gT2[j] * iht2;
-          if (nb >= 0) {
-            up[k] = gVp[j];
-            Gp[k][d] = gNp[j] * ihd;
-            Gp[k][t1] = gT1p[j] * iht1;
-            Gp[k][t2] = gT2p[j] * iht2;
-          }
-        }
-        if (nb < 0) {  // Dirichlet mirror
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            up[k] = -um[k];
-#pragma unroll
-            for (int l = 0; l < 3; ++l) Gp[k][l] = Gm[k][l];
-          }
-        }
-        T jmp[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) jmp[k] = um[k] - up[k];
-        const T jn = jmp[d] * nsign;
-        // (A + A^T) n with A = (nu^- G^- + nu^+ G^+)/2 and n = nsign e_d
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const T Akd = T(0.5f) * (num * Gm[k][d] + nup * Gp[k][d]);
-          const T Adk = T(0.5f) * (num * Gm[d][k] + nup * Gp[d][k]);
-          const T nk = k == d ? nsign : T(0);
-          const T P = -((Akd + Adk) * nsign - tau * (jmp[k] + nk * jn));
-          // test-gradient coefficient Q = -nu^- sym(jump (x) n)
-          // Q[k][l] = -nu^- (jmp_k n_l + n_k jmp_l) / 2
-          const T Qkd = -num * T(0.5f) * (jmp[k] * nsign + nk * jmp[d]);
-          const T Qkt1 = -num * T(0.5f) * (k == d ? nsign * jmp[t1] : T(0));
-          const T Qkt2 = -num * T(0.5f) * (k == d ? nsign * jmp[t2] : T(0));
-          const int j = (c * 3 + k) * N2 + p;
-          gV[j] = W * P;
-          gN[j] = W * Qkd * ihd;
-          gT1[j] = W * Qkt1 * iht1;
-          gT2[j] = W * Qkt2 * iht2;
-        }
-      } else {
-        const T tau = pen;
-        const int j = c * N2 + p;
-        const T pm = gV[j];
-        const T dnm = gN[j] * ihd;
-        T pp, dnp;
-        if (nb >= 0) {
-          pp = gVp[j];
-          dnp = gNp[j] * ihd;
-        } else {
-          pp = -pm;
-          dnp = dnm;
-        }
-        const T jmp = pm - pp;
-        // -grad q . n jump/2 - q ({{dp/dx_d}} n_d - tau jump)
-        gV[j] = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
-        gN[j] = -W * T(0.5f) * jmp * nsign * ihd;
-        gT1[j] = T(0);
-        gT2[j] = T(0);
-      }
-    }
-    __syncthreads();
-    sweep2<N, 0, true, true>(gT1, gV, Dg, nt);
-    sweep2<N, 1, true, true>(gT2, gV, Dg, nt);
-    __syncthreads();
-    sweep2<N, 1, true, false>(gV, T1, S, nt);
-    sweep2<N, 1, true, false>(gN, T2, S, nt);
-    __syncthreads();
-    sweep2<N, 0, true, false>(T1, sV, S, nt);
-    sweep2<N, 0, true, false>(T2, sN, S, nt);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) {
-      const int t = i / N3, r = i - t * N3;
-      const int ix = r % N, iy = (r / N) % N, iz = r / N2;
-      const int id = d == 0 ? ix : (d == 1 ? iy : iz);
-      const int a = d == 0 ? iy : ix;
-      const int b = d == 2 ? iy : iz;
-      const int fp = t * N2 + a + N * b;
-      T v = dS[id] * sN[fp];
-      if (id == layer) v += sV[fp];
-      B3[i] += v;
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(B3[i]);
+  // ---- face terms, both faces of one direction at a time (work region reused)
+  face_pair<N, NC, 0, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
+  face_pair<N, NC, 1, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
+  face_pair<N, NC, 2, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
+  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(Y[i]);
 }
 
 }  // namespace sipg

@@ -11,8 +11,7 @@
 //           velocity taken on each side from that side's own cell.
 // Output: nu_cell [C][n^3] (q = (qz n + qy) n + qx) and nu_face [C][6][n^2]
 // (own side, point a + n b over the face's tangential directions t1 < t2).
-#include "kernels.cuh"
-#include "operator.cuh"
+#include "apply_dispatch.cuh"
 
 namespace sipg {
 
@@ -84,14 +83,16 @@ __global__ void viscosity_position_kernel(LevelGeom g, Tab tab, RheologyDev rh, 
 
 // Carreau-Yasuda: gradients by sum factorisation (same sweeps as the operator).
 template <int N>
-__global__ void viscosity_carreau_kernel(LevelGeom g, Tab tab, RheologyDev rh, const double* __restrict__ u,
+__global__ void viscosity_carreau_kernel(LevelGeom g, CTab<double> ct, RheologyDev rh, const double* __restrict__ u,
                                          double* nu_cell, double* nu_face) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  __shared__ double S[N2], Dg[N2], dS0[N], dS1[N], gw[N];
+  __shared__ double dS0[N], dS1[N], gw[N];
+  const double* S = ct.S;
+  const double* Dg = ct.Dg;
   __shared__ double Xs[3 * N3], U[3 * N3], B1[3 * N3], B2[3 * N3], B3[3 * N3];
   __shared__ double fV[3 * N2], fN[3 * N2], T1[3 * N2], T2[3 * N2], gV[3 * N2], gN[3 * N2],
       gT1[3 * N2], gT2[3 * N2];
-  load_tables<N>(tab, S, Dg, dS0, dS1, gw);
+  load_tables<N>(ct, dS0, dS1, gw);
   const int e = blockIdx.x;
   for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) Xs[i] = u[(size_t)e * 3 * N3 + i];
   __syncthreads();
@@ -155,7 +156,7 @@ cudaError_t launch_viscosity_n(const LevelGeom& g, const Tab& tab, const Rheolog
                                double* nu_cell, double* nu_face, cudaStream_t st) {
   if (g.ncells == 0) return cudaSuccess;
   if (rh.law == 3)
-    viscosity_carreau_kernel<N><<<g.ncells, 64, 0, st>>>(g, tab, rh, u, nu_cell, nu_face);
+    viscosity_carreau_kernel<N><<<g.ncells, 64, 0, st>>>(g, make_ctab<double>(tab), rh, u, nu_cell, nu_face);
   else
     viscosity_position_kernel<N><<<g.ncells, 64, 0, st>>>(g, tab, rh, nu_cell, nu_face);
   return cudaGetLastError();
