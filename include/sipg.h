@@ -174,6 +174,18 @@ int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double m
  * copies y back (sync). */
 int sipg_apply_host(sipg_ctx* ctx, int op, const double* x_host, double* y_host, double mass_coeff);
 
+/* Same as sipg_apply_host without any device allocation, for callers that
+ * cannot let a library call allocate device memory (a caller whose memory
+ * pool or caching allocator owns the device budget, or a host-memory-only
+ * plain-C caller). No counterpart in the paper: it is an interface service.
+ * x and y are staged in one fixed device array of 524,288 doubles per vector
+ * (8 MiB, reserved on every GPU that loads the library until exit); a larger
+ * fine level is rejected with SIPG_ERR_INVALID. All calls on a device share
+ * that array, so calls that overlap on the GPU race: serialise them. The
+ * first call on a device looks up the array's device address; make it before
+ * any stream capture. (sync) */
+int sipg_apply_host_static(sipg_ctx* ctx, int op, const double* x_host, double* y_host, double mass_coeff);
+
 /* Level-operator apply on multigrid level `level` (level 0 = fine). */
 int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, const void* x, void* y,
                      double mass_coeff);

@@ -26,7 +26,7 @@ EXPORTS = [
     "sipg_default_opts", "sipg_create", "sipg_destroy", "sipg_last_error", "sipg_num_levels",
     "sipg_level_info", "sipg_set_viscosity", "sipg_apply", "sipg_apply_host", "sipg_level_apply",
     "sipg_solve", "sipg_get_viscosity", "sipg_get_inverse_diagonal", "sipg_get_lmax_estimate",
-    "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points",
+    "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points", "sipg_apply_host_static",
 ]
 
 
@@ -85,6 +85,7 @@ def load(path=None):
         "sipg_set_viscosity": (i, [vp, P(Rheology), vp]),
         "sipg_apply": (i, [vp, i, i, vp, vp, d]),
         "sipg_apply_host": (i, [vp, i, vp, vp, d]),
+        "sipg_apply_host_static": (i, [vp, i, vp, vp, d]),
         "sipg_level_apply": (i, [vp, i, i, i, vp, vp, d]),
         "sipg_solve": (i, [vp, i, vp, vp, P(SolveOpts), P(SolveStats)]),
         "sipg_get_viscosity": (i, [vp, i, vp, vp]),

@@ -159,6 +159,17 @@ class Context:
                                               y.ctypes.data_as(ctypes.c_void_p), float(mass)))
         return y
 
+    def apply_host_static(self, op, x, mass=0.0):
+        """apply_host without device allocation: fixed 524,288-value staging
+        area shared by all calls on the device (see include/sipg.h)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if x.size != self.n_dofs(op):
+            raise ValueError("vector size does not match the fine level")
+        y = np.empty_like(x)
+        self._check(self._lib.sipg_apply_host_static(self._h, L.OP[op], x.ctypes.data_as(ctypes.c_void_p),
+                                                     y.ctypes.data_as(ctypes.c_void_p), float(mass)))
+        return y
+
     # ---------------------------------------------------------------- solve
     def solve(self, op, b, x=None, rtol=1e-8, atol=0.0, maxit=500, precond="mg", mass=0.0, check=True):
         _need_cuda(b, torch.float64)
