@@ -178,7 +178,11 @@ __device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, in
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const int j = (c * NC + k) * N2 + p;
-        gV[j] = T(0); gN[j] = T(0); gT1[j] = T(0); gT2[j] = T(0);
+        gV[j] = T(0); gN[j] = T(0);
+      }
+      if (NC == 3) {
+        const int jd = (c * 3 + D) * N2 + p;
+        gT1[jd] = T(0); gT2[jd] = T(0);
       }
       continue;
     }
@@ -188,50 +192,49 @@ __device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, in
     if constexpr (NC == 3) {
       const T num = load_as<T>(nu_face[((size_t)e * 6 + f) * N2 + p]);
       const T nup = nb >= 0 ? load_as<T>(nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p]) : num;
-      const T tau = pe * nubar_of<T>(g.face_nu, num, nup);
-      // gradients in physical coordinates: G[k][l] = d u_k / d x_l
-      T um[3], up[3], Gm[3][3], Gp[3][3];
+      const T tW = pe * nubar_of<T>(g.face_nu, num, nup) * W;  // tau W
+      // Only grad u_D . e_l (l tangential) and d u_k / d x_D enter the flux:
+      // P_k = tau ([u]_k + d_kD [u]_D) - sigma (A_kD + A_Dk), A = (nu- G- + nu+ G+)/2;
+      // Q = -nu- sym([u] (x) n): Q_kD = -nu- sigma [u]_k (1 + d_kD)/2, Q_Dl = -nu- sigma [u]_l / 2.
+      const T am = T(0.5f) * nsign * num * W;   // sigma nu-/2 W
+      const T ap = T(0.5f) * nsign * nup * W;   // sigma nu+/2 W
+      const T cq = -am;                          // -sigma nu-/2 W
+      T um[3], nm[3], up[3], npd[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int j = (c * 3 + k) * N2 + p;
         um[k] = gV[j];
-        Gm[k][D] = gN[j] * ihd;
-        Gm[k][T1] = gT1[j] * iht1;
-        Gm[k][T2] = gT2[j] * iht2;
+        nm[k] = gN[j];
         if (nb >= 0) {
           up[k] = gVp[j];
-          Gp[k][D] = gNp[j] * ihd;
-          Gp[k][T1] = gT1p[j] * iht1;
-          Gp[k][T2] = gT2p[j] * iht2;
+          npd[k] = gNp[j];
         } else {  // Dirichlet mirror: u+ = -u-, grad u+ = grad u-
           up[k] = -um[k];
-          Gp[k][D] = Gm[k][D];
-          Gp[k][T1] = Gm[k][T1];
-          Gp[k][T2] = Gm[k][T2];
+          npd[k] = nm[k];
         }
       }
+      const int jd = (c * 3 + D) * N2 + p;
+      const T t1m = gT1[jd], t2m = gT2[jd];
+      const T t1p = nb >= 0 ? gT1p[jd] : t1m;
+      const T t2p = nb >= 0 ? gT2p[jd] : t2m;
       T jmp[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) jmp[k] = um[k] - up[k];
-      const T jn = jmp[D] * nsign;
-      const T hq = -num * T(0.5f);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        // value coefficient P = -[(A + A^T) n - tau ([u] + n ([u].n))],
-        // A = (nu- grad u- + nu+ grad u+)/2, n = nsign e_D
-        const T Akd = T(0.5f) * (num * Gm[k][D] + nup * Gp[k][D]);
-        const T Adk = T(0.5f) * (num * Gm[D][k] + nup * Gp[D][k]);
-        const T pen_k = k == D ? jmp[k] + nsign * jn : jmp[k];
-        const T P = tau * pen_k - (Akd + Adk) * nsign;
-        // test-gradient coefficient Q = -nu- sym([u] (x) n):
-        // Q[k][l] = -nu- (jmp_k n_l + n_k jmp_l) / 2
-        const T Qkd = k == D ? hq * (T(2) * jmp[D] * nsign) : hq * (jmp[k] * nsign);
         const int j = (c * 3 + k) * N2 + p;
-        gV[j] = W * P;
-        gN[j] = W * Qkd * ihd;
-        gT1[j] = k == D ? W * (hq * (nsign * jmp[T1])) * iht1 : T(0);
-        gT2[j] = k == D ? W * (hq * (nsign * jmp[T2])) * iht2 : T(0);
+        if (k == D) {
+          gV[j] = T(2) * (tW * jmp[k] - (am * nm[k] + ap * npd[k]) * ihd);
+          gN[j] = T(2) * cq * jmp[k] * ihd;
+        } else {
+          const T tm = k == T1 ? t1m * iht1 : t2m * iht2;
+          const T tp = k == T1 ? t1p * iht1 : t2p * iht2;
+          gV[j] = tW * jmp[k] - (am * (nm[k] * ihd + tm) + ap * (npd[k] * ihd + tp));
+          gN[j] = cq * jmp[k] * ihd;
+        }
       }
+      gT1[jd] = cq * jmp[T1] * iht1;
+      gT2[jd] = cq * jmp[T2] * iht2;
     } else {
       const T tau = pe;
       const int j = c * N2 + p;
@@ -249,8 +252,6 @@ __device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, in
       // -grad q . n jump/2 - q ({{dp/dx_d}} n_d - tau jump)
       gV[j] = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
       gN[j] = -W * T(0.5f) * jmp * nsign * ihd;
-      gT1[j] = T(0);
-      gT2[j] = T(0);
     }
   }
 }
@@ -334,7 +335,8 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
     for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(S, v, o);
   }
   __syncthreads();
-  // (C) along b: values at the face Gauss points and their b-derivatives
+  // (C) along b: values at the face Gauss points; the b-derivative of the
+  // traces is needed only for the normal component D of the velocity
   for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
     const int s = line / (nt * N);
     const int lt = line - s * nt * N;
@@ -358,28 +360,34 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
       Fs[2 * FS + o * N] = gvp[o];
       Fs[3 * FS + o * N] = line_dot<N, false>(S, v7, o);
     }
+    if (NC == 3 && t % 3 == D) {
 #pragma unroll
-    for (int o = 0; o < N; ++o) {
-      Fs[4 * FS + o * N] = line_dot<N, false>(Dg, gv, o);
-      Fs[6 * FS + o * N] = line_dot<N, false>(Dg, gvp, o);
+      for (int o = 0; o < N; ++o) {
+        Fs[4 * FS + o * N] = line_dot<N, false>(Dg, gv, o);
+        Fs[6 * FS + o * N] = line_dot<N, false>(Dg, gvp, o);
+      }
     }
   }
   __syncthreads();
-  // (D) along a: tangential a-derivatives of the own and neighbour traces
-  for (int line = threadIdx.x; line < 2 * 2 * nt * N; line += blockDim.x) {
-    const int s = line / (2 * nt * N);
-    const int rem = line - s * 2 * nt * N;
-    const int q = rem / (nt * N), lt = rem - q * nt * N;  // q = 0 own, 1 neighbour
-    const int t = lt / N, r = lt - t * N;
-    const T* in = F + (s * 8 + 2 * q) * FS + t * N2 + r * N;
-    T* out = F + (s * 8 + 5 + 2 * q) * FS + t * N2 + r * N;
-    T v[N];
+  // (D) along a: tangential a-derivatives of the own and neighbour traces of
+  // velocity component D (no tangential derivative enters the Poisson flux)
+  if (NC == 3) {
+    for (int line = threadIdx.x; line < 2 * 2 * ncell * N; line += blockDim.x) {
+      const int s = line / (2 * ncell * N);
+      const int rem = line - s * 2 * ncell * N;
+      const int q = rem / (ncell * N), lc = rem - q * ncell * N;  // q = 0 own, 1 neighbour
+      const int c = lc / N, r = lc - c * N;
+      const int t = c * 3 + D;
+      const T* in = F + (s * 8 + 2 * q) * FS + t * N2 + r * N;
+      T* out = F + (s * 8 + 5 + 2 * q) * FS + t * N2 + r * N;
+      T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = in[j];
+      for (int j = 0; j < N; ++j) v[j] = in[j];
 #pragma unroll
-    for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(Dg, v, o);
+      for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(Dg, v, o);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // (E) numerical flux
   face_flux_pair<N, NC, D, TN, T>(g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
   __syncthreads();
@@ -389,11 +397,16 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
     const int lt = line - s * nt * N;
     const int t = lt / N, r = lt - t * N;
     T* Fs = F + s * 8 * FS + t * N2 + r * N;
-    T g5[N];
+    if (NC == 3 && t % 3 == D) {
+      T g5[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) g5[j] = Fs[5 * FS + j];
+      for (int j = 0; j < N; ++j) g5[j] = Fs[5 * FS + j];
 #pragma unroll
-    for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o] + line_dot<N, true>(Dg, g5, o);
+      for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o] + line_dot<N, true>(Dg, g5, o);
+    } else {
+#pragma unroll
+      for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o];
+    }
   }
   __syncthreads();
   // (G) along b: slot 6 = S_b^T (slot 2 + Dg_b^T gT2), slot 7 = S_b^T gN
@@ -404,12 +417,16 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
     T* Fs = F + s * 8 * FS + t * N2 + r;
     T w[N], g4[N], g1[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      g4[j] = Fs[4 * FS + j * N];
-      g1[j] = Fs[1 * FS + j * N];
-    }
+    for (int j = 0; j < N; ++j) g1[j] = Fs[1 * FS + j * N];
+    if (NC == 3 && t % 3 == D) {
 #pragma unroll
-    for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N] + line_dot<N, true>(Dg, g4, o);
+      for (int j = 0; j < N; ++j) g4[j] = Fs[4 * FS + j * N];
+#pragma unroll
+      for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N] + line_dot<N, true>(Dg, g4, o);
+    } else {
+#pragma unroll
+      for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N];
+    }
 #pragma unroll
     for (int o = 0; o < N; ++o) {
       Fs[6 * FS + o * N] = line_dot<N, true>(S, w, o);
