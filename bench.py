@@ -293,6 +293,72 @@ def gpu_extras(ctx, xs, ys, stream):
         row["mixed_speedup"] = row["f64"]["seconds"] / row["f32"]["seconds"]
         solves.append(row)
     out["cfg3_mg_solves_16cubed_k4"] = solves
+    out["serving"] = serving_extras()
+    return out
+
+
+def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5):
+    """Served stream: Poisson arrivals, uneven sizes/degrees/contrasts, rtol 1e-8.
+
+    A bounded version of the 256-request stream (n^3 cells with n in {8, 12, 16},
+    k in {2, 3, 4}, contrast in {1, 1e2, 1e4}) so that the bench stays short; the
+    one-at-a-time baseline solves the same requests sequentially with the plain
+    FP64 path (FP64 CG and FP64 multigrid, one context per request) and is
+    queued against the same arrival times."""
+    import numpy as np
+
+    from paper_2506_14424_gb300 import Context, Server, inputs
+
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(n_req):
+        specs.append({"n": int(rng.choice([8, 12, 16])), "k": int(rng.choice([2, 3, 4])),
+                      "contrast": float(rng.choice([1.0, 1e2, 1e4])), "seed": 1000 + i})
+    out = {"requests": n_req, "mix": "n^3 cells n in {8,12,16}, k in {2,3,4}, contrast {1,1e2,1e4}, rtol 1e-8"}
+    # one-at-a-time FP64 service times
+    service = []
+    for sp in specs:
+        t0 = time.perf_counter()
+        c = Context(sp["n"], sp["n"], sp["n"], sp["k"], mg_precision="f64", krylov_arith="f64")
+        c.set_viscosity(inputs.sinker(seed=sp["seed"], count=8, radius=0.15, nu_max=sp["contrast"]))
+        import torch
+        u = torch.tensor(inputs.uniform_vector(c.n_dofs(), seed=sp["seed"]), device="cuda")
+        b = c.apply("viscous", u)
+        c.solve("viscous", b, rtol=1e-8, precond="mg", maxit=400, check=False)
+        torch.cuda.synchronize()
+        c.close()
+        service.append(time.perf_counter() - t0)
+    runs = []
+    for rate in rates:
+        arr = np.cumsum(np.random.default_rng(seed + int(rate)).exponential(1.0 / rate, n_req))
+        # FIFO one-at-a-time baseline against the same arrivals
+        fin, lat_seq = 0.0, []
+        for a_t, s_t in zip(arr, service):
+            fin = max(fin, a_t) + s_t
+            lat_seq.append(fin - a_t)
+        srv = Server(96 << 30, max_slots=8)
+        t0 = time.perf_counter()
+        ids = []
+        for sp, a_t in zip(specs, arr):
+            dt = t0 + a_t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(sp["n"], sp["k"], inputs.sinker(seed=sp["seed"], count=8, radius=0.15,
+                                                                  nu_max=sp["contrast"]),
+                                  rtol=1e-8, maxit=400, seed=sp["seed"]))
+        srv.drain(600)
+        t_end = time.perf_counter()
+        res = [srv.poll(i)[0] for i in ids]
+        srv.close()
+        lat = np.array([r["latency_s"] for r in res])
+        ok = sum(1 for r in res if r["status"] == 0 and r["rel_residual"] <= 1e-8)
+        runs.append({"rate_per_s": rate, "solves_per_s": n_req / (t_end - t0), "p50_s": float(np.percentile(lat, 50)),
+                     "p99_s": float(np.percentile(lat, 99)), "converged": ok,
+                     "max_rel_residual": max(r["rel_residual"] for r in res),
+                     "one_at_a_time_fp64": {"solves_per_s": n_req / max(fin, arr[-1]),
+                                            "p50_s": float(np.percentile(lat_seq, 50)),
+                                            "p99_s": float(np.percentile(lat_seq, 99))}})
+    out["runs"] = runs
     return out
 
 

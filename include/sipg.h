@@ -223,6 +223,57 @@ int sipg_vcycle(sipg_ctx* ctx, int op, const double* b, double* x);
  * buffer [cells][n^3][3] (for building interpolated input fields). */
 int sipg_node_points(const sipg_ctx* ctx, int op, int level, double* xyz_host);
 
+/* Device bytes sipg_create would allocate for this mesh and options
+ * (no allocation; used for admission by HBM budget). */
+int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* opts, int64_t* bytes);
+
+/* ------------------------------------------------------------- serving
+ * Continuous-batching solve server (spec systems pattern; the paper's
+ * solver is Sec. 5.4): requests are admitted when a slot is free and their
+ * context fits the HBM budget, every active request advances one FP64 CG
+ * iteration (float-float operator, FP32 hp-multigrid V-cycle) per round, the
+ * fine-level operator applies of all active requests of a degree run in one
+ * persistent launch, and requests join and leave between rounds. Each request
+ * solves the viscous system on the unit cube (Dirichlet walls, sphere
+ * viscosity) with b = A u*, u* uniform(-1,1) from its seed. One worker
+ * thread drives the GPU; submit/poll/drain are thread-safe. */
+typedef struct sipg_server sipg_server;
+typedef struct {
+  uint64_t hbm_budget_bytes; /* device bytes the server's contexts may hold */
+  int max_slots;             /* requests served concurrently */
+  int mg_precision;          /* SIPG_F32 (default for serving) or SIPG_F64 */
+  int cheb_degree;           /* 0 = 3 */
+} sipg_server_opts;
+typedef struct {
+  int n_cells;               /* n^3 cells on the unit cube */
+  int k_u;                   /* degree 2..5 */
+  int n_spheres;
+  const double* centers;     /* HOST, 3*n_spheres, copied by submit */
+  double radius, nu_max, nu_matrix;
+  double rtol;               /* relative residual target */
+  int maxit;
+  uint64_t seed;             /* of u* */
+  int keep_solution;         /* keep x for sipg_server_poll */
+} sipg_request;
+typedef struct {
+  int status;                /* SIPG_OK, SIPG_ERR_MAXIT, SIPG_ERR_BREAKDOWN, SIPG_ERR_NOMEM, ... */
+  int iterations;
+  double rel_residual;       /* true ||b - A x|| / ||b|| of the returned x */
+  double err_vs_ustar;       /* ||x - u*|| / ||u*|| */
+  int64_t n_dofs;
+  double queue_s, solve_s, latency_s;  /* submit->admit, admit->done, submit->done */
+} sipg_result;
+int sipg_server_create(const sipg_server_opts* opts, sipg_server** out);
+int sipg_server_submit(sipg_server* srv, const sipg_request* req, uint64_t* id);
+/* SIPG_PENDING while queued or running; SIPG_OK with *res (and x_host filled,
+ * n_dofs doubles, if the request kept its solution and x_host != NULL). */
+int sipg_server_poll(sipg_server* srv, uint64_t id, sipg_result* res, double* x_host);
+/* Wait until every submitted request is done (timeout_s <= 0: no limit);
+ * SIPG_ERR_TIMEOUT when the limit runs out. */
+int sipg_server_drain(sipg_server* srv, double timeout_s);
+const char* sipg_server_last_error(const sipg_server* srv);
+int sipg_server_destroy(sipg_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,8 @@ EXPORTS = [
     "sipg_level_info", "sipg_set_viscosity", "sipg_apply", "sipg_apply_host", "sipg_level_apply",
     "sipg_solve", "sipg_get_viscosity", "sipg_get_inverse_diagonal", "sipg_get_lmax_estimate",
     "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points", "sipg_apply_host_static",
+    "sipg_estimate_bytes", "sipg_server_create", "sipg_server_submit", "sipg_server_poll", "sipg_server_drain",
+    "sipg_server_last_error", "sipg_server_destroy",
 ]
 
 
@@ -59,6 +61,24 @@ class SolveOpts(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int), ("mg_precision", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("k_u", ctypes.c_int), ("n_spheres", ctypes.c_int),
+                ("centers", ctypes.POINTER(ctypes.c_double)), ("radius", ctypes.c_double),
+                ("nu_max", ctypes.c_double), ("nu_matrix", ctypes.c_double), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("seed", ctypes.c_uint64), ("keep_solution", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("err_vs_ustar", ctypes.c_double), ("n_dofs", ctypes.c_int64), ("queue_s", ctypes.c_double),
+                ("solve_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
 
 
 _lib = None
@@ -95,6 +115,13 @@ def load(path=None):
         "sipg_smooth": (i, [vp, i, i, i, vp, vp]),
         "sipg_vcycle": (i, [vp, i, vp, vp]),
         "sipg_node_points": (i, [vp, i, i, vp]),
+        "sipg_estimate_bytes": (i, [P(MeshDesc), P(Opts), P(i64)]),
+        "sipg_server_create": (i, [P(ServerOpts), P(vp)]),
+        "sipg_server_submit": (i, [vp, P(Request), P(ctypes.c_uint64)]),
+        "sipg_server_poll": (i, [vp, ctypes.c_uint64, P(Result), vp]),
+        "sipg_server_drain": (i, [vp, d]),
+        "sipg_server_last_error": (ctypes.c_char_p, [vp]),
+        "sipg_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -223,3 +223,78 @@ class Context:
         out = np.empty((nx * ny * nz, n ** 3, 3))
         self._check(self._lib.sipg_node_points(self._h, L.OP[op], level, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+class Server:
+    """Continuous-batching solve server (see include/sipg.h, sipg_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=8, mg_precision="f32", cheb_degree=3):
+        self._lib = L.load()
+        o = L.ServerOpts(int(hbm_budget_bytes), int(max_slots), L.PREC[mg_precision], int(cheb_degree))
+        h = ctypes.c_void_p()
+        rc = self._lib.sipg_server_create(ctypes.byref(o), ctypes.byref(h))
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, "sipg_server_create failed")
+        self._h = h
+        self._sizes = {}
+
+    def submit(self, n_cells, k_u, sinker, rtol=1e-8, maxit=300, seed=0, keep_solution=False):
+        c = np.ascontiguousarray(np.asarray(sinker["centers"], dtype=np.float64).reshape(-1))
+        r = L.Request(int(n_cells), int(k_u), len(c) // 3, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      float(sinker["radius"]), float(sinker["nu_max"]), float(sinker["nu_matrix"]), float(rtol),
+                      int(maxit), int(seed), int(bool(keep_solution)))
+        rid = ctypes.c_uint64()
+        rc = self._lib.sipg_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid))
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, "sipg_server_submit failed")
+        self._sizes[rid.value] = (int(n_cells) ** 3 * 3 * (int(k_u) + 1) ** 3, bool(keep_solution))
+        return rid.value
+
+    def poll(self, rid):
+        """None while pending, else (result dict, solution or None)."""
+        res = L.Result()
+        n, keep = self._sizes.get(rid, (0, False))
+        x = np.empty(n) if keep else None
+        rc = self._lib.sipg_server_poll(self._h, ctypes.c_uint64(rid), ctypes.byref(res),
+                                        x.ctypes.data_as(ctypes.c_void_p) if keep else None)
+        if rc == L.SIPG_PENDING:
+            return None
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, "sipg_server_poll failed")
+        out = {f: getattr(res, f) for f, _ in L.Result._fields_}
+        return out, x
+
+    def drain(self, timeout=0.0):
+        rc = self._lib.sipg_server_drain(self._h, float(timeout))
+        if rc != L.SIPG_OK:
+            raise SipgError(rc, self._lib.sipg_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sipg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(n_cells, k_u):
+    """Device bytes of a context for an n^3 unit-cube mesh of degree k_u."""
+    lib = L.load()
+    m = L.MeshDesc()
+    m.nx = m.ny = m.nz = int(n_cells)
+    m.lx = m.ly = m.lz = 1.0
+    for i in range(6):
+        m.bc_velocity[i] = 0
+        m.bc_pressure[i] = 1
+    o = L.Opts()
+    lib.sipg_default_opts(ctypes.byref(o))
+    o.k_u = int(k_u)
+    b = ctypes.c_int64()
+    rc = lib.sipg_estimate_bytes(ctypes.byref(m), ctypes.byref(o), ctypes.byref(b))
+    if rc != L.SIPG_OK:
+        raise SipgError(rc, "sipg_estimate_bytes failed")
+    return b.value

@@ -3,6 +3,8 @@
 #include "kernels.cuh"
 #include "operator.cuh"
 
+#include <algorithm>
+
 namespace sipg {
 
 // Host conversion of the FP64 tables to the kernel's arithmetic type (the
@@ -57,6 +59,49 @@ cudaError_t launch_apply_t(int n, int ncomp, const LevelGeom& g, const Tab& tab,
   case NN:                                                                                                  \
     return ncomp == 3 ? launch_apply_n<NN, 3, TS, TN, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st) \
                       : launch_apply_n<NN, 1, TS, TN, TC>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st);
+  switch (n) {
+    SIPG_CASE(2)
+    SIPG_CASE(3)
+    SIPG_CASE(4)
+    SIPG_CASE(5)
+    SIPG_CASE(6)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SIPG_CASE
+}
+
+template <int N, int NC, typename TS, typename TN, typename TC>
+cudaError_t launch_apply_multi_n(const ApplyDesc<TS, TN>* descs, const int2* tiles, int ntiles, const Tab& tab,
+                                 cudaStream_t st) {
+  using Cfg = OpCfg<N, NC>;
+  const size_t smem = sizeof(TC) * op_smem_elems<N, NC>();
+  static int resident = 0;  // CTAs per SM (per instantiation, single device)
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(apply_multi_kernel<N, NC, TS, TN, TC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, apply_multi_kernel<N, NC, TS, TN, TC>, Cfg::NT,
+                                                        smem);
+    if (e != cudaSuccess) return e;
+    if (resident < 1) resident = 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(ntiles, std::max(1, sms) * resident);
+  if (grid <= 0) return cudaSuccess;
+  apply_multi_kernel<N, NC, TS, TN, TC><<<grid, Cfg::NT, smem, st>>>(descs, tiles, ntiles, make_ctab<TC>(tab));
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TN, typename TC>
+cudaError_t launch_apply_multi_t(int n, int ncomp, const ApplyDesc<TS, TN>* descs, const int2* tiles, int ntiles,
+                                 const Tab& tab, cudaStream_t st) {
+#define SIPG_CASE(NN)                                                                                     \
+  case NN:                                                                                                \
+    return ncomp == 3 ? launch_apply_multi_n<NN, 3, TS, TN, TC>(descs, tiles, ntiles, tab, st)            \
+                      : launch_apply_multi_n<NN, 1, TS, TN, TC>(descs, tiles, ntiles, tab, st);
   switch (n) {
     SIPG_CASE(2)
     SIPG_CASE(3)

@@ -10,6 +10,23 @@ cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab
                                         reinterpret_cast<const ff*>(nu_face), mass, nbatch, st);
 }
 
+cudaError_t launch_apply_multi_ff(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
+                                  const Tab& tab, cudaStream_t st) {
+  return launch_apply_multi_t<double, ff, ff>(n, ncomp, static_cast<const ApplyDesc<double, ff>*>(descs), tiles,
+                                              ntiles, tab, st);
+}
+
+int op_cells_per_cta(int n, int ncomp) {
+  switch (n) {
+    case 2: return ncomp == 3 ? OpCfg<2, 3>::CPB : OpCfg<2, 1>::CPB;
+    case 3: return ncomp == 3 ? OpCfg<3, 3>::CPB : OpCfg<3, 1>::CPB;
+    case 4: return ncomp == 3 ? OpCfg<4, 3>::CPB : OpCfg<4, 1>::CPB;
+    case 5: return ncomp == 3 ? OpCfg<5, 3>::CPB : OpCfg<5, 1>::CPB;
+    case 6: return ncomp == 3 ? OpCfg<6, 3>::CPB : OpCfg<6, 1>::CPB;
+    default: return 1;
+  }
+}
+
 // nu split into (hi, lo) pairs for the float-float kernels
 __global__ void split_ff_kernel(int64_t n, const double* __restrict__ in, float2* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {

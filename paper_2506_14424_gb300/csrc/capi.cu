@@ -53,6 +53,17 @@ bool valid_bc(const int* bc) {
 }  // namespace
 
 // ------------------------------------------------------------ construction
+template <typename T>
+T* sipg_ctx::alloc(int64_t n, cudaError_t* e) {
+  const size_t bytes_n = sizeof(T) * (size_t)std::max<int64_t>(n, 1);
+  bytes += (int64_t)bytes_n;
+  if (dry) {
+    *e = cudaSuccess;
+    return nullptr;
+  }
+  return dalloc<T>(n, e);
+}
+
 int sipg_ctx::build_hierarchy(int op) {
   Hier& H = hier[op];
   H.op = op;
@@ -111,26 +122,29 @@ int sipg_ctx::build_hierarchy(int op) {
     Level& L = H.L[l];
     const int64_t C = L.g.ncells, n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
     if (op == SIPG_OP_VISCOUS) {
-      L.nu_cell64 = dalloc<double>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
-      L.nu_face64 = dalloc<double>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
-      L.nu_cell32 = dalloc<float>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
-      L.nu_face32 = dalloc<float>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_cell64 = alloc<double>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_face64 = alloc<double>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_cell32 = alloc<float>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+      L.nu_face32 = alloc<float>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
       if (l == 0) {
-        L.nu_cellff = dalloc<float2>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
-        L.nu_faceff = dalloc<float2>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+        L.nu_cellff = alloc<float2>(C * n3, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
+        L.nu_faceff = alloc<float2>(C * 6 * n2, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc nu", e);
       }
-      if (l > 0) { L.ulin = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc ulin", e); }
+      if (l > 0) { L.ulin = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc ulin", e); }
     }
-    L.diag64 = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
-    L.dinv64 = dalloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
-    L.dinv32 = dalloc<float>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    L.diag64 = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    L.dinv64 = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+    L.dinv32 = alloc<float>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
     for (int p = 0; p < 2; ++p) {
       const size_t es = p == 0 ? sizeof(double) : sizeof(float);
       for (int v = 0; v < 4; ++v) {
         void* ptr = nullptr;
-        e = cudaMalloc(&ptr, es * (size_t)L.ndofs);
-        if (e == cudaSuccess) e = cudaMemset(ptr, 0, es * (size_t)L.ndofs);
-        if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
+        bytes += (int64_t)(es * (size_t)L.ndofs);
+        if (!dry) {
+          e = cudaMalloc(&ptr, es * (size_t)L.ndofs);
+          if (e == cudaSuccess) e = cudaMemset(ptr, 0, es * (size_t)L.ndofs);
+          if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
+        }
         L.w[p][v] = ptr;
       }
     }
@@ -138,17 +152,18 @@ int sipg_ctx::build_hierarchy(int op) {
   Level& Cl = H.L.back();
   Cl.N = (int)Cl.ndofs;
   if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
-  Cl.Ainv = dalloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
-  Cl.Atmp = dalloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  Cl.Ainv = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  Cl.Atmp = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
   // CG vectors on level 0
   for (int v = 0; v < 5; ++v) {
-    H.cg[v] = dalloc<double>(H.L[0].ndofs, &e);
+    H.cg[v] = alloc<double>(H.L[0].ndofs, &e);
     if (e) return fail(SIPG_ERR_NOMEM, "alloc cg", e);
   }
   return SIPG_OK;
 }
 
 sipg_ctx::~sipg_ctx() {
+  if (dry) return;
   for (Hier& H : hier) {
     for (Level& L : H.L) {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
@@ -224,6 +239,36 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
     return rc;
   }
   *out = ctx;
+  return SIPG_OK;
+}
+
+// Device bytes a context of this mesh and options allocates (no allocation).
+extern "C" int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* opts_in, int64_t* bytes) {
+  if (!mesh || !bytes) return SIPG_ERR_INVALID;
+  sipg_opts o;
+  sipg_default_opts(&o);
+  if (opts_in) {
+    o = *opts_in;
+    sipg_opts d;
+    sipg_default_opts(&d);
+    if (o.coarse_max_dofs == 0) o.coarse_max_dofs = d.coarse_max_dofs;
+    if (o.k_u == 0) o.k_u = d.k_u;
+  }
+  if (o.k_u < 2 || o.k_u > 5 || mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return SIPG_ERR_INVALID;
+  sipg_ctx probe;
+  probe.dry = true;
+  probe.mesh = *mesh;
+  probe.opts = o;
+  for (int op = 0; op < 2; ++op) {
+    int rc = probe.build_hierarchy(op);
+    if (rc) return rc;
+  }
+  *bytes = probe.bytes + (int64_t)sizeof(double) * (kDotBlocks + 16) + 64;
+  for (sipg::Hier& H : probe.hier)
+    for (sipg::Level& L : H.L) {
+      for (int p = 0; p < 2; ++p)
+        for (int v = 0; v < 4; ++v) L.w[p][v] = nullptr;
+    }
   return SIPG_OK;
 }
 

@@ -56,9 +56,13 @@ struct sipg_ctx {
   double* host_x = nullptr;
   double* host_y = nullptr;
   int64_t host_n = 0;
+  bool dry = false;     // size accounting only (sipg_estimate_bytes)
+  int64_t bytes = 0;    // device bytes allocated by the hierarchy
 
   ~sipg_ctx();
   int fail(int code, const char* what, cudaError_t e = cudaSuccess);
+  template <typename T>
+  T* alloc(int64_t n, cudaError_t* e);
   int build_hierarchy(int op);
   int setup_level_smoother(int op, int l, double mass);
   int setup_coarse(int op, double mass);

@@ -13,6 +13,11 @@ cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, c
 cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
                             const float2* nu_cell, const float2* nu_face, double mass, int nbatch, cudaStream_t st);
 cudaError_t launch_split_ff(int64_t n, const double* in, float2* out, cudaStream_t st);
+// float-float applies of several problems of one degree in one persistent launch;
+// descs: device array of ApplyDesc<double, ff> (operator.cuh), tiles: (problem, cell0)
+cudaError_t launch_apply_multi_ff(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
+                                  const Tab& tab, cudaStream_t st);
+int op_cells_per_cta(int n, int ncomp);
 
 // ---- viscosity (viscosity.cu)
 struct RheologyDev {

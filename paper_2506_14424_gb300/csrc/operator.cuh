@@ -464,21 +464,17 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
   __syncthreads();
 }
 
-// y = (m M + A) x on the cells [blockIdx.x*CPB, ...) of a level.
+// y = (m M + A) x on the cells [cell0, cell0 + CPB) of a level, executed by
+// one CTA with shared memory sm (op_smem_elems<N, NC>() elements of T).
 // NC = 3: viscous operator (nu_cell [C][N^3], nu_face [C][6][N^2]);
 // NC = 1: Poisson operator (nu pointers unused).
 // TS is the storage type of x and y, TN that of nu, T the arithmetic type
 // (double, float, or ff = float-float with double x/y and pre-split nu).
 template <int N, int NC, typename TS, typename TN, typename T>
-__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
-apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
-             const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
+__device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const TS* __restrict__ x,
+                                            TS* __restrict__ y, const TN* __restrict__ nu_cell,
+                                            const TN* __restrict__ nu_face, double mass_d, int cell0, T* sm) {
   constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
-  // blockIdx.y selects one of several vectors applied in the same launch
-  x += (int64_t)blockIdx.y * batch_stride;
-  y += (int64_t)blockIdx.y * batch_stride;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
   T* dS0 = sm;
   T* dS1 = dS0 + N;
   T* gw = dS1 + N;
@@ -494,7 +490,6 @@ apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__
 
   load_tables<N>(ct, dS0, dS1, gw);
   const T mass = from_double<T>(mass_d);
-  const int cell0 = blockIdx.x * CPB;
   const int ncell = min(CPB, g.ncells - cell0);
   const int nt = ncell * NC;
   const size_t base0 = (size_t)cell0 * NC * N3;
@@ -580,6 +575,47 @@ apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__
   face_pair<N, NC, 1, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
   face_pair<N, NC, 2, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
   for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(Y[i]);
+}
+
+// One CTA per CPB consecutive cells of one level; blockIdx.y selects one of
+// several vectors applied in the same launch (columns of a batch).
+template <int N, int NC, typename TS, typename TN, typename T>
+__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
+apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
+             const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  x += (int64_t)blockIdx.y * batch_stride;
+  y += (int64_t)blockIdx.y * batch_stride;
+  apply_cells<N, NC, TS, TN, T>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
+                                reinterpret_cast<T*>(smem_raw));
+}
+
+// Operator applies of several problems of the same degree in one persistent
+// launch: tile i = (problem, first cell) of tiles[]; CTAs stride over the
+// tile list (static round robin, deterministic: every tile is computed by
+// exactly the same code as in apply_kernel, so results are bitwise equal).
+template <typename TS, typename TN>
+struct ApplyDesc {
+  LevelGeom g;
+  const TS* x;
+  TS* y;
+  const TN* nu_cell;
+  const TN* nu_face;
+  double mass;
+};
+
+template <int N, int NC, typename TS, typename TN, typename T>
+__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
+apply_multi_kernel(const ApplyDesc<TS, TN>* __restrict__ descs, const int2* __restrict__ tiles, int ntiles,
+                   CTab<T> ct) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int2 tl = tiles[tile];
+    const ApplyDesc<TS, TN> d = descs[tl.x];
+    apply_cells<N, NC, TS, TN, T>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y,
+                                  reinterpret_cast<T*>(smem_raw));
+    __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 }  // namespace sipg

@@ -1,0 +1,578 @@
+// Continuous-batching solve server.
+//
+// Requests (a box mesh, a degree, a sphere viscosity field, a tolerance) are
+// queued by sipg_server_submit and served by one worker thread:
+//  * admission: a queued request starts when a slot is free and the device
+//    bytes of its context (sipg_estimate_bytes) fit the HBM budget; contexts
+//    are cached per (mesh, degree) and reused, so finishing a request frees
+//    its slot and memory without a device-wide synchronisation;
+//  * rounds: every active request advances by one preconditioned CG
+//    iteration per round, with all CG scalars kept on the device. The
+//    fine-level operator applies of all active requests of one degree run in
+//    ONE persistent launch (apply_multi_kernel: CTAs stride over a tile list
+//    that spans the requests); dot products, vector updates and the
+//    multigrid V-cycle of each request run on that request's own stream, so
+//    the requests' work overlaps on the device;
+//  * requests that arrive while others are running join at the next round
+//    (continuous batching); a finished request leaves at the end of a round.
+// Each request's arithmetic is the same kernel sequence as a solve on its own
+// (the batched launch computes every cell with the same code as the single
+// launch), so its result does not depend on the mix.
+// The right-hand side is b = A u* for a seeded random u* (uniform in -1..1), so
+// the error against u* is reported with every result.
+#include "../../include/sipg.h"
+#include "ctx.h"
+#include "kernels.cuh"
+#include "operator.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+using namespace sipg;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// device CG scalars of one request: [0] rz, [1] pq, [2] rr, [3] rz_new,
+// [4] bnorm2, [5] breakdown flag
+__global__ void cg_step_x_r(int64_t n, const double* __restrict__ sc, const double* __restrict__ p,
+                            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+  const double pq = sc[1];
+  if (!(pq > 0.0) || !isfinite(pq)) return;  // breakdown: leave x, r (flag set by cg_check)
+  const double alpha = sc[0] / pq;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+__global__ void cg_step_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
+                          double* __restrict__ p) {
+  const double beta = sc[0] != 0.0 ? sc[3] / sc[0] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void cg_check(double* sc) {
+  const double pq = sc[1];
+  if (!(pq > 0.0) || !isfinite(pq)) sc[5] = 1.0;
+}
+
+__global__ void cg_rotate(double* sc) { sc[0] = sc[3]; }
+
+inline int vec_blocks(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 8); }
+
+struct Request {
+  uint64_t id = 0;
+  sipg_request spec{};
+  std::vector<double> centers;
+  bool keep_solution = false;
+  // runtime
+  sipg_ctx* ctx = nullptr;
+  int64_t n = 0, bytes = 0;
+  double *ustar = nullptr, *b = nullptr, *x = nullptr, *sc = nullptr;
+  double* hsc = nullptr;  // pinned: rr, flag
+  cudaEvent_t ev_ready = nullptr, ev_rr = nullptr;
+  int iters = 0;
+  double bnorm = 0.0;
+  Clock::time_point t_submit, t_admit, t_done;
+  sipg_result result{};
+  std::vector<double> solution;
+  bool done = false;
+};
+
+struct ContextEntry {
+  sipg_ctx* ctx;
+  int nc, k;
+  int64_t bytes;
+  bool busy;
+  // request-side buffers owned with the context (b, u*, x, scalars)
+  double *ustar, *b, *x, *sc;
+  double* hsc;
+  cudaEvent_t ev_ready, ev_rr;
+};
+
+}  // namespace
+
+struct sipg_server {
+  sipg_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  std::deque<std::unique_ptr<Request>> queue;
+  std::vector<Request*> active;
+  std::map<uint64_t, std::unique_ptr<Request>> finished;
+  std::vector<ContextEntry> pool;
+  uint64_t next_id = 1;
+  int64_t used_bytes = 0;
+  int pending = 0;  // queued + active
+  bool stop = false;
+  bool failed = false;
+  std::string err;
+  std::thread worker;
+  cudaStream_t sched = nullptr;
+  cudaEvent_t ev_applied = nullptr;
+  int device = 0;
+  // batched-apply tables per degree (device copies rebuilt when the set changes)
+  std::vector<ApplyDesc<double, ff>> h_desc;
+  std::vector<int2> h_tiles;
+  ApplyDesc<double, ff>* d_desc = nullptr;
+  int2* d_tiles = nullptr;
+  size_t d_desc_cap = 0, d_tiles_cap = 0;
+
+  void run();
+  bool admit_one(std::unique_ptr<Request>& rq);
+  int start_request(Request* r);
+  int round();
+  int finish(Request* r);
+  ContextEntry* acquire_context(int nc, int k, int64_t need);
+  void set_error(const std::string& m) {
+    failed = true;
+    err = m;
+  }
+};
+
+namespace {
+
+sipg_mesh_desc box_mesh(int nc) {
+  sipg_mesh_desc m{};
+  m.nx = m.ny = m.nz = nc;
+  m.lx = m.ly = m.lz = 1.0;
+  for (int i = 0; i < 6; ++i) {
+    m.bc_velocity[i] = SIPG_BC_DIRICHLET;
+    m.bc_pressure[i] = SIPG_BC_NEUMANN;
+  }
+  return m;
+}
+
+}  // namespace
+
+ContextEntry* sipg_server::acquire_context(int nc, int k, int64_t need) {
+  for (ContextEntry& c : pool)
+    if (!c.busy && c.nc == nc && c.k == k) {
+      c.busy = true;
+      return &c;
+    }
+  // evict idle contexts of other shapes until the new one fits
+  while (used_bytes + need > (int64_t)opts.hbm_budget_bytes) {
+    auto it = std::find_if(pool.begin(), pool.end(), [](const ContextEntry& c) { return !c.busy; });
+    if (it == pool.end()) return nullptr;
+    cudaFree(it->ustar);
+    cudaFree(it->b);
+    cudaFree(it->x);
+    cudaFree(it->sc);
+    cudaFreeHost(it->hsc);
+    cudaEventDestroy(it->ev_ready);
+    cudaEventDestroy(it->ev_rr);
+    cudaStream_t st = it->ctx->st;
+    sipg_destroy(it->ctx);
+    cudaStreamDestroy(st);
+    used_bytes -= it->bytes;
+    pool.erase(it);
+  }
+  sipg_opts o;
+  sipg_default_opts(&o);
+  o.k_u = k;
+  o.mg_precision = opts.mg_precision;
+  o.cheb_degree = opts.cheb_degree > 0 ? opts.cheb_degree : 3;
+  o.krylov_arith = SIPG_F64_FF;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  sipg_mesh_desc m = box_mesh(nc);
+  sipg_ctx* ctx = nullptr;
+  if (sipg_create(&m, &o, st, &ctx) != SIPG_OK) {
+    cudaStreamDestroy(st);
+    return nullptr;
+  }
+  ContextEntry c{};
+  c.ctx = ctx;
+  c.nc = nc;
+  c.k = k;
+  c.bytes = need;
+  c.busy = true;
+  const int64_t n = ctx->hier[SIPG_OP_VISCOUS].L[0].ndofs;
+  bool ok = cudaMalloc(&c.ustar, sizeof(double) * n) == cudaSuccess &&
+            cudaMalloc(&c.b, sizeof(double) * n) == cudaSuccess && cudaMalloc(&c.x, sizeof(double) * n) == cudaSuccess &&
+            cudaMalloc(&c.sc, sizeof(double) * 16) == cudaSuccess &&
+            cudaMallocHost(&c.hsc, sizeof(double) * 4) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c.ev_ready, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c.ev_rr, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) return nullptr;
+  used_bytes += need;
+  pool.push_back(c);
+  return &pool.back();
+}
+
+bool sipg_server::admit_one(std::unique_ptr<Request>& rq) {
+  sipg_mesh_desc m = box_mesh(rq->spec.n_cells);
+  sipg_opts o;
+  sipg_default_opts(&o);
+  o.k_u = rq->spec.k_u;
+  int64_t need = 0;
+  if (sipg_estimate_bytes(&m, &o, &need) != SIPG_OK) return false;
+  const int64_t n = (int64_t)rq->spec.n_cells * rq->spec.n_cells * rq->spec.n_cells * 3 * (rq->spec.k_u + 1) *
+                    (rq->spec.k_u + 1) * (rq->spec.k_u + 1);
+  need += 3 * 8 * n + 256;  // u*, b, x of the request
+  if (need > (int64_t)opts.hbm_budget_bytes) {  // can never fit: reject now
+    rq->result.status = SIPG_ERR_NOMEM;
+    rq->done = true;
+    return true;
+  }
+  ContextEntry* c = acquire_context(rq->spec.n_cells, rq->spec.k_u, need);
+  if (!c) return false;  // wait for memory or a slot
+  Request* r = rq.get();
+  r->ctx = c->ctx;
+  r->ustar = c->ustar;
+  r->b = c->b;
+  r->x = c->x;
+  r->sc = c->sc;
+  r->hsc = c->hsc;
+  r->ev_ready = c->ev_ready;
+  r->ev_rr = c->ev_rr;
+  r->bytes = need;
+  r->n = c->ctx->hier[SIPG_OP_VISCOUS].L[0].ndofs;
+  r->t_admit = Clock::now();
+  return true;
+}
+
+// viscosity, right-hand side b = A u*, and the first CG step, on the request's stream
+int sipg_server::start_request(Request* r) {
+  sipg_ctx* ctx = r->ctx;
+  sipg_rheology rh{};
+  rh.law = SIPG_LAW_SINKER;
+  rh.n_spheres = r->spec.n_spheres;
+  rh.centers = r->centers.data();
+  rh.radius = r->spec.radius;
+  rh.nu_max = r->spec.nu_max;
+  rh.nu_matrix = r->spec.nu_matrix;
+  int rc = sipg_set_viscosity(ctx, &rh, nullptr);
+  if (rc) return rc;
+  cudaStream_t st = ctx->st;
+  Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+  double *rr = H.cg[0], *z = H.cg[1], *p = H.cg[2];
+  const int64_t n = r->n;
+  if (launch_random(n, r->spec.seed, r->ustar, st)) return SIPG_ERR_CUDA;
+  rc = ctx->krylov_apply(SIPG_OP_VISCOUS, r->ustar, r->b, 0.0);
+  if (rc) return rc;
+  if (cudaMemsetAsync(r->x, 0, sizeof(double) * n, st)) return SIPG_ERR_CUDA;
+  if (cudaMemsetAsync(r->sc, 0, sizeof(double) * 16, st)) return SIPG_ERR_CUDA;
+  if (cudaMemcpyAsync(rr, r->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st)) return SIPG_ERR_CUDA;
+  if (launch_dot(n, r->b, r->b, ctx->partials, r->sc + 4, st)) return SIPG_ERR_CUDA;
+  if (cudaMemcpyAsync(r->hsc + 2, r->sc + 4, sizeof(double), cudaMemcpyDeviceToHost, st)) return SIPG_ERR_CUDA;
+  rc = ctx->precondition(SIPG_OP_VISCOUS, SIPG_PRECOND_MG, rr, z, 0.0);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st)) return SIPG_ERR_CUDA;
+  if (launch_dot(n, rr, z, ctx->partials, r->sc + 0, st)) return SIPG_ERR_CUDA;
+  if (cudaStreamSynchronize(st)) return SIPG_ERR_CUDA;
+  r->bnorm = std::sqrt(r->hsc[2]);
+  return SIPG_OK;
+}
+
+// One CG iteration of every active request; the fine-level applies are batched.
+int sipg_server::round() {
+  // (1) each request's previous work is done before the batched apply reads p
+  for (Request* r : active)
+    if (cudaEventRecord(r->ev_ready, r->ctx->st)) return SIPG_ERR_CUDA;
+  for (Request* r : active)
+    if (cudaStreamWaitEvent(sched, r->ev_ready, 0)) return SIPG_ERR_CUDA;
+  // (2) q_i = A_i p_i: one persistent launch per degree present
+  std::map<int, std::vector<Request*>> by_k;
+  for (Request* r : active) by_k[r->spec.k_u].push_back(r);
+  size_t ndesc = 0, ntile = 0;
+  for (auto& kv : by_k)
+    for (Request* r : kv.second) {
+      const int cpb = op_cells_per_cta(kv.first + 1, 3);
+      ntile += (r->ctx->hier[SIPG_OP_VISCOUS].L[0].g.ncells + cpb - 1) / cpb;
+      ++ndesc;
+    }
+  if (ndesc > d_desc_cap) {
+    cudaFree(d_desc);
+    d_desc_cap = std::max<size_t>(ndesc, 2 * d_desc_cap);
+    if (cudaMalloc(&d_desc, sizeof(ApplyDesc<double, ff>) * d_desc_cap)) return SIPG_ERR_NOMEM;
+  }
+  if (ntile > d_tiles_cap) {
+    cudaFree(d_tiles);
+    d_tiles_cap = std::max<size_t>(ntile, 2 * d_tiles_cap);
+    if (cudaMalloc(&d_tiles, sizeof(int2) * d_tiles_cap)) return SIPG_ERR_NOMEM;
+  }
+  h_desc.clear();
+  h_tiles.clear();
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> groups;  // degree, tile range
+  for (auto& kv : by_k) {
+    const size_t t0 = h_tiles.size();
+    for (Request* r : kv.second) {
+      const Level& L = r->ctx->hier[SIPG_OP_VISCOUS].L[0];
+      ApplyDesc<double, ff> d{};
+      d.g = L.g;
+      d.x = r->ctx->hier[SIPG_OP_VISCOUS].cg[2];  // p
+      d.y = r->ctx->hier[SIPG_OP_VISCOUS].cg[3];  // q
+      d.nu_cell = reinterpret_cast<const ff*>(L.nu_cellff);
+      d.nu_face = reinterpret_cast<const ff*>(L.nu_faceff);
+      d.mass = 0.0;
+      const int di = (int)h_desc.size();
+      h_desc.push_back(d);
+      const int cpb = op_cells_per_cta(kv.first + 1, 3);
+      for (int c0 = 0; c0 < L.g.ncells; c0 += cpb) h_tiles.push_back(make_int2(di, c0));
+    }
+    groups.push_back({kv.first, {t0, h_tiles.size() - t0}});
+  }
+  if (cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(ApplyDesc<double, ff>) * h_desc.size(), cudaMemcpyHostToDevice,
+                      sched))
+    return SIPG_ERR_CUDA;
+  if (cudaMemcpyAsync(d_tiles, h_tiles.data(), sizeof(int2) * h_tiles.size(), cudaMemcpyHostToDevice, sched))
+    return SIPG_ERR_CUDA;
+  for (auto& gp : groups) {
+    const int k = gp.first;
+    cudaError_t e = launch_apply_multi_ff(k + 1, 3, d_desc, d_tiles + gp.second.first, (int)gp.second.second,
+                                          active.front()->ctx->tabs[k + 1], sched);
+    if (e) return SIPG_ERR_CUDA;
+  }
+  if (cudaEventRecord(ev_applied, sched)) return SIPG_ERR_CUDA;
+  // (copies from pageable host memory return once the source is consumed, so
+  // the host tables may be rebuilt next round without waiting here)
+  // (3) per request: alpha, x, r, ||r||, V-cycle, beta, p on its own stream
+  for (Request* r : active) {
+    sipg_ctx* ctx = r->ctx;
+    cudaStream_t st = ctx->st;
+    Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+    double *rr = H.cg[0], *z = H.cg[1], *p = H.cg[2], *q = H.cg[3];
+    const int64_t n = r->n;
+    if (cudaStreamWaitEvent(st, ev_applied, 0)) return SIPG_ERR_CUDA;
+    if (launch_dot(n, p, q, ctx->partials, r->sc + 1, st)) return SIPG_ERR_CUDA;
+    cg_check<<<1, 1, 0, st>>>(r->sc);
+    cg_step_x_r<<<vec_blocks(n), 256, 0, st>>>(n, r->sc, p, q, r->x, rr);
+    if (launch_dot(n, rr, rr, ctx->partials, r->sc + 2, st)) return SIPG_ERR_CUDA;
+    if (cudaMemcpyAsync(r->hsc, r->sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st)) return SIPG_ERR_CUDA;
+    if (cudaMemcpyAsync(r->hsc + 1, r->sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st)) return SIPG_ERR_CUDA;
+    if (cudaEventRecord(r->ev_rr, st)) return SIPG_ERR_CUDA;
+    int rc = ctx->precondition(SIPG_OP_VISCOUS, SIPG_PRECOND_MG, rr, z, 0.0);
+    if (rc) return rc;
+    if (launch_dot(n, rr, z, ctx->partials, r->sc + 3, st)) return SIPG_ERR_CUDA;
+    cg_step_p<<<vec_blocks(n), 256, 0, st>>>(n, r->sc, z, p);
+    cg_rotate<<<1, 1, 0, st>>>(r->sc);
+    if (cudaGetLastError()) return SIPG_ERR_CUDA;
+    r->iters++;
+  }
+  // (4) convergence from this round's residual norms (V-cycles keep running)
+  std::vector<Request*> still;
+  for (Request* r : active) {
+    if (cudaEventSynchronize(r->ev_rr)) return SIPG_ERR_CUDA;
+    const double res = std::sqrt(std::max(r->hsc[0], 0.0));
+    const bool broke = r->hsc[1] != 0.0 || !std::isfinite(res);
+    const bool conv = res <= r->spec.rtol * r->bnorm;
+    if (conv || broke || r->iters >= r->spec.maxit) {
+      r->result.status = conv ? SIPG_OK : (broke ? SIPG_ERR_BREAKDOWN : SIPG_ERR_MAXIT);
+      int rc = finish(r);
+      if (rc) return rc;
+    } else {
+      still.push_back(r);
+    }
+  }
+  active.swap(still);
+  return SIPG_OK;
+}
+
+// Final true residual, error against u*, optional copy of x; frees the slot.
+int sipg_server::finish(Request* r) {
+  sipg_ctx* ctx = r->ctx;
+  cudaStream_t st = ctx->st;
+  Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+  double *t = H.cg[3], *rr = H.cg[0];
+  const int64_t n = r->n;
+  int rc = ctx->krylov_apply(SIPG_OP_VISCOUS, r->x, t, 0.0);
+  if (rc) return rc;
+  if (launch_sub<double>(n, r->b, t, rr, st)) return SIPG_ERR_CUDA;
+  double rr2 = 0.0, ee = 0.0, uu = 0.0;
+  if ((rc = ctx->dot(n, rr, rr, &rr2))) return rc;
+  if (launch_sub<double>(n, r->x, r->ustar, t, st)) return SIPG_ERR_CUDA;
+  if ((rc = ctx->dot(n, t, t, &ee))) return rc;
+  if ((rc = ctx->dot(n, r->ustar, r->ustar, &uu))) return rc;
+  if (r->keep_solution) {
+    r->solution.resize(n);
+    if (cudaMemcpyAsync(r->solution.data(), r->x, sizeof(double) * n, cudaMemcpyDeviceToHost, st)) return SIPG_ERR_CUDA;
+    if (cudaStreamSynchronize(st)) return SIPG_ERR_CUDA;
+  }
+  r->t_done = Clock::now();
+  r->result.iterations = r->iters;
+  r->result.rel_residual = r->bnorm > 0 ? std::sqrt(rr2) / r->bnorm : std::sqrt(rr2);
+  r->result.err_vs_ustar = uu > 0 ? std::sqrt(ee / uu) : 0.0;
+  r->result.n_dofs = n;
+  r->result.queue_s = std::chrono::duration<double>(r->t_admit - r->t_submit).count();
+  r->result.latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  r->result.solve_s = std::chrono::duration<double>(r->t_done - r->t_admit).count();
+  for (ContextEntry& c : pool)
+    if (c.ctx == ctx) c.busy = false;
+  r->ctx = nullptr;
+  r->done = true;
+  return SIPG_OK;
+}
+
+void sipg_server::run() {
+  if (cudaSetDevice(device) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    set_error("server worker: cudaSetDevice failed");
+    cv_done.notify_all();
+    return;
+  }
+  while (true) {
+    // admission (between rounds)
+    std::vector<std::unique_ptr<Request>> admitted;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return stop || !queue.empty() || !active.empty(); });
+      if (stop && queue.empty() && active.empty()) break;
+      while (!queue.empty() && (int)active.size() + (int)admitted.size() < opts.max_slots) {
+        std::unique_ptr<Request>& rq = queue.front();
+        if (!admit_one(rq)) break;  // memory busy: retry after the next round
+        admitted.push_back(std::move(rq));
+        queue.pop_front();
+      }
+    }
+    for (auto& up : admitted) {
+      Request* r = up.get();
+      if (!r->done) {
+        int rc = start_request(r);
+        if (rc) {
+          r->result.status = rc;
+          r->done = true;
+          for (ContextEntry& c : pool)
+            if (c.ctx == r->ctx) c.busy = false;
+        } else {
+          active.push_back(r);
+        }
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto& up : admitted) {
+        const uint64_t id = up->id;
+        if (up->done) --pending;
+        finished[id] = std::move(up);
+      }
+    }
+    if (active.empty()) {
+      cv_done.notify_all();
+      continue;
+    }
+    std::vector<Request*> before = active;
+    int rc = round();
+    std::lock_guard<std::mutex> lk(mu);
+    if (rc) {
+      set_error("server round failed with status " + std::to_string(rc));
+      for (Request* r : before) {
+        r->result.status = rc;
+        r->done = true;
+      }
+      active.clear();
+    }
+    for (Request* r : before)
+      if (r->done) --pending;
+    cv_done.notify_all();
+  }
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" int sipg_server_create(const sipg_server_opts* o, sipg_server** out) {
+  if (!o || !out || o->max_slots <= 0 || o->hbm_budget_bytes == 0) return SIPG_ERR_INVALID;
+  if (o->mg_precision != SIPG_F32 && o->mg_precision != SIPG_F64) return SIPG_ERR_INVALID;
+  auto* s = new sipg_server();
+  s->opts = *o;
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->sched, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_applied, cudaEventDisableTiming) != cudaSuccess) {
+    delete s;
+    return SIPG_ERR_CUDA;
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return SIPG_OK;
+}
+
+extern "C" int sipg_server_submit(sipg_server* s, const sipg_request* req, uint64_t* id) {
+  if (!s || !req || !id) return SIPG_ERR_INVALID;
+  if (req->n_cells <= 0 || req->k_u < 2 || req->k_u > 5 || req->n_spheres < 0 || req->n_spheres > 64 ||
+      (req->n_spheres > 0 && !req->centers) || !(req->nu_max > 0) || !(req->nu_matrix > 0) || !(req->rtol > 0) ||
+      req->maxit <= 0)
+    return SIPG_ERR_INVALID;
+  auto r = std::make_unique<Request>();
+  r->spec = *req;
+  r->centers.assign(req->centers, req->centers + 3 * req->n_spheres);
+  r->spec.centers = nullptr;
+  r->keep_solution = req->keep_solution != 0;
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->failed) return SIPG_ERR_STATE;
+  r->id = s->next_id++;
+  *id = r->id;
+  s->queue.push_back(std::move(r));
+  ++s->pending;
+  s->cv.notify_all();
+  return SIPG_OK;
+}
+
+extern "C" int sipg_server_poll(sipg_server* s, uint64_t id, sipg_result* res, double* x_host) {
+  if (!s || !res) return SIPG_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->finished.find(id);
+  if (it == s->finished.end() || !it->second->done) {
+    for (const auto& q : s->queue)
+      if (q->id == id) return SIPG_PENDING;
+    if (it != s->finished.end()) return SIPG_PENDING;
+    return id < s->next_id ? SIPG_PENDING : SIPG_ERR_INVALID;
+  }
+  *res = it->second->result;
+  if (x_host && !it->second->solution.empty())
+    std::memcpy(x_host, it->second->solution.data(), sizeof(double) * it->second->solution.size());
+  return SIPG_OK;
+}
+
+extern "C" int sipg_server_drain(sipg_server* s, double timeout_s) {
+  if (!s) return SIPG_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9);
+  while (s->pending > 0 && !s->failed) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->pending > 0) return SIPG_ERR_TIMEOUT;
+  }
+  return s->failed ? SIPG_ERR_STATE : SIPG_OK;
+}
+
+extern "C" const char* sipg_server_last_error(const sipg_server* s) { return s ? s->err.c_str() : "null server"; }
+
+extern "C" int sipg_server_destroy(sipg_server* s) {
+  if (!s) return SIPG_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();
+    s->cv.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->device);
+  for (ContextEntry& c : s->pool) {
+    cudaFree(c.ustar);
+    cudaFree(c.b);
+    cudaFree(c.x);
+    cudaFree(c.sc);
+    cudaFreeHost(c.hsc);
+    cudaEventDestroy(c.ev_ready);
+    cudaEventDestroy(c.ev_rr);
+    cudaStream_t st = c.ctx->st;
+    sipg_destroy(c.ctx);
+    cudaStreamDestroy(st);
+  }
+  cudaFree(s->d_desc);
+  cudaFree(s->d_tiles);
+  cudaEventDestroy(s->ev_applied);
+  cudaStreamDestroy(s->sched);
+  delete s;
+  return SIPG_OK;
+}

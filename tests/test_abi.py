@@ -59,3 +59,31 @@ def test_create_rejects_bad_arguments(lib, field, value):
 def test_null_arguments(lib):
     assert lib.sipg_create(None, None, None, None) == -1
     assert lib.sipg_destroy(None) == -1
+
+
+def test_server_rejects_bad_options(lib):
+    from paper_2506_14424_gb300 import _lib
+    o = _lib.ServerOpts(0, 4, 1, 3)           # zero budget
+    h = ctypes.c_void_p()
+    assert lib.sipg_server_create(ctypes.byref(o), ctypes.byref(h)) == -1
+    o = _lib.ServerOpts(1 << 30, 0, 1, 3)     # no slots
+    assert lib.sipg_server_create(ctypes.byref(o), ctypes.byref(h)) == -1
+
+
+def test_estimate_bytes_grows_with_the_mesh(lib):
+    """Size accounting runs without a device (dry run of the hierarchy)."""
+    from paper_2506_14424_gb300 import _lib
+    vals = []
+    for n in (4, 8, 16):
+        m = _lib.MeshDesc()
+        m.nx = m.ny = m.nz = n
+        m.lx = m.ly = m.lz = 1.0
+        for i in range(6):
+            m.bc_pressure[i] = 1
+        o = _lib.Opts()
+        lib.sipg_default_opts(ctypes.byref(o))
+        b = ctypes.c_int64()
+        assert lib.sipg_estimate_bytes(ctypes.byref(m), ctypes.byref(o), ctypes.byref(b)) == 0
+        vals.append(b.value)
+    # at least the level-0 velocity vectors: 8^3 cells, k=3, 192 DoFs per cell
+    assert vals[0] < vals[1] < vals[2] and vals[1] > 8 ** 3 * 192 * 8 * 10
