@@ -36,11 +36,13 @@ int sipg_ctx::fail(int code, const char* what, cudaError_t e) {
 
 namespace {
 
+// Allocate and zero on the context's stream (a plain cudaMemset runs on the
+// legacy default stream, which is not ordered with non-blocking streams).
 template <typename T>
-T* dalloc(int64_t n, cudaError_t* e) {
+T* dalloc(int64_t n, cudaError_t* e, cudaStream_t st) {
   void* p = nullptr;
   *e = cudaMalloc(&p, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
-  if (*e == cudaSuccess) *e = cudaMemset(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  if (*e == cudaSuccess) *e = cudaMemsetAsync(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1), st);
   return (T*)p;
 }
 
@@ -61,7 +63,7 @@ T* sipg_ctx::alloc(int64_t n, cudaError_t* e) {
     *e = cudaSuccess;
     return nullptr;
   }
-  return dalloc<T>(n, e);
+  return dalloc<T>(n, e, st);
 }
 
 int sipg_ctx::build_hierarchy(int op) {
@@ -142,7 +144,7 @@ int sipg_ctx::build_hierarchy(int op) {
         bytes += (int64_t)(es * (size_t)L.ndofs);
         if (!dry) {
           e = cudaMalloc(&ptr, es * (size_t)L.ndofs);
-          if (e == cudaSuccess) e = cudaMemset(ptr, 0, es * (size_t)L.ndofs);
+          if (e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, es * (size_t)L.ndofs, st);
           if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
         }
         L.w[p][v] = ptr;
@@ -226,13 +228,13 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   int rc = SIPG_OK;
   for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);
   if (rc == SIPG_OK) {
-    ctx->partials = dalloc<double>(kDotBlocks, &e);
-    if (!e) ctx->dscal = dalloc<double>(16, &e);
-    if (!e) ctx->dflag = dalloc<int>(4, &e);
+    ctx->partials = dalloc<double>(kDotBlocks, &e, ctx->st);
+    if (!e) ctx->dscal = dalloc<double>(16, &e, ctx->st);
+    if (!e) ctx->dflag = dalloc<int>(4, &e, ctx->st);
     if (!e) e = cudaMallocHost(&ctx->hscal, 16 * sizeof(double));
     if (e) rc = ctx->fail(SIPG_ERR_NOMEM, "alloc scalars", e);
   }
-  if (rc == SIPG_OK) rc = ctx->setup_operator(SIPG_OP_POISSON, 0.0);  // no viscosity needed
+  // the Poisson hierarchy's smoothers and coarse inverse are set up on first use
   if (rc != SIPG_OK) {
     fprintf(stderr, "sipg_create: %s\n", ctx->err.c_str());
     delete ctx;
@@ -469,6 +471,12 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   }
   if (A != C.Ainv) CK(cudaMemcpyAsync(C.Ainv, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
   return SIPG_OK;
+}
+
+int sipg_ctx::ensure_setup(int op) {
+  if (hier[op].ready) return SIPG_OK;
+  if (op == SIPG_OP_VISCOUS && !have_nu) return fail(SIPG_ERR_STATE, "set the viscosity first");
+  return setup_operator(op, hier[op].setup_mass);
 }
 
 int sipg_ctx::setup_operator(int op, double mass) {

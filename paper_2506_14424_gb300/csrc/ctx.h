@@ -67,6 +67,7 @@ struct sipg_ctx {
   int setup_level_smoother(int op, int l, double mass);
   int setup_coarse(int op, double mass);
   int setup_operator(int op, double mass);
+  int ensure_setup(int op);
   template <typename T>
   int level_apply(int op, int l, const T* x, T* y, double mass);
   int level_apply_ff(int op, int l, const double* x, double* y, double mass);

@@ -22,84 +22,109 @@ inline int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + kBS - 1) /
 //                 Dirichlet 2 x the same with tau of the wall
 //  Poisson cell:  sum_q W |grad phi|^2 + m W phi^2
 //  Poisson face:  interior  -sigma phi d_d phi + tau phi^2;  Dirichlet 2 x the same
+// The cell sums factor over the tensor product: sum_q F(q) prod_d A_d[q_d][i_d]^2
+// with F = W nu (or W) and A_d = DS (derivative direction) or S, one sweep per
+// direction; face terms vanish unless the DoF lies on the face layer.
+// One CTA per cell.
 template <int N, int NC>
 __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__ nu_cell,
                                 const double* __restrict__ nu_face, double mass, double* __restrict__ diag) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)g.ncells * NC * N3) return;
-  const int e = (int)(idx / (NC * N3));
-  const int rem = (int)(idx % (NC * N3));
-  const int c = rem / N3, r = rem % N3;
-  const int ii[3] = {r % N, (r / N) % N, r / N2};
-  const double ih[3] = {g.ih[0], g.ih[1], g.ih[2]};
+  __shared__ double F[N3], Fm[N3], T1[N3], T2[N3], C[4][N3];
+  __shared__ double S2[N2], D2[N2];
+  const int e = blockIdx.x;
   const double detJ = g.h[0] * g.h[1] * g.h[2];
-  double acc = 0.0;
-  for (int q = 0; q < N3; ++q) {
-    const int qq[3] = {q % N, (q / N) % N, q / N2};
-    double val = 1.0, gr[3];
-    for (int l = 0; l < 3; ++l) val *= tab.S[qq[l] * N + ii[l]];
-    for (int l = 0; l < 3; ++l) {
-      double p = ih[l];
-      for (int m = 0; m < 3; ++m) p *= (m == l ? tab.DS[qq[m] * N + ii[m]] : tab.S[qq[m] * N + ii[m]]);
-      gr[l] = p;
-    }
-    const double W = tab.gw[qq[0]] * tab.gw[qq[1]] * tab.gw[qq[2]] * detJ;
-    const double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
-    if (NC == 3)
-      acc += W * nu_cell[(size_t)e * N3 + q] * (g2 + gr[c] * gr[c]);
-    else
-      acc += W * g2;
-    acc += mass * W * val * val;
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    S2[i] = tab.S[i] * tab.S[i];
+    D2[i] = tab.DS[i] * tab.DS[i];
   }
-  double lam_e = penalty_lambda(g, e);
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, s = f & 1;
-    const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] == 1) continue;
-    const int layer = s ? N - 1 : 0;
-    const double sigma = s ? 1.0 : -1.0;
-    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
-    const double* dS = s ? tab.dS1 : tab.dS0;
-    const double on_face = ii[d] == layer ? 1.0 : 0.0;
-    const double area = g.h[t1] * g.h[t2];
-    const double mirror = nb >= 0 ? 1.0 : 2.0;
-    for (int p = 0; p < N2; ++p) {
-      const int a = p % N, b = p / N;
-      const double st = tab.S[a * N + ii[t1]] * tab.S[b * N + ii[t2]];
-      const double phi = on_face * st;
-      const double dd = dS[ii[d]] * st * ih[d];
-      const double W = tab.gw[a] * tab.gw[b] * area;
-      if (NC == 3) {
-        const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
-        const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p] : num;
-        double nub = num > nup ? num : nup;
-        if (g.face_nu == 1) nub = 0.5 * (num + nup);
-        if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
-        const double tau = g.cip * N * N * lam * nub;
-        const double fac = c == d ? 2.0 : 1.0;
-        acc += mirror * W * fac * (-num * sigma * phi * dd + tau * phi * phi);
-      } else {
-        const double tau = g.cip * N * N * lam;
-        acc += mirror * W * (-sigma * phi * dd + tau * phi * phi);
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const double W = tab.gw[q % N] * tab.gw[(q / N) % N] * tab.gw[q / N2] * detJ;
+    F[q] = NC == 3 ? W * nu_cell[(size_t)e * N3 + q] : W;
+    Fm[q] = mass * W;
+  }
+  __syncthreads();
+  // C[l] (l = 0, 1, 2: derivative direction l; l = 3: mass) by three sweeps
+  for (int l = 0; l < 4; ++l) {
+    const double* src = l < 3 ? F : Fm;
+    const double* Ax = l == 0 ? D2 : S2;
+    const double* Ay = l == 1 ? D2 : S2;
+    const double* Az = l == 2 ? D2 : S2;
+    for (int o = threadIdx.x; o < N3; o += blockDim.x) {  // (qz, qy, ix)
+      const int ix = o % N, qy = (o / N) % N, qz = o / N2;
+      double s = 0.0;
+      for (int qx = 0; qx < N; ++qx) s += Ax[qx * N + ix] * src[(qz * N + qy) * N + qx];
+      T1[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < N3; o += blockDim.x) {  // (qz, iy, ix)
+      const int ix = o % N, iy = (o / N) % N, qz = o / N2;
+      double s = 0.0;
+      for (int qy = 0; qy < N; ++qy) s += Ay[qy * N + iy] * T1[(qz * N + qy) * N + ix];
+      T2[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < N3; o += blockDim.x) {  // (iz, iy, ix)
+      const int ix = o % N, iy = (o / N) % N, iz = o / N2;
+      double s = 0.0;
+      for (int qz = 0; qz < N; ++qz) s += Az[qz * N + iz] * T2[(qz * N + iy) * N + ix];
+      C[l][o] = s;
+    }
+    __syncthreads();
+  }
+  const double lam_e = penalty_lambda(g, e);
+  for (int idx = threadIdx.x; idx < NC * N3; idx += blockDim.x) {
+    const int c = idx / N3, r = idx % N3;
+    const int ii[3] = {r % N, (r / N) % N, r / N2};
+    double acc = C[3][r];
+    for (int l = 0; l < 3; ++l) {
+      const double f = (NC == 3 && l == c) ? 2.0 : 1.0;
+      acc += f * g.ih[l] * g.ih[l] * C[l][r];
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, s = f & 1;
+      if (ii[d] != (s ? N - 1 : 0)) continue;  // shape function vanishes on this face
+      const int nb = cell_neighbor(g, e, f);
+      if (nb < 0 && g.bc[f] == 1) continue;
+      const double sigma = s ? 1.0 : -1.0;
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
+      const double* dS = s ? tab.dS1 : tab.dS0;
+      const double area = g.h[t1] * g.h[t2];
+      const double mirror = nb >= 0 ? 1.0 : 2.0;
+      for (int p = 0; p < N2; ++p) {
+        const int a = p % N, b = p / N;
+        const double phi = tab.S[a * N + ii[t1]] * tab.S[b * N + ii[t2]];
+        const double dd = dS[ii[d]] * phi * g.ih[d];
+        const double W = tab.gw[a] * tab.gw[b] * area;
+        if (NC == 3) {
+          const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
+          const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p] : num;
+          double nub = num > nup ? num : nup;
+          if (g.face_nu == 1) nub = 0.5 * (num + nup);
+          if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
+          const double tau = g.cip * N * N * lam * nub;
+          const double fac = c == d ? 2.0 : 1.0;
+          acc += mirror * W * fac * (-num * sigma * phi * dd + tau * phi * phi);
+        } else {
+          const double tau = g.cip * N * N * lam;
+          acc += mirror * W * (-sigma * phi * dd + tau * phi * phi);
+        }
       }
     }
+    diag[((size_t)e * NC + c) * N3 + r] = acc;
   }
-  diag[idx] = acc;
 }
 
 cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
                             const double* nu_face, double mass, double* diag, cudaStream_t st) {
-  const int64_t total = (int64_t)g.ncells * ncomp * n * n * n;
-  const int blocks = (int)((total + 127) / 128);
-  if (blocks == 0) return cudaSuccess;
-#define SIPG_DIAG(NN)                                                                             \
-  case NN:                                                                                        \
-    if (ncomp == 3)                                                                               \
-      diagonal_kernel<NN, 3><<<blocks, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);       \
-    else                                                                                          \
-      diagonal_kernel<NN, 1><<<blocks, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);       \
+  if (g.ncells == 0) return cudaSuccess;
+#define SIPG_DIAG(NN)                                                                              \
+  case NN:                                                                                         \
+    if (ncomp == 3)                                                                                \
+      diagonal_kernel<NN, 3><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);      \
+    else                                                                                           \
+      diagonal_kernel<NN, 1><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);      \
     break;
   switch (n) {
     SIPG_DIAG(2) SIPG_DIAG(3) SIPG_DIAG(4) SIPG_DIAG(5) SIPG_DIAG(6)

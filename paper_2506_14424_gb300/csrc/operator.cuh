@@ -130,7 +130,7 @@ __host__ __device__ constexpr int op_work_elems() {
 }
 template <int N, int NC>
 __host__ __device__ constexpr int op_smem_elems() {
-  return 4 * N + 2 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
+  return 2 * N * N + 4 * N + 2 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
 }
 
 template <int N, typename T>
@@ -150,13 +150,16 @@ __device__ __forceinline__ void load_tables(const CTab<T>& ct, T* dS0, T* dS1, T
 // and on exit slots 0, 1, 5, 4 hold the coefficients of the test value, of
 // the normal test derivative and of the two tangential test derivatives.
 // pen[s*CPB + c] = C_IP (k+1)^2 max(Lambda-, Lambda+).
-template <int N, int NC, int D, typename TN, typename T>
-__device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, int ncell, int FS, int CPB,
+template <typename T>
+__device__ __forceinline__ T sel3(const T* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
+
+template <int N, int NC, typename TN, typename T>
+__device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int cell0, int ncell, int FS, int CPB,
                                                const T* ih, const T* gw, const T* pen,
                                                const TN* __restrict__ nu_face, T* F) {
   constexpr int N2 = N * N;
-  constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
-  const T ihd = ih[D], iht1 = ih[T1], iht2 = ih[T2];
+  const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+  const T ihd = sel3(ih, D), iht1 = sel3(ih, T1), iht2 = sel3(ih, T2);
   const T area = from_double<T>(g.h[T1] * g.h[T2]);
   for (int i = threadIdx.x; i < 2 * ncell * N2; i += blockDim.x) {
     const int s = i / (ncell * N2);
@@ -233,8 +236,8 @@ __device__ __forceinline__ void face_flux_pair(const LevelGeom& g, int cell0, in
           gN[j] = cq * jmp[k] * ihd;
         }
       }
-      gT1[jd] = cq * jmp[T1] * iht1;
-      gT2[jd] = cq * jmp[T2] * iht2;
+      gT1[jd] = cq * sel3(jmp, T1) * iht1;
+      gT2[jd] = cq * sel3(jmp, T2) * iht2;
     } else {
       const T tau = pe;
       const int j = c * N2 + p;
@@ -265,18 +268,19 @@ __device__ __forceinline__ T line_dot(const T* M, const T* v, int o) {
   return acc.get();
 }
 
-// Face terms of direction D (both sides) added to Y.
-template <int N, int NC, int D, typename TS, typename TN, typename T>
-__device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct, int cell0, int ncell, int CPB,
-                                          const TS* __restrict__ x, const TN* __restrict__ nu_face,
-                                          const T* Xs, T* Y, T* F, T* pen, const T* ih, const T* gw,
-                                          const T* dS0, const T* dS1) {
+// Face terms of direction D (both sides) added to Y. One non-inlined copy
+// serves the three directions (the direction only changes indices), which
+// keeps the unrolled float-float code within the instruction cache.
+// S and Dg point to shared-memory copies of the 1D matrices.
+template <int N, int NC, typename TS, typename TN, typename T>
+__device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, const T* Dg, int cell0, int ncell,
+                                       int CPB, const TS* __restrict__ x, const TN* __restrict__ nu_face,
+                                       const T* Xs, T* Y, T* F, T* pen, const T* ih, const T* gw,
+                                       const T* dS0, const T* dS1) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  constexpr int STD = D == 0 ? 1 : (D == 1 ? N : N2);
+  const int STD = D == 0 ? 1 : (D == 1 ? N : N2);
   const int nt = ncell * NC;
   const int FS = CPB * NC * N2;
-  const T* S = ct.S;
-  const T* Dg = ct.Dg;
   // (A) traces and normal derivatives at the face Gauss-Lobatto nodes of both
   // sides (neighbour data straight from global memory); penalty per cell/side
   for (int i = threadIdx.x; i < 2 * nt * N2; i += blockDim.x) {
@@ -389,7 +393,7 @@ __device__ __forceinline__ void face_pair(const LevelGeom& g, const CTab<T>& ct,
     __syncthreads();
   }
   // (E) numerical flux
-  face_flux_pair<N, NC, D, TN, T>(g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
+  face_flux_pair<N, NC, TN, T>(D, g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
   __syncthreads();
   // (F) test side, along a: slot 2 = gV + Dg_a^T gT1
   for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
@@ -475,7 +479,9 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
                                             TS* __restrict__ y, const TN* __restrict__ nu_cell,
                                             const TN* __restrict__ nu_face, double mass_d, int cell0, T* sm) {
   constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
-  T* dS0 = sm;
+  T* Ssh = sm;                     // N2, copies of the 1D matrices for the face routine
+  T* Dsh = Ssh + N2;               // N2
+  T* dS0 = Dsh + N2;
   T* dS1 = dS0 + N;
   T* gw = dS1 + N;
   T* pen = gw + 2 * N;             // 2 * CPB
@@ -489,6 +495,10 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
   const T* Dg = ct.Dg;
 
   load_tables<N>(ct, dS0, dS1, gw);
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    Ssh[i] = ct.S[i];
+    Dsh[i] = ct.Dg[i];
+  }
   const T mass = from_double<T>(mass_d);
   const int ncell = min(CPB, g.ncells - cell0);
   const int nt = ncell * NC;
@@ -571,9 +581,8 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
   __syncthreads();
 
   // ---- face terms, both faces of one direction at a time (work region reused)
-  face_pair<N, NC, 0, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
-  face_pair<N, NC, 1, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
-  face_pair<N, NC, 2, TS, TN, T>(g, ct, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
+  for (int d = 0; d < 3; ++d)
+    face_pair<N, NC, TS, TN, T>(d, g, Ssh, Dsh, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
   for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(Y[i]);
 }
 

@@ -250,7 +250,7 @@ static int check_level(sipg_ctx* ctx, int op, int level) {
   if (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) return ctx->fail(SIPG_ERR_INVALID, "unknown operator");
   if (op == SIPG_OP_VISCOUS && !ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
   if (level < 0 || level >= (int)ctx->hier[op].L.size()) return ctx->fail(SIPG_ERR_INVALID, "bad level");
-  return SIPG_OK;
+  return ctx->ensure_setup(op);  // multigrid data of this operator
 }
 
 extern "C" int sipg_get_inverse_diagonal(const sipg_ctx* cctx, int op, int level, double* out) {
