@@ -137,10 +137,14 @@ cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab
 // --------------------------------------------------------------- transfers
 // p-transfer on one cell and component: fine = (E x E x E) coarse with
 // E[i*nc + j] = l^coarse_j(xi^fine_i) (prolongation, dir +1), or the
-// transpose (restriction, dir -1). One thread per output value.
+// transpose (restriction, dir -1). One thread per output value; the 1D
+// weights are staged in shared memory in the vector's precision.
 template <typename T>
 __global__ void p_transfer_kernel(int nf, int nc, int ntens, TransferTab tt, int dir, const T* __restrict__ in,
                                   T* __restrict__ out) {
+  __shared__ T E[kMaxN * kMaxN];
+  for (int i = threadIdx.x; i < nf * nc; i += blockDim.x) E[i] = T(tt.E[i]);
+  __syncthreads();
   const int nin = dir > 0 ? nc : nf, nout = dir > 0 ? nf : nc;
   const int in3 = nin * nin * nin, out3 = nout * nout * nout;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -150,13 +154,13 @@ __global__ void p_transfer_kernel(int nf, int nc, int ntens, TransferTab tt, int
   const T* src = in + (size_t)t * in3;
   T acc = T(0);
   for (int k = 0; k < nin; ++k) {
-    const double ez = dir > 0 ? tt.E[o[2] * nc + k] : tt.E[k * nc + o[2]];
+    const T ez = dir > 0 ? E[o[2] * nc + k] : E[k * nc + o[2]];
     for (int j = 0; j < nin; ++j) {
-      const double ey = dir > 0 ? tt.E[o[1] * nc + j] : tt.E[j * nc + o[1]];
-      for (int i = 0; i < nin; ++i) {
-        const double ex = dir > 0 ? tt.E[o[0] * nc + i] : tt.E[i * nc + o[0]];
-        acc += T(ex * ey * ez) * src[(k * nin + j) * nin + i];
-      }
+      const T ezy = ez * (dir > 0 ? E[o[1] * nc + j] : E[j * nc + o[1]]);
+      const T* row = src + (k * nin + j) * nin;
+      T s = T(0);
+      for (int i = 0; i < nin; ++i) s += (dir > 0 ? E[o[0] * nc + i] : E[i * nc + o[0]]) * row[i];
+      acc += ezy * s;
     }
   }
   out[idx] = acc;
@@ -179,6 +183,12 @@ cudaError_t launch_p_transfer(int nf, int nc, int ncomp, int ncells, const Trans
 template <typename T>
 __global__ void h_prolong_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coarse, TransferTab tt,
                                  const T* __restrict__ in, T* __restrict__ out) {
+  __shared__ T E0[kMaxN * kMaxN], E1[kMaxN * kMaxN];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    E0[i] = T(tt.E[i]);
+    E1[i] = T(tt.E1[i]);
+  }
+  __syncthreads();
   const int n3 = n * n * n;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)fine.ncells * ncomp * n3) return;
@@ -187,22 +197,31 @@ __global__ void h_prolong_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coa
   const int comp = rem / n3, r = rem % n3;
   const int fx = ef % fine.nx, fy = (ef / fine.nx) % fine.ny, fz = ef / (fine.nx * fine.ny);
   const int ec = ((fz / 2) * coarse.ny + fy / 2) * coarse.nx + fx / 2;
-  const double* Ex = (fx & 1) ? tt.E1 : tt.E;
-  const double* Ey = (fy & 1) ? tt.E1 : tt.E;
-  const double* Ez = (fz & 1) ? tt.E1 : tt.E;
+  const T* Ex = (fx & 1) ? E1 : E0;
+  const T* Ey = (fy & 1) ? E1 : E0;
+  const T* Ez = (fz & 1) ? E1 : E0;
   const int o[3] = {r % n, (r / n) % n, r / (n * n)};
   const T* src = in + ((size_t)ec * ncomp + comp) * n3;
   T acc = T(0);
   for (int k = 0; k < n; ++k)
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i)
-        acc += T(Ex[o[0] * n + i] * Ey[o[1] * n + j] * Ez[o[2] * n + k]) * src[(k * n + j) * n + i];
+    for (int j = 0; j < n; ++j) {
+      const T wzy = Ez[o[2] * n + k] * Ey[o[1] * n + j];
+      T s = T(0);
+      for (int i = 0; i < n; ++i) s += Ex[o[0] * n + i] * src[(k * n + j) * n + i];
+      acc += wzy * s;
+    }
   out[idx] = acc;
 }
 
 template <typename T>
 __global__ void h_restrict_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coarse, TransferTab tt,
                                   const T* __restrict__ in, T* __restrict__ out) {
+  __shared__ T E0[kMaxN * kMaxN], E1[kMaxN * kMaxN];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    E0[i] = T(tt.E[i]);
+    E1[i] = T(tt.E1[i]);
+  }
+  __syncthreads();
   const int n3 = n * n * n;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)coarse.ncells * ncomp * n3) return;
@@ -215,14 +234,17 @@ __global__ void h_restrict_kernel(int n, int ncomp, LevelGeom fine, LevelGeom co
   for (int ch = 0; ch < 8; ++ch) {
     const int bx = ch & 1, by = (ch >> 1) & 1, bz = ch >> 2;
     const int ef = ((2 * cz + bz) * fine.ny + 2 * cy + by) * fine.nx + 2 * cx + bx;
-    const double* Ex = bx ? tt.E1 : tt.E;
-    const double* Ey = by ? tt.E1 : tt.E;
-    const double* Ez = bz ? tt.E1 : tt.E;
+    const T* Ex = bx ? E1 : E0;
+    const T* Ey = by ? E1 : E0;
+    const T* Ez = bz ? E1 : E0;
     const T* src = in + ((size_t)ef * ncomp + comp) * n3;
     for (int k = 0; k < n; ++k)
-      for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i)
-          acc += T(Ex[i * n + o[0]] * Ey[j * n + o[1]] * Ez[k * n + o[2]]) * src[(k * n + j) * n + i];
+      for (int j = 0; j < n; ++j) {
+        const T wzy = Ez[k * n + o[2]] * Ey[j * n + o[1]];
+        T s = T(0);
+        for (int i = 0; i < n; ++i) s += Ex[i * n + o[0]] * src[(k * n + j) * n + i];
+        acc += wzy * s;
+      }
   }
   out[idx] = acc;
 }
