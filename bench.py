@@ -139,6 +139,23 @@ def algorithmic_bytes(n_dofs, cells, n):
     return 16.0 * n_dofs + 8.0 * (cells * n ** 3 + 6 * cells * n ** 2)
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """Largest value over the ranks of the default process group (the bench
+    times every rank and reports the slowest)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def aggregate_throughput(units_per_rank, ms_max, world):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -176,14 +193,11 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
         dist.barrier()
     ms_step = ms / args.steps
-    value = n * args.steps * world / (ms * 1e-3) / 1e9
+    value = aggregate_throughput(n * args.steps, ms, world) / 1e9
 
     # end to end through the C ABI with host buffers (copies inside the region)
     xh = np.ascontiguousarray(inputs.uniform_vector(n, seed=200))

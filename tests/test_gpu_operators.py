@@ -189,3 +189,49 @@ def test_inverse_diagonal_matches_oracle(op, dims, k):
             A = S.assemble()
         dinv = ctx.inverse_diagonal(op, level).cpu().numpy()
         assert _rel(1.0 / dinv, A.diagonal()) <= TOL64, level
+
+
+@pytest.mark.parametrize("arith", ["f64", "f64ff"])
+def test_anisotropic_cells_and_mixed_walls(arith):
+    """Non-cubic box and cells (hx != hy != hz), both operators, mixed boundary types."""
+    dims, extent, k = (3, 2, 4), (1.3, 0.7, 2.1), 3
+    bcv, bcp = "DNDDND", "NDNNDN"
+    ctx = Context(*dims, k, extent=extent, bc_velocity=bcv, bc_pressure=bcp)
+    rheo = {'law': 'analytic'}
+    ctx.set_viscosity(rheo)
+    S = SIPG(BoxMesh(*dims, extent=extent, bc=_bc(bcv)), k, 3)
+    x = inputs.uniform_vector(S.n_dofs, seed=21)
+    y = ctx.apply('viscous', _dev(x), mass=3.0, arith=arith).cpu().numpy()
+    assert _rel(y, S.apply(x, *S.viscosity_at_points(rheo), mass=3.0)) <= TOL64
+    P = SIPG(BoxMesh(*dims, extent=extent, bc=_bc(bcp)), k - 1, 1)
+    xp = inputs.uniform_vector(P.n_dofs, seed=22)
+    yp = ctx.apply('poisson', _dev(xp), arith=arith).cpu().numpy()
+    assert _rel(yp, P.apply(xp)) <= TOL64
+
+
+def test_maximum_size_sampled_rows():
+    """48^3 cells, k = 5 (71.7e6 velocity DoFs, the largest served mesh), sphere viscosity."""
+    N, k = 48, 5
+    mesh = BoxMesh(N, N, N)
+    S = SIPG(mesh, k, 3)
+    rheo = inputs.sinker(seed=3, count=8, radius=0.1, nu_max=1e2)
+    ctx = Context(N, N, N, k)
+    ctx.set_viscosity(rheo)
+    n = ctx.n_dofs()
+    assert n == N ** 3 * 3 * 216
+    x = inputs.uniform_vector(n, seed=23)
+    xd = _dev(x)
+    y = ctx.apply('viscous', xd).cpu().numpy().reshape(mesh.n_cells, -1)
+    yff = ctx.apply('viscous', xd, arith='f64ff').cpu().numpy().reshape(mesh.n_cells, -1)
+    cells = [0, N * N * N - 1, (N // 2) * (N * N + N + 1) + 7, 12345]
+    need = set(cells)
+    for e in cells:
+        for f in range(6):
+            nb = mesh.neighbor(e, f)
+            if nb is not None:
+                need.add(nb)
+    nc, nf = S.viscosity_at_points(rheo, cells=sorted(need))
+    y_ref = S.apply(x, nc, nf, cells=cells)
+    assert _rel(y[cells], y_ref) <= TOL64
+    assert _rel(yff[cells], y_ref) <= TOL64
+    ctx.close()
