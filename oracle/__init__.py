@@ -22,6 +22,10 @@ for fluids with variable viscosity"):
 * ``multigrid``    transfers, inverse diagonal, Chebyshev-Jacobi smoother and
                    V-cycle of Sec. 5.4 (matrix-free preconditioners).
 * ``manufactured`` body-force loads for manufactured solutions (Sec. 7.1).
+* ``mass``         element mass matrices (v, u)_e and their inverses (Sec. 3.2,
+                   Eqs. convective_step_weak / projection_step_weak).
+* ``nonlinear``    Picard iteration of the viscosity with Aitken relaxation
+                   (Sec. 5.4, Alg. 1).
 
 Parity status: see the header of each module. The multigrid V-cycle as a whole
 is "parity unpinned" against the paper (the paper prints no iteration counts
