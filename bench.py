@@ -307,8 +307,61 @@ def gpu_extras(ctx, xs, ys, stream):
         row["mixed_speedup"] = row["f64"]["seconds"] / row["f32"]["seconds"]
         solves.append(row)
     out["cfg3_mg_solves_16cubed_k4"] = solves
+    out["mass_32cubed_k3"] = mass_timings(ctx, xs, ys, stream)
+    out["picard_viscous_step_32cubed_k3"] = picard_extras(ctx)
     out["components_16cubed_k4"] = component_timings(stream)
     out["serving"] = serving_extras()
+    return out
+
+
+def mass_timings(ctx, xs, ys, stream, reps=40):
+    """Cell mass matrix and its inverse on the bench mesh: HBM-bound streaming
+    kernels (16 bytes per DoF), rotating over the bench's x/y pairs (> L2)."""
+    import torch
+    n = ctx.n_dofs("viscous")
+    hbm = peaks().get("hbm_gbs", 6686.1)
+    out = {}
+    for arith in ("f64", "f64ff"):
+        for inverse in (False, True):
+            def run(i):
+                ctx.mass("viscous", xs[i % len(xs)], ys[i % len(ys)], coeff=2.0, arith=arith, inverse=inverse)
+            for i in range(3):
+                run(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(reps):
+                run(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 16.0 * n / (ms * 1e-3) / 1e9
+            out[f"{'inverse_' if inverse else ''}mass_{arith}"] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm}
+    return out
+
+
+def picard_extras(ctx, dt=1e-2):
+    """Viscous step of BDF2 (gamma_0 = 3/2) with the Carreau-Yasuda law treated
+    implicitly: Picard updates with and without Aitken relaxation, each linear
+    solve to 1e-3 of its initial residual, nonlinear tolerance 1e-6."""
+    import numpy as np
+    import torch
+
+    from paper_2506_14424_gb300 import inputs
+    k = ctx.k_u
+    pts = ctx.node_points("viscous", 0)
+    vals = inputs.fourier_field(pts.reshape(-1, 3), inputs.fourier_modes(3)).reshape(-1, (k + 1) ** 3, 3)
+    uh = torch.tensor(np.ascontiguousarray(vals.transpose(0, 2, 1)).reshape(-1), device="cuda")
+    m = 1.5 / dt
+    b = ctx.mass("viscous", uh, coeff=m, arith="f64ff")
+    rh = inputs.carreau_blood_like()
+    out = {"mass_coeff": m}
+    for aitken in (True, False):
+        u = uh.clone()
+        r = ctx.picard_solve(rh, b, u, mass=m, rtol=1e-6, maxit=40, aitken=aitken, lin_rtol=1e-3)
+        out["aitken" if aitken else "plain_picard"] = {
+            "status": r["status"], "updates": r["iterations"], "cg_iterations": r["lin_iterations"],
+            "seconds": r["seconds"], "res0": r["res0"], "res": r["res"],
+            "omegas": [round(w, 4) for w in r["omegas"]]}
     return out
 
 

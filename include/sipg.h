@@ -199,7 +199,70 @@ int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, const void* x, 
 int sipg_solve(sipg_ctx* ctx, int op, const double* b, double* x, const sipg_solve_opts* so,
                sipg_solve_stats* stats);
 
+/* y = coeff M x with the cell mass matrix M of operator op (the element-local
+ * L2 inner product (v, u)_{Omega_e} of Eqs. convective_step_weak,
+ * projection_step_weak and viscous_step_weak, k+1 point Gauss rule); M is
+ * block diagonal over cells. prec as for sipg_apply. x and y may be the same
+ * buffer. */
+int sipg_mass_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double coeff);
+
+/* y = (coeff M)^-1 x: the "simple mass matrix solve" of the convective and
+ * projection steps (Sec. 3.2), exact and cell-local (tensor product of the 1D
+ * inverse mass matrix on the affine box). coeff != 0. x and y may alias. */
+int sipg_inverse_mass_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double coeff);
+
+/* ------------------------------------------- nonlinear viscous step (Alg. 1) */
+typedef struct {
+  double mass_coeff; /* gamma_0/dt of the viscous step operator (gamma_0/dt) M + A(nu) [0] */
+  double rtol;       /* eps_nl^rel: stop when ||r^k|| <= rtol ||r^0|| [1e-6] */
+  double atol;       /* eps_nl^abs: ... or when ||r^k|| <= atol [1e-12] */
+  int maxit;         /* N_nl, the limit on Picard updates [20] */
+  int aitken;        /* 1 Aitken relaxation of the updates, 0 plain Picard [1] */
+  double omega_init; /* relaxation factor of the first update [1] */
+  double lin_rtol;   /* each linear solve to lin_rtol times its initial residual ... [1e-3] */
+  double lin_atol;   /* ... or to lin_atol, whichever is larger [0] */
+  int lin_maxit;     /* CG iteration limit per solve (reaching it is not an error) [500] */
+  int precond;       /* SIPG_PRECOND_* of the linear solves [MG] */
+} sipg_picard_opts;
+
+typedef struct {
+  int iterations;     /* Picard updates made (= linear solves) */
+  int lin_iterations; /* CG iterations summed over the linear solves */
+  double res0;        /* ||r^visc,0|| */
+  double res;         /* ||r^visc|| of the returned iterate */
+  double seconds;     /* wall time (host clock, sync) */
+  int status;         /* SIPG_OK converged; SIPG_ERR_MAXIT maxit updates without converging */
+  int history_len;    /* capacity of the two optional arrays below (0: none) */
+  double* residuals;  /* HOST, optional: ||r^k||, k = 0..iterations */
+  double* omegas;     /* HOST, optional: relaxation factor of update k = 0..iterations-1 */
+} sipg_picard_stats;
+
+/* Fill *o with the defaults listed above. */
+void sipg_default_picard_opts(sipg_picard_opts* o);
+
+/* Viscous step with a velocity-dependent viscosity (Sec. 5.4, Alg. 1 with the
+ * convective term explicit): find u with
+ *     r(u) = b - ((gamma_0/dt) M + A(nu(u))) u = 0,  nu(u) = eta(gamma_dot(eps(u)))
+ * by Picard updates of the viscosity (Eq. viscosity_pointwise) and linear
+ * solves of the viscous step, the iterates relaxed by Aitken's factor
+ *     omega_k = -omega_{k-1} r_{k-1}.(r_k - r_{k-1}) / ||r_k - r_{k-1}||^2
+ * computed from the full nonlinear residuals r_k = r(u^k). Stops as soon as
+ * ||r^k|| <= rtol ||r^0|| or ||r^k|| <= atol. Each linear solve is the CG of
+ * sipg_solve started from u^k (its initial residual is r^k).
+ * b, u: DEVICE double* on the fine velocity level; u holds the initial guess
+ * (the extrapolation u#) on entry and the last iterate on return. On return
+ * the stored viscosity is nu(u). The first call allocates four fine-level
+ * work vectors that live as long as the context. (sync) */
+int sipg_picard_solve(sipg_ctx* ctx, const sipg_rheology* rh, const double* b, double* u,
+                      const sipg_picard_opts* po, sipg_picard_stats* stats);
+
 /* ------------------------------------------------ multigrid pieces (tests) */
+/* Test hook for the float-float conversions of the SIPG_F64_FF kernels' loads
+ * and stores: hilo[2i], hilo[2i+1] = (RN(x_i), RN(x_i - RN(x_i))) as binary32,
+ * back[i] = hi + lo rounded to binary64. DEVICE buffers of n doubles, 2n
+ * floats and n doubles, on the context's stream (sync). */
+int sipg_ff_convert(sipg_ctx* ctx, const double* x, float* hilo, double* back, int64_t n);
+
 /* Copy the stored viscosity of a level to DEVICE buffers: nu_cell
  * [cells][n^3] and nu_face [cells][6][n^2] (the cell's own side of each face;
  * faces -x,+x,-y,+y,-z,+z; face point a + n b over the face's tangential

@@ -28,7 +28,8 @@ EXPORTS = [
     "sipg_solve", "sipg_get_viscosity", "sipg_get_inverse_diagonal", "sipg_get_lmax_estimate",
     "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points", "sipg_apply_host_static",
     "sipg_estimate_bytes", "sipg_server_create", "sipg_server_submit", "sipg_server_poll", "sipg_server_drain",
-    "sipg_server_last_error", "sipg_server_destroy",
+    "sipg_server_last_error", "sipg_server_destroy", "sipg_mass_apply", "sipg_inverse_mass_apply",
+    "sipg_default_picard_opts", "sipg_picard_solve", "sipg_ff_convert",
 ]
 
 
@@ -61,6 +62,20 @@ class SolveOpts(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class PicardOpts(ctypes.Structure):
+    _fields_ = [("mass_coeff", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("aitken", ctypes.c_int), ("omega_init", ctypes.c_double),
+                ("lin_rtol", ctypes.c_double), ("lin_atol", ctypes.c_double), ("lin_maxit", ctypes.c_int),
+                ("precond", ctypes.c_int)]
+
+
+class PicardStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("lin_iterations", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("history_len", ctypes.c_int), ("residuals", ctypes.POINTER(ctypes.c_double)),
+                ("omegas", ctypes.POINTER(ctypes.c_double))]
 
 
 class ServerOpts(ctypes.Structure):
@@ -122,6 +137,11 @@ def load(path=None):
         "sipg_server_drain": (i, [vp, d]),
         "sipg_server_last_error": (ctypes.c_char_p, [vp]),
         "sipg_server_destroy": (i, [vp]),
+        "sipg_mass_apply": (i, [vp, i, i, vp, vp, d]),
+        "sipg_inverse_mass_apply": (i, [vp, i, i, vp, vp, d]),
+        "sipg_default_picard_opts": (None, [P(PicardOpts)]),
+        "sipg_picard_solve": (i, [vp, P(Rheology), vp, vp, P(PicardOpts), P(PicardStats)]),
+        "sipg_ff_convert": (i, [vp, vp, vp, vp, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -150,6 +150,57 @@ class Context:
         self._check(self._lib.sipg_level_apply(self._h, L.OP[op], level, prec, _ptr(x), _ptr(y), float(mass)))
         return y
 
+    def mass(self, op, x, y=None, coeff=1.0, arith=None, inverse=False):
+        """y = coeff M x (or (coeff M)^-1 x with inverse=True), cell mass matrix of op."""
+        _need_cuda(x)
+        prec = L.PREC[arith or ("f64" if x.dtype == torch.float64 else "f32")]
+        if (prec == L.PREC["f32"]) != (x.dtype == torch.float32):
+            raise TypeError("f32 arithmetic needs float32 vectors, f64/f64ff need float64")
+        if y is None:
+            y = torch.empty_like(x)
+        _need_cuda(y, x.dtype)
+        if x.numel() != self.n_dofs(op) or y.numel() != x.numel():
+            raise ValueError("vector size does not match the fine level")
+        fn = self._lib.sipg_inverse_mass_apply if inverse else self._lib.sipg_mass_apply
+        self._check(fn(self._h, L.OP[op], prec, _ptr(x), _ptr(y), float(coeff)))
+        return y
+
+    def ff_convert(self, x):
+        """Float-float split (hi, lo) and its binary64 recombination, as the kernels do it."""
+        _need_cuda(x, torch.float64)
+        hilo = torch.empty(2 * x.numel(), dtype=torch.float32, device=x.device)
+        back = torch.empty_like(x)
+        self._check(self._lib.sipg_ff_convert(self._h, _ptr(x), _ptr(hilo), _ptr(back), x.numel()))
+        return hilo.view(-1, 2), back
+
+    def picard_solve(self, rheology, b, u, mass=0.0, rtol=1e-6, atol=1e-12, maxit=20, aitken=True,
+                     omega_init=1.0, lin_rtol=1e-3, lin_atol=0.0, lin_maxit=500, precond="mg", check=True):
+        """Nonlinear viscous step by Picard/Aitken; u: initial guess in, last iterate out."""
+        _need_cuda(b, torch.float64)
+        _need_cuda(u, torch.float64)
+        r, keep = rheology_struct(rheology)
+        o = L.PicardOpts()
+        self._lib.sipg_default_picard_opts(ctypes.byref(o))
+        o.mass_coeff, o.rtol, o.atol, o.maxit = float(mass), float(rtol), float(atol), int(maxit)
+        o.aitken, o.omega_init = int(bool(aitken)), float(omega_init)
+        o.lin_rtol, o.lin_atol, o.lin_maxit = float(lin_rtol), float(lin_atol), int(lin_maxit)
+        o.precond = L.PRECOND[precond]
+        cap = int(maxit) + 1
+        res_h = (ctypes.c_double * cap)()
+        om_h = (ctypes.c_double * cap)()
+        st = L.PicardStats()
+        st.history_len = cap
+        st.residuals = ctypes.cast(res_h, ctypes.POINTER(ctypes.c_double))
+        st.omegas = ctypes.cast(om_h, ctypes.POINTER(ctypes.c_double))
+        rc = self._lib.sipg_picard_solve(self._h, ctypes.byref(r), _ptr(b), _ptr(u), ctypes.byref(o),
+                                         ctypes.byref(st))
+        del keep
+        if check and rc not in (L.SIPG_OK, -4):
+            self._check(rc)
+        k = st.iterations
+        return {"status": rc, "iterations": k, "lin_iterations": st.lin_iterations, "res0": st.res0,
+                "res": st.res, "seconds": st.seconds, "residuals": list(res_h[:k + 1]), "omegas": list(om_h[:k])}
+
     def apply_host(self, op, x, mass=0.0):
         x = np.ascontiguousarray(x, dtype=np.float64)
         if x.size != self.n_dofs(op):

@@ -34,6 +34,22 @@ __global__ void split_ff_kernel(int64_t n, const double* __restrict__ in, float2
     out[i] = make_float2(v.hi, v.lo);
   }
 }
+// integer float-float conversions of the streaming kernels, exposed for their test
+__global__ void ff_convert_kernel(int64_t n, const double* __restrict__ in, float2* __restrict__ hilo,
+                                  double* __restrict__ back) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const ff v = stream_load<ff, double>(in[i]);
+    hilo[i] = make_float2(v.hi, v.lo);
+    back[i] = stream_store<double, ff>(v);
+  }
+}
+cudaError_t launch_ff_convert(int64_t n, const double* in, float2* hilo, double* back, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  ff_convert_kernel<<<blocks, 256, 0, st>>>(n, in, hilo, back);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_ff(int64_t n, const double* in, float2* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);

@@ -177,6 +177,7 @@ sipg_ctx::~sipg_ctx() {
     for (double*& p : H.cg) cudaFree(p);
   }
   cudaFree(partials); cudaFree(dscal); cudaFree(dflag); cudaFree(host_x); cudaFree(host_y);
+  for (double* p : pic) cudaFree(p);
   if (hscal) cudaFreeHost(hscal);
 }
 
@@ -495,21 +496,21 @@ int sipg_ctx::setup_operator(int op, double mass) {
 }
 
 // ------------------------------------------------------------ viscosity
-extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const double* u_lin) {
-  if (!ctx || !rh) return SIPG_ERR_INVALID;
-  RheologyDev r{};
+int sipg_ctx::parse_rheology(const sipg_rheology* rh, const double* u_lin, RheologyDev* out) {
+  RheologyDev& r = *out;
+  r = RheologyDev{};
   r.law = rh->law;
   switch (rh->law) {
     case SIPG_LAW_CONSTANT:
-      if (!(rh->nu > 0)) return ctx->fail(SIPG_ERR_INVALID, "constant viscosity must be positive");
+      if (!(rh->nu > 0)) return fail(SIPG_ERR_INVALID, "constant viscosity must be positive");
       r.nu = rh->nu;
       break;
     case SIPG_LAW_ANALYTIC:
       break;
     case SIPG_LAW_SINKER:
       if (rh->n_spheres < 0 || rh->n_spheres > 64 || (rh->n_spheres > 0 && !rh->centers))
-        return ctx->fail(SIPG_ERR_INVALID, "sinker: 0..64 spheres with a host centre array");
-      if (!(rh->nu_max > 0) || !(rh->nu_matrix > 0)) return ctx->fail(SIPG_ERR_INVALID, "sinker viscosities must be positive");
+        return fail(SIPG_ERR_INVALID, "sinker: 0..64 spheres with a host centre array");
+      if (!(rh->nu_max > 0) || !(rh->nu_matrix > 0)) return fail(SIPG_ERR_INVALID, "sinker viscosities must be positive");
       r.n_spheres = rh->n_spheres;
       std::memcpy(r.centers, rh->centers, sizeof(double) * 3 * rh->n_spheres);
       r.radius = rh->radius;
@@ -517,16 +518,22 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
       r.nu_matrix = rh->nu_matrix;
       break;
     case SIPG_LAW_CARREAU:
-      if (!u_lin) return ctx->fail(SIPG_ERR_INVALID, "Carreau-Yasuda viscosity needs the linearization velocity");
+      if (!u_lin) return fail(SIPG_ERR_INVALID, "Carreau-Yasuda viscosity needs the linearization velocity");
       if (!(rh->eta0 > 0) || !(rh->eta_inf >= 0) || !(rh->a > 0))
-        return ctx->fail(SIPG_ERR_INVALID, "Carreau-Yasuda parameters out of range");
+        return fail(SIPG_ERR_INVALID, "Carreau-Yasuda parameters out of range");
       r.eta0 = rh->eta0; r.eta_inf = rh->eta_inf; r.kappa = rh->kappa; r.lambda = rh->lambda;
       r.a = rh->a; r.b = rh->b;
       break;
     default:
-      return ctx->fail(SIPG_ERR_INVALID, "unknown viscosity law");
+      return fail(SIPG_ERR_INVALID, "unknown viscosity law");
   }
-  Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+  return SIPG_OK;
+}
+
+// nu at the quadrature points of every level of the viscous hierarchy (no
+// smoother or coarse setup; the hierarchy is marked stale)
+int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
+  Hier& H = hier[SIPG_OP_VISCOUS];
   for (size_t l = 0; l < H.L.size(); ++l) {
     Level& L = H.L[l];
     const double* u = nullptr;
@@ -537,9 +544,9 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
         Level& F = H.L[l - 1];
         const double* uf = l == 1 ? u_lin : F.ulin;
         cudaError_t e = F.next_kind == 1
-                            ? launch_p_interp_down(F.n, L.n, 3, L.g.ncells, F.interp, uf, L.ulin, ctx->st)
-                            : launch_h_interp_down(L.n, 3, F.g, L.g, F.interp, F.child, uf, L.ulin, ctx->st);
-        if (e) return ctx->fail(SIPG_ERR_CUDA, "interpolate linearization velocity", e);
+                            ? launch_p_interp_down(F.n, L.n, 3, L.g.ncells, F.interp, uf, L.ulin, st)
+                            : launch_h_interp_down(L.n, 3, F.g, L.g, F.interp, F.child, uf, L.ulin, st);
+        if (e) return fail(SIPG_ERR_CUDA, "interpolate linearization velocity", e);
         u = L.ulin;
       }
     }
@@ -547,19 +554,29 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
     if (r.law == SIPG_LAW_SINKER && l > 0) {
       // cellwise-constant field: carried down by the transfer of piecewise constants
       const Level& F = H.L[l - 1];
-      e = launch_cell_nu_transfer(F.g, L.g, F.next_kind, F.n, L.n, F.nu_cell64, L.nu_cell64, L.nu_face64, ctx->st);
+      e = launch_cell_nu_transfer(F.g, L.g, F.next_kind, F.n, L.n, F.nu_cell64, L.nu_cell64, L.nu_face64, st);
     } else {
-      e = launch_viscosity(L.n, L.g, ctx->tabs[L.n], r, u, L.nu_cell64, L.nu_face64, ctx->st);
+      e = launch_viscosity(L.n, L.g, tabs[L.n], r, u, L.nu_cell64, L.nu_face64, st);
     }
-    if (e) return ctx->fail(SIPG_ERR_CUDA, "viscosity kernel", e);
+    if (e) return fail(SIPG_ERR_CUDA, "viscosity kernel", e);
     const int64_t n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
-    e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, ctx->st);
-    if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, ctx->st);
-    if (!e && L.nu_cellff) e = launch_split_ff(L.g.ncells * n3, L.nu_cell64, L.nu_cellff, ctx->st);
-    if (!e && L.nu_faceff) e = launch_split_ff(L.g.ncells * 6 * n2, L.nu_face64, L.nu_faceff, ctx->st);
-    if (e) return ctx->fail(SIPG_ERR_CUDA, "viscosity cast", e);
+    e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, st);
+    if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, st);
+    if (!e && L.nu_cellff) e = launch_split_ff(L.g.ncells * n3, L.nu_cell64, L.nu_cellff, st);
+    if (!e && L.nu_faceff) e = launch_split_ff(L.g.ncells * 6 * n2, L.nu_face64, L.nu_faceff, st);
+    if (e) return fail(SIPG_ERR_CUDA, "viscosity cast", e);
   }
-  ctx->have_nu = true;
+  have_nu = true;
+  H.ready = false;
+  return SIPG_OK;
+}
+
+extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const double* u_lin) {
+  if (!ctx || !rh) return SIPG_ERR_INVALID;
+  RheologyDev r;
+  int rc = ctx->parse_rheology(rh, u_lin, &r);
+  if (rc) return rc;
+  if ((rc = ctx->eval_viscosity(r, u_lin))) return rc;
   return ctx->setup_operator(SIPG_OP_VISCOUS, 0.0);
 }
 
@@ -584,6 +601,37 @@ extern "C" int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, cons
 
 extern "C" int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double mass) {
   return sipg_level_apply(ctx, op, 0, prec, x, y, mass);
+}
+
+int sipg_ctx::mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse) {
+  sipg_ctx* ctx = this;
+  if (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) return fail(SIPG_ERR_INVALID, "unknown operator");
+  if (prec != SIPG_F64 && prec != SIPG_F32 && prec != SIPG_F64_FF) return fail(SIPG_ERR_INVALID, "unknown arithmetic");
+  if (!x || !y) return fail(SIPG_ERR_INVALID, "null vector");
+  if (!std::isfinite(coeff) || (inverse && coeff == 0.0)) return fail(SIPG_ERR_INVALID, "mass coefficient");
+  const Hier& H = hier[op];
+  const Level& L = H.L[0];
+  const double detJ = L.g.h[0] * L.g.h[1] * L.g.h[2];
+  const double scale = inverse ? 1.0 / (coeff * detJ) : coeff * detJ;
+  CK(launch_cell_mass(L.n, H.ncomp, L.g.ncells, tabs[L.n], prec, inverse, scale, x, y, st));
+  return SIPG_OK;
+}
+
+extern "C" int sipg_ff_convert(sipg_ctx* ctx, const double* x, float* hilo, double* back, int64_t n) {
+  if (!ctx || n < 0 || (n > 0 && (!x || !hilo || !back))) return SIPG_ERR_INVALID;
+  CK(launch_ff_convert(n, x, reinterpret_cast<float2*>(hilo), back, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return SIPG_OK;
+}
+
+extern "C" int sipg_mass_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double coeff) {
+  if (!ctx) return SIPG_ERR_INVALID;
+  return ctx->mass_apply(op, prec, x, y, coeff, false);
+}
+
+extern "C" int sipg_inverse_mass_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* y, double coeff) {
+  if (!ctx) return SIPG_ERR_INVALID;
+  return ctx->mass_apply(op, prec, x, y, coeff, true);
 }
 
 extern "C" int sipg_apply_host(sipg_ctx* ctx, int op, const double* xh, double* yh, double mass) {

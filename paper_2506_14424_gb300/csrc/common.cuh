@@ -24,6 +24,8 @@ struct Tab {
   double DS[kMaxN * kMaxN];
   double dS0[kMaxN], dS1[kMaxN];
   double gw[kMaxN], gp[kMaxN], gll[kMaxN];
+  double M1[kMaxN * kMaxN];     // 1D mass matrix sum_q gw_q S[q][i] S[q][j] on [0, 1]
+  double M1inv[kMaxN * kMaxN];  // its inverse
 };
 
 // Embedding matrices of the transfers (prolongation = interpolation of the

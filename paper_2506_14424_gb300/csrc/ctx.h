@@ -8,6 +8,8 @@
 
 namespace sipg {
 
+struct RheologyDev;
+
 struct Level {
   LevelGeom g{};
   int k = 0, n = 0;
@@ -56,6 +58,7 @@ struct sipg_ctx {
   double* host_x = nullptr;
   double* host_y = nullptr;
   int64_t host_n = 0;
+  double* pic[4] = {nullptr};  // Picard work vectors: r_k, r_{k-1}, u^k, r_k - r_{k-1}
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
   int64_t bytes = 0;    // device bytes allocated by the hierarchy
 
@@ -84,4 +87,7 @@ struct sipg_ctx {
   int coarse_solve64(int op);
   int precondition(int op, int kind, const double* r, double* z, double mass);
   int solve(int op, const double* b, double* x, const sipg_solve_opts* so, sipg_solve_stats* stats);
+  int parse_rheology(const sipg_rheology* rh, const double* u_lin, sipg::RheologyDev* out);
+  int eval_viscosity(const sipg::RheologyDev& r, const double* u_lin);
+  int mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse);
 };

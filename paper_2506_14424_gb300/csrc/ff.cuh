@@ -30,6 +30,56 @@ struct ff {
 
 __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// ---- the same conversions with integer instructions, for streaming kernels.
+// The FP64 pipe of this GPU issues about 1.5 instructions per cycle per SM,
+// and ff(double) / to_double put three instructions on it (two F2F, one
+// DADD), which bounds a kernel with little arithmetic per value far below
+// HBM speed. split_double gives the same bits as ff(double) (hi = RN(d),
+// lo = RN(d - hi), both round-to-nearest-even) by assembling them from the
+// fields of d wherever hi and lo are normal floats (|d| in [2^-70, 2^127));
+// elsewhere (zero, tiny, huge, inf, nan) it takes the hardware path.
+// join_double gives the bits of to_double with one FP64 addition.
+__device__ __forceinline__ ff split_double(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
+  if (E < 1023u - 70u || E > 1023u + 126u) return ff(d);
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  // top 23 mantissa bits: bits 51..29 of b = bits 19..0 of hi32 and 31..29 of lo32
+  unsigned hib = sgn | ((E - 1023u + 127u) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+  const unsigned R = lo32 & 0x1FFFFFFFu;  // the 29 bits below hi's last bit
+  const bool up = R > 0x10000000u || (R == 0x10000000u && (hib & 1u));
+  hib += up ? 1u : 0u;  // a mantissa carry moves into the exponent, as it should
+  const unsigned mag = up ? 0x20000000u - R : R;  // |d - hi| in units of 2^(E-1075)
+  if (mag == 0u) return ff(__uint_as_float(hib), 0.0f);
+  const int p = 31 - __clz(mag);  // leading bit of mag, 0..28
+  unsigned q;
+  if (p > 23) {  // round mag to 24 significant bits, nearest even
+    const int sh = p - 23;
+    q = mag >> sh;
+    const unsigned rem = mag & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+  } else {
+    q = mag << (23 - p);
+  }
+  const unsigned ex = (unsigned)((int)E - 1075 + p + 127);
+  const unsigned lsg = up ? sgn ^ 0x80000000u : sgn;
+  const unsigned lob = lsg | ((ex << 23) + (q - 0x800000u));  // q = 2^24 carries into the exponent
+  return ff(__uint_as_float(hib), __uint_as_float(lob));
+}
+
+// exact binary32 -> binary64 by re-biasing the exponent (normal floats and zero)
+__device__ __forceinline__ double widen_float(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned a = b & 0x7FFFFFFFu;
+  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  if (a - 0x00800000u >= 0x7F000000u) return (double)f;  // subnormal, inf, nan
+  return __hiloint2double((int)((b & 0x80000000u) | (((a >> 23) + 896u) << 20) | ((a & 0x7FFFFFu) >> 3)),
+                          (int)(a << 29));
+}
+
+__device__ __forceinline__ double join_double(ff a) { return widen_float(a.hi) + widen_float(a.lo); }
+
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ ff two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
@@ -105,6 +155,16 @@ __device__ __forceinline__ double store_as<double, ff>(ff v) { return to_double(
 }  // namespace sipg
 
 namespace sipg {
+// storage <-> compute conversions of the streaming kernels (integer split)
+template <typename TC, typename TS>
+__device__ __forceinline__ TC stream_load(TS v) { return TC(v); }
+template <>
+__device__ __forceinline__ ff stream_load<ff, double>(double v) { return split_double(v); }
+template <typename TS, typename TC>
+__device__ __forceinline__ TS stream_store(TC v) { return TS(v); }
+template <>
+__device__ __forceinline__ double stream_store<double, ff>(ff v) { return join_double(v); }
+
 template <typename T>
 __device__ __forceinline__ T from_double(double d) { return T(d); }
 template <>

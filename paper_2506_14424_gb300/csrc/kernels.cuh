@@ -13,11 +13,17 @@ cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, c
 cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
                             const float2* nu_cell, const float2* nu_face, double mass, int nbatch, cudaStream_t st);
 cudaError_t launch_split_ff(int64_t n, const double* in, float2* out, cudaStream_t st);
+cudaError_t launch_ff_convert(int64_t n, const double* in, float2* hilo, double* back, cudaStream_t st);
 // float-float applies of several problems of one degree in one persistent launch;
 // descs: device array of ApplyDesc<double, ff> (operator.cuh), tiles: (problem, cell0)
 cudaError_t launch_apply_multi_ff(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
                                   const Tab& tab, cudaStream_t st);
 int op_cells_per_cta(int n, int ncomp);
+
+// ---- cell mass matrix and its inverse (mass.cu): y = scale (M1 (x) M1 (x) M1) x per
+// component and cell, or with M1^-1; arith 0 FP64, 1 FP32, 2 float-float (FP64 storage)
+cudaError_t launch_cell_mass(int n, int ncomp, int ncells, const Tab& tab, int arith, bool inverse, double scale,
+                             const void* x, void* y, cudaStream_t st);
 
 // ---- viscosity (viscosity.cu)
 struct RheologyDev {

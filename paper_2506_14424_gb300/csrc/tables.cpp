@@ -3,6 +3,7 @@
 #include "tables.h"
 
 #include <cmath>
+#include <utility>
 #include <vector>
 
 namespace sipg {
@@ -111,6 +112,39 @@ Tab make_tab(int n) {
     T.gp[j] = gp[j];
     T.gll[j] = gll[j];
   }
+  // 1D mass matrix with the n-point Gauss rule, and its inverse by Gauss-Jordan
+  // elimination with partial pivoting (symmetric positive definite, n <= 6)
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += gw[q] * T.S[q * n + i] * T.S[q * n + j];
+      T.M1[i * n + j] = s;
+    }
+  std::vector<double> a(T.M1, T.M1 + n * n), inv(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[p * n + c])) p = r;
+    for (int j = 0; j < n; ++j) {
+      std::swap(a[c * n + j], a[p * n + j]);
+      std::swap(inv[c * n + j], inv[p * n + j]);
+    }
+    const double d = a[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      a[c * n + j] /= d;
+      inv[c * n + j] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[r * n + c];
+      for (int j = 0; j < n; ++j) {
+        a[r * n + j] -= f * a[c * n + j];
+        inv[r * n + j] -= f * inv[c * n + j];
+      }
+    }
+  }
+  for (int i = 0; i < n * n; ++i) T.M1inv[i] = inv[i];
   return T;
 }
 
