@@ -26,6 +26,10 @@ for fluids with variable viscosity"):
                    Eqs. convective_step_weak / projection_step_weak).
 * ``nonlinear``    Picard iteration of the viscosity with Aitken relaxation
                    (Sec. 5.4, Alg. 1).
+* ``splitting``    one step of the projection scheme on a box: BDF, explicit
+                   convective step, pressure Poisson step with the consistent
+                   Neumann datum, projection, viscous step, CFL time step
+                   (Sec. 3.2 / 5.1, Alg. 1).
 
 Parity status: see the header of each module. The multigrid V-cycle as a whole
 is "parity unpinned" against the paper (the paper prints no iteration counts

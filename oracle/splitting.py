@@ -1,0 +1,362 @@
+"""One time step of the dual splitting (projection) scheme on a box (oracle, test infrastructure).
+
+Sec. 3.2 / 5.1 / 5.4, Alg. 1 of the paper, with the convective term explicit
+(alpha_c = 0), on a box of affine hexahedra whose six walls carry steady
+Dirichlet velocity data g (one constant vector per box face: no-slip walls, or
+the moving lid of a cavity). Every form below is evaluated element by element
+with explicit basis functions at the Gauss points, as written in the paper:
+
+* BDF-m and extrapolation coefficients (textbook values, "see Hairer1993";
+  READING: BDF1 = (1; 1; 1), BDF2 = (3/2; 2, -1/2; 2, -1); the first step of a
+  run uses BDF1, then BDF2 - "sequentially increasing the order").
+* Convective term, Eq. (convective_term_weak), w = u:
+      c_h(v, u; w) = (v, (w.grad) u)_e - (v, ({{w}}.n) u)_de + (v, ({{w}}.n) u^dag)_de,
+      u^dag = {{u}} + 1/2 sign({{w}}.n) [u],   [u] = u^- - u^+,
+  with the mirror principle on Dirichlet faces (u^+ = -u^- + 2g, and w^+ alike).
+* Convective step, Eq. (convective_step_weak):
+      (gamma0/dt) M uhat = M b + sum_i (alpha_i/dt) M u^{n-i} - sum_i beta_i C(u^{n-i}).
+  READING: the body force b is given by its interpolant b_h in the velocity space.
+* Pressure step, Eq. (pressure_step_weak): the SIPG Laplacian (oracle.sipg)
+  against the right-hand side
+      (gamma0/dt) [ (grad q, uhat)_e - (q, {{uhat}}.n)_de ]
+  where on Dirichlet faces {{uhat}} = g_uhat of Eq. (guhat_consistent_BC) and the
+  Neumann datum h_p of Eq. (pressure_Neumann_BC) enters as +(q, h_p)_GammaD
+  (the average normal gradient of the mirrored pressure equals h_p). Hence on a
+  Dirichlet face the integrand is  h_p - (gamma0/dt) g_uhat.n.
+      g_uhat = (dt/gamma0) b - (dt/gamma0) sum_{i<m} beta_i (u^{n-i}.grad)u^{n-i}
+               + sum_{i<m} (alpha_i/gamma0) g
+      h_p = n.b - n.d_t g - sum_{i<m_p} betabar_i n.(u^{n-i}.grad)u^{n-i}
+            - nu^dd n.(curl omega^dd) + 2 n.(eps(u^dd) grad nu^dd)
+  with m_p = min(m - 1, 2), u^dd = sum_{i<m_p} betabar_i u^{n-i} (betabar the
+  extrapolation coefficients of order m_p), nu^dd = eta(gamma_dot(eps(u^dd)))
+  pointwise, omega^dd the element-local L2 projection of curl u^dd onto Q_k
+  (Sec. 5.1, vorticity projection of Alg. 1). d_t g = 0 (steady data; the
+  paper's BDF approximation of d_t g gives exactly 0 for constant g).
+  READINGS: (i) the convective sum in h_p is written with beta_i but runs to
+  m_p - 1; the order-m_p coefficients betabar_i are taken (consistent
+  extrapolation); (ii) grad nu^dd is the gradient of the element-local L2
+  projection of nu^dd onto Q_k (the paper does not say how it is formed; the
+  same mechanism as the vorticity); (iii) the traces in h_p and g_uhat are the
+  interior (own cell) traces.
+  The pure-Neumann pressure problem (velocity Dirichlet on every wall) is made
+  solvable by a mean-free right-hand side and solved for the mean-free
+  solution (Sec. 3.2).
+* Projection step, Eq. (projection_step_weak):
+      (gamma0/dt) M uhathat = (gamma0/dt) M uhat + (div v, p)_e - (v, {{p}} n)_de,
+  {{p}} = p^- on velocity-Dirichlet (pressure-Neumann) faces.
+* Viscous step, Eq. (viscous_step_weak) with alpha_c = 0:
+      ((gamma0/dt) M + A(nu)) u^{n+1} = (gamma0/dt) M uhathat + D(g, nu),
+  D the Dirichlet data terms of the SIPG viscous form (mirror u^+ = -u^- + 2g):
+      D_a = -(2 nu eps(phi_a) n, g)_GammaD + (2 tau, phi_a.g + (phi_a.n)(g.n))_GammaD.
+  nu "linear implicit" = eta(gamma_dot(eps(u^#))), u^# = sum_{i<m} beta_i u^{n-i}
+  (Alg. 1 then leaves its loop after one pass), or "implicit" by the
+  Picard/Aitken loop of oracle.nonlinear.
+* Time step, Eq. (CFL_timestep_selection): dt = Cr / k^1.5 / max_{e,q} |J^-1 u|.
+
+The oracle solves every linear system exactly (sparse LU; the pressure with a
+rank-one term that fixes the mean). Pins: tests/test_oracle_splitting.py.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import mass as omass
+from . import nonlinear
+from . import viscosity
+from .mesh import BoxMesh
+from .sipg import SIPG, _sym
+
+BDF = {1: (1.0, (1.0,), (1.0,)), 2: (1.5, (2.0, -0.5), (2.0, -1.0))}
+EXTRAP = {0: (), 1: (1.0,), 2: (2.0, -1.0)}
+
+
+def face_normal(f):
+    d, s = divmod(f, 2)
+    n = np.zeros(3)
+    n[d] = 2.0 * s - 1.0
+    return d, s, n
+
+
+def _cell(S, x, e):
+    return np.asarray(x).reshape(S.mesh.n_cells, S.ncomp, S.n ** 3)[e]
+
+
+def _values(phi, U):
+    """values (P, ncomp) of nodal coefficients U (ncomp, n^3) at points with basis phi (P, n^3)."""
+    return np.einsum('pi,ci->pc', phi, U)
+
+
+def _grads(S, dphi, U):
+    """gradients G[p, c, l] = d u_c / d x_l."""
+    return np.einsum('pil,ci->pcl', S._phys_grad(dphi), U)
+
+
+def wall_data(S, g_faces, e, f):
+    """Dirichlet datum g at the face points of (e, f): a constant vector per box face, or a
+    callable of the points (used by the consistency pins)."""
+    g = g_faces[f] if g_faces is not None else np.zeros(3)
+    if callable(g):
+        return np.asarray(g(S.face_points(e, f)), dtype=np.float64)
+    return np.broadcast_to(np.asarray(g, dtype=np.float64), (S.nq ** 2, 3))
+
+
+def _exterior(S, x, e, f, g_faces):
+    """Trace values and gradients of the exterior state at the face points of (e, f)."""
+    mesh = S.mesh
+    d, s, nvec = face_normal(f)
+    U = _cell(S, x, e)
+    um, Gm = _values(S.face_phi[f], U), _grads(S, S.face_dphi[f], U)
+    bt = mesh.boundary_type(e, f)
+    if bt == 'I':
+        nb = mesh.neighbor(e, f)
+        fo = 2 * d + (1 - s)
+        Un = _cell(S, x, nb)
+        return um, Gm, _values(S.face_phi[fo], Un), _grads(S, S.face_dphi[fo], Un), bt
+    if bt == 'D':
+        g = wall_data(S, g_faces, e, f)
+        return um, Gm, -um + 2.0 * g, Gm, bt
+    return um, Gm, um, Gm, bt
+
+
+def convective_vector(S, u, g_faces):
+    """C_a = sum_e c_h(phi_a, u; u) (velocity space S, ncomp = 3)."""
+    C = S.mesh.n_cells
+    out = np.zeros((C, 3, S.n ** 3))
+    W = S.cell_w * S.mesh.volume()
+    for e in range(C):
+        U = _cell(S, u, e)
+        uq, Gq = _values(S.cell_phi, U), _grads(S, S.cell_dphi, U)
+        conv = np.einsum('pl,pcl->pc', uq, Gq)
+        out[e] += np.einsum('p,pi,pc->ci', W, S.cell_phi, conv)
+        for f in range(6):
+            d, s, nvec = face_normal(f)
+            um, _, up, _, bt = _exterior(S, u, e, f, g_faces)
+            wn = 0.5 * (um + up) @ nvec
+            udag = 0.5 * (um + up) + 0.5 * np.sign(wn)[:, None] * (um - up)
+            flux = wn[:, None] * (udag - um)
+            Wf = S.face_w2 * S.mesh.face_area(d)
+            out[e] += np.einsum('p,pi,pc->ci', Wf, S.face_phi[f], flux)
+    return out.reshape(-1)
+
+
+def convective_at_face(S, u, e, f):
+    """(u.grad) u at the face points of (e, f) from the cell's own trace."""
+    U = _cell(S, u, e)
+    return np.einsum('pl,pcl->pc', _values(S.face_phi[f], U), _grads(S, S.face_dphi[f], U))
+
+
+def l2_project_cell(S, e, values):
+    """Element-local L2 projection onto Q_k of point values (P,) or (P, c) at the cell Gauss points."""
+    W = S.cell_w * S.mesh.volume()
+    phi = S.cell_phi
+    Ms = np.einsum('p,pi,pj->ij', W, phi, phi)
+    v = values if values.ndim == 2 else values[:, None]
+    rhs = np.einsum('p,pi,pc->ic', W, phi, v)
+    coef = np.linalg.solve(Ms, rhs)  # (n^3, c)
+    return coef.T if values.ndim == 2 else coef[:, 0]
+
+
+def _curl(G):
+    return np.stack([G[:, 2, 1] - G[:, 1, 2], G[:, 0, 2] - G[:, 2, 0], G[:, 1, 0] - G[:, 0, 1]], axis=1)
+
+
+def viscous_boundary_terms(S, e, f, u_dd, rheology):
+    """-nu n.(curl omega) + 2 n.(eps(u) grad nu) at the face points of (e, f) for the field u_dd."""
+    d, s, nvec = face_normal(f)
+    U = _cell(S, u_dd, e)
+    Gc = _grads(S, S.cell_dphi, U)
+    omega = l2_project_cell(S, e, _curl(Gc))                       # (3, n^3)
+    Gw = _grads(S, S.face_dphi[f], omega)
+    curl_omega = _curl(Gw)
+    Gf = _grads(S, S.face_dphi[f], U)
+    pts_f = S.face_points(e, f)
+    nu_f = viscosity.evaluate(rheology, pts_f, Gf)
+    nu_c = viscosity.evaluate(rheology, S.cell_points(e), Gc)
+    nu_coef = l2_project_cell(S, e, nu_c)                          # (n^3,)
+    grad_nu = np.einsum('pil,i->pl', S._phys_grad(S.face_dphi[f]), nu_coef)
+    eps = viscosity.strain_rate(Gf)
+    return -nu_f * (curl_omega @ nvec) + 2.0 * np.einsum('l,plk,pk->p', nvec, eps, grad_nu)
+
+
+def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology):
+    """h_p - (gamma0/dt) g_uhat.n at the face points of the Dirichlet face (e, f).
+
+    hist: [u^n, u^{n-1}, ...] (velocity DoF vectors), body: b_h DoF vector or None."""
+    gamma0, alpha, beta = BDF[order]
+    m_p = min(order - 1, 2)
+    betabar = EXTRAP[m_p]
+    d, s, nvec = face_normal(f)
+    P = S.nq ** 2
+    nb = np.zeros(P)
+    if body is not None:
+        nb = _values(S.face_phi[f], _cell(S, body, e)) @ nvec
+    g = wall_data(S, g_faces, e, f)
+    conv_m = sum(beta[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(order))
+    conv_mp = sum((betabar[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(m_p)), np.zeros(P))
+    visc = np.zeros(P)
+    if m_p > 0:
+        u_dd = sum(betabar[i] * np.asarray(hist[i]) for i in range(m_p))
+        visc = viscous_boundary_terms(S, e, f, u_dd, rheology)
+    h_p = nb - 0.0 - conv_mp + visc   # d_t g = 0 for steady data
+    g_uhat_n = dt / gamma0 * nb - dt / gamma0 * conv_m + sum(alpha[i] / gamma0 for i in range(order)) * (g @ nvec)
+    return h_p - gamma0 / dt * g_uhat_n
+
+
+def ppe_rhs(Su, Sp, uhat, coef, boundary):
+    """(gamma0/dt)[(grad q, uhat) - (q, {{uhat}}.n)] with the Dirichlet-face integrand replaced
+    by ``boundary[(e, f)]`` (P,) values. Sp: pressure space with Su's Gauss rule."""
+    mesh = Su.mesh
+    C = mesh.n_cells
+    out = np.zeros((C, Sp.n ** 3))
+    W = Su.cell_w * mesh.volume()
+    for e in range(C):
+        uq = _values(Su.cell_phi, _cell(Su, uhat, e))
+        out[e] += coef * np.einsum('p,pil,pl->i', W, Sp._phys_grad(Sp.cell_dphi), uq)
+        for f in range(6):
+            d, s, nvec = face_normal(f)
+            Wf = Su.face_w2 * mesh.face_area(d)
+            bt = mesh.boundary_type(e, f)
+            if bt == 'I':
+                um, _, up, _, _ = _exterior(Su, uhat, e, f, None)
+                out[e] -= coef * np.einsum('p,pi,p->i', Wf, Sp.face_phi[f], 0.5 * (um + up) @ nvec)
+            elif bt == 'D':
+                out[e] += np.einsum('p,pi,p->i', Wf, Sp.face_phi[f], boundary[(e, f)])
+    return out.reshape(-1)
+
+
+def projection_rhs(Su, Sp, p):
+    """(div v, p)_e - (v, {{p}} n)_de for the velocity test functions."""
+    mesh = Su.mesh
+    C = mesh.n_cells
+    out = np.zeros((C, 3, Su.n ** 3))
+    W = Su.cell_w * mesh.volume()
+    for e in range(C):
+        pq = Sp.cell_phi @ _cell(Sp, p, e)[0]
+        out[e] += np.einsum('p,pic,p->ci', W, Su._phys_grad(Su.cell_dphi), pq)
+        for f in range(6):
+            d, s, nvec = face_normal(f)
+            Wf = Su.face_w2 * mesh.face_area(d)
+            pm = Sp.face_phi[f] @ _cell(Sp, p, e)[0]
+            bt = mesh.boundary_type(e, f)
+            if bt == 'I':
+                nb = mesh.neighbor(e, f)
+                fo = 2 * d + (1 - s)
+                pavg = 0.5 * (pm + Sp.face_phi[fo] @ _cell(Sp, p, nb)[0])
+            elif bt == 'D':
+                pavg = pm
+            else:
+                continue
+            out[e] -= np.einsum('p,pi,p,c->ci', Wf, Su.face_phi[f], pavg, nvec)
+    return out.reshape(-1)
+
+
+def viscous_dirichlet_rhs(S, nu_face, g_faces):
+    """D_a = -(2 nu eps(phi_a) n, g) + (2 tau, phi_a.g + (phi_a.n)(g.n)) over Dirichlet faces."""
+    mesh = S.mesh
+    C = mesh.n_cells
+    out = np.zeros((C, 3 * S.n ** 3))
+    for e in range(C):
+        for f in range(6):
+            if mesh.boundary_type(e, f) != 'D':
+                continue
+            g = wall_data(S, g_faces, e, f)
+            if not np.any(g):
+                continue
+            d, s, nvec = face_normal(f)
+            Wf = S.face_w2 * mesh.face_area(d)
+            Vt, Gt = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
+            num = nu_face[e, f]
+            tau = S._tau(e, None, num, num)
+            epsn = np.einsum('pakl,l->pak', _sym(Gt), nvec)
+            out[e] -= np.einsum('p,p,pak,pk->a', Wf, 2.0 * num, epsn, g)
+            out[e] += np.einsum('p,p,pa->a', Wf, 2.0 * tau, np.einsum('pak,pk->pa', Vt, g)
+                                + np.einsum('pak,k->pa', Vt, nvec) * (g @ nvec)[:, None])
+    return out.reshape(-1)
+
+
+def cfl_dt(S, u, Cr):
+    """Eq. (CFL_timestep_selection): Cr / k^1.5 / max_{e,q} |J^-1 u|."""
+    vmax = 0.0
+    for e in range(S.mesh.n_cells):
+        uq = _values(S.cell_phi, _cell(S, u, e)) / S.mesh.h[None, :]
+        vmax = max(vmax, float(np.sqrt((uq ** 2).sum(axis=1)).max()))
+    return Cr / S.k ** 1.5 / vmax
+
+
+def pressure_solve(Sp_op, rhs):
+    """Mean-free solution of the all-Neumann SIPG Laplacian with a mean-free right-hand side."""
+    A = Sp_op.assemble().tocsc()
+    N = A.shape[0]
+    r = rhs - rhs.mean()
+    c = float(A.diagonal().mean()) / N
+    one = np.ones((N, 1))
+    K = (A + sp.csc_matrix(c * (one @ one.T))).tocsc()
+    return spla.spsolve(K, r)
+
+
+class Splitting:
+    """State and one-step driver of the projection scheme on a box."""
+
+    def __init__(self, mesh, k, rheology, g_faces=None, body=None, viscosity_mode='linear', penalty_factor=1.0):
+        self.mesh, self.k = mesh, int(k)
+        self.rheology = rheology
+        self.g_faces = [np.zeros(3) if g_faces is None else
+                        (g_faces[f] if callable(g_faces[f]) else np.asarray(g_faces[f], float)) for f in range(6)]
+        self.Su = SIPG(mesh, k, 3, penalty_factor=penalty_factor)
+        self.Sp = SIPG(mesh, k - 1, 1, penalty_factor=penalty_factor, n_quad=k + 1)   # mixed forms
+        # the pressure is Neumann where the velocity is Dirichlet and vice versa (Sec. 3.2)
+        pbc = tuple('N' if b == 'D' else 'D' for b in mesh.bc)
+        self.pmesh = BoxMesh(*mesh.n_cells_dir, extent=mesh.extent, bc=pbc)
+        self.Sp_op = SIPG(self.pmesh, k - 1, 1, penalty_factor=penalty_factor)      # PPE operator
+        self.body = None if body is None else np.asarray(body, dtype=np.float64)
+        self.mode = viscosity_mode
+        self.hist = []
+        self.p = None
+        self.steps = 0
+
+    def set_initial(self, u0, p0=None):
+        self.hist = [np.array(u0, dtype=np.float64)]
+        self.p = np.zeros(self.Sp_op.n_dofs) if p0 is None else np.array(p0, dtype=np.float64)
+        self.steps = 0
+
+    def step(self, dt, picard=None):
+        Su, Sp = self.Su, self.Sp
+        order = min(2, len(self.hist))
+        gamma0, alpha, beta = BDF[order]
+        hist = self.hist
+        # convective step
+        rhs = sum(alpha[i] / dt * omass.apply_mass(Su, hist[i]) for i in range(order))
+        if self.body is not None:
+            rhs = rhs + omass.apply_mass(Su, self.body)
+        rhs = rhs - sum(beta[i] * convective_vector(Su, hist[i], self.g_faces) for i in range(order))
+        uhat = omass.apply_inverse_mass(Su, rhs, gamma0 / dt)
+        # pressure step
+        bnd = {}
+        for e in range(self.mesh.n_cells):
+            for f in range(6):
+                if self.mesh.boundary_type(e, f) == 'D':
+                    bnd[(e, f)] = ppe_boundary_datum(Su, e, f, hist, order, dt, self.body, self.g_faces,
+                                                     self.rheology)
+        rp = ppe_rhs(Su, Sp, uhat, gamma0 / dt, bnd)
+        p = pressure_solve(self.Sp_op, rp)
+        # projection step
+        uhh = uhat + omass.apply_inverse_mass(Su, projection_rhs(Su, Sp, p), gamma0 / dt)
+        # viscous step
+        m = gamma0 / dt
+        u_sharp = sum(beta[i] * hist[i] for i in range(order))
+        nc, nf = Su.viscosity_at_points(self.rheology, u_sharp)
+        b = omass.apply_mass(Su, uhh, m)
+        if picard is None:
+            b = b + viscous_dirichlet_rhs(Su, nf, self.g_faces)
+            u_new = spla.spsolve(Su.assemble(nc, nf, mass=m).tocsc(), b)
+            info = None
+        else:
+            if any(callable(g) or np.any(g) for g in self.g_faces):
+                raise ValueError("the implicit-viscosity step is built for zero wall velocity")
+            info = nonlinear.viscous_step_picard(Su, self.rheology, b, u_sharp, m, **picard)
+            u_new = info['u']
+        self.hist = [u_new] + hist[:1]
+        self.p = p
+        self.steps += 1
+        return {'uhat': uhat, 'p': p, 'uhathat': uhh, 'u': u_new, 'order': order, 'picard': info,
+                'ppe_rhs': rp}

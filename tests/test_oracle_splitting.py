@@ -1,0 +1,156 @@
+"""Pins for the oracle's splitting step (Sec. 3.2 / 5.1, Alg. 1) on a box.
+
+* convective term: for a continuous linear field with matching wall data the
+  face terms vanish and c_h(v, u; u) = (v, (u.grad)u) exactly; across a face
+  between two constant states the upwind flux charges the downstream cell with
+  ({{w}}.n)(u^+ - u^-) and the upstream cell with nothing (closed form);
+* vorticity / viscous Neumann datum: -nu n.curl curl u for u = (y^2, 0, 0)
+  in closed form;
+* divergence and gradient forms: for continuous polynomials with matching
+  boundary values they integrate by parts exactly,
+  (grad q, u) - (q, u.n) = -(q, div u) and (div v, p) - (v, p n) = -(v, grad p);
+* Dirichlet data of the viscous step: A u_I = D(g = u) for a linear velocity
+  (Galerkin consistency with inhomogeneous walls);
+* CFL time step in closed form for a uniform field;
+* whole steps: a uniform flow with matching wall velocity and a fluid at rest
+  under a gradient body force (hydrostatic: the pressure takes the force, the
+  velocity stays zero, p = z up to its mean) are preserved exactly by BDF1 and
+  BDF2 steps - which pins the consistent pressure Neumann datum against the
+  boundary value of uhat, the PPE, the projection and the viscous step.
+"""
+import numpy as np
+import pytest
+
+from oracle import mass as omass
+from oracle import splitting as osp
+from oracle.mesh import BoxMesh
+from oracle.sipg import SIPG
+
+
+def _interp_vec(S, fn):
+    return S.interpolate(fn)
+
+
+def test_convective_linear_field_exact():
+    mesh = BoxMesh(2, 2, 1, extent=(1.0, 0.8, 0.5))
+    S = SIPG(mesh, 2, 3)
+    A = np.array([[0.3, -0.2, 0.1], [0.5, 0.2, -0.4], [0.1, 0.3, -0.5]])
+    c0 = np.array([0.2, -0.1, 0.3])
+    ufn = lambda x: x @ A.T + c0
+    u = _interp_vec(S, ufn)
+    g = [ufn] * 6
+    C = osp.convective_vector(S, u, g)
+    ref = omass.apply_mass(S, _interp_vec(S, lambda x: ufn(x) @ A.T))
+    assert np.abs(C - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_upwind_flux_between_constant_states():
+    mesh = BoxMesh(2, 1, 1, extent=(2.0, 1.0, 1.0))
+    S = SIPG(mesh, 2, 3)
+    a, b = 1.5, 0.5
+    n3 = S.n ** 3
+    u = np.zeros((2, 3, n3))
+    u[0, 0] = a
+    u[1, 0] = b
+    C = osp.convective_vector(S, u.reshape(-1), [np.zeros(3)] * 6).reshape(2, 3, n3)
+    # partition of unity: the row sum of a component is the integral of its flux
+    assert abs(C[0, 0].sum()) <= 1e-14
+    assert abs(C[1, 0].sum() - (-(a + b) / 2.0 * (a - b) * 1.0)) <= 1e-13
+    assert np.abs(C[:, 1:]).max() <= 1e-14
+
+
+def test_viscous_neumann_datum_closed_form():
+    mesh = BoxMesh(2, 2, 2)
+    S = SIPG(mesh, 3, 3)
+    u = _interp_vec(S, lambda x: np.stack([x[:, 1] ** 2, 0 * x[:, 0], 0 * x[:, 0]], axis=1))
+    rh = {'law': 'constant', 'nu': 0.7}
+    for f in range(6):
+        e = 0 if f % 2 == 0 else mesh.n_cells - 1
+        val = osp.viscous_boundary_terms(S, e, f, u, rh)
+        _, _, nvec = osp.face_normal(f)
+        # curl curl (y^2, 0, 0) = (-2, 0, 0)
+        assert np.abs(val - (-0.7 * (-2.0 * nvec[0]))).max() <= 1e-12
+
+
+def test_divergence_and_gradient_forms_integrate_by_parts():
+    mesh = BoxMesh(2, 3, 2, extent=(1.0, 1.2, 0.7))
+    k = 3
+    Su = SIPG(mesh, k, 3)
+    Sp = SIPG(mesh, k - 1, 1, n_quad=k + 1)
+    ufn = lambda x: np.stack([x[:, 0] ** 2 * x[:, 1], x[:, 2] ** 3, x[:, 0] * x[:, 1] * x[:, 2]], axis=1)
+    divfn = lambda x: 2 * x[:, 0] * x[:, 1] + x[:, 0] * x[:, 1]
+    u = Su.interpolate(ufn)
+    bnd = {}
+    for e in range(mesh.n_cells):
+        for f in range(6):
+            if mesh.boundary_type(e, f) == 'D':
+                _, _, nvec = osp.face_normal(f)
+                bnd[(e, f)] = -2.0 * ufn(Su.face_points(e, f)) @ nvec
+    r = osp.ppe_rhs(Su, Sp, u, 2.0, bnd)
+    Spp = SIPG(mesh, k - 1, 1)
+    # -(q, div u) by a (k+3)-point rule on every cell
+    Sq = SIPG(mesh, k - 1, 1, n_quad=k + 3)
+    ref = np.zeros(Sq.n_dofs).reshape(mesh.n_cells, -1)
+    for e in range(mesh.n_cells):
+        ref[e] = -2.0 * np.einsum('p,pi,p->i', Sq.cell_w * mesh.volume(), Sq.cell_phi, divfn(Sq.cell_points(e)))
+    assert np.abs(r - ref.reshape(-1)).max() <= 1e-13 * np.abs(ref).max()
+    # gradient form with a continuous pressure of degree k-1
+    pfn = lambda x: x[:, 0] * x[:, 1] ** 2 - x[:, 2]
+    gradp = lambda x: np.stack([x[:, 1] ** 2, 2 * x[:, 0] * x[:, 1], -np.ones(len(x))], axis=1)
+    p = Spp.interpolate(pfn)
+    r = osp.projection_rhs(Su, Sp, p)
+    ref = -omass.apply_mass(Su, Su.interpolate(gradp))
+    assert np.abs(r - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_viscous_dirichlet_data_consistency():
+    mesh = BoxMesh(2, 2, 2)
+    S = SIPG(mesh, 2, 3)
+    B = np.array([[0.2, 0.5, -0.1], [0.0, -0.3, 0.4], [0.6, 0.1, 0.1]])
+    ufn = lambda x: x @ B.T + np.array([0.1, 0.2, -0.3])
+    rh = {'law': 'constant', 'nu': 1.3}
+    nc, nf = S.viscosity_at_points(rh)
+    u = S.interpolate(ufn)
+    lhs = S.apply(u, nc, nf)
+    D = osp.viscous_dirichlet_rhs(S, nf, [ufn] * 6)
+    assert np.abs(lhs - D).max() <= 1e-12 * np.abs(D).max()
+
+
+def test_cfl_closed_form():
+    mesh = BoxMesh(4, 2, 5)
+    S = SIPG(mesh, 3, 3)
+    U = np.array([1.0, -2.0, 0.5])
+    u = S.interpolate(lambda x: np.broadcast_to(U, x.shape).copy())
+    dt = osp.cfl_dt(S, u, 0.4)
+    assert abs(dt - 0.4 / 3 ** 1.5 / np.linalg.norm(U * np.array([4, 2, 5]))) <= 1e-14
+
+
+@pytest.mark.parametrize("law", [{'law': 'constant', 'nu': 0.05},
+                                 {'law': 'carreau', 'eta0': 1.0, 'eta_inf': 1e-3, 'kappa': 1.0, 'lam': 1.0,
+                                  'a': 2.0, 'b': 0.5}])
+def test_uniform_flow_preserved(law):
+    mesh = BoxMesh(2, 2, 2)
+    U = np.array([0.4, -0.3, 0.2])
+    sp = osp.Splitting(mesh, 2, law, g_faces=[U] * 6)
+    u0 = sp.Su.interpolate(lambda x: np.broadcast_to(U, x.shape).copy())
+    sp.set_initial(u0)
+    for _ in range(2):
+        out = sp.step(0.05)
+        assert np.abs(out['u'] - u0).max() <= 1e-12
+        assert np.abs(out['p']).max() <= 1e-11
+
+
+def test_hydrostatic_state_preserved():
+    mesh = BoxMesh(2, 2, 3)
+    k = 3
+    rh = {'law': 'carreau', 'eta0': 1.0, 'eta_inf': 1e-3, 'kappa': 1.0, 'lam': 1.0, 'a': 2.0, 'b': 0.5}
+    Su = SIPG(mesh, k, 3)
+    body = Su.interpolate(lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], np.ones(len(x))], axis=1))
+    sp = osp.Splitting(mesh, k, rh, body=body)
+    sp.set_initial(np.zeros(Su.n_dofs))
+    pz = SIPG(mesh, k - 1, 1).interpolate(lambda x: x[:, 2])
+    pz = pz - pz.mean()
+    for _ in range(2):
+        out = sp.step(0.02)
+        assert np.abs(out['u']).max() <= 1e-12
+        assert np.abs(out['p'] - pz).max() <= 1e-11
