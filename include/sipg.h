@@ -256,6 +256,77 @@ void sipg_default_picard_opts(sipg_picard_opts* o);
 int sipg_picard_solve(sipg_ctx* ctx, const sipg_rheology* rh, const double* b, double* u,
                       const sipg_picard_opts* po, sipg_picard_stats* stats);
 
+/* ------------------------------------ one step of the projection scheme */
+/* Box with velocity-Dirichlet walls on all six sides (pressure Neumann there),
+ * steady wall velocity g constant per box side (no-slip walls: zero; a
+ * lid-driven cavity: the lid's tangential velocity), convective term explicit
+ * (Sec. 3.2 / 5.1, Alg. 1):
+ *  1 convective step  (gamma0/dt) M uhat = M b + sum_i alpha_i/dt M u^{n-i}
+ *                                          - sum_i beta_i C(u^{n-i}),
+ *    C = c_h(., u; u) of Eq. (convective_term_weak) with the upwind flux;
+ *  2 pressure step    SIPG Laplacian p = (gamma0/dt)[(grad q, uhat) - (q, {{uhat}}.n)],
+ *    on the walls the consistent Neumann datum h_p (Eq. pressure_Neumann_BC,
+ *    vorticity and viscosity by element-local L2 projection onto Q_k) against
+ *    g_uhat (Eq. guhat_consistent_BC); solved by MG-CG, mean-free;
+ *  3 projection step  (gamma0/dt) M uhathat = (gamma0/dt) M uhat + (div v, p) - (v, {{p}} n);
+ *  4 viscous step     ((gamma0/dt) M + A(nu)) u^{n+1} = (gamma0/dt) M uhathat + wall-data terms,
+ *    nu = eta(gamma_dot(eps(u#))) with u# the extrapolation of order m (linear
+ *    implicit), or the Picard/Aitken loop of sipg_picard_solve (implicit; zero
+ *    wall velocity only).
+ * BDF1 for the first step after sipg_step_init, BDF2 afterwards (gamma0 = 3/2,
+ * alpha = (2, -1/2), beta = (2, -1)). Laws: SIPG_LAW_CONSTANT or SIPG_LAW_CARREAU. */
+enum { SIPG_VISC_LINEAR_IMPLICIT = 0, SIPG_VISC_IMPLICIT = 1 };
+enum { SIPG_FIELD_U = 0, SIPG_FIELD_P = 1, SIPG_FIELD_UHAT = 2, SIPG_FIELD_UHATHAT = 3, SIPG_FIELD_PPE_RHS = 4,
+       SIPG_FIELD_U_PREV = 5 };
+
+typedef struct {
+  double dt;                 /* time step (constant; sipg_cfl_dt gives Eq. CFL_timestep_selection) */
+  double wall_velocity[18];  /* g on box sides -x,+x,-y,+y,-z,+z (3 components each) [0] */
+  const double* body;        /* DEVICE body force b_h on the velocity space, or NULL [NULL] */
+  int viscosity_mode;        /* SIPG_VISC_* [LINEAR_IMPLICIT] */
+  double ppe_rtol;           /* pressure CG: ||r|| <= ppe_rtol ||rhs|| [1e-8] */
+  double visc_rtol;          /* viscous CG (linear implicit) [1e-8] */
+  int maxit;                 /* CG iteration limit of both [1000] */
+  sipg_picard_opts picard;   /* SIPG_VISC_IMPLICIT: mass_coeff is set by the step */
+} sipg_step_opts;
+
+typedef struct {
+  int order;                                  /* BDF order of this step */
+  int ppe_iterations, visc_iterations;        /* CG iterations (viscous: summed over Picard updates) */
+  int picard_updates;
+  double ppe_rel_residual, visc_rel_residual; /* final relative residuals (Picard: ||r||/||r0||) */
+  double t_convective, t_pressure, t_projection, t_viscous, seconds; /* host clock, synchronised */
+  int status;
+} sipg_step_stats;
+
+void sipg_default_step_opts(sipg_step_opts* o);
+
+/* Start a run from u0 (DEVICE velocity, fine level) and p0 (DEVICE pressure or
+ * NULL for zero); the first call allocates the step's vectors (about ten
+ * velocity vectors; they live as long as the context). */
+int sipg_step_init(sipg_ctx* ctx, const double* u0, const double* p0);
+
+/* Advance one time step (sync). */
+int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step_opts* so, sipg_step_stats* stats);
+
+/* Copy a field of the current state or of the last step to a DEVICE buffer:
+ * U (u^n), U_PREV (u^{n-1}), P (p^n), UHAT, UHATHAT, PPE_RHS (the pressure
+ * step's right-hand side before the mean is removed). */
+int sipg_step_field(sipg_ctx* ctx, int which, double* out);
+
+/* dt = courant / k_u^1.5 / max over cells and Gauss points of |J^-1 u|
+ * (Eq. CFL_timestep_selection); u: DEVICE velocity. Returns SIPG_ERR_INVALID
+ * (dt untouched) for a zero field. (sync) */
+int sipg_cfl_dt(sipg_ctx* ctx, const double* u, double courant, double* dt);
+
+/* The forms on their own (DEVICE vectors of the fine level):
+ * y = C(u) for wall velocity wall_g (18 host doubles, NULL for no-slip);
+ * y = (div v, p) - (v, {{p}} n) for a pressure p; y = wall-data terms of the
+ * viscous form with the stored level-0 viscosity. */
+int sipg_convective_apply(sipg_ctx* ctx, const double* wall_g, const double* u, double* y);
+int sipg_projection_rhs(sipg_ctx* ctx, const double* p, double* y);
+int sipg_viscous_wall_rhs(sipg_ctx* ctx, const double* wall_g, double* y);
+
 /* ------------------------------------------------ multigrid pieces (tests) */
 /* Test hook for the float-float conversions of the SIPG_F64_FF kernels' loads
  * and stores: hilo[2i], hilo[2i+1] = (RN(x_i), RN(x_i - RN(x_i))) as binary32,

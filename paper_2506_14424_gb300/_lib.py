@@ -29,8 +29,12 @@ EXPORTS = [
     "sipg_transfer", "sipg_smooth", "sipg_vcycle", "sipg_node_points", "sipg_apply_host_static",
     "sipg_estimate_bytes", "sipg_server_create", "sipg_server_submit", "sipg_server_poll", "sipg_server_drain",
     "sipg_server_last_error", "sipg_server_destroy", "sipg_mass_apply", "sipg_inverse_mass_apply",
-    "sipg_default_picard_opts", "sipg_picard_solve", "sipg_ff_convert",
+    "sipg_default_picard_opts", "sipg_picard_solve", "sipg_ff_convert", "sipg_default_step_opts",
+    "sipg_step_init", "sipg_step", "sipg_step_field", "sipg_cfl_dt", "sipg_convective_apply",
+    "sipg_projection_rhs", "sipg_viscous_wall_rhs",
 ]
+FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
+VISC_MODE = {"linear": 0, "implicit": 1}
 
 
 class MeshDesc(ctypes.Structure):
@@ -76,6 +80,20 @@ class PicardStats(ctypes.Structure):
                 ("res", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
                 ("history_len", ctypes.c_int), ("residuals", ctypes.POINTER(ctypes.c_double)),
                 ("omegas", ctypes.POINTER(ctypes.c_double))]
+
+
+class StepOpts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("wall_velocity", ctypes.c_double * 18),
+                ("body", ctypes.c_void_p), ("viscosity_mode", ctypes.c_int), ("ppe_rtol", ctypes.c_double),
+                ("visc_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("picard", PicardOpts)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("ppe_iterations", ctypes.c_int), ("visc_iterations", ctypes.c_int),
+                ("picard_updates", ctypes.c_int), ("ppe_rel_residual", ctypes.c_double),
+                ("visc_rel_residual", ctypes.c_double), ("t_convective", ctypes.c_double),
+                ("t_pressure", ctypes.c_double), ("t_projection", ctypes.c_double),
+                ("t_viscous", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -142,6 +160,14 @@ def load(path=None):
         "sipg_default_picard_opts": (None, [P(PicardOpts)]),
         "sipg_picard_solve": (i, [vp, P(Rheology), vp, vp, P(PicardOpts), P(PicardStats)]),
         "sipg_ff_convert": (i, [vp, vp, vp, vp, i64]),
+        "sipg_default_step_opts": (None, [P(StepOpts)]),
+        "sipg_step_init": (i, [vp, vp, vp]),
+        "sipg_step": (i, [vp, P(Rheology), P(StepOpts), P(StepStats)]),
+        "sipg_step_field": (i, [vp, i, vp]),
+        "sipg_cfl_dt": (i, [vp, vp, d, P(d)]),
+        "sipg_convective_apply": (i, [vp, vp, vp, vp]),
+        "sipg_projection_rhs": (i, [vp, vp, vp]),
+        "sipg_viscous_wall_rhs": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -201,6 +201,73 @@ class Context:
         return {"status": rc, "iterations": k, "lin_iterations": st.lin_iterations, "res0": st.res0,
                 "res": st.res, "seconds": st.seconds, "residuals": list(res_h[:k + 1]), "omegas": list(om_h[:k])}
 
+    # ------------------------------------------------ splitting step
+    @staticmethod
+    def _wall(wall):
+        if wall is None:
+            return None
+        w = np.ascontiguousarray(np.asarray(wall, dtype=np.float64).reshape(18))
+        return w
+
+    def convective(self, u, wall=None, y=None):
+        """y = C(u) = c_h(., u; u) with wall velocity wall (6 x 3, box sides -x..+z)."""
+        _need_cuda(u, torch.float64)
+        y = torch.empty_like(u) if y is None else y
+        w = self._wall(wall)
+        wp = w.ctypes.data_as(ctypes.c_void_p) if w is not None else None
+        self._check(self._lib.sipg_convective_apply(self._h, wp, _ptr(u), _ptr(y)))
+        return y
+
+    def projection_rhs(self, p):
+        _need_cuda(p, torch.float64)
+        y = torch.empty(self.n_dofs("viscous"), dtype=torch.float64, device=p.device)
+        self._check(self._lib.sipg_projection_rhs(self._h, _ptr(p), _ptr(y)))
+        return y
+
+    def viscous_wall_rhs(self, wall):
+        y = torch.empty(self.n_dofs("viscous"), dtype=torch.float64, device="cuda")
+        w = self._wall(wall)
+        self._check(self._lib.sipg_viscous_wall_rhs(self._h, w.ctypes.data_as(ctypes.c_void_p), _ptr(y)))
+        return y
+
+    def cfl_dt(self, u, courant):
+        _need_cuda(u, torch.float64)
+        dt = ctypes.c_double()
+        self._check(self._lib.sipg_cfl_dt(self._h, _ptr(u), float(courant), ctypes.byref(dt)))
+        return dt.value
+
+    def step_init(self, u0, p0=None):
+        _need_cuda(u0, torch.float64)
+        self._check(self._lib.sipg_step_init(self._h, _ptr(u0), _ptr(p0)))
+
+    def step(self, rheology, dt, wall=None, body=None, viscosity_mode="linear", ppe_rtol=1e-8, visc_rtol=1e-8,
+             maxit=1000, picard=None):
+        """One step of the projection scheme (see include/sipg.h, sipg_step)."""
+        r, keep = rheology_struct(rheology)
+        o = L.StepOpts()
+        self._lib.sipg_default_step_opts(ctypes.byref(o))
+        o.dt = float(dt)
+        if wall is not None:
+            for i, v in enumerate(np.asarray(wall, dtype=np.float64).reshape(18)):
+                o.wall_velocity[i] = float(v)
+        if body is not None:
+            _need_cuda(body, torch.float64)
+            o.body = body.data_ptr()
+        o.viscosity_mode = L.VISC_MODE[viscosity_mode]
+        o.ppe_rtol, o.visc_rtol, o.maxit = float(ppe_rtol), float(visc_rtol), int(maxit)
+        for key, val in (picard or {}).items():
+            setattr(o.picard, key, val)
+        st = L.StepStats()
+        self._check(self._lib.sipg_step(self._h, ctypes.byref(r), ctypes.byref(o), ctypes.byref(st)))
+        del keep
+        return {f: getattr(st, f) for f, _ in L.StepStats._fields_}
+
+    def step_field(self, which):
+        n = self.n_dofs("poisson") if which in ("p", "ppe_rhs") else self.n_dofs("viscous")
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        self._check(self._lib.sipg_step_field(self._h, L.FIELD[which], _ptr(out)))
+        return out
+
     def apply_host(self, op, x, mass=0.0):
         x = np.ascontiguousarray(x, dtype=np.float64)
         if x.size != self.n_dofs(op):

@@ -178,6 +178,10 @@ sipg_ctx::~sipg_ctx() {
   }
   cudaFree(partials); cudaFree(dscal); cudaFree(dflag); cudaFree(host_x); cudaFree(host_y);
   for (double* p : pic) cudaFree(p);
+  for (double* p : {ss.u[0], ss.u[1], ss.conv[0], ss.conv[1], ss.uhat, ss.uhh, ss.tmp, ss.usharp, ss.bv, ss.p,
+                    ss.prhs, ss.sb})
+    cudaFree(p);
+  cudaFree(ss.vmax);
   if (hscal) cudaFreeHost(hscal);
 }
 
@@ -225,6 +229,7 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   ctx->opts = o;
   ctx->st = (cudaStream_t)stream;
   for (int n = 2; n <= kMaxN; ++n) ctx->tabs[n] = make_tab(n);
+  for (int n = 3; n <= kMaxN; ++n) ctx->stabs[n] = make_split_tab(n);
   cudaError_t e = cudaSuccess;
   int rc = SIPG_OK;
   for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);

@@ -28,6 +28,23 @@ struct Tab {
   double M1inv[kMaxN * kMaxN];  // its inverse
 };
 
+// 1D tables of the splitting-step forms of one velocity degree (n = k+1 Gauss
+// points; the pressure basis has n-1 Gauss-Lobatto nodes), row-major [q][j]:
+//  S, DS     velocity basis values / derivatives at the Gauss points
+//  Dg        collocation derivative on the Gauss points
+//  Sp, DSp   pressure basis values / derivatives at the velocity Gauss points
+//  dS0, dS1  velocity basis derivatives at 0 and 1
+//  lg0, lg1, dlg0, dlg1  Lagrange basis on the Gauss points: values and
+//            derivatives at 0 and 1 (traces of fields given at Gauss points)
+struct SplitTab {
+  int n;
+  double S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN];
+  double Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
+  double dS0[kMaxN], dS1[kMaxN];
+  double lg0[kMaxN], lg1[kMaxN], dlg0[kMaxN], dlg1[kMaxN];
+  double gw[kMaxN];
+};
+
 // Embedding matrices of the transfers (prolongation = interpolation of the
 // coarse polynomial at the fine Gauss-Lobatto nodes), row-major [nf][nc].
 struct TransferTab {

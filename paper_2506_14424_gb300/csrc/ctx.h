@@ -59,6 +59,18 @@ struct sipg_ctx {
   double* host_y = nullptr;
   int64_t host_n = 0;
   double* pic[4] = {nullptr};  // Picard work vectors: r_k, r_{k-1}, u^k, r_k - r_{k-1}
+  sipg::SplitTab stabs[sipg::kMaxN + 1]{};
+  // state of the splitting step (allocated by sipg_step_init)
+  struct StepState {
+    double* u[2] = {nullptr, nullptr};     // u^n, u^{n-1}
+    double* conv[2] = {nullptr, nullptr};  // C(u^n), C(u^{n-1})
+    double *uhat = nullptr, *uhh = nullptr, *tmp = nullptr, *usharp = nullptr, *bv = nullptr;
+    double *p = nullptr, *prhs = nullptr, *sb = nullptr;
+    unsigned long long* vmax = nullptr;
+    int n_hist = 0;       // velocity histories held (1 after init, 2 after a step)
+    bool conv1 = false;   // conv[1] holds C(u^{n-1})
+    int64_t steps = 0;
+  } ss;
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
   int64_t bytes = 0;    // device bytes allocated by the hierarchy
 

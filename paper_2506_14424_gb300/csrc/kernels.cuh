@@ -39,6 +39,29 @@ cudaError_t launch_viscosity(int n, const LevelGeom& g, const Tab& tab, const Rh
 cudaError_t launch_cell_nu_transfer(const LevelGeom& fine, const LevelGeom& coarse, int kind, int nf, int nc,
                                     const double* fine_cell, double* nu_cell, double* nu_face, cudaStream_t st);
 
+// ---- forms of the splitting step (split.cu); n = velocity degree + 1 (3..6)
+struct PpeBndArgs {
+  int n_hist;        // m: velocity histories entering the convective terms
+  double wconv[2];   // beta_i - betabar_i
+  int visc;          // viscous terms of u^dd present (m_p > 0)
+  double betabar[2]; // extrapolation of order m_p
+  double gn_coef;    // -(gamma0/dt)
+};
+cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                              const double* u, double* y, cudaStream_t st);
+int n_wall_faces(const LevelGeom& g);
+cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                                const PpeBndArgs& a, const RheologyDev& rh, const double* u0, const double* u1,
+                                double* sb, cudaStream_t st);
+cudaError_t launch_ppe_rhs(int n, const LevelGeom& g, const SplitTab& tab, double coef, const double* uhat,
+                           const double* sb, double* r, cudaStream_t st);
+cudaError_t launch_projection_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* p, double* y,
+                                  cudaStream_t st);
+cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                                    const double* nu_face, double* y, cudaStream_t st);
+cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
+                           unsigned long long* vmax_bits, cudaStream_t st);
+
 // ---- multigrid and vector kernels (mg.cu)
 cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
                             const double* nu_face, double mass, double* diag, cudaStream_t st);

@@ -1,0 +1,662 @@
+// Forms of one step of the projection scheme on a box (Sec. 3.2 / 5.1, Alg. 1),
+// convective term explicit:
+//   conv_kernel       C_a = c_h(phi_a, u; u), Eq. (convective_term_weak), upwind flux,
+//                     mirror principle on Dirichlet walls
+//   ppe_bnd_kernel    h_p - (gamma0/dt) g_uhat.n at the Gauss points of every
+//                     wall face, Eqs. (pressure_Neumann_BC), (guhat_consistent_BC)
+//   ppe_rhs_kernel    (gamma0/dt)[(grad q, uhat) - (q, {{uhat}}.n)] with the wall
+//                     datum above on Dirichlet faces, Eq. (pressure_step_weak)
+//   proj_rhs_kernel   (div v, p) - (v, {{p}} n), Eq. (projection_step_weak)
+//   visc_dir_kernel   Dirichlet wall-data terms of the SIPG viscous form (mirror
+//                     u^+ = -u^- + 2g) for the viscous step's right-hand side
+//   cfl_kernel        max over Gauss points of |J^-1 u|, Eq. (CFL_timestep_selection)
+//
+// All FP64, one CTA per cell (or per wall face), one thread per tensor entry in
+// each 1D sweep; every CTA writes only its own rows (no atomics except the max
+// of the CFL reduction, which is order independent). Fields given at the n^3
+// Gauss points of a cell are the values of a Q_k polynomial there (n = k+1
+// points per direction determine it), so traces and derivatives of such a
+// field are taken exactly with the Lagrange basis on the Gauss points; in
+// particular the element-local L2 projection onto Q_k of point values at the
+// Gauss points is the polynomial interpolating them (M1^-1 S^T W = S^-1).
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace sipg {
+namespace {
+
+constexpr int kSplitThreads = 128;
+
+// out = A along DIR applied to the tensor in (extents EX, EY, EZ, x fastest);
+// A row-major [NO][E_DIR] (TR = false) or [E_DIR][NO] (TR = true), leading dim lda
+template <int EX, int EY, int EZ, int DIR, int NO, bool TR>
+__device__ __forceinline__ void sweep(const double* A, int lda, const double* in, double* out) {
+  constexpr int OX = DIR == 0 ? NO : EX, OY = DIR == 1 ? NO : EY, OZ = DIR == 2 ? NO : EZ;
+  constexpr int EIN = DIR == 0 ? EX : (DIR == 1 ? EY : EZ);
+  constexpr int SIN = DIR == 0 ? 1 : (DIR == 1 ? EX : EX * EY);
+  for (int t = threadIdx.x; t < OX * OY * OZ; t += blockDim.x) {
+    const int x = t % OX, y = (t / OX) % OY, z = t / (OX * OY);
+    const int o = DIR == 0 ? x : (DIR == 1 ? y : z);
+    const int base = (DIR == 0 ? 0 : x) + (DIR == 1 ? 0 : y) * EX + (DIR == 2 ? 0 : z) * EX * EY;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < EIN; ++m) acc += (TR ? A[m * lda + o] : A[o * lda + m]) * in[base + m * SIN];
+    out[t] = acc;
+  }
+}
+
+// three sweeps with the same matrix (N -> NO per direction); tmp: two buffers of N^3
+template <int N, int NO, bool TR>
+__device__ __forceinline__ void sweep3(const double* A, int lda, const double* in, double* t0, double* t1,
+                                       double* out) {
+  sweep<N, N, N, 0, NO, TR>(A, lda, in, t0);
+  __syncthreads();
+  sweep<NO, N, N, 1, NO, TR>(A, lda, t0, t1);
+  __syncthreads();
+  sweep<NO, NO, N, 2, NO, TR>(A, lda, t1, out);
+  __syncthreads();
+}
+
+// single sweep along a runtime direction (n^3 -> n^3)
+template <int N, bool TR>
+__device__ __forceinline__ void sweep_dir(int dir, const double* A, const double* in, double* out) {
+  if (dir == 0) sweep<N, N, N, 0, N, TR>(A, N, in, out);
+  else if (dir == 1) sweep<N, N, N, 1, N, TR>(A, N, in, out);
+  else sweep<N, N, N, 2, N, TR>(A, N, in, out);
+}
+
+__device__ __forceinline__ void face_dirs(int d, int* t1, int* t2) {
+  *t1 = d == 0 ? 1 : 0;
+  *t2 = d == 2 ? 1 : 2;
+}
+
+// cell index of face point (a, b) (a along t1 < t2) of face (d, s) in an n^3 tensor
+__device__ __forceinline__ int fnode(int d, int s, int a, int b, int n) {
+  int i[3];
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  i[d] = s ? n - 1 : 0;
+  i[t1] = a;
+  i[t2] = b;
+  return (i[2] * n + i[1]) * n + i[0];
+}
+
+// index of the wall face of box side f holding cell e (sides in order, faces
+// lexicographic over the tangential cell indices t1 < t2)
+__device__ __forceinline__ int bface_index(const LevelGeom& g, int e, int f) {
+  const int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
+  int off = 0;
+  for (int s = 0; s < f; ++s) off += side[s >> 1];
+  const int d = f >> 1;
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  return off + ijk[t2] * dims[t1] + ijk[t1];
+}
+
+// load the split tables into shared memory
+struct STabSm {
+  double S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN], Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
+  double dS[2][kMaxN], lg[2][kMaxN], dlg[2][kMaxN], gw[kMaxN];
+};
+__device__ __forceinline__ void load_tab(const SplitTab& t, STabSm& s) {
+  for (int i = threadIdx.x; i < kMaxN * kMaxN; i += blockDim.x) {
+    s.S[i] = t.S[i];
+    s.DS[i] = t.DS[i];
+    s.Dg[i] = t.Dg[i];
+    s.Sp[i] = t.Sp[i];
+    s.DSp[i] = t.DSp[i];
+  }
+  for (int i = threadIdx.x; i < kMaxN; i += blockDim.x) {
+    s.dS[0][i] = t.dS0[i];
+    s.dS[1][i] = t.dS1[i];
+    s.lg[0][i] = t.lg0[i];
+    s.lg[1][i] = t.lg1[i];
+    s.dlg[0][i] = t.dlg0[i];
+    s.dlg[1][i] = t.dlg1[i];
+    s.gw[i] = t.gw[i];
+  }
+}
+
+__device__ __forceinline__ double cell_weight(const STabSm& t, int q, int n, double detJ) {
+  return t.gw[q % n] * t.gw[(q / n) % n] * t.gw[q / (n * n)] * detJ;
+}
+
+// trace on face (d, s) of a field F given at the n^3 Gauss points, with the 1D
+// vector L over the normal index (values lg or derivatives dlg at 0 / 1)
+template <int N>
+__device__ __forceinline__ void trace(const double* F, const double* L, int d, double* out) {
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  const int str[3] = {1, N, N * N};
+  for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+    const int a = p % N, b = p / N;
+    const int base = a * str[t1] + b * str[t2];
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc += L[q] * F[base + q * str[d]];
+    out[p] = acc;
+  }
+}
+
+struct Wall {
+  double g[6][3];
+};
+
+// --------------------------------------------------------------- convective
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) conv_kernel(LevelGeom g, SplitTab tab, Wall wall,
+                                                             const double* __restrict__ u, double* __restrict__ y) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double U[3][N3], Q[3][N3], G[3][3][N3], CV[3][N3], T0[N3], T1[N3], OUT[3][N3];
+  __shared__ double UM[3][N2], UP[3][N2], FT[N2], FL[3][N2], FR[N2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) U[i / N3][i % N3] = u[(size_t)e * 3 * N3 + i];
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+  for (int c = 0; c < 3; ++c)
+    for (int l = 0; l < 3; ++l) sweep_dir<N, false>(l, T.Dg, Q[c], G[c][l]);
+  __syncthreads();
+  const double detJ = g.h[0] * g.h[1] * g.h[2];
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const double w = cell_weight(T, q, N, detJ);
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int l = 0; l < 3; ++l) acc += Q[l][q] * G[c][l][q] * g.ih[l];
+      CV[c][q] = w * acc;
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, true>(T.S, N, CV[c], T0, T1, OUT[c]);
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const double nd = 2.0 * s - 1.0;
+    const int nb = cell_neighbor(g, e, f);
+    for (int i = threadIdx.x; i < 3 * N2; i += blockDim.x) {
+      const int c = i / N2, p = i % N2;
+      FL[c][p] = U[c][fnode(d, s, p % N, p / N, N)];
+      if (nb >= 0) CV[c][p] = u[(size_t)nb * 3 * N3 + c * N3 + fnode(d, 1 - s, p % N, p / N, N)];
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+      sweep<N, N, 1, 0, N, false>(T.S, N, FL[c], FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, false>(T.S, N, FT, UM[c]);
+      __syncthreads();
+      if (nb >= 0) {
+        sweep<N, N, 1, 0, N, false>(T.S, N, CV[c], FT);
+        __syncthreads();
+        sweep<N, N, 1, 1, N, false>(T.S, N, FT, UP[c]);
+        __syncthreads();
+      }
+    }
+    const double area = g.h[t1] * g.h[t2];
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double um[3], up[3];
+      for (int c = 0; c < 3; ++c) {
+        um[c] = UM[c][p];
+        up[c] = nb >= 0 ? UP[c][p] : (g.bc[f] == 0 ? -um[c] + 2.0 * wall.g[f][c] : um[c]);
+      }
+      const double wn = 0.5 * (um[d] + up[d]) * nd;
+      const double sg = wn > 0.0 ? 1.0 : (wn < 0.0 ? -1.0 : 0.0);
+      const double w = T.gw[p % N] * T.gw[p / N] * area;
+      for (int c = 0; c < 3; ++c) FL[c][p] = w * wn * 0.5 * (1.0 - sg) * (up[c] - um[c]);
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+      sweep<N, N, 1, 0, N, true>(T.S, N, FL[c], FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.S, N, FT, FR);
+      __syncthreads();
+      for (int p = threadIdx.x; p < N2; p += blockDim.x) OUT[c][fnode(d, s, p % N, p / N, N)] += FR[p];
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) y[(size_t)e * 3 * N3 + i] = OUT[i / N3][i % N3];
+}
+
+// ----------------------------------------------------- PPE wall datum
+// h_p - (gamma0/dt) g_uhat.n = sum_{i<m} (beta_i - betabar_i) n.(u^{n-i}.grad)u^{n-i}
+//     - nu^dd n.curl omega^dd + 2 n.(eps(u^dd) grad nu^dd) - (gamma0/dt) g.n
+// (n.b cancels between h_p and g_uhat; sum_i alpha_i = gamma0 for BDF).
+struct PpeBnd {
+  PpeBndArgs a;
+  RheologyDev rh;  // constant or Carreau-Yasuda
+};
+
+__device__ __forceinline__ double eta_of(const RheologyDev& r, const double G[3][3]) {
+  if (r.law == 0) return r.nu;
+  double ee = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      const double e = 0.5 * (G[k][l] + G[l][k]);
+      ee += e * e;
+    }
+  const double gdot = sqrt(2.0 * ee);
+  return r.eta_inf + (r.eta0 - r.eta_inf) * pow(r.kappa + pow(r.lambda * gdot, r.a), (r.b - 1.0) / r.a);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) ppe_bnd_kernel(LevelGeom g, SplitTab tab, Wall wall, PpeBnd pb,
+                                                                const double* __restrict__ u0,
+                                                                const double* __restrict__ u1,
+                                                                double* __restrict__ sb) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double U[3][N3], Q[3][N3], G[3][3][N3], T0[N3], T1[N3], W3[3][N3];
+  __shared__ double TR[12][N2], ACC[N2];
+  // decode the wall face
+  int bf = blockIdx.x, f = 0;
+  const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
+  while (bf >= side[f >> 1]) {
+    bf -= side[f >> 1];
+    ++f;
+  }
+  const int d = f >> 1, s = f & 1;
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  int ijk[3];
+  ijk[d] = s ? dims[d] - 1 : 0;
+  ijk[t1] = bf % dims[t1];
+  ijk[t2] = bf / dims[t1];
+  const int e = (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+  const double nd = 2.0 * s - 1.0;
+  load_tab(tab, T);
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) ACC[p] = pb.a.gn_coef * wall.g[f][d] * nd;
+  __syncthreads();
+  // convective terms: n.(u.grad)u of each history, weight beta_i - betabar_i
+  for (int h = 0; h < pb.a.n_hist; ++h) {
+    const double* uh = h == 0 ? u0 : u1;
+    if (pb.a.wconv[h] == 0.0) continue;
+    for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) U[i / N3][i % N3] = uh[(size_t)e * 3 * N3 + i];
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+    for (int l = 0; l < 3; ++l) sweep_dir<N, false>(l, T.Dg, Q[d], G[d][l]);
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) trace<N>(Q[c], T.lg[s], d, TR[c]);
+    for (int l = 0; l < 3; ++l) trace<N>(G[d][l], T.lg[s], d, TR[3 + l]);
+    __syncthreads();
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double cv = 0.0;
+      for (int l = 0; l < 3; ++l) cv += TR[l][p] * TR[3 + l][p] * g.ih[l];
+      ACC[p] += pb.a.wconv[h] * nd * cv;
+    }
+    __syncthreads();
+  }
+  if (pb.a.visc) {
+    // u^dd = sum_i betabar_i u^{n-i}
+    for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+      const size_t k = (size_t)e * 3 * N3 + i;
+      double v = pb.a.betabar[0] * u0[k];
+      if (pb.a.betabar[1] != 0.0) v += pb.a.betabar[1] * u1[k];
+      U[i / N3][i % N3] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+    for (int c = 0; c < 3; ++c)
+      for (int l = 0; l < 3; ++l) sweep_dir<N, false>(l, T.Dg, Q[c], G[c][l]);
+    __syncthreads();
+    // vorticity and viscosity at the Gauss points (their L2 projections onto Q_k)
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+      double Gq[3][3];
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) Gq[k][l] = G[k][l][q] * g.ih[l];
+      W3[0][q] = Gq[2][1] - Gq[1][2];
+      W3[1][q] = Gq[0][2] - Gq[2][0];
+      W3[2][q] = Gq[1][0] - Gq[0][1];
+      T0[q] = eta_of(pb.rh, Gq);
+    }
+    __syncthreads();
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    // traces: omega_{d1}, omega_{d2}, nu, d nu / dn, and the 9 gradient entries
+    trace<N>(W3[d1], T.lg[s], d, TR[0]);
+    trace<N>(W3[d2], T.lg[s], d, TR[1]);
+    trace<N>(T0, T.lg[s], d, TR[2]);
+    trace<N>(T0, T.dlg[s], d, TR[3]);
+    __syncthreads();
+    // tangential derivatives on the face Gauss grid: d/dt1 of a field = Dg along a
+    // (TR[4..7]: d omega_{d1}/dt1, /dt2, d omega_{d2}/dt1, /dt2; TR[8], TR[9]: d nu/dt1, /dt2)
+    sweep<N, N, 1, 0, N, false>(T.Dg, N, TR[0], TR[4]);
+    sweep<N, N, 1, 1, N, false>(T.Dg, N, TR[0], TR[5]);
+    sweep<N, N, 1, 0, N, false>(T.Dg, N, TR[1], TR[6]);
+    sweep<N, N, 1, 1, N, false>(T.Dg, N, TR[1], TR[7]);
+    sweep<N, N, 1, 0, N, false>(T.Dg, N, TR[2], TR[8]);
+    sweep<N, N, 1, 1, N, false>(T.Dg, N, TR[2], TR[9]);
+    __syncthreads();
+    // d/d x_{d1} and d/d x_{d2} in terms of t1 < t2
+    const bool d1_is_t1 = d1 == t1;
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      const double dw2_dd1 = (d1_is_t1 ? TR[6][p] : TR[7][p]) * g.ih[d1];
+      const double dw1_dd2 = (d1_is_t1 ? TR[5][p] : TR[4][p]) * g.ih[d2];
+      const double curl_d = dw2_dd1 - dw1_dd2;
+      double gradnu[3];
+      gradnu[d] = TR[3][p] * g.ih[d];
+      gradnu[t1] = TR[8][p] * g.ih[t1];
+      gradnu[t2] = TR[9][p] * g.ih[t2];
+      T1[p] = curl_d;
+      for (int l = 0; l < 3; ++l) Q[0][p * 3 + l] = gradnu[l];  // Q is free now: grad nu at face points
+    }
+    __syncthreads();
+    // gradient of u^dd at the face points (traces of the Gauss-point gradients)
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) trace<N>(G[k][l], T.lg[s], d, W3[0] + (k * 3 + l) * N2);
+    __syncthreads();
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double Gf[3][3];
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) Gf[k][l] = W3[0][(k * 3 + l) * N2 + p] * g.ih[l];
+      const double nu = eta_of(pb.rh, Gf);
+      double epsgrad = 0.0;
+      for (int l = 0; l < 3; ++l) epsgrad += 0.5 * (Gf[d][l] + Gf[l][d]) * Q[0][p * 3 + l];
+      ACC[p] += -nu * nd * T1[p] + 2.0 * nd * epsgrad;
+    }
+    __syncthreads();
+  }
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) sb[(size_t)blockIdx.x * N2 + p] = ACC[p];
+}
+
+// ------------------------------------------------------ PPE right-hand side
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) ppe_rhs_kernel(LevelGeom g, SplitTab tab, double coef,
+                                                                const double* __restrict__ uh,
+                                                                const double* __restrict__ sb,
+                                                                double* __restrict__ r) {
+  constexpr int N3 = N * N * N, N2 = N * N, NP = N - 1, NP3 = NP * NP * NP, NP2 = NP * NP;
+  __shared__ STabSm T;
+  __shared__ double U[3][N3], Q[N3], T0[N3], T1[N3], R[NP3], TMP[NP3];
+  __shared__ double FA[N2], FB[N2], FT[N2], FR[NP2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) U[i / N3][i % N3] = uh[(size_t)e * 3 * N3 + i];
+  for (int i = threadIdx.x; i < NP3; i += blockDim.x) R[i] = 0.0;
+  __syncthreads();
+  const double detJ = g.h[0] * g.h[1] * g.h[2];
+  for (int l = 0; l < 3; ++l) {
+    sweep3<N, N, false>(T.S, N, U[l], T0, T1, Q);
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) Q[q] *= coef * cell_weight(T, q, N, detJ) * g.ih[l];
+    __syncthreads();
+    // (grad q)_l: derivative of the pressure basis along l, values along the others
+    sweep<N, N, N, 0, NP, true>(l == 0 ? T.DSp : T.Sp, NP, Q, T0);
+    __syncthreads();
+    sweep<NP, N, N, 1, NP, true>(l == 1 ? T.DSp : T.Sp, NP, T0, T1);
+    __syncthreads();
+    sweep<NP, NP, N, 2, NP, true>(l == 2 ? T.DSp : T.Sp, NP, T1, TMP);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP3; i += blockDim.x) R[i] += TMP[i];
+    __syncthreads();
+  }
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const double nd = 2.0 * s - 1.0;
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] != 0) continue;  // velocity Neumann: not used on the box
+    const double area = g.h[t1] * g.h[t2];
+    if (nb >= 0) {
+      for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+        FA[p] = U[d][fnode(d, s, p % N, p / N, N)];
+        FB[p] = uh[(size_t)nb * 3 * N3 + d * N3 + fnode(d, 1 - s, p % N, p / N, N)];
+      }
+      __syncthreads();
+      sweep<N, N, 1, 0, N, false>(T.S, N, FA, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, false>(T.S, N, FT, FA);
+      __syncthreads();
+      sweep<N, N, 1, 0, N, false>(T.S, N, FB, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, false>(T.S, N, FT, FB);
+      __syncthreads();
+      for (int p = threadIdx.x; p < N2; p += blockDim.x)
+        FA[p] = -coef * 0.5 * (FA[p] + FB[p]) * nd * T.gw[p % N] * T.gw[p / N] * area;
+    } else {
+      const int bf = bface_index(g, e, f);
+      for (int p = threadIdx.x; p < N2; p += blockDim.x)
+        FA[p] = sb[(size_t)bf * N2 + p] * T.gw[p % N] * T.gw[p / N] * area;
+    }
+    __syncthreads();
+    sweep<N, N, 1, 0, NP, true>(T.Sp, NP, FA, FT);
+    __syncthreads();
+    sweep<NP, N, 1, 1, NP, true>(T.Sp, NP, FT, FR);
+    __syncthreads();
+    for (int p = threadIdx.x; p < NP2; p += blockDim.x) R[fnode(d, s, p % NP, p / NP, NP)] += FR[p];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NP3; i += blockDim.x) r[(size_t)e * NP3 + i] = R[i];
+}
+
+// ----------------------------------------------- projection right-hand side
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) proj_rhs_kernel(LevelGeom g, SplitTab tab,
+                                                                 const double* __restrict__ p,
+                                                                 double* __restrict__ y) {
+  constexpr int N3 = N * N * N, N2 = N * N, NP = N - 1, NP3 = NP * NP * NP, NP2 = NP * NP;
+  __shared__ STabSm T;
+  __shared__ double P[NP3], PQ[N3], T0[N3], T1[N3], OUT[3][N3];
+  __shared__ double FA[N2], FB[N2], FT[N2], FR[N2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < NP3; i += blockDim.x) P[i] = p[(size_t)e * NP3 + i];
+  __syncthreads();
+  sweep<NP, NP, NP, 0, N, false>(T.Sp, NP, P, T0);
+  __syncthreads();
+  sweep<N, NP, NP, 1, N, false>(T.Sp, NP, T0, T1);
+  __syncthreads();
+  sweep<N, N, NP, 2, N, false>(T.Sp, NP, T1, PQ);
+  __syncthreads();
+  const double detJ = g.h[0] * g.h[1] * g.h[2];
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) PQ[q] *= cell_weight(T, q, N, detJ);
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    // (div v, p) for v = phi_i e_c: d phi_i / d x_c
+    sweep<N, N, N, 0, N, true>(c == 0 ? T.DS : T.S, N, PQ, T0);
+    __syncthreads();
+    sweep<N, N, N, 1, N, true>(c == 1 ? T.DS : T.S, N, T0, T1);
+    __syncthreads();
+    sweep<N, N, N, 2, N, true>(c == 2 ? T.DS : T.S, N, T1, OUT[c]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N3; i += blockDim.x) OUT[c][i] *= g.ih[c];
+    __syncthreads();
+  }
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const double nd = 2.0 * s - 1.0;
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] != 0) continue;
+    for (int q = threadIdx.x; q < NP2; q += blockDim.x) {
+      FA[q] = P[fnode(d, s, q % NP, q / NP, NP)];
+      FB[q] = nb >= 0 ? p[(size_t)nb * NP3 + fnode(d, 1 - s, q % NP, q / NP, NP)] : FA[q];
+    }
+    __syncthreads();
+    sweep<NP, NP, 1, 0, N, false>(T.Sp, NP, FA, FT);
+    __syncthreads();
+    sweep<N, NP, 1, 1, N, false>(T.Sp, NP, FT, FA);
+    __syncthreads();
+    sweep<NP, NP, 1, 0, N, false>(T.Sp, NP, FB, FT);
+    __syncthreads();
+    sweep<N, NP, 1, 1, N, false>(T.Sp, NP, FT, FB);
+    __syncthreads();
+    const double area = g.h[t1] * g.h[t2];
+    for (int q = threadIdx.x; q < N2; q += blockDim.x)
+      FA[q] = -0.5 * (FA[q] + FB[q]) * nd * T.gw[q % N] * T.gw[q / N] * area;
+    __syncthreads();
+    sweep<N, N, 1, 0, N, true>(T.S, N, FA, FT);
+    __syncthreads();
+    sweep<N, N, 1, 1, N, true>(T.S, N, FT, FR);
+    __syncthreads();
+    for (int q = threadIdx.x; q < N2; q += blockDim.x) OUT[d][fnode(d, s, q % N, q / N, N)] += FR[q];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) y[(size_t)e * 3 * N3 + i] = OUT[i / N3][i % N3];
+}
+
+// ---------------------------------------- viscous wall data (right-hand side)
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) visc_dir_kernel(LevelGeom g, SplitTab tab, Wall wall,
+                                                                 const double* __restrict__ nu_face,
+                                                                 double* __restrict__ y) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double OUT[3][N3], CA[N2], CB[N2], CC[N2], CE[N2], FT[N2], FR[N2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) OUT[i / N3][i % N3] = 0.0;
+  __syncthreads();
+  const double lam = penalty_lambda(g, e);
+  for (int f = 0; f < 6; ++f) {
+    if (cell_neighbor(g, e, f) >= 0 || g.bc[f] != 0) continue;
+    const double* gv = wall.g[f];
+    if (gv[0] == 0.0 && gv[1] == 0.0 && gv[2] == 0.0) continue;
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const double nd = 2.0 * s - 1.0;
+    const double area = g.h[t1] * g.h[t2];
+    for (int c = 0; c < 3; ++c) {
+      const double nc = c == d ? nd : 0.0;
+      for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+        const double w = T.gw[p % N] * T.gw[p / N] * area;
+        const double nu = nu_face[((size_t)e * 6 + f) * N2 + p];
+        const double tau = g.cip * (double)(N * N) * lam * nu;
+        CA[p] = -nu * w * (gv[c] * nd + nc * gv[d]) * g.ih[d];
+        CB[p] = -nu * w * nc * gv[t1] * g.ih[t1];
+        CC[p] = -nu * w * nc * gv[t2] * g.ih[t2];
+        CE[p] = 2.0 * tau * w * (gv[c] + nc * gv[d] * nd);
+      }
+      __syncthreads();
+      // normal derivative: every node along the normal line, weight l'_i(s)
+      sweep<N, N, 1, 0, N, true>(T.S, N, CA, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.S, N, FT, FR);
+      __syncthreads();
+      for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+        int idx[3] = {i % N, (i / N) % N, i / N2};
+        OUT[c][i] += T.dS[s][idx[d]] * FR[idx[t1] + N * idx[t2]];
+      }
+      __syncthreads();
+      // tangential derivatives and values: face nodes only
+      sweep<N, N, 1, 0, N, true>(T.DS, N, CB, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.S, N, FT, FR);
+      __syncthreads();
+      sweep<N, N, 1, 0, N, true>(T.S, N, CC, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.DS, N, FT, CB);
+      __syncthreads();
+      sweep<N, N, 1, 0, N, true>(T.S, N, CE, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.S, N, FT, CC);
+      __syncthreads();
+      for (int p = threadIdx.x; p < N2; p += blockDim.x)
+        OUT[c][fnode(d, s, p % N, p / N, N)] += FR[p] + CB[p] + CC[p];
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) y[(size_t)e * 3 * N3 + i] = OUT[i / N3][i % N3];
+}
+
+// ------------------------------------------------------------------- CFL
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) cfl_kernel(LevelGeom g, SplitTab tab, const double* __restrict__ u,
+                                                            unsigned long long* __restrict__ vmax_bits) {
+  constexpr int N3 = N * N * N;
+  __shared__ STabSm T;
+  __shared__ double U[3][N3], Q[3][N3], T0[N3], T1[N3];
+  __shared__ double red[kSplitThreads];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) U[i / N3][i % N3] = u[(size_t)e * 3 * N3 + i];
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+  double m = 0.0;
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const double a = Q[0][q] * g.ih[0], b = Q[1][q] * g.ih[1], c = Q[2][q] * g.ih[2];
+    m = fmax(m, sqrt(a * a + b * b + c * c));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  // non-negative doubles order like their bit patterns
+  if (threadIdx.x == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+}  // namespace
+
+#define SIPG_SPLIT_DISPATCH(NN, CALL) \
+  switch (NN) {                       \
+    case 3: { constexpr int N = 3; CALL; break; } \
+    case 4: { constexpr int N = 4; CALL; break; } \
+    case 5: { constexpr int N = 5; CALL; break; } \
+    case 6: { constexpr int N = 6; CALL; break; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                              const double* u, double* y, cudaStream_t st) {
+  Wall w;
+  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (conv_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, u, y)));
+  return cudaGetLastError();
+}
+
+int n_wall_faces(const LevelGeom& g) { return 2 * (g.ny * g.nz + g.nx * g.nz + g.nx * g.ny); }
+
+cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                                const PpeBndArgs& a, const RheologyDev& rh, const double* u0, const double* u1,
+                                double* sb, cudaStream_t st) {
+  Wall w;
+  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  PpeBnd pb{};
+  pb.a = a;
+  pb.rh = rh;
+  const int nbf = n_wall_faces(g);
+  if (nbf == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (ppe_bnd_kernel<N><<<nbf, kSplitThreads, 0, st>>>(g, tab, w, pb, u0, u1, sb)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ppe_rhs(int n, const LevelGeom& g, const SplitTab& tab, double coef, const double* uhat,
+                           const double* sb, double* r, cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (ppe_rhs_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, coef, uhat, sb, r)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_projection_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* p, double* y,
+                                  cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (proj_rhs_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, p, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                                    const double* nu_face, double* y, cudaStream_t st) {
+  Wall w;
+  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (visc_dir_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, nu_face, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
+                           unsigned long long* vmax_bits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || g.ncells == 0) return e;
+  SIPG_SPLIT_DISPATCH(n, (cfl_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, u, vmax_bits)));
+  return cudaGetLastError();
+}
+
+}  // namespace sipg

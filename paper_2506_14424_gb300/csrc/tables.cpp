@@ -148,6 +148,46 @@ Tab make_tab(int n) {
   return T;
 }
 
+SplitTab make_split_tab(int n) {
+  SplitTab T{};
+  T.n = n;
+  std::vector<double> gll(n), gllw(n), gp(n), gw(n), pl(n - 1), plw(n - 1);
+  gauss_lobatto(n, gll.data(), gllw.data());
+  gauss_legendre(n, gp.data(), gw.data());
+  if (n - 1 >= 2) gauss_lobatto(n - 1, pl.data(), plw.data());
+  for (int q = 0; q < n; ++q) {
+    const auto s = lagrange_values(gll, gp[q]);
+    const auto ds = lagrange_derivs(gll, gp[q]);
+    const auto dg = lagrange_derivs(gp, gp[q]);
+    for (int j = 0; j < n; ++j) {
+      T.S[q * n + j] = s[j];
+      T.DS[q * n + j] = ds[j];
+      T.Dg[q * n + j] = dg[j];
+    }
+    if (n - 1 >= 2) {
+      const auto sp = lagrange_values(pl, gp[q]);
+      const auto dsp = lagrange_derivs(pl, gp[q]);
+      for (int j = 0; j < n - 1; ++j) {
+        T.Sp[q * (n - 1) + j] = sp[j];
+        T.DSp[q * (n - 1) + j] = dsp[j];
+      }
+    }
+  }
+  const auto d0 = lagrange_derivs(gll, 0.0), d1 = lagrange_derivs(gll, 1.0);
+  const auto l0 = lagrange_values(gp, 0.0), l1 = lagrange_values(gp, 1.0);
+  const auto e0 = lagrange_derivs(gp, 0.0), e1 = lagrange_derivs(gp, 1.0);
+  for (int j = 0; j < n; ++j) {
+    T.dS0[j] = d0[j];
+    T.dS1[j] = d1[j];
+    T.lg0[j] = l0[j];
+    T.lg1[j] = l1[j];
+    T.dlg0[j] = e0[j];
+    T.dlg1[j] = e1[j];
+    T.gw[j] = gw[j];
+  }
+  return T;
+}
+
 TransferTab make_p_transfer(int nf, int nc) {
   TransferTab T{};
   T.nf = nf;
