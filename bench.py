@@ -309,6 +309,7 @@ def gpu_extras(ctx, xs, ys, stream):
     out["cfg3_mg_solves_16cubed_k4"] = solves
     out["mass_32cubed_k3"] = mass_timings(ctx, xs, ys, stream)
     out["picard_viscous_step_32cubed_k3"] = picard_extras(ctx)
+    out["splitting_step_32cubed_k3"] = step_extras()
     out["components_16cubed_k4"] = component_timings(stream)
     out["serving"] = serving_extras()
     return out
@@ -362,6 +363,59 @@ def picard_extras(ctx, dt=1e-2):
             "status": r["status"], "updates": r["iterations"], "cg_iterations": r["lin_iterations"],
             "seconds": r["seconds"], "res0": r["res0"], "res": r["res"],
             "omegas": [round(w, 4) for w in r["omegas"]]}
+    return out
+
+
+def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
+    """Projection-scheme time steps on a lid-driven box (lid velocity (1, 0, 0)
+    on +z, no-slip elsewhere), Carreau-Yasuda viscosity linear implicit, the
+    cfg-2 Fourier field as initial velocity, dt from the CFL rule (Cr = 0.3),
+    pressure and viscous CG to 1e-8. Host-clock step times (the step
+    synchronises); CUDA-event times of the step's form kernels."""
+    import numpy as np
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+    ctx = Context(n_cells, n_cells, n_cells, k, krylov_arith="f64ff")
+    rh = inputs.carreau_blood_like()
+    pts = ctx.node_points("viscous", 0)
+    vals = inputs.fourier_field(pts.reshape(-1, 3), inputs.fourier_modes(1)).reshape(-1, (k + 1) ** 3, 3)
+    u0 = torch.tensor(np.ascontiguousarray(vals.transpose(0, 2, 1)).reshape(-1), device="cuda")
+    wall = np.zeros((6, 3))
+    wall[5, 0] = 1.0
+    out = {"n_dofs_velocity": ctx.n_dofs("viscous"), "n_dofs_pressure": ctx.n_dofs("poisson")}
+
+    def ev(fn, reps=10):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    y = torch.empty_like(u0)
+    p = torch.tensor(inputs.uniform_vector(ctx.n_dofs("poisson"), 3), device="cuda")
+    out["convective_ms"] = ev(lambda: ctx.convective(u0, wall, y))
+    out["projection_rhs_ms"] = ev(lambda: ctx.projection_rhs(p))
+    out["inverse_mass_f64ff_ms"] = ev(lambda: ctx.mass("viscous", u0, y, coeff=2.0, arith="f64ff", inverse=True))
+    dt = ctx.cfl_dt(u0, courant)
+    out["dt"] = dt
+    ctx.step_init(u0)
+    rows = []
+    for i in range(warm + steps):
+        st = ctx.step(rh, dt, wall=wall, ppe_rtol=1e-8, visc_rtol=1e-8)
+        if i >= warm:
+            rows.append(st)
+    keys = ("seconds", "t_convective", "t_pressure", "t_projection", "t_viscous")
+    out.update({f"mean_{k2}": float(np.mean([r[k2] for r in rows])) for k2 in keys})
+    out["ppe_iterations"] = [r["ppe_iterations"] for r in rows]
+    out["visc_iterations"] = [r["visc_iterations"] for r in rows]
+    out["steps_per_s"] = 1.0 / out["mean_seconds"]
+    ctx.close()
     return out
 
 

@@ -392,7 +392,12 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   CK(launch_reciprocal(L.ndofs, L.diag64, L.dinv64, st));
   CK((launch_cast<double, float>(L.ndofs, L.dinv64, L.dinv32, st)));
   if (l + 1 == (int)H.L.size()) return SIPG_OK;
-  // Lanczos on D^-1/2 A D^-1/2 with FP64 level applies
+  // Lanczos on D^-1/2 A D^-1/2 with level applies in the multigrid's arithmetic:
+  // the Chebyshev smoother applies that operator, and the estimate needs a few
+  // digits only (FP32 applies are 8x cheaper than FP64 ones on this GPU)
+  const bool f32 = opts.mg_precision == SIPG_F32;
+  float* w32 = (float*)L.w[1][2];
+  float* t32 = (float*)L.w[1][3];
   double* q = (double*)L.w[0][0];
   double* qp = (double*)L.w[0][1];
   double* w = (double*)L.w[0][2];
@@ -407,16 +412,24 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   CK(launch_fill<double>(n, 0.0, qp, st));
   std::vector<double> al, be;
   double beta = 0.0;
+  // s = sqrt(dinv) once, kept in diag64 (the diagonal itself is not needed again
+  // below the coarsest level)
+  double* sd = L.diag64;
+  CK((launch_cast<double, double>(n, L.dinv64, sd, st)));
+  sqrt_inplace(n, sd);
   for (int j = 0; j < opts.lanczos_steps; ++j) {
-    // w = s A (s q) - beta q_prev, s = sqrt(dinv)
-    CK((launch_cast<double, double>(n, L.dinv64, t, st)));
-    sqrt_inplace(n, t);
-    CK(launch_mul(n, t, q, w, st));
-    rc = level_apply<double>(op, l, w, t, mass);
-    if (rc) return rc;
-    CK((launch_cast<double, double>(n, L.dinv64, w, st)));
-    sqrt_inplace(n, w);
-    CK(launch_mul(n, w, t, w, st));
+    // w = s A (s q) - beta q_prev
+    CK(launch_mul(n, sd, q, w, st));
+    if (f32) {
+      CK((launch_cast<double, float>(n, w, w32, st)));
+      rc = level_apply<float>(op, l, w32, t32, mass);
+      if (rc) return rc;
+      CK((launch_cast<float, double>(n, t32, t, st)));
+    } else {
+      rc = level_apply<double>(op, l, w, t, mass);
+      if (rc) return rc;
+    }
+    CK(launch_mul(n, sd, t, w, st));
     if (j > 0) CK(launch_add_scaled_f64(n, -beta, qp, w, st));
     double alpha;
     rc = dot(n, q, w, &alpha);
@@ -436,6 +449,7 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   L.lmax = tridiag_lmax(al, be);
   // leave the work vectors zeroed for later use
   for (int v = 0; v < 4; ++v) CK(cudaMemsetAsync(L.w[0][v], 0, sizeof(double) * (size_t)n, st));
+  for (int v = 2; v < 4; ++v) CK(cudaMemsetAsync(L.w[1][v], 0, sizeof(float) * (size_t)n, st));
   return SIPG_OK;
 }
 
@@ -468,14 +482,19 @@ int sipg_ctx::setup_coarse(int op, double mass) {
     const double mean_diag = hscal[0] / N;
     CK(launch_add_rank1(N, mean_diag / N, C.Ainv, st));
   }
-  // Gauss-Jordan inverse, ping-pong between Ainv and Atmp
-  double* A = C.Ainv;
-  double* B = C.Atmp;
+  // Gauss-Jordan inverse in float-float storage (48-bit significands, the FP32
+  // pipe instead of the 75x slower FP64 one), ping-pong between the two
+  // buffers, converted back to binary64 once at the end
+  CK(launch_to_ff_inplace((int64_t)N * N, C.Ainv, st));
+  float2* A = reinterpret_cast<float2*>(C.Ainv);
+  float2* B = reinterpret_cast<float2*>(C.Atmp);
   for (int k = 0; k < N; ++k) {
-    CK(launch_gj_step(N, k, A, B, dscal + 8, st));
+    CK(launch_gj_step_ff(N, k, A, B, reinterpret_cast<float2*>(dscal + 8), st));
     std::swap(A, B);
   }
-  if (A != C.Ainv) CK(cudaMemcpyAsync(C.Ainv, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
+  if (A != reinterpret_cast<float2*>(C.Ainv))
+    CK(cudaMemcpyAsync(C.Ainv, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st));
+  CK(launch_from_ff_inplace((int64_t)N * N, C.Ainv, st));
   return SIPG_OK;
 }
 

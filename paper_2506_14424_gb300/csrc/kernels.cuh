@@ -104,7 +104,9 @@ cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, doubl
 cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st);
 // dense FP64 helpers for the coarse level
 cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st);
-cudaError_t launch_gj_step(int N, int k, const double* A, double* B, double* recip, cudaStream_t st);
+cudaError_t launch_gj_step_ff(int N, int k, const float2* A, float2* B, float2* recip, cudaStream_t st);
+cudaError_t launch_to_ff_inplace(int64_t n, double* v, cudaStream_t st);
+cudaError_t launch_from_ff_inplace(int64_t n, double* v, cudaStream_t st);
 cudaError_t launch_gemv(int N, const double* M, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_add_rank1(int N, double c, double* M, cudaStream_t st);
 cudaError_t launch_node_points(int n, const LevelGeom& g, const Tab& tab, double* xyz, cudaStream_t st);

@@ -1,6 +1,7 @@
 // Multigrid and Krylov building blocks: operator diagonal, p/h transfers,
 // Chebyshev and CG vector updates, deterministic reductions and the dense FP64
 // coarse-level helpers (Sec. 5.4 of the paper).
+#include "ff.cuh"
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -24,14 +25,15 @@ inline int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + kBS - 1) /
 //  Poisson face:  interior  -sigma phi d_d phi + tau phi^2;  Dirichlet 2 x the same
 // The cell sums factor over the tensor product: sum_q F(q) prod_d A_d[q_d][i_d]^2
 // with F = W nu (or W) and A_d = DS (derivative direction) or S, one sweep per
-// direction; face terms vanish unless the DoF lies on the face layer.
+// direction; face terms vanish unless the DoF lies on the face layer, and
+// there they reduce to 2D contractions with S^2 (one per face).
 // One CTA per cell.
 template <int N, int NC>
 __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__ nu_cell,
                                 const double* __restrict__ nu_face, double mass, double* __restrict__ diag) {
   constexpr int N2 = N * N, N3 = N2 * N;
   __shared__ double F[N3], Fm[N3], T1[N3], T2[N3], C[4][N3];
-  __shared__ double S2[N2], D2[N2];
+  __shared__ double S2[N2], D2[N2], FD[6][N2];
   const int e = blockIdx.x;
   const double detJ = g.h[0] * g.h[1] * g.h[2];
   for (int i = threadIdx.x; i < N2; i += blockDim.x) {
@@ -72,7 +74,55 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
     }
     __syncthreads();
   }
+  // faces: both face terms are proportional to phi_i(p)^2 (d_d phi_i = l'(layer) phi_i / h_d
+  // on the face), so each face is a 2D contraction of a per-point factor with S^2:
+  //   FD_f[a_i, b_i] = sum_{a,b} S[a][a_i]^2 S[b][b_i]^2 F_f(a, b)
   const double lam_e = penalty_lambda(g, e);
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    const int nb = cell_neighbor(g, e, f);
+    const bool skip = nb < 0 && g.bc[f] == 1;  // homogeneous Neumann: no face term
+    const double sigma = s ? 1.0 : -1.0;
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
+    const double dl = (s ? tab.dS1[N - 1] : tab.dS0[0]) * g.ih[d];  // l'(layer) / h_d
+    const double area = g.h[t1] * g.h[t2];
+    const double mirror = nb >= 0 ? 1.0 : 2.0;
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      const double W = tab.gw[p % N] * tab.gw[p / N] * area;
+      double v = 0.0;
+      if (!skip) {
+        if (NC == 3) {
+          const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
+          const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p] : num;
+          double nub = num > nup ? num : nup;
+          if (g.face_nu == 1) nub = 0.5 * (num + nup);
+          if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
+          const double tau = g.cip * N * N * lam * nub;
+          v = mirror * W * (-num * sigma * dl + tau);
+        } else {
+          const double tau = g.cip * N * N * lam;
+          v = mirror * W * (-sigma * dl + tau);
+        }
+      }
+      T1[p] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < N2; o += blockDim.x) {  // (b, a_i)
+      const int ai = o % N, bq = o / N;
+      double acc = 0.0;
+      for (int aq = 0; aq < N; ++aq) acc += S2[aq * N + ai] * T1[bq * N + aq];
+      T2[o] = acc;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < N2; o += blockDim.x) {  // (b_i, a_i)
+      const int ai = o % N, bi = o / N;
+      double acc = 0.0;
+      for (int bq = 0; bq < N; ++bq) acc += S2[bq * N + bi] * T2[bq * N + ai];
+      FD[f][o] = acc;
+    }
+    __syncthreads();
+  }
   for (int idx = threadIdx.x; idx < NC * N3; idx += blockDim.x) {
     const int c = idx / N3, r = idx % N3;
     const int ii[3] = {r % N, (r / N) % N, r / N2};
@@ -84,33 +134,9 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, s = f & 1;
       if (ii[d] != (s ? N - 1 : 0)) continue;  // shape function vanishes on this face
-      const int nb = cell_neighbor(g, e, f);
-      if (nb < 0 && g.bc[f] == 1) continue;
-      const double sigma = s ? 1.0 : -1.0;
       const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-      const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
-      const double* dS = s ? tab.dS1 : tab.dS0;
-      const double area = g.h[t1] * g.h[t2];
-      const double mirror = nb >= 0 ? 1.0 : 2.0;
-      for (int p = 0; p < N2; ++p) {
-        const int a = p % N, b = p / N;
-        const double phi = tab.S[a * N + ii[t1]] * tab.S[b * N + ii[t2]];
-        const double dd = dS[ii[d]] * phi * g.ih[d];
-        const double W = tab.gw[a] * tab.gw[b] * area;
-        if (NC == 3) {
-          const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
-          const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p] : num;
-          double nub = num > nup ? num : nup;
-          if (g.face_nu == 1) nub = 0.5 * (num + nup);
-          if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
-          const double tau = g.cip * N * N * lam * nub;
-          const double fac = c == d ? 2.0 : 1.0;
-          acc += mirror * W * fac * (-num * sigma * phi * dd + tau * phi * phi);
-        } else {
-          const double tau = g.cip * N * N * lam;
-          acc += mirror * W * (-sigma * phi * dd + tau * phi * phi);
-        }
-      }
+      const double fac = (NC == 3 && c == d) ? 2.0 : 1.0;
+      acc += fac * FD[f][ii[t1] + N * ii[t2]];
     }
     diag[((size_t)e * NC + c) * N3 + r] = acc;
   }
@@ -530,33 +556,64 @@ cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStrea
   return cudaGetLastError();
 }
 
-// One Gauss-Jordan step (pivot k) from A into B (both N x N row-major): the
-// inverse of an SPD matrix after N steps, no pivoting. recip[k & 1] holds
-// 1 / A[k][k]; the thread that writes the next pivot B[k+1][k+1] stores its
-// reciprocal in recip[(k + 1) & 1], so no thread divides per element.
-__global__ void gj_step_kernel(int N, int k, const double* __restrict__ A, double* __restrict__ B,
-                               double* __restrict__ recip) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)N * N) return;
-  const int i = (int)(idx / N), j = (int)(idx % N);
-  const double rp = recip[k & 1];
-  double v;
+// Gauss-Jordan step k on the dense coarse matrix (no pivoting: the coarse
+// operator is SPD, or SPD after the rank-one term of the singular Poisson
+// case): B = A with row k scaled by 1/A[k][k] and column k eliminated from
+// the other rows. The thread that writes the next pivot B[k+1][k+1] stores
+// its reciprocal in recip[(k + 1) & 1], so no thread divides per element.
+// Entries are float-float (float2 = (hi, lo)), one row per blockIdx.y; recip
+// holds two float-float pivot reciprocals.
+__global__ void gj_step_ff_kernel(int N, int k, const float2* __restrict__ A, float2* __restrict__ B,
+                                  float2* __restrict__ recip) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const float2 r2 = recip[k & 1];
+  const ff rp(r2.x, r2.y);
+  auto ld = [&](size_t at) { const float2 v = A[at]; return ff(v.x, v.y); };
+  ff v;
   if (i == k && j == k)
     v = rp;
   else if (i == k)
-    v = A[(size_t)k * N + j] * rp;
+    v = ld((size_t)k * N + j) * rp;
   else if (j == k)
-    v = -A[(size_t)i * N + k] * rp;
+    v = -(ld((size_t)i * N + k) * rp);
   else
-    v = A[idx] - A[(size_t)i * N + k] * (A[(size_t)k * N + j] * rp);
-  B[idx] = v;
-  if (i == k + 1 && j == k + 1) recip[(k + 1) & 1] = 1.0 / v;
+    v = ld((size_t)i * N + j) - ld((size_t)i * N + k) * (ld((size_t)k * N + j) * rp);
+  B[(size_t)i * N + j] = make_float2(v.hi, v.lo);
+  if (i == k + 1 && j == k + 1) {
+    const ff r = ff(1.0f) / v;
+    recip[(k + 1) & 1] = make_float2(r.hi, r.lo);
+  }
 }
-__global__ void recip_first_kernel(const double* A, double* recip) { recip[0] = 1.0 / A[0]; }
-cudaError_t launch_gj_step(int N, int k, const double* A, double* B, double* recip, cudaStream_t st) {
-  if (k == 0) recip_first_kernel<<<1, 1, 0, st>>>(A, recip);
-  const int64_t total = (int64_t)N * N;
-  gj_step_kernel<<<(int)((total + kBS - 1) / kBS), kBS, 0, st>>>(N, k, A, B, recip);
+__global__ void recip_first_ff_kernel(const float2* A, float2* recip) {
+  const ff r = ff(1.0f) / ff(A[0].x, A[0].y);
+  recip[0] = make_float2(r.hi, r.lo);
+}
+cudaError_t launch_gj_step_ff(int N, int k, const float2* A, float2* B, float2* recip, cudaStream_t st) {
+  if (k == 0) recip_first_ff_kernel<<<1, 1, 0, st>>>(A, recip);
+  gj_step_ff_kernel<<<dim3((N + kBS - 1) / kBS, N), kBS, 0, st>>>(N, k, A, B, recip);
+  return cudaGetLastError();
+}
+// in-place binary64 <-> float-float (same 8 bytes per entry)
+__global__ void to_ff_kernel(int64_t n, double* v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const ff a(v[i]);
+    reinterpret_cast<float2*>(v)[i] = make_float2(a.hi, a.lo);
+  }
+}
+__global__ void from_ff_kernel(int64_t n, double* v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = reinterpret_cast<const float2*>(v)[i];
+    v[i] = to_double(ff(a.x, a.y));
+  }
+}
+cudaError_t launch_to_ff_inplace(int64_t n, double* v, cudaStream_t st) {
+  to_ff_kernel<<<blocks_for(n), kBS, 0, st>>>(n, v);
+  return cudaGetLastError();
+}
+cudaError_t launch_from_ff_inplace(int64_t n, double* v, cudaStream_t st) {
+  from_ff_kernel<<<blocks_for(n), kBS, 0, st>>>(n, v);
   return cudaGetLastError();
 }
 

@@ -90,8 +90,11 @@ def test_smoother_matches_oracle_chebyshev(prec, tol):
         assert _rel(x, ref) <= tol, level
 
 
-def test_lanczos_estimate_bounded_by_exact():
-    ctx = Context(2, 2, 2, 3)
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 2e-6)])
+def test_lanczos_estimate_bounded_by_exact(prec, tol):
+    # the estimate is of the operator the smoother applies: FP32 multigrid
+    # estimates the FP32-rounded operator (relative perturbation ~ 1e-7)
+    ctx = Context(2, 2, 2, 3, mg_precision=prec)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     mats, _, _ = _oracle_hierarchy(ctx, "viscous", rheo, "DDDDDD")
@@ -100,7 +103,7 @@ def test_lanczos_estimate_bounded_by_exact():
         s = 1.0 / np.sqrt(np.diag(A))
         exact = np.linalg.eigvalsh(s[:, None] * A * s[None, :])[-1]
         est = ctx.lmax_estimate("viscous", level)
-        assert est <= exact * (1 + 1e-10) and est >= 0.8 * exact, (level, est, exact)
+        assert est <= exact * (1 + tol) and est >= 0.8 * exact, (level, est, exact)
 
 
 @pytest.mark.parametrize("op,bc", [("viscous", "DDDDDD"), ("poisson", "NNNNNN")])
