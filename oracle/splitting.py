@@ -51,6 +51,10 @@ with explicit basis functions at the Gauss points, as written in the paper:
   nu "linear implicit" = eta(gamma_dot(eps(u^#))), u^# = sum_{i<m} beta_i u^{n-i}
   (Alg. 1 then leaves its loop after one pass), or "implicit" by the
   Picard/Aitken loop of oracle.nonlinear.
+  With alpha_c = 1 and u* = u^# (the linearly implicit convective term of
+  Eq. viscous_step_with_convection) the operator gains c_h(v, u; u^#) - not
+  symmetric - and the right-hand side sum_i beta_i c_h(v, u^{n-i}; u^{n-i})
+  (``convective_blocks``, ``convective_wall_rhs``).
 * Time step, Eq. (CFL_timestep_selection): dt = Cr / k^1.5 / max_{e,q} |J^-1 u|.
 
 The oracle solves every linear system exactly (sparse LU; the pressure with a
@@ -136,6 +140,68 @@ def convective_vector(S, u, g_faces):
             flux = wn[:, None] * (udag - um)
             Wf = S.face_w2 * S.mesh.face_area(d)
             out[e] += np.einsum('p,pi,pc->ci', Wf, S.face_phi[f], flux)
+    return out.reshape(-1)
+
+
+def convective_blocks(S, w, g_w):
+    """Sparse matrix of u -> sum_e c_h(phi_a, u; w) for a fixed transport velocity w
+    (Eq. convective_term_weak, linear in u), homogeneous wall data for u (u^+ = -u^-);
+    w's exterior on walls from its own data g_w. The linearly implicit convective term
+    of the viscous step (alpha_c = 1, u* = u^#)."""
+    mesh = S.mesh
+    C = mesh.n_cells
+    m = S.n_dofs_cell
+    n3 = S.n ** 3
+    W = S.cell_w * mesh.volume()
+    rows, cols, vals = [], [], []
+    ii, jj = np.meshgrid(np.arange(n3), np.arange(n3), indexing='ij')
+
+    def put(e_row, e_col, blk):
+        for c in range(3):
+            rows.append(e_row * m + c * n3 + ii.ravel())
+            cols.append(e_col * m + c * n3 + jj.ravel())
+            vals.append(blk.ravel())
+
+    for e in range(C):
+        wq = _values(S.cell_phi, _cell(S, w, e))
+        dphi = S._phys_grad(S.cell_dphi)
+        put(e, e, np.einsum('p,pi,pl,pjl->ij', W, S.cell_phi, wq, dphi))
+        for f in range(6):
+            d, s, nvec = face_normal(f)
+            wm, _, wp, _, bt = _exterior(S, w, e, f, g_w)
+            if bt == 'N':
+                continue
+            wn = 0.5 * (wm + wp) @ nvec
+            up_fac = 0.5 * (1.0 - np.sign(wn)) * wn      # coefficient of (u^+ - u^-)
+            Wf = S.face_w2 * mesh.face_area(d)
+            phi = S.face_phi[f]
+            if bt == 'I':
+                nb = mesh.neighbor(e, f)
+                fo = 2 * d + (1 - s)
+                put(e, e, -np.einsum('p,pi,pj->ij', Wf * up_fac, phi, phi))
+                put(e, nb, np.einsum('p,pi,pj->ij', Wf * up_fac, phi, S.face_phi[fo]))
+            else:  # Dirichlet, homogeneous: u^+ - u^- = -2 u^-
+                put(e, e, -2.0 * np.einsum('p,pi,pj->ij', Wf * up_fac, phi, phi))
+    N = S.n_dofs
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N)).tocsr()
+
+
+def convective_wall_rhs(S, w, g_w, g_u):
+    """The wall-data part of c_h(., u; w) (u^+ = -u^- + 2 g_u), moved to the right-hand side."""
+    mesh = S.mesh
+    out = np.zeros((mesh.n_cells, 3, S.n ** 3))
+    for e in range(mesh.n_cells):
+        for f in range(6):
+            if mesh.boundary_type(e, f) != 'D':
+                continue
+            d, s, nvec = face_normal(f)
+            wm, _, wp, _, _ = _exterior(S, w, e, f, g_w)
+            wn = 0.5 * (wm + wp) @ nvec
+            up_fac = 0.5 * (1.0 - np.sign(wn)) * wn
+            g = wall_data(S, g_u, e, f)
+            Wf = S.face_w2 * mesh.face_area(d)
+            out[e] -= np.einsum('p,pi,pc->ci', Wf * up_fac * 2.0, S.face_phi[f], g)
     return out.reshape(-1)
 
 
@@ -297,7 +363,8 @@ def pressure_solve(Sp_op, rhs):
 class Splitting:
     """State and one-step driver of the projection scheme on a box."""
 
-    def __init__(self, mesh, k, rheology, g_faces=None, body=None, viscosity_mode='linear', penalty_factor=1.0):
+    def __init__(self, mesh, k, rheology, g_faces=None, body=None, viscosity_mode='linear', penalty_factor=1.0,
+                 convective='explicit'):
         self.mesh, self.k = mesh, int(k)
         self.rheology = rheology
         self.g_faces = [np.zeros(3) if g_faces is None else
@@ -310,6 +377,7 @@ class Splitting:
         self.Sp_op = SIPG(self.pmesh, k - 1, 1, penalty_factor=penalty_factor)      # PPE operator
         self.body = None if body is None else np.asarray(body, dtype=np.float64)
         self.mode = viscosity_mode
+        self.convective = convective   # 'explicit' (alpha_c = 0) or 'linear_implicit' (alpha_c = 1, u* = u#)
         self.hist = []
         self.p = None
         self.steps = 0
@@ -328,7 +396,8 @@ class Splitting:
         rhs = sum(alpha[i] / dt * omass.apply_mass(Su, hist[i]) for i in range(order))
         if self.body is not None:
             rhs = rhs + omass.apply_mass(Su, self.body)
-        rhs = rhs - sum(beta[i] * convective_vector(Su, hist[i], self.g_faces) for i in range(order))
+        conv = [convective_vector(Su, hist[i], self.g_faces) for i in range(order)]
+        rhs = rhs - sum(beta[i] * conv[i] for i in range(order))
         uhat = omass.apply_inverse_mass(Su, rhs, gamma0 / dt)
         # pressure step
         bnd = {}
@@ -346,7 +415,17 @@ class Splitting:
         u_sharp = sum(beta[i] * hist[i] for i in range(order))
         nc, nf = Su.viscosity_at_points(self.rheology, u_sharp)
         b = omass.apply_mass(Su, uhh, m)
-        if picard is None:
+        if self.convective == 'linear_implicit':
+            # alpha_c = 1: + c_h(v, u^{n+1}; u#) on the left, + sum_i beta_i c_h(v, u^{n-i}; u^{n-i})
+            # on the right (Eq. viscous_step_weak); wall data of both terms on the right
+            if picard is not None:
+                raise ValueError("the linearly implicit convective step takes the linear-implicit viscosity")
+            b = b + viscous_dirichlet_rhs(Su, nf, self.g_faces) + sum(beta[i] * conv[i] for i in range(order))
+            b = b + convective_wall_rhs(Su, u_sharp, self.g_faces, self.g_faces)
+            K = Su.assemble(nc, nf, mass=m) + convective_blocks(Su, u_sharp, self.g_faces)
+            u_new = spla.spsolve(K.tocsc(), b)
+            info = None
+        elif picard is None:
             b = b + viscous_dirichlet_rhs(Su, nf, self.g_faces)
             u_new = spla.spsolve(Su.assemble(nc, nf, mass=m).tocsc(), b)
             info = None

@@ -154,3 +154,57 @@ def test_hydrostatic_state_preserved():
         out = sp.step(0.02)
         assert np.abs(out['u']).max() <= 1e-12
         assert np.abs(out['p'] - pz).max() <= 1e-11
+
+
+def test_linearised_convective_matches_nonlinear_form():
+    """c_h(., u; w) assembled for w = u (with the wall data moved back) is C(u)."""
+    mesh = BoxMesh(2, 2, 1, extent=(1.0, 0.8, 0.5))
+    S = SIPG(mesh, 2, 3)
+    u = np.random.default_rng(3).uniform(-1, 1, S.n_dofs)
+    g = [np.random.default_rng(10 + f).uniform(-1, 1, 3) for f in range(6)]
+    K = osp.convective_blocks(S, u, g)
+    lhs = K @ u - osp.convective_wall_rhs(S, u, g, g)
+    ref = osp.convective_vector(S, u, g)
+    assert np.abs(lhs - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_upwind_energy_identity():
+    """For a continuous divergence-free w with w.n = 0 on the walls, u^T C(w) u equals the
+    upwind dissipation sum over interior faces of 1/2 |w.n| |u^- - u^+|^2 (integration by
+    parts of (u, (w.grad) u) = -(1/2)(div w, |u|^2) + boundary terms)."""
+    mesh = BoxMesh(2, 2, 2)
+    k = 3
+    S = SIPG(mesh, k, 3)
+    # w = curl of a stream function vanishing on the walls' normal directions: divergence free,
+    # w.n = 0 on every wall; w = (sin(pi x)... ) chosen in Q_3: psi-free form below
+    wfn = lambda x: np.stack([x[:, 0] * (1 - x[:, 0]) * (1 - 2 * x[:, 1]),
+                              -(1 - 2 * x[:, 0]) * x[:, 1] * (1 - x[:, 1]),
+                              0 * x[:, 0]], axis=1)
+    w = S.interpolate(wfn)
+    u = np.random.default_rng(4).uniform(-1, 1, S.n_dofs)
+    K = osp.convective_blocks(S, w, [np.zeros(3)] * 6)
+    lhs = u @ (K @ u)
+    diss = 0.0
+    for e in range(mesh.n_cells):
+        for f in range(6):
+            if mesh.boundary_type(e, f) != 'I':
+                continue
+            d, s, nvec = osp.face_normal(f)
+            um, _, up, _, _ = osp._exterior(S, u, e, f, None)
+            wm, _, wp, _, _ = osp._exterior(S, w, e, f, None)
+            wn = 0.5 * (wm + wp) @ nvec
+            Wf = S.face_w2 * mesh.face_area(d)
+            diss += 0.5 * 0.5 * np.sum(Wf * np.abs(wn) * np.sum((um - up) ** 2, axis=1))  # each face seen twice
+    assert abs(lhs - diss) <= 1e-12 * max(abs(diss), 1.0)
+
+
+def test_linearly_implicit_convective_step_preserves_uniform_flow():
+    mesh = BoxMesh(2, 2, 2)
+    U = np.array([0.4, -0.3, 0.2])
+    law = {'law': 'constant', 'nu': 0.05}
+    sp = osp.Splitting(mesh, 2, law, g_faces=[U] * 6, convective='linear_implicit')
+    u0 = sp.Su.interpolate(lambda x: np.broadcast_to(U, x.shape).copy())
+    sp.set_initial(u0)
+    for _ in range(2):
+        out = sp.step(0.05)
+        assert np.abs(out['u'] - u0).max() <= 1e-12
