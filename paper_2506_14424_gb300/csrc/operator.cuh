@@ -121,6 +121,28 @@ template <int N, int NC> struct OpCfg {
   static constexpr int NT = ((LINES + 31) / 32) * 32;
 };
 
+// Minimum resident CTAs per SM requested from the compiler, from a register
+// budget per thread: the float-float and FP32 kernels are issue and latency
+// bound, and more resident warps hide more of it. Measured at 32^3, k = 3:
+// float-float 72 -> 56 registers 1.347 -> 1.266 ms (36 bytes of spills),
+// FP32 59 -> 48 registers 0.398 -> 0.361 ms; lower budgets spill more and run
+// slower. The native FP64 kernel is bound by the FP64 pipe and keeps MIN = 1.
+#ifndef SIPG_FF_REG
+#define SIPG_FF_REG 56
+#endif
+template <int N, int NC, typename T> struct OccCfg { static constexpr int MIN = 1; };
+#ifndef SIPG_F32_REG
+#define SIPG_F32_REG 48
+#endif
+template <int N, int NC> struct OccCfg<N, NC, float> {
+  static constexpr int REG = SIPG_F32_REG;
+  static constexpr int MIN = REG == 0 ? 1 : (65536 / (OpCfg<N, NC>::NT * REG) > 0 ? 65536 / (OpCfg<N, NC>::NT * REG) : 1);
+};
+template <int N, int NC> struct OccCfg<N, NC, ff> {
+  static constexpr int REG = SIPG_FF_REG;
+  static constexpr int MIN = 65536 / (OpCfg<N, NC>::NT * REG) > 0 ? 65536 / (OpCfg<N, NC>::NT * REG) : 1;
+};
+
 // Shared-memory layout per cell (elements of T): staged x, the y accumulator,
 // and a work region used by the cell phase (3 tensors) and then by the face
 // phase (16 face slots: 8 per side of one direction).
@@ -589,7 +611,7 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
 // One CTA per CPB consecutive cells of one level; blockIdx.y selects one of
 // several vectors applied in the same launch (columns of a batch).
 template <int N, int NC, typename TS, typename TN, typename T>
-__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
+__global__ void __launch_bounds__(OpCfg<N, NC>::NT, (OccCfg<N, NC, T>::MIN))
 apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
              const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -614,7 +636,7 @@ struct ApplyDesc {
 };
 
 template <int N, int NC, typename TS, typename TN, typename T>
-__global__ void __launch_bounds__(OpCfg<N, NC>::NT)
+__global__ void __launch_bounds__(OpCfg<N, NC>::NT, (OccCfg<N, NC, T>::MIN))
 apply_multi_kernel(const ApplyDesc<TS, TN>* __restrict__ descs, const int2* __restrict__ tiles, int ntiles,
                    CTab<T> ct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
