@@ -415,6 +415,18 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
     out["ppe_iterations"] = [r["ppe_iterations"] for r in rows]
     out["visc_iterations"] = [r["visc_iterations"] for r in rows]
     out["steps_per_s"] = 1.0 / out["mean_seconds"]
+    # the convective term linearly implicit in the viscous step (alpha_c = 1, GMRES(30)
+    # right-preconditioned by the V-cycle), same Courant number
+    ctx.step_init(u0)
+    rows = []
+    for i in range(warm + steps):
+        st = ctx.step(rh, dt, wall=wall, ppe_rtol=1e-8, visc_rtol=1e-8, convective_mode="linear_implicit")
+        if i >= warm:
+            rows.append(st)
+    out["linear_implicit_convection"] = {
+        "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
+        "mean_t_viscous": float(np.mean([r["t_viscous"] for r in rows])),
+        "gmres_iterations": [r["visc_iterations"] for r in rows]}
     ctx.close()
     return out
 

@@ -276,6 +276,7 @@ int sipg_picard_solve(sipg_ctx* ctx, const sipg_rheology* rh, const double* b, d
  * BDF1 for the first step after sipg_step_init, BDF2 afterwards (gamma0 = 3/2,
  * alpha = (2, -1/2), beta = (2, -1)). Laws: SIPG_LAW_CONSTANT or SIPG_LAW_CARREAU. */
 enum { SIPG_VISC_LINEAR_IMPLICIT = 0, SIPG_VISC_IMPLICIT = 1 };
+enum { SIPG_CONV_EXPLICIT = 0, SIPG_CONV_LINEAR_IMPLICIT = 1 };
 enum { SIPG_FIELD_U = 0, SIPG_FIELD_P = 1, SIPG_FIELD_UHAT = 2, SIPG_FIELD_UHATHAT = 3, SIPG_FIELD_PPE_RHS = 4,
        SIPG_FIELD_U_PREV = 5 };
 
@@ -284,6 +285,10 @@ typedef struct {
   double wall_velocity[18];  /* g on box sides -x,+x,-y,+y,-z,+z (3 components each) [0] */
   const double* body;        /* DEVICE body force b_h on the velocity space, or NULL [NULL] */
   int viscosity_mode;        /* SIPG_VISC_* [LINEAR_IMPLICIT] */
+  int convective_mode;       /* SIPG_CONV_EXPLICIT (alpha_c = 0) or SIPG_CONV_LINEAR_IMPLICIT
+                                (alpha_c = 1, u* = u#: c_h(v, u^{n+1}; u#) in the viscous step,
+                                solved by GMRES; linear-implicit viscosity only) [EXPLICIT] */
+  int gmres_restart;         /* GMRES restart length [30] */
   double ppe_rtol;           /* pressure CG: ||r|| <= ppe_rtol ||rhs|| [1e-8] */
   double visc_rtol;          /* viscous CG (linear implicit) [1e-8] */
   int maxit;                 /* CG iteration limit of both [1000] */
@@ -325,7 +330,24 @@ int sipg_cfl_dt(sipg_ctx* ctx, const double* u, double courant, double* dt);
  * viscous form with the stored level-0 viscosity. */
 int sipg_convective_apply(sipg_ctx* ctx, const double* wall_g, const double* u, double* y);
 int sipg_projection_rhs(sipg_ctx* ctx, const double* p, double* y);
+/* y = sum_e c_h(v, u; w): the convective form linear in u for a fixed transport
+ * velocity w, walls u^+ = -u^- + 2 wall_u, w^+ = -w^- + 2 wall_w (18 host
+ * doubles each, NULL = 0). */
+int sipg_convective_lin_apply(sipg_ctx* ctx, const double* w, const double* wall_w, const double* wall_u,
+                              const double* u, double* y);
 int sipg_viscous_wall_rhs(sipg_ctx* ctx, const double* wall_g, double* y);
+
+/* Solve ((mass_coeff M + A(nu)) + C(w)) x = b, C(w) u = sum_e c_h(v, u; w) the
+ * upwind convective form of Eq. (convective_term_weak) linear in u for the
+ * transport velocity w (DEVICE, fine velocity level; NULL: no convective
+ * term): the viscous step with the linearly implicit convective term
+ * (alpha_c = 1, u* = u#, Eq. viscous_step_with_convection). The operator is
+ * not symmetric: restarted GMRES(restart) with right preconditioning by so->
+ * precond (the multigrid V-cycle of the symmetric part mass_coeff M + A).
+ * Homogeneous wall data for x; wall_w (18 host doubles or NULL) is w's wall
+ * velocity. The first call allocates restart + 4 fine-level vectors. (sync) */
+int sipg_solve_convective(sipg_ctx* ctx, const double* w, const double* wall_w, const double* b, double* x,
+                          const sipg_solve_opts* so, int restart, sipg_solve_stats* stats);
 
 /* ------------------------------------------------ multigrid pieces (tests) */
 /* Test hook for the float-float conversions of the SIPG_F64_FF kernels' loads

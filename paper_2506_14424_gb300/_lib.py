@@ -31,10 +31,11 @@ EXPORTS = [
     "sipg_server_last_error", "sipg_server_destroy", "sipg_mass_apply", "sipg_inverse_mass_apply",
     "sipg_default_picard_opts", "sipg_picard_solve", "sipg_ff_convert", "sipg_default_step_opts",
     "sipg_step_init", "sipg_step", "sipg_step_field", "sipg_cfl_dt", "sipg_convective_apply",
-    "sipg_projection_rhs", "sipg_viscous_wall_rhs",
+    "sipg_projection_rhs", "sipg_viscous_wall_rhs", "sipg_solve_convective", "sipg_convective_lin_apply",
 ]
 FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
 VISC_MODE = {"linear": 0, "implicit": 1}
+CONV_MODE = {"explicit": 0, "linear_implicit": 1}
 
 
 class MeshDesc(ctypes.Structure):
@@ -84,7 +85,8 @@ class PicardStats(ctypes.Structure):
 
 class StepOpts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("wall_velocity", ctypes.c_double * 18),
-                ("body", ctypes.c_void_p), ("viscosity_mode", ctypes.c_int), ("ppe_rtol", ctypes.c_double),
+                ("body", ctypes.c_void_p), ("viscosity_mode", ctypes.c_int), ("convective_mode", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("ppe_rtol", ctypes.c_double),
                 ("visc_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("picard", PicardOpts)]
 
 
@@ -168,6 +170,8 @@ def load(path=None):
         "sipg_convective_apply": (i, [vp, vp, vp, vp]),
         "sipg_projection_rhs": (i, [vp, vp, vp]),
         "sipg_viscous_wall_rhs": (i, [vp, vp, vp]),
+        "sipg_solve_convective": (i, [vp, vp, vp, vp, vp, P(SolveOpts), i, P(SolveStats)]),
+        "sipg_convective_lin_apply": (i, [vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -218,6 +218,17 @@ class Context:
         self._check(self._lib.sipg_convective_apply(self._h, wp, _ptr(u), _ptr(y)))
         return y
 
+    def convective_lin(self, w, u, wall_w=None, wall_u=None):
+        """y = sum_e c_h(., u; w) (linear in u; see sipg_convective_lin_apply)."""
+        _need_cuda(w, torch.float64)
+        _need_cuda(u, torch.float64)
+        y = torch.empty_like(u)
+        ww, wu = self._wall(wall_w), self._wall(wall_u)
+        self._check(self._lib.sipg_convective_lin_apply(
+            self._h, _ptr(w), ww.ctypes.data_as(ctypes.c_void_p) if ww is not None else None,
+            wu.ctypes.data_as(ctypes.c_void_p) if wu is not None else None, _ptr(u), _ptr(y)))
+        return y
+
     def projection_rhs(self, p):
         _need_cuda(p, torch.float64)
         y = torch.empty(self.n_dofs("viscous"), dtype=torch.float64, device=p.device)
@@ -240,8 +251,26 @@ class Context:
         _need_cuda(u0, torch.float64)
         self._check(self._lib.sipg_step_init(self._h, _ptr(u0), _ptr(p0)))
 
+    def solve_convective(self, w, b, x=None, wall=None, rtol=1e-8, atol=0.0, maxit=500, precond="mg", mass=0.0,
+                         restart=30, check=True):
+        """GMRES solve of ((mass M + A(nu)) + C(w)) x = b (see sipg_solve_convective)."""
+        _need_cuda(b, torch.float64)
+        if w is not None:
+            _need_cuda(w, torch.float64)
+        x = torch.zeros_like(b) if x is None else x
+        so = L.SolveOpts(float(rtol), float(atol), int(maxit), L.PRECOND[precond], float(mass))
+        st = L.SolveStats()
+        wl = self._wall(wall)
+        wp = wl.ctypes.data_as(ctypes.c_void_p) if wl is not None else None
+        rc = self._lib.sipg_solve_convective(self._h, _ptr(w), wp, _ptr(b), _ptr(x), ctypes.byref(so), int(restart),
+                                             ctypes.byref(st))
+        if check:
+            self._check(rc)
+        return x, {"iterations": st.iterations, "rel_residual": st.rel_residual, "seconds": st.seconds,
+                   "status": rc}
+
     def step(self, rheology, dt, wall=None, body=None, viscosity_mode="linear", ppe_rtol=1e-8, visc_rtol=1e-8,
-             maxit=1000, picard=None):
+             maxit=1000, picard=None, convective_mode="explicit", gmres_restart=30):
         """One step of the projection scheme (see include/sipg.h, sipg_step)."""
         r, keep = rheology_struct(rheology)
         o = L.StepOpts()
@@ -254,6 +283,8 @@ class Context:
             _need_cuda(body, torch.float64)
             o.body = body.data_ptr()
         o.viscosity_mode = L.VISC_MODE[viscosity_mode]
+        o.convective_mode = L.CONV_MODE[convective_mode]
+        o.gmres_restart = int(gmres_restart)
         o.ppe_rtol, o.visc_rtol, o.maxit = float(ppe_rtol), float(visc_rtol), int(maxit)
         for key, val in (picard or {}).items():
             setattr(o.picard, key, val)

@@ -182,6 +182,8 @@ sipg_ctx::~sipg_ctx() {
                     ss.prhs, ss.sb})
     cudaFree(p);
   cudaFree(ss.vmax);
+  for (double* p : gm.V) cudaFree(p);
+  cudaFree(gm.z); cudaFree(gm.tmp); cudaFree(gm.r);
   if (hscal) cudaFreeHost(hscal);
 }
 

@@ -60,6 +60,12 @@ struct sipg_ctx {
   int64_t host_n = 0;
   double* pic[4] = {nullptr};  // Picard work vectors: r_k, r_{k-1}, u^k, r_k - r_{k-1}
   sipg::SplitTab stabs[sipg::kMaxN + 1]{};
+  struct GmresWork {  // GMRES Krylov basis and scratch (allocated on first use)
+    std::vector<double*> V;
+    double *z = nullptr, *tmp = nullptr, *r = nullptr;
+    int m = 0;
+    int64_t n = 0;
+  } gm;
   // state of the splitting step (allocated by sipg_step_init)
   struct StepState {
     double* u[2] = {nullptr, nullptr};     // u^n, u^{n-1}
@@ -102,4 +108,7 @@ struct sipg_ctx {
   int parse_rheology(const sipg_rheology* rh, const double* u_lin, sipg::RheologyDev* out);
   int eval_viscosity(const sipg::RheologyDev& r, const double* u_lin);
   int mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse);
+  int convective_apply_total(const double* w, const double* wall_w, const double* x, double* y, double mass);
+  int gmres_solve(const double* w, const double* wall_w, const double* b, double* x, const sipg_solve_opts& so,
+                  int restart, sipg_solve_stats* stats);
 };

@@ -49,6 +49,10 @@ struct PpeBndArgs {
 };
 cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
                               const double* u, double* y, cudaStream_t st);
+// y = sum_e c_h(phi, u; w), walls u^+ = -u^- + 2 wall_u, w^+ = -w^- + 2 wall_w (NULL = 0)
+cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_w,
+                                  const double* wall_u, const double* w, const double* u, double* y,
+                                  cudaStream_t st);
 int n_wall_faces(const LevelGeom& g);
 cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
                                 const PpeBndArgs& a, const RheologyDev& rh, const double* u0, const double* u1,

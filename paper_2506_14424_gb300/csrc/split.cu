@@ -221,6 +221,110 @@ __global__ void __launch_bounds__(kSplitThreads) conv_kernel(LevelGeom g, SplitT
   for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) y[(size_t)e * 3 * N3 + i] = OUT[i / N3][i % N3];
 }
 
+// --------------------------------------------- linearised convective term
+// y = sum_e c_h(phi, u; w) for a fixed transport velocity w (linear in u; the
+// alpha_c = 1, u* = u# term of Eq. viscous_step_weak). Walls: u^+ = -u^- + 2 gu,
+// w^+ = -w^- + 2 gw. With gu = 0 this is the homogeneous operator of the
+// Krylov solve; with u = 0 it is the wall-data part (right-hand side, negated).
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) conv_lin_kernel(LevelGeom g, SplitTab tab, Wall wall_w, Wall wall_u,
+                                                                 const double* __restrict__ w,
+                                                                 const double* __restrict__ u,
+                                                                 double* __restrict__ y) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double U[3][N3], Q[3][N3], G[3][3][N3], CV[3][N3], T0[N3], T1[N3], OUT[3][N3];
+  __shared__ double UM[3][N2], UP[3][N2], WM[3][N2], WP[3][N2], FT[N2], FL[3][N2], FR[N2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) {
+    U[i / N3][i % N3] = u[(size_t)e * 3 * N3 + i];
+    CV[i / N3][i % N3] = w[(size_t)e * 3 * N3 + i];
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+  for (int c = 0; c < 3; ++c)
+    for (int l = 0; l < 3; ++l) sweep_dir<N, false>(l, T.Dg, Q[c], G[c][l]);
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, CV[c], T0, T1, Q[c]);  // w at the Gauss points
+  const double detJ = g.h[0] * g.h[1] * g.h[2];
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const double wq = cell_weight(T, q, N, detJ);
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int l = 0; l < 3; ++l) acc += Q[l][q] * G[c][l][q] * g.ih[l];
+      CV[c][q] = wq * acc;
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) sweep3<N, N, true>(T.S, N, CV[c], T0, T1, OUT[c]);
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const double nd = 2.0 * s - 1.0;
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] != 0) continue;  // Neumann: u^+ = u^-, w^+ = w^-: no flux
+    // face nodes: own u, own w, neighbour u, neighbour w (in Q as scratch)
+    for (int i = threadIdx.x; i < 3 * N2; i += blockDim.x) {
+      const int c = i / N2, p = i % N2;
+      const int own = fnode(d, s, p % N, p / N, N);
+      Q[0][i] = U[c][own];
+      Q[1][i] = w[(size_t)e * 3 * N3 + c * N3 + own];
+      if (nb >= 0) {
+        const int oth = fnode(d, 1 - s, p % N, p / N, N);
+        Q[2][i] = u[(size_t)nb * 3 * N3 + c * N3 + oth];
+        CV[0][i] = w[(size_t)nb * 3 * N3 + c * N3 + oth];
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+      sweep<N, N, 1, 0, N, false>(T.S, N, Q[0] + c * N2, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, false>(T.S, N, FT, UM[c]);
+      __syncthreads();
+      sweep<N, N, 1, 0, N, false>(T.S, N, Q[1] + c * N2, FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, false>(T.S, N, FT, WM[c]);
+      __syncthreads();
+      if (nb >= 0) {
+        sweep<N, N, 1, 0, N, false>(T.S, N, Q[2] + c * N2, FT);
+        __syncthreads();
+        sweep<N, N, 1, 1, N, false>(T.S, N, FT, UP[c]);
+        __syncthreads();
+        sweep<N, N, 1, 0, N, false>(T.S, N, CV[0] + c * N2, FT);
+        __syncthreads();
+        sweep<N, N, 1, 1, N, false>(T.S, N, FT, WP[c]);
+        __syncthreads();
+      }
+    }
+    const double area = g.h[t1] * g.h[t2];
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double um[3], up[3], wm, wp;
+      for (int c = 0; c < 3; ++c) {
+        um[c] = UM[c][p];
+        up[c] = nb >= 0 ? UP[c][p] : -um[c] + 2.0 * wall_u.g[f][c];
+      }
+      wm = WM[d][p];
+      wp = nb >= 0 ? WP[d][p] : -wm + 2.0 * wall_w.g[f][d];
+      const double wn = 0.5 * (wm + wp) * nd;
+      const double sg = wn > 0.0 ? 1.0 : (wn < 0.0 ? -1.0 : 0.0);
+      const double wt = T.gw[p % N] * T.gw[p / N] * area;
+      for (int c = 0; c < 3; ++c) FL[c][p] = wt * wn * 0.5 * (1.0 - sg) * (up[c] - um[c]);
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+      sweep<N, N, 1, 0, N, true>(T.S, N, FL[c], FT);
+      __syncthreads();
+      sweep<N, N, 1, 1, N, true>(T.S, N, FT, FR);
+      __syncthreads();
+      for (int p = threadIdx.x; p < N2; p += blockDim.x) OUT[c][fnode(d, s, p % N, p / N, N)] += FR[p];
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) y[(size_t)e * 3 * N3 + i] = OUT[i / N3][i % N3];
+}
+
 // ----------------------------------------------------- PPE wall datum
 // h_p - (gamma0/dt) g_uhat.n = sum_{i<m} (beta_i - betabar_i) n.(u^{n-i}.grad)u^{n-i}
 //     - nu^dd n.curl omega^dd + 2 n.(eps(u^dd) grad nu^dd) - (gamma0/dt) g.n
@@ -609,6 +713,19 @@ cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, co
   for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
   if (g.ncells == 0) return cudaSuccess;
   SIPG_SPLIT_DISPATCH(n, (conv_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, u, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_w,
+                                  const double* wall_u, const double* w, const double* u, double* y,
+                                  cudaStream_t st) {
+  Wall ww, wu;
+  for (int i = 0; i < 18; ++i) {
+    ww.g[i / 3][i % 3] = wall_w ? wall_w[i] : 0.0;
+    wu.g[i / 3][i % 3] = wall_u ? wall_u[i] : 0.0;
+  }
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_SPLIT_DISPATCH(n, (conv_lin_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, ww, wu, w, u, y)));
   return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // One time step of the projection (dual splitting) scheme on a box, Sec. 3.2 /
-// 5.1, Alg. 1, with the convective term explicit: host sequence of library
-// kernels (split.cu forms, cell mass operators, MG-CG solves, the Picard loop).
+// 5.1, Alg. 1, the convective term explicit (alpha_c = 0) or linearly implicit
+// in the viscous step (alpha_c = 1, u* = u#, GMRES): host sequence of library
+// kernels (split.cu forms, cell mass operators, MG-CG / GMRES solves, the
+// Picard loop).
 //
 // State between steps: u^n, u^{n-1}, C(u^{n-1}) (the convective vector of the
 // previous step is reused), p^n (initial guess of the next pressure solve).
@@ -46,6 +48,8 @@ extern "C" void sipg_default_step_opts(sipg_step_opts* o) {
   o->dt = 0.0;
   o->body = nullptr;
   o->viscosity_mode = SIPG_VISC_LINEAR_IMPLICIT;
+  o->convective_mode = SIPG_CONV_EXPLICIT;
+  o->gmres_restart = 30;
   o->ppe_rtol = 1e-8;
   o->visc_rtol = 1e-8;
   o->maxit = 1000;
@@ -58,6 +62,16 @@ extern "C" int sipg_convective_apply(sipg_ctx* ctx, const double* wall_g, const 
   if (rc) return rc;
   const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
   CK(launch_convective(L.n, L.g, ctx->stabs[L.n], wall_g, u, y, ctx->st));
+  return SIPG_OK;
+}
+
+extern "C" int sipg_convective_lin_apply(sipg_ctx* ctx, const double* w, const double* wall_w, const double* wall_u,
+                                         const double* u, double* y) {
+  if (!ctx || !w || !u || !y || u == y || w == y) return SIPG_ERR_INVALID;
+  int rc = check_forms(ctx);
+  if (rc) return rc;
+  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
+  CK(launch_convective_lin(L.n, L.g, ctx->stabs[L.n], wall_w, wall_u, w, u, y, ctx->st));
   return SIPG_OK;
 }
 
@@ -170,6 +184,10 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
     return ctx->fail(SIPG_ERR_INVALID, "the implicit-viscosity step is built for zero wall velocity");
   if (so.viscosity_mode != SIPG_VISC_IMPLICIT && so.viscosity_mode != SIPG_VISC_LINEAR_IMPLICIT)
     return ctx->fail(SIPG_ERR_INVALID, "unknown viscosity mode");
+  if (so.convective_mode != SIPG_CONV_EXPLICIT && so.convective_mode != SIPG_CONV_LINEAR_IMPLICIT)
+    return ctx->fail(SIPG_ERR_INVALID, "unknown convective mode");
+  if (so.convective_mode == SIPG_CONV_LINEAR_IMPLICIT && so.viscosity_mode != SIPG_VISC_LINEAR_IMPLICIT)
+    return ctx->fail(SIPG_ERR_INVALID, "the linearly implicit convective step takes the linear-implicit viscosity");
   RheologyDev law;
   const double* u0 = S.u[0];
   int rc = ctx->parse_rheology(rh, u0, &law);
@@ -245,7 +263,20 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
     }
     sipg_solve_opts vs{so.visc_rtol, 0.0, so.maxit, SIPG_PRECOND_MG, mc};
     sipg_solve_stats vst{};
-    rc = ctx->solve(SIPG_OP_VISCOUS, S.bv, S.u[1], &vs, &vst);
+    if (so.convective_mode == SIPG_CONV_LINEAR_IMPLICIT) {
+      // alpha_c = 1: + sum_i beta_i C(u^{n-i}) on the right, c_h(v, u; u#) on the left;
+      // the wall-data part of c_h(v, u; u#) is the form at u = 0 with u's wall data
+      CK(launch_add_scaled_f64(nu, beta[0], S.conv[0], S.bv, st));
+      if (m == 2) CK(launch_add_scaled_f64(nu, beta[1], S.conv[1], S.bv, st));
+      if (wall_moving) {
+        CK(cudaMemsetAsync(S.uhat, 0, sizeof(double) * nu, st));
+        CK(launch_convective_lin(Lu.n, Lu.g, tab, wall, wall, S.usharp, S.uhat, S.tmp, st));
+        CK(launch_add_scaled_f64(nu, -1.0, S.tmp, S.bv, st));
+      }
+      rc = ctx->gmres_solve(S.usharp, wall, S.bv, S.u[1], vs, so.gmres_restart, &vst);
+    } else {
+      rc = ctx->solve(SIPG_OP_VISCOUS, S.bv, S.u[1], &vs, &vst);
+    }
     if (rc != SIPG_OK) return rc;
     visc_its = vst.iterations;
     visc_res = vst.rel_residual;
