@@ -26,6 +26,8 @@ for fluids with variable viscosity"):
                    Eqs. convective_step_weak / projection_step_weak).
 * ``nonlinear``    Picard iteration of the viscosity with Aitken relaxation
                    (Sec. 5.4, Alg. 1).
+* ``mapped``       the SIPG operators on trilinear (non-affine) hexahedra:
+                   per-point Jacobians, normals and surface weights (Sec. 5).
 * ``splitting``    one step of the projection scheme on a box: BDF, explicit
                    convective step, pressure Poisson step with the consistent
                    Neumann datum, projection, viscous step, CFL time step
