@@ -310,6 +310,7 @@ def gpu_extras(ctx, xs, ys, stream):
     out["mass_32cubed_k3"] = mass_timings(ctx, xs, ys, stream)
     out["picard_viscous_step_32cubed_k3"] = picard_extras(ctx)
     out["splitting_step_32cubed_k3"] = step_extras()
+    out["trilinear_cells_32cubed_k3"] = trilinear_extras()
     out["components_16cubed_k4"] = component_timings(stream)
     out["serving"] = serving_extras()
     return out
@@ -428,6 +429,45 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
         "mean_t_viscous": float(np.mean([r["t_viscous"] for r in rows])),
         "gmres_iterations": [r["visc_iterations"] for r in rows]}
     ctx.close()
+    return out
+
+
+def trilinear_extras(n_cells=32, k=3, reps=10):
+    """Viscous apply (FP64) on trilinear cells: the box's interior vertices jittered by
+    U(-0.05 h, 0.05 h)^3 (seed 4, the channel-mesh recipe), Carreau-Yasuda viscosity,
+    rotating x/y pairs; the same mesh without jitter through the affine kernel beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+    N = n_cells
+    h = 1.0 / N
+    g = np.linspace(0.0, 1.0, N + 1)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    V = np.stack([X, Y, Z], axis=-1)
+    J = np.random.default_rng(4).uniform(-0.05 * h, 0.05 * h, size=V.shape)
+    J[[0, -1], :, :] = 0.0
+    J[:, [0, -1], :] = 0.0
+    J[:, :, [0, -1]] = 0.0
+    out = {}
+    for name, verts in (("trilinear", V + J), ("affine", None)):
+        ctx = Context(N, N, N, k, vertices=verts)
+        n = ctx.n_dofs("viscous")
+        ctx.set_viscosity(inputs.carreau_blood_like(), torch.tensor(inputs.uniform_vector(n, 1), device="cuda"))
+        xs = [torch.tensor(inputs.uniform_vector(n, seed=100 + i), device="cuda") for i in range(4)]
+        ys = [torch.empty_like(xs[0]) for _ in range(4)]
+        for i in range(3):
+            ctx.apply("viscous", xs[i % 4], ys[i % 4], arith="f64")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for i in range(reps):
+            ctx.apply("viscous", xs[i % 4], ys[i % 4], arith="f64")
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "gdofs": n / ms / 1e6}
+        ctx.close()
     return out
 
 

@@ -70,6 +70,16 @@ typedef struct {
   double lx, ly, lz;
   int bc_velocity[6];
   int bc_pressure[6];
+  /* HOST, optional: positions of the (nx+1)(ny+1)(nz+1) vertices of the
+   * structured cells, x fastest, 3 doubles each; each cell is the trilinear
+   * image of the unit cube through its 8 vertices (general hexahedra, Sec. 5;
+   * the jittered channel mesh). Copied during sipg_create. NULL: the box
+   * [0,lx]x[0,ly]x[0,lz] (lx, ly, lz are then ignored otherwise). On such a
+   * mesh the library builds the fine level only: sipg_set_viscosity, FP64
+   * sipg_apply / sipg_level_apply(level 0) and sipg_solve with
+   * SIPG_PRECOND_NONE; multigrid, float-float and FP32 applies, mass
+   * operators, the splitting step and serving return SIPG_ERR_INVALID. */
+  const double* vertices;
 } sipg_mesh_desc;
 
 /* Discretisation and solver options. Zero-initialised fields take the

@@ -13,7 +13,9 @@ Everything the affine oracle gets from h is computed per quadrature point:
   on a face with tangents t1 = dx/dxi_t1, t2 = dx/dxi_t2: the outward unit
   normal n = +-(t1 x t2)/|t1 x t2| and the surface weight w_a w_b |t1 x t2|;
   the penalty factor Lambda_e = sum_f w_f |f| / |Omega_e| with the integrated
-  face areas and cell volume (w_f = 1/2 interior, 1 boundary).
+  face areas and cell volume (w_f = 1/2 interior, 1 boundary). READING: |f| and
+  |Omega_e| are integrated with the operator's own Gauss rule (|t1 x t2| is
+  not a polynomial on a trilinear face, so the rule is part of the definition).
 The element forms, fluxes, mirror boundary conditions and penalty are those of
 ``oracle.sipg`` (same readings), with the normal taken per point.
 
@@ -194,13 +196,13 @@ class MappedSIPG:
         return out.reshape(-1)
 
     # ------------------------------------------------------------- viscosity
-    def viscosity_at_points(self, rheology, u=None):
+    def viscosity_at_points(self, rheology, u=None, cells=None):
         C = self.mesh.n_cells
         nq3, nq2 = self.nq ** 3, self.nq ** 2
         nu_cell = np.zeros((C, nq3))
         nu_face = np.zeros((C, 6, nq2))
         needs_u = rheology['law'] == 'carreau'
-        for e in range(C):
+        for e in (range(C) if cells is None else cells):
             ue = np.asarray(u).reshape(C, 3, self.n ** 3)[e] if needs_u else None
             x, J, W, _ = self.cell_geometry(e)
             grad = np.einsum('ci,pil->pcl', ue, self._grad(self.cell_dphi, J)) if needs_u else None
@@ -307,6 +309,20 @@ class MappedSIPG:
                     tau = self._tau(e, None, ones, ones)
                     own += self._poisson_face(qt, gt, qt, gt, -qt, gt, tau, nvec, Wf)
         return own, nbs
+
+    def rows(self, x, cells, nu_cell=None, nu_face=None, mass=0.0):
+        """Rows of y = A x of the listed cells only (the viscosity of those cells and of
+        their face neighbours must be set)."""
+        m = self.n_dofs_cell
+        X = np.asarray(x, dtype=np.float64).reshape(self.mesh.n_cells, m)
+        out = []
+        for e in cells:
+            own, nbs = self.blocks_of(e, nu_cell, nu_face, mass)
+            r = own @ X[e]
+            for f, (nb, blk) in nbs.items():
+                r = r + blk @ X[nb]
+            out.append(r)
+        return np.array(out)
 
     def apply(self, x, nu_cell=None, nu_face=None, mass=0.0):
         m = self.n_dofs_cell

@@ -41,7 +41,8 @@ CONV_MODE = {"explicit": 0, "linear_implicit": 1}
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
-                ("bc_velocity", ctypes.c_int * 6), ("bc_pressure", ctypes.c_int * 6)]
+                ("bc_velocity", ctypes.c_int * 6), ("bc_pressure", ctypes.c_int * 6),
+                ("vertices", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):

@@ -55,7 +55,9 @@ class Context:
     def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
                  penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
                  cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, krylov_arith="f64",
-                 stream=None):
+                 stream=None, vertices=None):
+        """vertices: optional (nz+1, ny+1, nx+1, 3) host array of vertex positions
+        (trilinear cells; fine level only, see include/sipg.h)."""
         self._lib = L.load()
         m = L.MeshDesc()
         m.nx, m.ny, m.nz = int(nx), int(ny), int(nz)
@@ -63,6 +65,12 @@ class Context:
         for i in range(6):
             m.bc_velocity[i] = L.BC[bc_velocity[i]]
             m.bc_pressure[i] = L.BC[bc_pressure[i]]
+        verts = None
+        if vertices is not None:
+            verts = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+            if verts.size != (int(nx) + 1) * (int(ny) + 1) * (int(nz) + 1) * 3:
+                raise ValueError("vertices: (nz+1, ny+1, nx+1, 3) values expected")
+            m.vertices = verts.ctypes.data
         o = L.Opts()
         o.k_u = int(k_u)
         o.penalty_factor = float(penalty_factor)
@@ -79,6 +87,7 @@ class Context:
         h = ctypes.c_void_p()
         rc = self._lib.sipg_create(ctypes.byref(m), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))
+        del verts  # copied by sipg_create
         if rc != L.SIPG_OK:
             raise SipgError(rc, "sipg_create failed (see stderr)")
         self._h = h

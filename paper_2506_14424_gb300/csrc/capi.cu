@@ -73,8 +73,8 @@ int sipg_ctx::build_hierarchy(int op) {
   const int k0 = op == SIPG_OP_VISCOUS ? opts.k_u : opts.k_u - 1;
   const int* bc = op == SIPG_OP_VISCOUS ? mesh.bc_velocity : mesh.bc_pressure;
   std::vector<int> ks{k0};
-  if (k0 > 2) ks.push_back(2);
-  if (k0 > 1) ks.push_back(1);
+  if (k0 > 2 && !mapped) ks.push_back(2);
+  if (k0 > 1 && !mapped) ks.push_back(1);
   int nx = mesh.nx, ny = mesh.ny, nz = mesh.nz;
   auto make_level = [&](int k, int lnx, int lny, int lnz) {
     Level L{};
@@ -96,7 +96,7 @@ int sipg_ctx::build_hierarchy(int op) {
   };
   H.L.clear();
   for (int k : ks) H.L.push_back(make_level(k, nx, ny, nz));
-  while (H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
+  while (!mapped && H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
     nx /= 2;
     ny /= 2;
     nz /= 2;
@@ -151,11 +151,13 @@ int sipg_ctx::build_hierarchy(int op) {
       }
     }
   }
-  Level& Cl = H.L.back();
-  Cl.N = (int)Cl.ndofs;
-  if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
-  Cl.Ainv = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
-  Cl.Atmp = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  if (!mapped) {
+    Level& Cl = H.L.back();
+    Cl.N = (int)Cl.ndofs;
+    if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
+    Cl.Ainv = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+    Cl.Atmp = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  }
   // CG vectors on level 0
   for (int v = 0; v < 5; ++v) {
     H.cg[v] = alloc<double>(H.L[0].ndofs, &e);
@@ -184,6 +186,7 @@ sipg_ctx::~sipg_ctx() {
   cudaFree(ss.vmax);
   for (double* p : gm.V) cudaFree(p);
   cudaFree(gm.z); cudaFree(gm.tmp); cudaFree(gm.r);
+  cudaFree(dverts); cudaFree(dlam[0]); cudaFree(dlam[1]);
   if (hscal) cudaFreeHost(hscal);
 }
 
@@ -226,15 +229,32 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (o.mg_precision != SIPG_F32 && o.mg_precision != SIPG_F64) return SIPG_ERR_INVALID;
   if (o.face_nu < 0 || o.face_nu > 2 || o.cheb_degree < 1 || o.lanczos_steps < 2) return SIPG_ERR_INVALID;
   if (o.krylov_arith != SIPG_F64 && o.krylov_arith != SIPG_F64_FF) return SIPG_ERR_INVALID;
+  if (mesh->vertices && o.krylov_arith != SIPG_F64) return SIPG_ERR_INVALID;  // FP64 applies only
   sipg_ctx* ctx = new sipg_ctx();
   ctx->mesh = *mesh;
+  ctx->mesh.vertices = nullptr;  // the caller's array is copied below, not kept
+  ctx->mapped = mesh->vertices != nullptr;
   ctx->opts = o;
   ctx->st = (cudaStream_t)stream;
   for (int n = 2; n <= kMaxN; ++n) ctx->tabs[n] = make_tab(n);
-  for (int n = 3; n <= kMaxN; ++n) ctx->stabs[n] = make_split_tab(n);
+  for (int n = 2; n <= kMaxN; ++n) ctx->stabs[n] = make_split_tab(n);
   cudaError_t e = cudaSuccess;
   int rc = SIPG_OK;
   for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);
+  if (rc == SIPG_OK && ctx->mapped) {
+    const size_t nv = (size_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) * 3;
+    e = cudaMalloc(&ctx->dverts, sizeof(double) * nv);
+    if (!e) e = cudaMemcpyAsync(ctx->dverts, mesh->vertices, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->st);
+    // Lambda_e with each operator's own Gauss rule (face areas of trilinear cells are
+    // not polynomial, so the rule matters at the level of rounding-plus)
+    for (int op = 0; op < 2 && !e; ++op) {
+      e = cudaMalloc(&ctx->dlam[op], sizeof(double) * (size_t)mesh->nx * mesh->ny * mesh->nz);
+      const Level& L0 = ctx->hier[op].L[0];
+      if (!e) e = launch_mapped_lambda(L0.n, L0.g, ctx->stabs[L0.n], ctx->dverts, ctx->dlam[op], ctx->st);
+    }
+    if (!e) e = cudaStreamSynchronize(ctx->st);
+    if (e) rc = ctx->fail(SIPG_ERR_NOMEM, "vertices", e);
+  }
   if (rc == SIPG_OK) {
     ctx->partials = dalloc<double>(kDotBlocks, &e, ctx->st);
     if (!e) ctx->dscal = dalloc<double>(16, &e, ctx->st);
@@ -314,6 +334,15 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
   sipg_ctx* ctx = this;
   const Hier& H = hier[op];
   const Level& L = H.L[l];
+  if (mapped) {
+    if constexpr (sizeof(T) == 8) {
+      CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], dverts, dlam[op], op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
+                             op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr, mass, (const double*)x, (double*)y, st));
+      return SIPG_OK;
+    } else {
+      return fail(SIPG_ERR_INVALID, "trilinear cells: FP64 applies only");
+    }
+  }
   const T* nc = nullptr;
   const T* nf = nullptr;
   if (op == SIPG_OP_VISCOUS) {
@@ -326,6 +355,7 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
 
 int sipg_ctx::level_apply_ff(int op, int l, const double* x, double* y, double mass) {
   sipg_ctx* ctx = this;
+  if (mapped) return fail(SIPG_ERR_INVALID, "trilinear cells: FP64 applies only");
   const Hier& H = hier[op];
   const Level& L = H.L[l];
   if (op == SIPG_OP_VISCOUS && !L.nu_cellff) return fail(SIPG_ERR_INVALID, "float-float apply on level 0 only");
@@ -507,6 +537,7 @@ int sipg_ctx::ensure_setup(int op) {
 }
 
 int sipg_ctx::setup_operator(int op, double mass) {
+  if (mapped) return fail(SIPG_ERR_INVALID, "multigrid is built for the box only");
   sipg_ctx* ctx = this;
   Hier& H = hier[op];
   for (size_t l = 0; l < H.L.size(); ++l) {
@@ -560,6 +591,17 @@ int sipg_ctx::parse_rheology(const sipg_rheology* rh, const double* u_lin, Rheol
 // smoother or coarse setup; the hierarchy is marked stale)
 int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
   Hier& H = hier[SIPG_OP_VISCOUS];
+  if (mapped) {
+    Level& L = H.L[0];
+    cudaError_t e = launch_mapped_viscosity(L.n, L.g, stabs[L.n], dverts, r, u_lin, L.nu_cell64, L.nu_face64, st);
+    const int64_t n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
+    if (!e) e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, st);
+    if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, st);
+    if (e) return fail(SIPG_ERR_CUDA, "viscosity kernel (trilinear cells)", e);
+    have_nu = true;
+    H.ready = false;
+    return SIPG_OK;
+  }
   for (size_t l = 0; l < H.L.size(); ++l) {
     Level& L = H.L[l];
     const double* u = nullptr;
@@ -603,6 +645,7 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
   int rc = ctx->parse_rheology(rh, u_lin, &r);
   if (rc) return rc;
   if ((rc = ctx->eval_viscosity(r, u_lin))) return rc;
+  if (ctx->mapped) return SIPG_OK;  // no multigrid on trilinear cells
   return ctx->setup_operator(SIPG_OP_VISCOUS, 0.0);
 }
 
@@ -631,6 +674,7 @@ extern "C" int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* 
 
 int sipg_ctx::mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse) {
   sipg_ctx* ctx = this;
+  if (mapped) return fail(SIPG_ERR_INVALID, "cell mass operators are built for the box only");
   if (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) return fail(SIPG_ERR_INVALID, "unknown operator");
   if (prec != SIPG_F64 && prec != SIPG_F32 && prec != SIPG_F64_FF) return fail(SIPG_ERR_INVALID, "unknown arithmetic");
   if (!x || !y) return fail(SIPG_ERR_INVALID, "null vector");

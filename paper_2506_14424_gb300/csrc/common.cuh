@@ -42,7 +42,7 @@ struct SplitTab {
   double Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
   double dS0[kMaxN], dS1[kMaxN];
   double lg0[kMaxN], lg1[kMaxN], dlg0[kMaxN], dlg1[kMaxN];
-  double gw[kMaxN];
+  double gw[kMaxN], gp[kMaxN];  // Gauss weights and points on [0, 1]
 };
 
 // Embedding matrices of the transfers (prolongation = interpolation of the

@@ -77,6 +77,9 @@ struct sipg_ctx {
     bool conv1 = false;   // conv[1] holds C(u^{n-1})
     int64_t steps = 0;
   } ss;
+  bool mapped = false;          // trilinear cells from a vertex array (fine level only)
+  double* dverts = nullptr;     // device copy of the vertices
+  double* dlam[2] = {nullptr, nullptr};  // per-cell Lambda_e of the mapped cells, per operator (own rule)
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
   int64_t bytes = 0;    // device bytes allocated by the hierarchy
 

@@ -163,6 +163,7 @@ extern "C" int sipg_solve_convective(sipg_ctx* ctx, const double* w, const doubl
   if (!ctx || !b || !x || b == x) return SIPG_ERR_INVALID;
   if (!ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
   if (ctx->opts.k_u < 2 || ctx->opts.k_u > 5) return ctx->fail(SIPG_ERR_INVALID, "velocity degree 2..5");
+  if (ctx->mapped && w) return ctx->fail(SIPG_ERR_INVALID, "the convective form is built for the box only");
   sipg_solve_opts so{1e-8, 0.0, 500, SIPG_PRECOND_MG, 0.0};
   if (so_in) so = *so_in;
   if (so.maxit < 0 || !(so.rtol >= 0) || so.precond < 0 || so.precond > 2)

@@ -66,6 +66,16 @@ cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& t
 cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
                            unsigned long long* vmax_bits, cudaStream_t st);
 
+// ---- operators on trilinear cells (mapped.cu); n = degree + 1 (2..6)
+cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                const double* lam, const double* nu_cell, const double* nu_face, double mass,
+                                const double* x, double* y, cudaStream_t st);
+cudaError_t launch_mapped_lambda(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double* lam,
+                                 cudaStream_t st);
+cudaError_t launch_mapped_viscosity(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                    const RheologyDev& rh, const double* u, double* nu_cell, double* nu_face,
+                                    cudaStream_t st);
+
 // ---- multigrid and vector kernels (mg.cu)
 cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
                             const double* nu_face, double mass, double* diag, cudaStream_t st);

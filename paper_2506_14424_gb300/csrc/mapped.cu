@@ -1,0 +1,499 @@
+// SIPG viscous and Poisson operators on trilinear (non-affine) hexahedra,
+// Sec. 5 of the paper on general hexahedral cells (the jittered channel mesh
+// of the backward-facing-step workload). Same forms, fluxes, mirror boundary
+// conditions and penalty as the affine kernels (operator.cuh); the geometry is
+// evaluated per quadrature point from the cell's 8 vertices:
+//   J = dx/dxi of the trilinear map, W = w det J, grad = J^-T grad_xi;
+//   faces: n = +-(t1 x t2)/|t1 x t2| from the tangents t = dx/dxi_t, surface
+//   weight w_a w_b |t1 x t2|; Lambda_e = sum_f w_f |f| / |Omega_e| from the
+//   integrated areas and volume (mapped_lambda_kernel).
+// The topology is structured (cells (i, j, k), neighbours across the faces),
+// vertex (i, j, k) at verts[((k (ny+1) + j)(nx+1) + i) * 3 + c].
+//
+// FP64, one CTA per cell, one thread per tensor entry of each sweep (the
+// split.cu style). The Jacobian is recomputed in the thread that owns a point
+// instead of being stored: per point, reference gradients -> physical ->
+// flux -> back to reference coefficients in one pass.
+#include "kernels.cuh"
+#include "sweeps.cuh"
+
+namespace sipg {
+namespace {
+using namespace sweeps;
+
+__device__ __forceinline__ void load_cell_vertices(const LevelGeom& g, const double* __restrict__ verts, int e,
+                                                   double (*X)[3]) {
+  const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
+  for (int t = threadIdx.x; t < 24; t += blockDim.x) {
+    const int v = t / 3, c = t % 3;
+    const int a = v & 1, b = (v >> 1) & 1, cc = (v >> 2) & 1;
+    const size_t idx = ((size_t)(k + cc) * (g.ny + 1) + (j + b)) * (g.nx + 1) + (i + a);
+    X[v][c] = verts[idx * 3 + c];
+  }
+}
+
+// J[k][l] = d x_k / d xi_l of the trilinear map at xi; also x if wanted
+__device__ __forceinline__ void trilinear_jac(const double (*X)[3], double x0, double x1, double x2, double J[3][3],
+                                              double* pos = nullptr) {
+  for (int k = 0; k < 3; ++k) {
+    J[k][0] = J[k][1] = J[k][2] = 0.0;
+    if (pos) pos[k] = 0.0;
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
+    const double fx = a ? x0 : 1.0 - x0, fy = b ? x1 : 1.0 - x1, fz = c ? x2 : 1.0 - x2;
+    const double sx = a ? 1.0 : -1.0, sy = b ? 1.0 : -1.0, sz = c ? 1.0 : -1.0;
+    const double d0 = sx * fy * fz, d1 = fx * sy * fz, d2 = fx * fy * sz;
+    for (int k = 0; k < 3; ++k) {
+      J[k][0] += X[v][k] * d0;
+      J[k][1] += X[v][k] * d1;
+      J[k][2] += X[v][k] * d2;
+      if (pos) pos[k] += X[v][k] * fx * fy * fz;
+    }
+  }
+}
+
+__device__ __forceinline__ double inverse3(const double J[3][3], double Ji[3][3]) {
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const double id = 1.0 / det;
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+// node (layer along d, a along t1, b along t2) of an n^3 tensor
+__device__ __forceinline__ int lnode(int d, int layer, int a, int b, int n) {
+  int i[3];
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  i[d] = layer;
+  i[t1] = a;
+  i[t2] = b;
+  return (i[2] * n + i[1]) * n + i[0];
+}
+
+// Values and reference derivatives at the face Gauss points of a nodal field U
+// (n^3): out[0] values, out[1] d/dxi_d, out[2] d/dxi_t1, out[3] d/dxi_t2 (N^2
+// each); scratch: 5 N^2.
+template <int N>
+__device__ void face_eval(const double* U, int d, int s, const STabSm& T, double* out, double* sc) {
+  constexpr int N2 = N * N;
+  double *L = sc, *D = sc + N2, *A = sc + 2 * N2, *B = sc + 3 * N2, *C = sc + 4 * N2;
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+    const int a = p % N, b = p / N;
+    L[p] = U[lnode(d, s ? N - 1 : 0, a, b, N)];
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc += T.dS[s][i] * U[lnode(d, i, a, b, N)];
+    D[p] = acc;
+  }
+  __syncthreads();
+  sweep<N, N, 1, 0, N, false>(T.S, N, L, A);
+  sweep<N, N, 1, 0, N, false>(T.DS, N, L, B);
+  sweep<N, N, 1, 0, N, false>(T.S, N, D, C);
+  __syncthreads();
+  sweep<N, N, 1, 1, N, false>(T.S, N, A, out);            // values
+  sweep<N, N, 1, 1, N, false>(T.S, N, C, out + N2);       // d/dxi_d
+  sweep<N, N, 1, 1, N, false>(T.S, N, B, out + 2 * N2);   // d/dxi_t1
+  sweep<N, N, 1, 1, N, false>(T.DS, N, A, out + 3 * N2);  // d/dxi_t2
+  __syncthreads();
+}
+
+// Transpose of face_eval: add to the nodal tensor Y the test-side contributions
+// of coefficients cf[0] (value), cf[1] (d/dxi_d), cf[2] (d/dxi_t1), cf[3] (d/dxi_t2).
+template <int N>
+__device__ void face_eval_t(const double* cf, int d, int s, const STabSm& T, double* Y, double* sc) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  double *A = sc, *B = sc + N2, *C = sc + 2 * N2, *L = sc + 3 * N2, *D = sc + 4 * N2;
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf, A);
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf + N2, C);
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf + 2 * N2, B);
+  __syncthreads();
+  sweep<N, N, 1, 0, N, true>(T.S, N, A, L);   // value part
+  sweep<N, N, 1, 0, N, true>(T.S, N, C, D);   // normal part
+  __syncthreads();
+  sweep<N, N, 1, 0, N, true>(T.DS, N, B, A);  // d/dxi_t1 part (A is free again)
+  sweep<N, N, 1, 1, N, true>(T.DS, N, cf + 3 * N2, C);
+  __syncthreads();
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) L[p] += A[p];
+  sweep<N, N, 1, 0, N, true>(T.S, N, C, B);   // d/dxi_t2 part
+  __syncthreads();
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) A[p] = L[p] + B[p];
+  __syncthreads();
+  // layer nodes: values and tangential parts; every node along the normal line: normal part
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    const int idx[3] = {i % N, (i / N) % N, i / N2};
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const int p = idx[t1] + N * idx[t2];
+    double v = T.dS[s][idx[d]] * D[p];
+    if (idx[d] == (s ? N - 1 : 0)) v += A[p];
+    Y[i] += v;
+  }
+  __syncthreads();
+}
+
+template <int N, int NC>
+__global__ void __launch_bounds__(kSplitThreads) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+                                                                     const double* __restrict__ verts,
+                                                                     const double* __restrict__ lam,
+                                                                     const double* __restrict__ nu_cell,
+                                                                     const double* __restrict__ nu_face, double mass,
+                                                                     const double* __restrict__ x,
+                                                                     double* __restrict__ y) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double X[8][3], XN[8][3];
+  __shared__ double U[NC][N3], Q[NC][N3], G[NC][3][N3], T0[N3], T1[N3], OUT[NC][N3];
+  __shared__ double FM[NC][4 * N2], FP[NC][4 * N2], CF[NC][4 * N2], SC[5 * N2];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  load_cell_vertices(g, verts, e, X);
+  for (int i = threadIdx.x; i < NC * N3; i += blockDim.x) U[i / N3][i % N3] = x[(size_t)e * NC * N3 + i];
+  __syncthreads();
+  // ---- cell term
+  for (int c = 0; c < NC; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+  for (int c = 0; c < NC; ++c)
+    for (int m = 0; m < 3; ++m) sweep_dir<N, false>(m, T.Dg, Q[c], G[c][m]);
+  __syncthreads();
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
+    double J[3][3], Ji[3][3];
+    trilinear_jac(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J);
+    const double det = inverse3(J, Ji);
+    const double W = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
+    double Gp[NC][3];
+    for (int c = 0; c < NC; ++c)
+      for (int l = 0; l < 3; ++l) Gp[c][l] = G[c][0][q] * Ji[0][l] + G[c][1][q] * Ji[1][l] + G[c][2][q] * Ji[2][l];
+    double Tf[NC][3];
+    if (NC == 3) {
+      const double nu = nu_cell[(size_t)e * N3 + q];
+      for (int c = 0; c < 3; ++c)
+        for (int l = 0; l < 3; ++l) Tf[c][l] = nu * (Gp[c][l] + Gp[l][c]);  // 2 nu eps(u)
+    } else {
+      for (int l = 0; l < 3; ++l) Tf[0][l] = Gp[0][l];
+    }
+    for (int c = 0; c < NC; ++c) {
+      for (int m = 0; m < 3; ++m) G[c][m][q] = W * (Tf[c][0] * Ji[m][0] + Tf[c][1] * Ji[m][1] + Tf[c][2] * Ji[m][2]);
+      Q[c][q] = mass * W * Q[c][q];
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < NC; ++c) {
+    for (int m = 0; m < 3; ++m) {
+      sweep_dir<N, true>(m, T.Dg, G[c][m], T0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < N3; q += blockDim.x) Q[c][q] += T0[q];
+      __syncthreads();
+    }
+    sweep3<N, N, true>(T.S, N, Q[c], T0, T1, OUT[c]);
+  }
+  // ---- faces
+  const double lam_e = lam[e];
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] == 1) continue;  // homogeneous Neumann: no term
+    const int fo = 2 * d + (1 - s);
+    for (int c = 0; c < NC; ++c) face_eval<N>(U[c], d, s, T, FM[c], SC);
+    if (nb >= 0) {
+      load_cell_vertices(g, verts, nb, XN);
+      for (int c = 0; c < NC; ++c) face_eval<N>(x + (size_t)nb * NC * N3 + c * N3, d, 1 - s, T, FP[c], SC);
+    }
+    __syncthreads();
+    const double orient = (2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0);
+    const double lam_p = nb >= 0 ? lam[nb] : lam_e;
+    const double tau0 = g.cip * (double)(N * N) * fmax(lam_e, lam_p);
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double xi[3];
+      xi[d] = s ? 1.0 : 0.0;
+      xi[t1] = tab.gp[p % N];
+      xi[t2] = tab.gp[p / N];
+      double Jm[3][3], Jim[3][3], Jp[3][3], Jip[3][3];
+      trilinear_jac(X, xi[0], xi[1], xi[2], Jm);
+      inverse3(Jm, Jim);
+      if (nb >= 0) {
+        double xo[3] = {xi[0], xi[1], xi[2]};
+        xo[d] = s ? 0.0 : 1.0;
+        trilinear_jac(XN, xo[0], xo[1], xo[2], Jp);
+        inverse3(Jp, Jip);
+      } else {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) Jip[a][b] = Jim[a][b];
+      }
+      const double ta[3] = {Jm[0][t1], Jm[1][t1], Jm[2][t1]}, tb[3] = {Jm[0][t2], Jm[1][t2], Jm[2][t2]};
+      double n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
+      const double area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      for (int k = 0; k < 3; ++k) n[k] *= orient / area;
+      const double W = T.gw[p % N] * T.gw[p / N] * area;
+      // physical traces
+      double um[NC], up[NC], Gm[NC][3], Gq[NC][3];
+      for (int c = 0; c < NC; ++c) {
+        double rm[3], rp[3];
+        rm[d] = FM[c][N2 + p];
+        rm[t1] = FM[c][2 * N2 + p];
+        rm[t2] = FM[c][3 * N2 + p];
+        um[c] = FM[c][p];
+        for (int l = 0; l < 3; ++l) Gm[c][l] = rm[0] * Jim[0][l] + rm[1] * Jim[1][l] + rm[2] * Jim[2][l];
+        if (nb >= 0) {
+          rp[d] = FP[c][N2 + p];
+          rp[t1] = FP[c][2 * N2 + p];
+          rp[t2] = FP[c][3 * N2 + p];
+          up[c] = FP[c][p];
+          for (int l = 0; l < 3; ++l) Gq[c][l] = rp[0] * Jip[0][l] + rp[1] * Jip[1][l] + rp[2] * Jip[2][l];
+        } else {  // Dirichlet mirror
+          up[c] = -um[c];
+          for (int l = 0; l < 3; ++l) Gq[c][l] = Gm[c][l];
+        }
+      }
+      double cv[NC], S[NC][3];
+      if (NC == 3) {
+        const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
+        const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + fo) * N2 + p] : num;
+        double nub = num > nup ? num : nup;
+        if (g.face_nu == 1) nub = 0.5 * (num + nup);
+        if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
+        const double tau = tau0 * nub;
+        double jm[3], jn = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          jm[c] = um[c] - up[c];
+          jn += jm[c] * n[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+          // (A + A^T) n, A = (nu- Gm + nu+ Gp)/2
+          double an = 0.0;
+          for (int l = 0; l < 3; ++l)
+            an += 0.5 * (num * (Gm[c][l] + Gm[l][c]) + nup * (Gq[c][l] + Gq[l][c])) * n[l];
+          cv[c] = W * (-an + tau * (jm[c] + n[c] * jn));
+          for (int l = 0; l < 3; ++l) S[c][l] = -W * num * 0.5 * (jm[c] * n[l] + jm[l] * n[c]);
+        }
+      } else {
+        const double tau = tau0;
+        const double jm = um[0] - up[0];
+        double gn = 0.0;
+        for (int l = 0; l < 3; ++l) gn += 0.5 * (Gm[0][l] + Gq[0][l]) * n[l];
+        cv[0] = W * (-gn + tau * jm);
+        for (int l = 0; l < 3; ++l) S[0][l] = -W * 0.5 * jm * n[l];
+      }
+      for (int c = 0; c < NC; ++c) {
+        double R[3];
+        for (int m = 0; m < 3; ++m) R[m] = S[c][0] * Jim[m][0] + S[c][1] * Jim[m][1] + S[c][2] * Jim[m][2];
+        CF[c][p] = cv[c];
+        CF[c][N2 + p] = R[d];
+        CF[c][2 * N2 + p] = R[t1];
+        CF[c][3 * N2 + p] = R[t2];
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < NC; ++c) face_eval_t<N>(CF[c], d, s, T, OUT[c], SC);
+  }
+  for (int i = threadIdx.x; i < NC * N3; i += blockDim.x) y[(size_t)e * NC * N3 + i] = OUT[i / N3][i % N3];
+}
+
+// Lambda_e = sum_f w_f |f| / |Omega_e| (w = 1/2 interior, 1 boundary), one thread per cell
+__global__ void mapped_lambda_kernel(LevelGeom g, SplitTab tab, int n, const double* __restrict__ verts,
+                                     double* __restrict__ lam) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ncells) return;
+  double X[8][3];
+  const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
+  for (int v = 0; v < 8; ++v) {
+    const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
+    const size_t idx = ((size_t)(k + c) * (g.ny + 1) + (j + b)) * (g.nx + 1) + (i + a);
+    for (int t = 0; t < 3; ++t) X[v][t] = verts[idx * 3 + t];
+  }
+  double vol = 0.0, J[3][3], Ji[3][3];
+  for (int q = 0; q < n * n * n; ++q) {
+    const int qx = q % n, qy = (q / n) % n, qz = q / (n * n);
+    trilinear_jac(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J);
+    vol += tab.gw[qx] * tab.gw[qy] * tab.gw[qz] * inverse3(J, Ji);
+  }
+  double acc = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    double area = 0.0;
+    for (int p = 0; p < n * n; ++p) {
+      double xi[3];
+      xi[d] = s ? 1.0 : 0.0;
+      xi[t1] = tab.gp[p % n];
+      xi[t2] = tab.gp[p / n];
+      trilinear_jac(X, xi[0], xi[1], xi[2], J);
+      const double c0 = J[1][t1] * J[2][t2] - J[2][t1] * J[1][t2];
+      const double c1 = J[2][t1] * J[0][t2] - J[0][t1] * J[2][t2];
+      const double c2 = J[0][t1] * J[1][t2] - J[1][t1] * J[0][t2];
+      area += tab.gw[p % n] * tab.gw[p / n] * sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    }
+    acc += (cell_neighbor(g, e, f) >= 0 ? 0.5 : 1.0) * area;
+  }
+  lam[e] = acc / vol;
+}
+
+// nu at the cell and face Gauss points of trilinear cells (Eq. viscosity_pointwise):
+// law 0 constant, 1 analytic (position), 2 sphere field (position, then the
+// element-local projection onto a constant with the weights w det J),
+// 3 Carreau-Yasuda (physical gradient of u)
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) mapped_viscosity_kernel(LevelGeom g, SplitTab tab,
+                                                                         const double* __restrict__ verts,
+                                                                         RheologyDev rh,
+                                                                         const double* __restrict__ u,
+                                                                         double* __restrict__ nu_cell,
+                                                                         double* __restrict__ nu_face) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double X[8][3];
+  __shared__ double U[3][N3], Q[3][N3], G[3][3][N3], T0[N3], T1[N3];
+  __shared__ double FM[3][4 * N2], SC[5 * N2], red[2][kSplitThreads];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  load_cell_vertices(g, verts, e, X);
+  const bool carreau = rh.law == 3;
+  if (carreau)
+    for (int i = threadIdx.x; i < 3 * N3; i += blockDim.x) U[i / N3][i % N3] = u[(size_t)e * 3 * N3 + i];
+  __syncthreads();
+  if (carreau) {
+    for (int c = 0; c < 3; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
+    for (int c = 0; c < 3; ++c)
+      for (int m = 0; m < 3; ++m) sweep_dir<N, false>(m, T.Dg, Q[c], G[c][m]);
+    __syncthreads();
+  }
+  auto point_nu = [&](const double pos[3], const double Gp[3][3]) -> double {
+    if (rh.law == 0) return rh.nu;
+    if (rh.law == 1) {
+      const double sx = sin(M_PI * pos[0]), sy = sin(M_PI * pos[1]), sz = sin(M_PI * pos[2]);
+      return 1.0 + 9.0 * sx * sx * sy * sy * sz * sz;
+    }
+    if (rh.law == 2) {
+      for (int i = 0; i < rh.n_spheres; ++i) {
+        const double dx = pos[0] - rh.centers[3 * i], dy = pos[1] - rh.centers[3 * i + 1],
+                     dz = pos[2] - rh.centers[3 * i + 2];
+        if (dx * dx + dy * dy + dz * dz <= rh.radius * rh.radius) return rh.nu_max;
+      }
+      return rh.nu_matrix;
+    }
+    double ee = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        const double v = 0.5 * (Gp[k][l] + Gp[l][k]);
+        ee += v * v;
+      }
+    const double gdot = sqrt(2.0 * ee);
+    return rh.eta_inf + (rh.eta0 - rh.eta_inf) * pow(rh.kappa + pow(rh.lambda * gdot, rh.a), (rh.b - 1.0) / rh.a);
+  };
+  double wsum = 0.0, nsum = 0.0;
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
+    double J[3][3], Ji[3][3], pos[3], Gp[3][3] = {{0}};
+    trilinear_jac(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J, pos);
+    const double det = inverse3(J, Ji);
+    if (carreau)
+      for (int c = 0; c < 3; ++c)
+        for (int l = 0; l < 3; ++l) Gp[c][l] = G[c][0][q] * Ji[0][l] + G[c][1][q] * Ji[1][l] + G[c][2][q] * Ji[2][l];
+    const double nu = point_nu(pos, Gp);
+    nu_cell[(size_t)e * N3 + q] = nu;
+    const double w = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
+    wsum += w;
+    nsum += w * nu;
+  }
+  if (rh.law == 2) {  // sphere field: element-local L2 projection onto a constant
+    red[0][threadIdx.x] = wsum;
+    red[1][threadIdx.x] = nsum;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + w];
+        red[1][threadIdx.x] += red[1][threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    const double nu_e = red[1][0] / red[0][0];
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) nu_cell[(size_t)e * N3 + q] = nu_e;
+    for (int p = threadIdx.x; p < 6 * N2; p += blockDim.x) nu_face[(size_t)e * 6 * N2 + p] = nu_e;
+    return;
+  }
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    if (carreau)
+      for (int c = 0; c < 3; ++c) face_eval<N>(U[c], d, s, T, FM[c], SC);
+    __syncthreads();
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double xi[3];
+      xi[d] = s ? 1.0 : 0.0;
+      xi[t1] = tab.gp[p % N];
+      xi[t2] = tab.gp[p / N];
+      double J[3][3], Ji[3][3], pos[3], Gp[3][3] = {{0}};
+      trilinear_jac(X, xi[0], xi[1], xi[2], J, pos);
+      inverse3(J, Ji);
+      if (carreau)
+        for (int c = 0; c < 3; ++c) {
+          double r[3];
+          r[d] = FM[c][N2 + p];
+          r[t1] = FM[c][2 * N2 + p];
+          r[t2] = FM[c][3 * N2 + p];
+          for (int l = 0; l < 3; ++l) Gp[c][l] = r[0] * Ji[0][l] + r[1] * Ji[1][l] + r[2] * Ji[2][l];
+        }
+      nu_face[((size_t)e * 6 + f) * N2 + p] = point_nu(pos, Gp);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+#define SIPG_MAPPED_DISPATCH(NN, CALL)              \
+  switch (NN) {                                     \
+    case 2: { constexpr int N = 2; CALL; break; }   \
+    case 3: { constexpr int N = 3; CALL; break; }   \
+    case 4: { constexpr int N = 4; CALL; break; }   \
+    case 5: { constexpr int N = 5; CALL; break; }   \
+    case 6: { constexpr int N = 6; CALL; break; }   \
+    default: return cudaErrorInvalidValue;          \
+  }
+
+cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                const double* lam, const double* nu_cell, const double* nu_face, double mass,
+                                const double* x, double* y, cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  if (ncomp == 3) {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3><<<g.ncells, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y)));
+  } else {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1><<<g.ncells, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mapped_lambda(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double* lam,
+                                 cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  mapped_lambda_kernel<<<(g.ncells + 127) / 128, 128, 0, st>>>(g, tab, n, verts, lam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mapped_viscosity(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                    const RheologyDev& rh, const double* u, double* nu_cell, double* nu_face,
+                                    cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_MAPPED_DISPATCH(n, (mapped_viscosity_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(
+                              g, tab, verts, rh, u, nu_cell, nu_face)));
+  return cudaGetLastError();
+}
+
+}  // namespace sipg

@@ -227,6 +227,8 @@ extern "C" int sipg_solve(sipg_ctx* ctx, int op, const double* b, double* x, con
   if (op == SIPG_OP_VISCOUS && !ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
   if (so && (so->maxit < 0 || !(so->rtol >= 0) || so->precond < 0 || so->precond > 2))
     return ctx->fail(SIPG_ERR_INVALID, "bad solve options");
+  if (ctx->mapped && (!so || so->precond != SIPG_PRECOND_NONE))
+    return ctx->fail(SIPG_ERR_INVALID, "trilinear cells: unpreconditioned CG only (no multigrid or diagonal)");
   return ctx->solve(op, b, x, so, stats);
 }
 
@@ -316,6 +318,7 @@ extern "C" int sipg_vcycle(sipg_ctx* ctx, int op, const double* b, double* x) {
 extern "C" int sipg_node_points(const sipg_ctx* cctx, int op, int level, double* xyz_host) {
   sipg_ctx* ctx = const_cast<sipg_ctx*>(cctx);
   if (!ctx || !xyz_host || (op != 0 && op != 1)) return SIPG_ERR_INVALID;
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "node points of trilinear cells: map the reference nodes on the host");
   const Hier& H = ctx->hier[op];
   if (level < 0 || level >= (int)H.L.size()) return SIPG_ERR_INVALID;
   const Level& L = H.L[level];

@@ -37,6 +37,7 @@ bool box_walls_ok(const sipg_ctx* ctx) {
 
 int check_forms(sipg_ctx* ctx) {
   if (ctx->opts.k_u < 2 || ctx->opts.k_u > 5) return ctx->fail(SIPG_ERR_INVALID, "velocity degree 2..5");
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the splitting-step forms are built for the box only");
   return SIPG_OK;
 }
 

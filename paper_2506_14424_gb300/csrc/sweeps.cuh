@@ -1,0 +1,127 @@
+// Generic shared-memory tensor sweeps and the split-step tables in shared
+// memory, used by the splitting-step forms (split.cu) and by the operators on
+// trilinear cells (mapped.cu). Device code only; one CTA per cell, the CTA's
+// threads share each sweep's outputs.
+#pragma once
+#include "common.cuh"
+
+namespace sipg {
+namespace sweeps {
+
+constexpr int kSplitThreads = 128;
+
+// out = A along DIR applied to the tensor in (extents EX, EY, EZ, x fastest);
+// A row-major [NO][E_DIR] (TR = false) or [E_DIR][NO] (TR = true), leading dim lda
+template <int EX, int EY, int EZ, int DIR, int NO, bool TR>
+__device__ __forceinline__ void sweep(const double* A, int lda, const double* in, double* out) {
+  constexpr int OX = DIR == 0 ? NO : EX, OY = DIR == 1 ? NO : EY, OZ = DIR == 2 ? NO : EZ;
+  constexpr int EIN = DIR == 0 ? EX : (DIR == 1 ? EY : EZ);
+  constexpr int SIN = DIR == 0 ? 1 : (DIR == 1 ? EX : EX * EY);
+  for (int t = threadIdx.x; t < OX * OY * OZ; t += blockDim.x) {
+    const int x = t % OX, y = (t / OX) % OY, z = t / (OX * OY);
+    const int o = DIR == 0 ? x : (DIR == 1 ? y : z);
+    const int base = (DIR == 0 ? 0 : x) + (DIR == 1 ? 0 : y) * EX + (DIR == 2 ? 0 : z) * EX * EY;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < EIN; ++m) acc += (TR ? A[m * lda + o] : A[o * lda + m]) * in[base + m * SIN];
+    out[t] = acc;
+  }
+}
+
+// three sweeps with the same matrix (N -> NO per direction); tmp: two buffers of N^3
+template <int N, int NO, bool TR>
+__device__ __forceinline__ void sweep3(const double* A, int lda, const double* in, double* t0, double* t1,
+                                       double* out) {
+  sweep<N, N, N, 0, NO, TR>(A, lda, in, t0);
+  __syncthreads();
+  sweep<NO, N, N, 1, NO, TR>(A, lda, t0, t1);
+  __syncthreads();
+  sweep<NO, NO, N, 2, NO, TR>(A, lda, t1, out);
+  __syncthreads();
+}
+
+// single sweep along a runtime direction (n^3 -> n^3)
+template <int N, bool TR>
+__device__ __forceinline__ void sweep_dir(int dir, const double* A, const double* in, double* out) {
+  if (dir == 0) sweep<N, N, N, 0, N, TR>(A, N, in, out);
+  else if (dir == 1) sweep<N, N, N, 1, N, TR>(A, N, in, out);
+  else sweep<N, N, N, 2, N, TR>(A, N, in, out);
+}
+
+__device__ __forceinline__ void face_dirs(int d, int* t1, int* t2) {
+  *t1 = d == 0 ? 1 : 0;
+  *t2 = d == 2 ? 1 : 2;
+}
+
+// cell index of face point (a, b) (a along t1 < t2) of face (d, s) in an n^3 tensor
+__device__ __forceinline__ int fnode(int d, int s, int a, int b, int n) {
+  int i[3];
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  i[d] = s ? n - 1 : 0;
+  i[t1] = a;
+  i[t2] = b;
+  return (i[2] * n + i[1]) * n + i[0];
+}
+
+// index of the wall face of box side f holding cell e (sides in order, faces
+// lexicographic over the tangential cell indices t1 < t2)
+__device__ __forceinline__ int bface_index(const LevelGeom& g, int e, int f) {
+  const int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
+  int off = 0;
+  for (int s = 0; s < f; ++s) off += side[s >> 1];
+  const int d = f >> 1;
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  return off + ijk[t2] * dims[t1] + ijk[t1];
+}
+
+// load the split tables into shared memory
+struct STabSm {
+  double S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN], Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
+  double dS[2][kMaxN], lg[2][kMaxN], dlg[2][kMaxN], gw[kMaxN];
+};
+__device__ __forceinline__ void load_tab(const SplitTab& t, STabSm& s) {
+  for (int i = threadIdx.x; i < kMaxN * kMaxN; i += blockDim.x) {
+    s.S[i] = t.S[i];
+    s.DS[i] = t.DS[i];
+    s.Dg[i] = t.Dg[i];
+    s.Sp[i] = t.Sp[i];
+    s.DSp[i] = t.DSp[i];
+  }
+  for (int i = threadIdx.x; i < kMaxN; i += blockDim.x) {
+    s.dS[0][i] = t.dS0[i];
+    s.dS[1][i] = t.dS1[i];
+    s.lg[0][i] = t.lg0[i];
+    s.lg[1][i] = t.lg1[i];
+    s.dlg[0][i] = t.dlg0[i];
+    s.dlg[1][i] = t.dlg1[i];
+    s.gw[i] = t.gw[i];
+  }
+}
+
+__device__ __forceinline__ double cell_weight(const STabSm& t, int q, int n, double detJ) {
+  return t.gw[q % n] * t.gw[(q / n) % n] * t.gw[q / (n * n)] * detJ;
+}
+
+// trace on face (d, s) of a field F given at the n^3 Gauss points, with the 1D
+// vector L over the normal index (values lg or derivatives dlg at 0 / 1)
+template <int N>
+__device__ __forceinline__ void trace(const double* F, const double* L, int d, double* out) {
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  const int str[3] = {1, N, N * N};
+  for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+    const int a = p % N, b = p / N;
+    const int base = a * str[t1] + b * str[t2];
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc += L[q] * F[base + q * str[d]];
+    out[p] = acc;
+  }
+}
+
+}  // namespace sweeps
+}  // namespace sipg

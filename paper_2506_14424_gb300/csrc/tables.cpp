@@ -184,6 +184,7 @@ SplitTab make_split_tab(int n) {
     T.dlg0[j] = e0[j];
     T.dlg1[j] = e1[j];
     T.gw[j] = gw[j];
+    T.gp[j] = gp[j];
   }
   return T;
 }
