@@ -157,6 +157,7 @@ int sipg_ctx::build_hierarchy(int op) {
     if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
     Cl.Ainv = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
     Cl.Atmp = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+    Cl.gjw = alloc<double>(256 + 16 * (int64_t)Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
   }
   // CG vectors on level 0
   for (int v = 0; v < 5; ++v) {
@@ -172,7 +173,7 @@ sipg_ctx::~sipg_ctx() {
     for (Level& L : H.L) {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
       cudaFree(L.nu_cellff); cudaFree(L.nu_faceff);
-      cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32);
+      cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
       for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
       cudaFree(L.Ainv); cudaFree(L.Atmp);
     }
@@ -520,8 +521,11 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   CK(launch_to_ff_inplace((int64_t)N * N, C.Ainv, st));
   float2* A = reinterpret_cast<float2*>(C.Ainv);
   float2* B = reinterpret_cast<float2*>(C.Atmp);
-  for (int k = 0; k < N; ++k) {
-    CK(launch_gj_step_ff(N, k, A, B, reinterpret_cast<float2*>(dscal + 8), st));
+  // blocks of 16 pivots: three launches per block instead of one per pivot
+  float2* Pinv = reinterpret_cast<float2*>(C.gjw);
+  float2* R = Pinv + 256;
+  for (int k0 = 0; k0 < N; k0 += 16) {
+    CK(launch_gj_block(N, k0, std::min(16, N - k0), A, B, Pinv, R, st));
     std::swap(A, B);
   }
   if (A != reinterpret_cast<float2*>(C.Ainv))

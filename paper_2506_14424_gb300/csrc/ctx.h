@@ -30,6 +30,7 @@ struct Level {
   int N = 0;                 // coarsest level: dense size
   double* Ainv = nullptr;    // coarsest level: FP64 inverse (row-major)
   double* Atmp = nullptr;
+  double* gjw = nullptr;     // coarsest level: blocked Gauss-Jordan scratch (16 x 16 + 16 x N pairs)
 };
 
 struct Hier {

@@ -118,7 +118,9 @@ cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, doubl
 cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st);
 // dense FP64 helpers for the coarse level
 cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st);
-cudaError_t launch_gj_step_ff(int N, int k, const float2* A, float2* B, float2* recip, cudaStream_t st);
+// blocked step: pivots k0 .. k0+b-1 (b <= 16); Pinv: b*b, R: b*N float-float scratch
+cudaError_t launch_gj_block(int N, int k0, int b, const float2* A, float2* B, float2* Pinv, float2* R,
+                            cudaStream_t st);
 cudaError_t launch_to_ff_inplace(int64_t n, double* v, cudaStream_t st);
 cudaError_t launch_from_ff_inplace(int64_t n, double* v, cudaStream_t st);
 cudaError_t launch_gemv(int N, const double* M, const double* x, double* y, cudaStream_t st);

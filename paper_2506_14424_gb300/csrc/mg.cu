@@ -556,45 +556,106 @@ cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStrea
   return cudaGetLastError();
 }
 
-// Gauss-Jordan step k on the dense coarse matrix (no pivoting: the coarse
+// Gauss-Jordan inverse of the dense coarse matrix (no pivoting: the coarse
 // operator is SPD, or SPD after the rank-one term of the singular Poisson
-// case): B = A with row k scaled by 1/A[k][k] and column k eliminated from
-// the other rows. The thread that writes the next pivot B[k+1][k+1] stores
-// its reciprocal in recip[(k + 1) & 1], so no thread divides per element.
-// Entries are float-float (float2 = (hi, lo)), one row per blockIdx.y; recip
-// holds two float-float pivot reciprocals.
-__global__ void gj_step_ff_kernel(int N, int k, const float2* __restrict__ A, float2* __restrict__ B,
-                                  float2* __restrict__ recip) {
-  const int i = blockIdx.y;
+// case), entries in float-float (float2 = (hi, lo)) for the FP32 pipe.
+// Blocked Gauss-Jordan: pivots k0 .. k0+b-1 at once (b <= 16). With P = A[K,K],
+// R = P^-1 A[K,:]:  new[K,K] = P^-1, new[K,j] = R[.,j], new[i,K] = -A[i,K] P^-1,
+// new[i,j] = A[i,j] - A[i,K] R[.,j]  (b = 1 is the step above).
+constexpr int kGjBlock = 16;
+__global__ void gj_block_inv_kernel(int N, int k0, int b, const float2* __restrict__ A, float2* __restrict__ Pinv) {
+  __shared__ ff M[kGjBlock][kGjBlock], I[kGjBlock][kGjBlock];
+  const int t = threadIdx.x, ti = t / b, tj = t % b;
+  const bool act = t < b * b;
+  if (act) {
+    const float2 v = A[(size_t)(k0 + ti) * N + k0 + tj];
+    M[ti][tj] = ff(v.x, v.y);
+    I[ti][tj] = ff(ti == tj ? 1.0f : 0.0f);
+  }
+  for (int p = 0; p < b; ++p) {
+    __syncthreads();
+    const ff inv = ff(1.0f) / M[p][p];
+    const ff fac = act ? M[ti][p] : ff(0.0f);
+    __syncthreads();
+    if (act && ti == p) {
+      M[p][tj] = M[p][tj] * inv;
+      I[p][tj] = I[p][tj] * inv;
+    }
+    __syncthreads();
+    if (act && ti != p) {
+      M[ti][tj] = M[ti][tj] - fac * M[p][tj];
+      I[ti][tj] = I[ti][tj] - fac * I[p][tj];
+    }
+  }
+  __syncthreads();
+  if (act) Pinv[ti * b + tj] = make_float2(I[ti][tj].hi, I[ti][tj].lo);
+}
+__global__ void gj_block_r_kernel(int N, int k0, int b, const float2* __restrict__ A, const float2* __restrict__ Pinv,
+                                  float2* __restrict__ R) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  const float2 r2 = recip[k & 1];
-  const ff rp(r2.x, r2.y);
-  auto ld = [&](size_t at) { const float2 v = A[at]; return ff(v.x, v.y); };
-  ff v;
-  if (i == k && j == k)
-    v = rp;
-  else if (i == k)
-    v = ld((size_t)k * N + j) * rp;
-  else if (j == k)
-    v = -(ld((size_t)i * N + k) * rp);
-  else
-    v = ld((size_t)i * N + j) - ld((size_t)i * N + k) * (ld((size_t)k * N + j) * rp);
-  B[(size_t)i * N + j] = make_float2(v.hi, v.lo);
-  if (i == k + 1 && j == k + 1) {
-    const ff r = ff(1.0f) / v;
-    recip[(k + 1) & 1] = make_float2(r.hi, r.lo);
+  ff col[kGjBlock];
+  for (int l = 0; l < b; ++l) {
+    const float2 v = A[(size_t)(k0 + l) * N + j];
+    col[l] = ff(v.x, v.y);
+  }
+  for (int m = 0; m < b; ++m) {
+    Acc<ff> acc;
+    for (int l = 0; l < b; ++l) {
+      const float2 pv = Pinv[m * b + l];
+      acc.add(ff(pv.x, pv.y), col[l]);
+    }
+    const ff r = acc.get();
+    R[(size_t)m * N + j] = make_float2(r.hi, r.lo);
   }
 }
-__global__ void recip_first_ff_kernel(const float2* A, float2* recip) {
-  const ff r = ff(1.0f) / ff(A[0].x, A[0].y);
-  recip[0] = make_float2(r.hi, r.lo);
+__global__ void gj_block_update_kernel(int N, int k0, int b, const float2* __restrict__ A,
+                                       const float2* __restrict__ Pinv, const float2* __restrict__ R,
+                                       float2* __restrict__ B) {
+  __shared__ ff rowK[kGjBlock];
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x < b) {
+    const float2 v = A[(size_t)i * N + k0 + threadIdx.x];
+    rowK[threadIdx.x] = ff(v.x, v.y);
+  }
+  __syncthreads();
+  if (j >= N) return;
+  const bool ik = i >= k0 && i < k0 + b, jk = j >= k0 && j < k0 + b;
+  ff v;
+  if (ik && jk) {
+    const float2 p = Pinv[(i - k0) * b + (j - k0)];
+    v = ff(p.x, p.y);
+  } else if (ik) {
+    const float2 r = R[(size_t)(i - k0) * N + j];
+    v = ff(r.x, r.y);
+  } else if (jk) {
+    Acc<ff> acc;
+    for (int m = 0; m < b; ++m) {
+      const float2 p = Pinv[m * b + (j - k0)];
+      acc.add(rowK[m], ff(p.x, p.y));
+    }
+    v = -acc.get();
+  } else {
+    Acc<ff> acc;
+    for (int m = 0; m < b; ++m) {
+      const float2 r = R[(size_t)m * N + j];
+      acc.add(rowK[m], ff(r.x, r.y));
+    }
+    const float2 a = A[(size_t)i * N + j];
+    v = ff(a.x, a.y) - acc.get();
+  }
+  B[(size_t)i * N + j] = make_float2(v.hi, v.lo);
 }
-cudaError_t launch_gj_step_ff(int N, int k, const float2* A, float2* B, float2* recip, cudaStream_t st) {
-  if (k == 0) recip_first_ff_kernel<<<1, 1, 0, st>>>(A, recip);
-  gj_step_ff_kernel<<<dim3((N + kBS - 1) / kBS, N), kBS, 0, st>>>(N, k, A, B, recip);
+cudaError_t launch_gj_block(int N, int k0, int b, const float2* A, float2* B, float2* Pinv, float2* R,
+                            cudaStream_t st) {
+  if (b < 1 || b > kGjBlock) return cudaErrorInvalidValue;
+  gj_block_inv_kernel<<<1, kGjBlock * kGjBlock, 0, st>>>(N, k0, b, A, Pinv);
+  gj_block_r_kernel<<<(N + kBS - 1) / kBS, kBS, 0, st>>>(N, k0, b, A, Pinv, R);
+  gj_block_update_kernel<<<dim3((N + kBS - 1) / kBS, N), kBS, 0, st>>>(N, k0, b, A, Pinv, R, B);
   return cudaGetLastError();
 }
+
 // in-place binary64 <-> float-float (same 8 bytes per entry)
 __global__ void to_ff_kernel(int64_t n, double* v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
