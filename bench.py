@@ -468,6 +468,24 @@ def trilinear_extras(n_cells=32, k=3, reps=10):
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms": ms, "gdofs": n / ms / 1e6}
         ctx.close()
+    # FP64 hp-multigrid CG on the jittered 16^3, k = 3 mesh (h-levels from every other vertex)
+    M = 16
+    gm = np.linspace(0.0, 1.0, M + 1)
+    Zm, Ym, Xm = np.meshgrid(gm, gm, gm, indexing="ij")
+    Vm = np.stack([Xm, Ym, Zm], axis=-1)
+    Jm = np.random.default_rng(4).uniform(-0.05 / M, 0.05 / M, size=Vm.shape)
+    Jm[[0, -1], :, :] = 0.0
+    Jm[:, [0, -1], :] = 0.0
+    Jm[:, :, [0, -1]] = 0.0
+    ctx = Context(M, M, M, k, vertices=Vm + Jm)
+    n = ctx.n_dofs("viscous")
+    ctx.set_viscosity(inputs.carreau_blood_like(), torch.tensor(inputs.uniform_vector(n, 1), device="cuda"))
+    b = torch.tensor(inputs.uniform_vector(n, 2), device="cuda")
+    ctx.solve("viscous", b, rtol=1e-8, maxit=500, precond="mg")
+    _, st = ctx.solve("viscous", b, rtol=1e-8, maxit=500, precond="mg")
+    out["mg_cg_16cubed_k3"] = {"levels": ctx.num_levels("viscous"), "iterations": st["iterations"],
+                               "seconds": st["seconds"], "rel_residual": st["rel_residual"]}
+    ctx.close()
     return out
 
 

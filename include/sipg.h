@@ -75,10 +75,11 @@ typedef struct {
    * image of the unit cube through its 8 vertices (general hexahedra, Sec. 5;
    * the jittered channel mesh). Copied during sipg_create. NULL: the box
    * [0,lx]x[0,ly]x[0,lz] (lx, ly, lz are then ignored otherwise). On such a
-   * mesh the library builds the fine level only: sipg_set_viscosity, FP64
-   * sipg_apply / sipg_level_apply(level 0) and sipg_solve with
-   * SIPG_PRECOND_NONE; multigrid, float-float and FP32 applies, mass
-   * operators, the splitting step and serving return SIPG_ERR_INVALID. */
+   * mesh: sipg_set_viscosity, FP64 applies on every level, sipg_solve with any
+   * preconditioner (the multigrid runs in FP64: mg_precision is set to
+   * SIPG_F64; h-levels take every other vertex, the transfers are the
+   * reference-cell embeddings); float-float and FP32 applies, mass operators,
+   * the splitting step and serving return SIPG_ERR_INVALID. */
   const double* vertices;
 } sipg_mesh_desc;
 

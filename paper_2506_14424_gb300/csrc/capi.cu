@@ -73,8 +73,8 @@ int sipg_ctx::build_hierarchy(int op) {
   const int k0 = op == SIPG_OP_VISCOUS ? opts.k_u : opts.k_u - 1;
   const int* bc = op == SIPG_OP_VISCOUS ? mesh.bc_velocity : mesh.bc_pressure;
   std::vector<int> ks{k0};
-  if (k0 > 2 && !mapped) ks.push_back(2);
-  if (k0 > 1 && !mapped) ks.push_back(1);
+  if (k0 > 2) ks.push_back(2);
+  if (k0 > 1) ks.push_back(1);
   int nx = mesh.nx, ny = mesh.ny, nz = mesh.nz;
   auto make_level = [&](int k, int lnx, int lny, int lnz) {
     Level L{};
@@ -96,7 +96,7 @@ int sipg_ctx::build_hierarchy(int op) {
   };
   H.L.clear();
   for (int k : ks) H.L.push_back(make_level(k, nx, ny, nz));
-  while (!mapped && H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
+  while (H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
     nx /= 2;
     ny /= 2;
     nz /= 2;
@@ -151,13 +151,34 @@ int sipg_ctx::build_hierarchy(int op) {
       }
     }
   }
-  if (!mapped) {
+  {
     Level& Cl = H.L.back();
     Cl.N = (int)Cl.ndofs;
     if (Cl.ndofs > 20000) return fail(SIPG_ERR_INVALID, "coarse level too large for the dense direct solve");
     Cl.Ainv = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
     Cl.Atmp = alloc<double>((int64_t)Cl.N * Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
     Cl.gjw = alloc<double>(256 + 16 * (int64_t)Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
+  }
+  // trilinear cells: vertices of every level (p-levels share the finer level's, h-levels
+  // take every other vertex) and the penalty factors with each level's Gauss rule
+  if (mapped && !dry) {
+    for (size_t l = 0; l < H.L.size(); ++l) {
+      Level& L = H.L[l];
+      if (l == 0) {
+        L.verts = dverts;
+      } else if (H.L[l - 1].g.ncells == L.g.ncells) {
+        L.verts = H.L[l - 1].verts;
+      } else {
+        const Level& F = H.L[l - 1];
+        e = cudaMalloc(&L.verts, sizeof(double) * 3 * (size_t)(L.g.nx + 1) * (L.g.ny + 1) * (L.g.nz + 1));
+        if (!e) e = launch_gather_vertices(F.g.nx, F.g.ny, L.g.nx, L.g.ny, L.g.nz, 2, F.verts, L.verts, st);
+        if (e) return fail(SIPG_ERR_NOMEM, "level vertices", e);
+        L.own_verts = true;
+      }
+      e = cudaMalloc(&L.lam, sizeof(double) * (size_t)L.g.ncells);
+      if (!e) e = launch_mapped_lambda(L.n, L.g, stabs[L.n], L.verts, L.lam, st);
+      if (e) return fail(SIPG_ERR_NOMEM, "level penalty factors", e);
+    }
   }
   // CG vectors on level 0
   for (int v = 0; v < 5; ++v) {
@@ -174,6 +195,8 @@ sipg_ctx::~sipg_ctx() {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
       cudaFree(L.nu_cellff); cudaFree(L.nu_faceff);
       cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
+      cudaFree(L.lam);
+      if (L.own_verts) cudaFree(L.verts);
       for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
       cudaFree(L.Ainv); cudaFree(L.Atmp);
     }
@@ -187,7 +210,7 @@ sipg_ctx::~sipg_ctx() {
   cudaFree(ss.vmax);
   for (double* p : gm.V) cudaFree(p);
   cudaFree(gm.z); cudaFree(gm.tmp); cudaFree(gm.r);
-  cudaFree(dverts); cudaFree(dlam[0]); cudaFree(dlam[1]);
+  cudaFree(dverts);
   if (hscal) cudaFreeHost(hscal);
 }
 
@@ -241,20 +264,18 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   for (int n = 2; n <= kMaxN; ++n) ctx->stabs[n] = make_split_tab(n);
   cudaError_t e = cudaSuccess;
   int rc = SIPG_OK;
-  for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);
-  if (rc == SIPG_OK && ctx->mapped) {
+  if (ctx->mapped) {
+    // the multigrid of trilinear cells runs in FP64 (the trilinear kernels are FP64)
+    ctx->opts.mg_precision = SIPG_F64;
     const size_t nv = (size_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) * 3;
     e = cudaMalloc(&ctx->dverts, sizeof(double) * nv);
     if (!e) e = cudaMemcpyAsync(ctx->dverts, mesh->vertices, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->st);
-    // Lambda_e with each operator's own Gauss rule (face areas of trilinear cells are
-    // not polynomial, so the rule matters at the level of rounding-plus)
-    for (int op = 0; op < 2 && !e; ++op) {
-      e = cudaMalloc(&ctx->dlam[op], sizeof(double) * (size_t)mesh->nx * mesh->ny * mesh->nz);
-      const Level& L0 = ctx->hier[op].L[0];
-      if (!e) e = launch_mapped_lambda(L0.n, L0.g, ctx->stabs[L0.n], ctx->dverts, ctx->dlam[op], ctx->st);
-    }
-    if (!e) e = cudaStreamSynchronize(ctx->st);
     if (e) rc = ctx->fail(SIPG_ERR_NOMEM, "vertices", e);
+  }
+  for (int op = 0; op < 2 && rc == SIPG_OK; ++op) rc = ctx->build_hierarchy(op);
+  if (rc == SIPG_OK && ctx->mapped) {
+    e = cudaStreamSynchronize(ctx->st);
+    if (e) rc = ctx->fail(SIPG_ERR_CUDA, "vertices", e);
   }
   if (rc == SIPG_OK) {
     ctx->partials = dalloc<double>(kDotBlocks, &e, ctx->st);
@@ -337,8 +358,8 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
   const Level& L = H.L[l];
   if (mapped) {
     if constexpr (sizeof(T) == 8) {
-      CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], dverts, dlam[op], op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
-                             op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr, mass, (const double*)x, (double*)y, st));
+      CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam, op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
+                             op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr, mass, (const double*)x, (double*)y, 1, st));
       return SIPG_OK;
     } else {
       return fail(SIPG_ERR_INVALID, "trilinear cells: FP64 applies only");
@@ -421,7 +442,10 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   Level& L = H.L[l];
   const double* nc = op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr;
   const double* nf = op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr;
-  CK(launch_diagonal(L.n, H.ncomp, L.g, tabs[L.n], nc, nf, mass, L.diag64, st));
+  if (mapped)
+    CK(launch_mapped_diagonal(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam, nc, nf, mass, L.diag64, st));
+  else
+    CK(launch_diagonal(L.n, H.ncomp, L.g, tabs[L.n], nc, nf, mass, L.diag64, st));
   CK(launch_reciprocal(L.ndofs, L.diag64, L.dinv64, st));
   CK((launch_cast<double, float>(L.ndofs, L.dinv64, L.dinv32, st)));
   if (l + 1 == (int)H.L.size()) return SIPG_OK;
@@ -503,7 +527,10 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   CK(launch_unit_columns(N, 0, N, C.Atmp, st));
   const double* nc = op == SIPG_OP_VISCOUS ? C.nu_cell64 : nullptr;
   const double* nf = op == SIPG_OP_VISCOUS ? C.nu_face64 : nullptr;
-  CK((launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, N, st)));
+  if (mapped)
+    CK(launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.verts, C.lam, nc, nf, mass, C.Atmp, C.Ainv, N, st));
+  else
+    CK((launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, N, st)));
   (void)l;
   // column j of A is stored contiguously: that is A^T row-major = A (symmetric)
   if (H.singular && op == SIPG_OP_POISSON && mass == 0.0) {
@@ -541,7 +568,6 @@ int sipg_ctx::ensure_setup(int op) {
 }
 
 int sipg_ctx::setup_operator(int op, double mass) {
-  if (mapped) return fail(SIPG_ERR_INVALID, "multigrid is built for the box only");
   sipg_ctx* ctx = this;
   Hier& H = hier[op];
   for (size_t l = 0; l < H.L.size(); ++l) {
@@ -595,17 +621,6 @@ int sipg_ctx::parse_rheology(const sipg_rheology* rh, const double* u_lin, Rheol
 // smoother or coarse setup; the hierarchy is marked stale)
 int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
   Hier& H = hier[SIPG_OP_VISCOUS];
-  if (mapped) {
-    Level& L = H.L[0];
-    cudaError_t e = launch_mapped_viscosity(L.n, L.g, stabs[L.n], dverts, r, u_lin, L.nu_cell64, L.nu_face64, st);
-    const int64_t n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
-    if (!e) e = launch_cast<double, float>(L.g.ncells * n3, L.nu_cell64, L.nu_cell32, st);
-    if (!e) e = launch_cast<double, float>(L.g.ncells * 6 * n2, L.nu_face64, L.nu_face32, st);
-    if (e) return fail(SIPG_ERR_CUDA, "viscosity kernel (trilinear cells)", e);
-    have_nu = true;
-    H.ready = false;
-    return SIPG_OK;
-  }
   for (size_t l = 0; l < H.L.size(); ++l) {
     Level& L = H.L[l];
     const double* u = nullptr;
@@ -627,6 +642,8 @@ int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
       // cellwise-constant field: carried down by the transfer of piecewise constants
       const Level& F = H.L[l - 1];
       e = launch_cell_nu_transfer(F.g, L.g, F.next_kind, F.n, L.n, F.nu_cell64, L.nu_cell64, L.nu_face64, st);
+    } else if (mapped) {
+      e = launch_mapped_viscosity(L.n, L.g, stabs[L.n], L.verts, r, u, L.nu_cell64, L.nu_face64, st);
     } else {
       e = launch_viscosity(L.n, L.g, tabs[L.n], r, u, L.nu_cell64, L.nu_face64, st);
     }
@@ -649,7 +666,6 @@ extern "C" int sipg_set_viscosity(sipg_ctx* ctx, const sipg_rheology* rh, const 
   int rc = ctx->parse_rheology(rh, u_lin, &r);
   if (rc) return rc;
   if ((rc = ctx->eval_viscosity(r, u_lin))) return rc;
-  if (ctx->mapped) return SIPG_OK;  // no multigrid on trilinear cells
   return ctx->setup_operator(SIPG_OP_VISCOUS, 0.0);
 }
 

@@ -31,6 +31,9 @@ struct Level {
   double* Ainv = nullptr;    // coarsest level: FP64 inverse (row-major)
   double* Atmp = nullptr;
   double* gjw = nullptr;     // coarsest level: blocked Gauss-Jordan scratch (16 x 16 + 16 x N pairs)
+  double* verts = nullptr;   // trilinear cells: this level's vertices (device)
+  bool own_verts = false;    //   allocated for this level (h-levels); p-levels share the finer one's
+  double* lam = nullptr;     // trilinear cells: Lambda_e per cell with this level's Gauss rule
 };
 
 struct Hier {
@@ -80,7 +83,6 @@ struct sipg_ctx {
   } ss;
   bool mapped = false;          // trilinear cells from a vertex array (fine level only)
   double* dverts = nullptr;     // device copy of the vertices
-  double* dlam[2] = {nullptr, nullptr};  // per-cell Lambda_e of the mapped cells, per operator (own rule)
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
   int64_t bytes = 0;    // device bytes allocated by the hierarchy
 

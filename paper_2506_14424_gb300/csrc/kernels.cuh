@@ -69,7 +69,12 @@ cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const
 // ---- operators on trilinear cells (mapped.cu); n = degree + 1 (2..6)
 cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                 const double* lam, const double* nu_cell, const double* nu_face, double mass,
-                                const double* x, double* y, cudaStream_t st);
+                                const double* x, double* y, int nbatch, cudaStream_t st);
+cudaError_t launch_mapped_diagonal(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                   const double* lam, const double* nu_cell, const double* nu_face, double mass,
+                                   double* diag, cudaStream_t st);
+cudaError_t launch_gather_vertices(int nxf, int nyf, int nxc, int nyc, int nzc, int stride, const double* fine,
+                                   double* coarse, cudaStream_t st);
 cudaError_t launch_mapped_lambda(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double* lam,
                                  cudaStream_t st);
 cudaError_t launch_mapped_viscosity(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,

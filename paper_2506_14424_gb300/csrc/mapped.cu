@@ -151,10 +151,12 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_apply_kernel(LevelGeom g
                                                                      const double* __restrict__ nu_cell,
                                                                      const double* __restrict__ nu_face, double mass,
                                                                      const double* __restrict__ x,
-                                                                     double* __restrict__ y) {
+                                                                     double* __restrict__ y, int64_t batch_stride) {
   constexpr int N3 = N * N * N, N2 = N * N;
   __shared__ STabSm T;
   __shared__ double X[8][3], XN[8][3];
+  x += (int64_t)blockIdx.y * batch_stride;
+  y += (int64_t)blockIdx.y * batch_stride;
   __shared__ double U[NC][N3], Q[NC][N3], G[NC][3][N3], T0[N3], T1[N3], OUT[NC][N3];
   __shared__ double FM[NC][4 * N2], FP[NC][4 * N2], CF[NC][4 * N2], SC[5 * N2];
   const int e = blockIdx.x;
@@ -468,14 +470,175 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_viscosity_kernel(LevelGe
 
 cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                 const double* lam, const double* nu_cell, const double* nu_face, double mass,
-                                const double* x, double* y, cudaStream_t st) {
+                                const double* x, double* y, int nbatch, cudaStream_t st) {
+  if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
+  const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
+  const dim3 grid(g.ncells, nbatch);
+  if (ncomp == 3) {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3><<<grid, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+  } else {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1><<<grid, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+  }
+  return cudaGetLastError();
+}
+
+// Vertices of a coarser level of the same structured mesh: every (stride)-th vertex.
+__global__ void gather_vertices_kernel(int nxf, int nyf, int nxc, int nyc, int nzc, int stride,
+                                       const double* __restrict__ fine, double* __restrict__ coarse) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nv = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
+  if (t >= nv * 3) return;
+  const int c = (int)(t % 3);
+  const int64_t v = t / 3;
+  const int i = (int)(v % (nxc + 1)), j = (int)((v / (nxc + 1)) % (nyc + 1)), k = (int)(v / ((int64_t)(nxc + 1) * (nyc + 1)));
+  const int64_t vf = ((int64_t)k * stride * (nyf + 1) + (int64_t)j * stride) * (nxf + 1) + (int64_t)i * stride;
+  coarse[t] = fine[vf * 3 + c];
+}
+cudaError_t launch_gather_vertices(int nxf, int nyf, int nxc, int nyc, int nzc, int stride, const double* fine,
+                                   double* coarse, cudaStream_t st) {
+  const int64_t n = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1) * 3;
+  gather_vertices_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(nxf, nyf, nxc, nyc, nzc, stride, fine, coarse);
+  return cudaGetLastError();
+}
+
+// Diagonal of (mass M + A) on trilinear cells, DoF (c, i) (own-side blocks with
+// trial = test = phi_i e_c; g = physical gradient of phi_i, W the point weight):
+//  viscous cell:  sum_q W (nu (|g|^2 + g_c^2) + mass phi^2)
+//  viscous face:  sum_p W (-nu phi (g.n + n_c g_c) + tau phi^2 (1 + n_c^2)), twice that on a
+//                 Dirichlet wall (mirror), nothing on a Neumann wall
+//  Poisson:       sum_q W (|g|^2 + mass phi^2);  faces sum_p W (-phi g.n + tau phi^2), x2 on walls
+// Face terms reach only the DoFs of the face layer (phi_i vanishes on the face otherwise).
+template <int N, int NC>
+__global__ void __launch_bounds__(kSplitThreads) mapped_diagonal_kernel(LevelGeom g, SplitTab tab,
+                                                                        const double* __restrict__ verts,
+                                                                        const double* __restrict__ lam,
+                                                                        const double* __restrict__ nu_cell,
+                                                                        const double* __restrict__ nu_face,
+                                                                        double mass, double* __restrict__ diag) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ STabSm T;
+  __shared__ double X[8][3], XN[8][3];
+  __shared__ double JI[9][N3], WQ[N3], NU[N3];
+  __shared__ double FJ[9][N2], FNm[3][N2], FW[N2], FT[N2], FNU[N2];
+  __shared__ double ACC[NC][N3];
+  const int e = blockIdx.x;
+  load_tab(tab, T);
+  load_cell_vertices(g, verts, e, X);
+  __syncthreads();
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
+    double J[3][3], Ji[3][3];
+    trilinear_jac(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J);
+    const double det = inverse3(J, Ji);
+    for (int m = 0; m < 9; ++m) JI[m][q] = Ji[m / 3][m % 3];
+    WQ[q] = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
+    NU[q] = NC == 3 ? nu_cell[(size_t)e * N3 + q] : 1.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    const int ix = i % N, iy = (i / N) % N, iz = i / N2;
+    double a0 = 0.0, ac[3] = {0.0, 0.0, 0.0}, am = 0.0;
+    for (int q = 0; q < N3; ++q) {
+      const int qx = q % N, qy = (q / N) % N, qz = q / N2;
+      const double sx = T.S[qx * N + ix], sy = T.S[qy * N + iy], sz = T.S[qz * N + iz];
+      const double r[3] = {T.DS[qx * N + ix] * sy * sz, sx * T.DS[qy * N + iy] * sz, sx * sy * T.DS[qz * N + iz]};
+      double gg[3];
+      for (int l = 0; l < 3; ++l) gg[l] = r[0] * JI[l][q] + r[1] * JI[3 + l][q] + r[2] * JI[6 + l][q];
+      const double w = WQ[q] * NU[q];
+      const double g2 = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
+      a0 += w * g2;
+      for (int c = 0; c < 3; ++c) ac[c] += w * gg[c] * gg[c];
+      const double ph = sx * sy * sz;
+      am += WQ[q] * ph * ph;
+    }
+    for (int c = 0; c < NC; ++c) ACC[c][i] = a0 + (NC == 3 ? ac[c] : 0.0) + mass * am;
+  }
+  __syncthreads();
+  const double lam_e = lam[e];
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const int nb = cell_neighbor(g, e, f);
+    if (nb < 0 && g.bc[f] == 1) continue;
+    const int fo = 2 * d + (1 - s);
+    const double orient = (2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0);
+    const double lam_p = nb >= 0 ? lam[nb] : lam_e;
+    const double tau0 = g.cip * (double)(N * N) * fmax(lam_e, lam_p);
+    const double mirror = nb >= 0 ? 1.0 : 2.0;
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+      double xi[3];
+      xi[d] = s ? 1.0 : 0.0;
+      xi[t1] = tab.gp[p % N];
+      xi[t2] = tab.gp[p / N];
+      double J[3][3], Ji[3][3];
+      trilinear_jac(X, xi[0], xi[1], xi[2], J);
+      inverse3(J, Ji);
+      for (int m = 0; m < 9; ++m) FJ[m][p] = Ji[m / 3][m % 3];
+      const double ta[3] = {J[0][t1], J[1][t1], J[2][t1]}, tb[3] = {J[0][t2], J[1][t2], J[2][t2]};
+      double n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
+      const double area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      for (int k = 0; k < 3; ++k) FNm[k][p] = n[k] * orient / area;
+      FW[p] = mirror * T.gw[p % N] * T.gw[p / N] * area;
+      double nub = 1.0, num = 1.0;
+      if (NC == 3) {
+        num = nu_face[((size_t)e * 6 + f) * N2 + p];
+        const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + fo) * N2 + p] : num;
+        nub = num > nup ? num : nup;
+        if (g.face_nu == 1) nub = 0.5 * (num + nup);
+        if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
+      }
+      FNU[p] = num;
+      FT[p] = tau0 * nub;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < N2; t += blockDim.x) {
+      const int ia = t % N, ib = t / N;
+      int idx[3];
+      idx[d] = s ? N - 1 : 0;
+      idx[t1] = ia;
+      idx[t2] = ib;
+      const int i = (idx[2] * N + idx[1]) * N + idx[0];
+      double acc0 = 0.0, accc[3] = {0.0, 0.0, 0.0};
+      for (int p = 0; p < N2; ++p) {
+        const int a = p % N, b = p / N;
+        const double sa = T.S[a * N + ia], sb = T.S[b * N + ib];
+        const double ph = sa * sb;
+        double r[3];
+        r[d] = T.dS[s][idx[d]] * ph;
+        r[t1] = T.DS[a * N + ia] * sb;
+        r[t2] = sa * T.DS[b * N + ib];
+        double gg[3];
+        for (int l = 0; l < 3; ++l) gg[l] = r[0] * FJ[l][p] + r[1] * FJ[3 + l][p] + r[2] * FJ[6 + l][p];
+        const double gn = gg[0] * FNm[0][p] + gg[1] * FNm[1][p] + gg[2] * FNm[2][p];
+        if (NC == 3) {
+          for (int c = 0; c < 3; ++c) {
+            const double nc = FNm[c][p];
+            accc[c] += FW[p] * (-FNU[p] * ph * (gn + nc * gg[c]) + FT[p] * ph * ph * (1.0 + nc * nc));
+          }
+        } else {
+          acc0 += FW[p] * (-ph * gn + FT[p] * ph * ph);
+        }
+      }
+      for (int c = 0; c < NC; ++c) ACC[c][i] += NC == 3 ? accc[c] : acc0;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NC * N3; i += blockDim.x) diag[(size_t)e * NC * N3 + i] = ACC[i / N3][i % N3];
+}
+
+cudaError_t launch_mapped_diagonal(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                   const double* lam, const double* nu_cell, const double* nu_face, double mass,
+                                   double* diag, cudaStream_t st) {
   if (g.ncells == 0) return cudaSuccess;
   if (ncomp == 3) {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3><<<g.ncells, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y)));
+    SIPG_MAPPED_DISPATCH(n, (mapped_diagonal_kernel<N, 3><<<g.ncells, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, diag)));
   } else {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1><<<g.ncells, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y)));
+    SIPG_MAPPED_DISPATCH(n, (mapped_diagonal_kernel<N, 1><<<g.ncells, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, diag)));
   }
   return cudaGetLastError();
 }

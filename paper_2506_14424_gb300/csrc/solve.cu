@@ -227,8 +227,6 @@ extern "C" int sipg_solve(sipg_ctx* ctx, int op, const double* b, double* x, con
   if (op == SIPG_OP_VISCOUS && !ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
   if (so && (so->maxit < 0 || !(so->rtol >= 0) || so->precond < 0 || so->precond > 2))
     return ctx->fail(SIPG_ERR_INVALID, "bad solve options");
-  if (ctx->mapped && (!so || so->precond != SIPG_PRECOND_NONE))
-    return ctx->fail(SIPG_ERR_INVALID, "trilinear cells: unpreconditioned CG only (no multigrid or diagonal)");
   return ctx->solve(op, b, x, so, stats);
 }
 
