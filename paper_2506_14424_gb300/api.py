@@ -308,11 +308,19 @@ class Context:
         self._check(self._lib.sipg_step_field(self._h, L.FIELD[which], _ptr(out)))
         return out
 
-    def apply_host(self, op, x, mass=0.0):
+    def apply_host(self, op, x, mass=0.0, out=None):
+        """y = (mass M + A) x for host arrays (copies inside the call). Pinned host
+        memory (e.g. numpy views of torch.empty(..., pin_memory=True)) copies at
+        the link's speed; out: optional preallocated result array."""
         x = np.ascontiguousarray(x, dtype=np.float64)
         if x.size != self.n_dofs(op):
             raise ValueError("vector size does not match the fine level")
-        y = np.empty_like(x)
+        if out is None:
+            y = np.empty_like(x)
+        else:
+            y = out
+            if not (isinstance(y, np.ndarray) and y.dtype == np.float64 and y.flags.c_contiguous and y.size == x.size):
+                raise ValueError("out: contiguous float64 array of the vector's size")
         self._check(self._lib.sipg_apply_host(self._h, L.OP[op], x.ctypes.data_as(ctypes.c_void_p),
                                               y.ctypes.data_as(ctypes.c_void_p), float(mass)))
         return y
