@@ -38,7 +38,32 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     p.add_argument("--arith", default="f64ff", choices=["f64", "f64ff"],
                    help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
+    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear"],
+                   help="run one extra workload alone and print its JSON (profiling runs)")
     return p.parse_args()
+
+
+def run_extra(name):
+    """One extra workload on its own (the commands of the ncu summaries in profiles/)."""
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+    torch.cuda.set_device(0)
+    if name == "step":
+        out = step_extras()
+    elif name == "trilinear":
+        out = trilinear_extras()
+    else:
+        ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U, krylov_arith="f64ff")
+        n = ctx.n_dofs("viscous")
+        if name == "mass":
+            xs = [torch.tensor(inputs.uniform_vector(n, seed=100 + i), device="cuda") for i in range(4)]
+            ys = [torch.empty_like(xs[0]) for _ in range(4)]
+            out = mass_timings(ctx, xs, ys, torch.cuda.current_stream())
+        else:
+            out = picard_extras(ctx)
+        ctx.close()
+    print(json.dumps({"extra": name, "result": out}), flush=True)
 
 
 def dist_env():
@@ -691,7 +716,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.extra:
+        run_extra(a.extra)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)

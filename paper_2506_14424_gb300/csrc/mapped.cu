@@ -17,6 +17,13 @@
 #include "kernels.cuh"
 #include "sweeps.cuh"
 
+// Resident CTAs per SM requested from the compiler for the trilinear apply: the
+// kernel is latency bound (barriers between sweeps, one CTA of 128 threads per
+// cell) and at its natural 204 registers only 2 CTAs fit. Measured at 32^3, k = 3:
+// 2 CTAs 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers, ~1 KB of spills) 11.1 ms.
+// Shared memory caps the count at higher degree (n = 6: 48 KB per CTA).
+template <int N> struct MappedMinBlocks { static constexpr int value = N <= 4 ? 8 : (N == 5 ? 6 : 4); };
+
 namespace sipg {
 namespace {
 using namespace sweeps;
@@ -145,7 +152,7 @@ __device__ void face_eval_t(const double* cf, int d, int s, const STabSm& T, dou
 }
 
 template <int N, int NC>
-__global__ void __launch_bounds__(kSplitThreads) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+__global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapped_apply_kernel(LevelGeom g, SplitTab tab,
                                                                      const double* __restrict__ verts,
                                                                      const double* __restrict__ lam,
                                                                      const double* __restrict__ nu_cell,
