@@ -21,6 +21,8 @@ for fluids with variable viscosity"):
 * ``solvers``      CG / Jacobi-PCG / dense Cholesky on the assembled matrix.
 * ``multigrid``    transfers, inverse diagonal, Chebyshev-Jacobi smoother and
                    V-cycle of Sec. 5.4 (matrix-free preconditioners).
+* ``cph``          continuous multigrid levels below the DG level: injection,
+                   Galerkin operators, composed transfers (Sec. 5.4).
 * ``manufactured`` body-force loads for manufactured solutions (Sec. 7.1).
 * ``mass``         element mass matrices (v, u)_e and their inverses (Sec. 3.2,
                    Eqs. convective_step_weak / projection_step_weak).
