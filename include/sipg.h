@@ -112,6 +112,10 @@ typedef struct {
   uint64_t seed;
   int krylov_arith;  /* arithmetic of the FP64 operator applies inside CG:
                         SIPG_F64 or SIPG_F64_FF [F64] */
+  int mg_cph;        /* 1: "cph" hierarchy of Sec. 5.4 - below the DG level, the
+                        continuous space of the same degree, then lower degrees and
+                        coarser meshes in the continuous space (Galerkin operators
+                        P^T A_DG P); 0: DG on every level [0]; box meshes only */
 } sipg_opts;
 
 /* Viscosity field (Eq. viscosity_general and Sec. 2).

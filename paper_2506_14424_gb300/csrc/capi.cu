@@ -151,6 +151,51 @@ int sipg_ctx::build_hierarchy(int op) {
       }
     }
   }
+  H.cph = false;
+  H.T.clear();
+  if (opts.mg_cph && !mapped) {
+    // cph: [DG level 0, continuous twins of every DG level]; the DG levels below 0 keep
+    // their viscosity storage (and ulin) for the twins
+    H.cph = true;
+    H.T = H.L;
+    std::vector<Level> lv;
+    Level d0 = H.T[0];
+    d0.alias = true;
+    d0.next_kind = 3;  // DG -> continuous, same mesh and degree
+    lv.push_back(d0);
+    for (size_t j = 0; j < H.T.size(); ++j) {
+      const Level& Tj = H.T[j];
+      Level c{};
+      c.g = Tj.g;
+      c.k = Tj.k;
+      c.n = Tj.n;
+      c.cg = true;
+      c.twin = (int)j;
+      c.cgg = CgGrid{Tj.g.nx, Tj.g.ny, Tj.g.nz, Tj.k, Tj.g.nx * Tj.k + 1, Tj.g.ny * Tj.k + 1, Tj.g.nz * Tj.k + 1,
+                     H.ncomp};
+      c.ndofs = (int64_t)H.ncomp * c.cgg.Gx * c.cgg.Gy * c.cgg.Gz;
+      c.ndg = Tj.ndofs;
+      c.nu_cell64 = Tj.nu_cell64;
+      c.nu_face64 = Tj.nu_face64;
+      c.nu_cell32 = Tj.nu_cell32;
+      c.nu_face32 = Tj.nu_face32;
+      c.next_kind = Tj.next_kind;
+      c.tt = Tj.tt;
+      c.diag64 = alloc<double>(c.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+      c.dinv64 = alloc<double>(c.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+      c.dinv32 = alloc<float>(c.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
+      for (int v = 0; v < 4; ++v) {
+        c.w[0][v] = alloc<double>(c.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
+        c.w[1][v] = alloc<float>(c.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc mg work", e);
+      }
+      for (int v = 0; v < 2; ++v) {
+        c.tdg[0][v] = alloc<double>(c.ndg, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc cph work", e);
+        c.tdg[1][v] = alloc<float>(c.ndg, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc cph work", e);
+      }
+      lv.push_back(c);
+    }
+    H.L = lv;
+  }
   {
     Level& Cl = H.L.back();
     Cl.N = (int)Cl.ndofs;
@@ -191,7 +236,17 @@ int sipg_ctx::build_hierarchy(int op) {
 sipg_ctx::~sipg_ctx() {
   if (dry) return;
   for (Hier& H : hier) {
-    for (Level& L : H.L) {
+    if (H.cph) {
+      // continuous levels own their work storage; level 0 is a copy of the DG level T[0]
+      for (Level& L : H.L) {
+        if (!L.cg) continue;
+        cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
+        for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
+        for (int p = 0; p < 2; ++p) for (int v = 0; v < 2; ++v) cudaFree(L.tdg[p][v]);
+        cudaFree(L.Ainv); cudaFree(L.Atmp);
+      }
+    }
+    for (Level& L : (H.cph ? H.T : H.L)) {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
       cudaFree(L.nu_cellff); cudaFree(L.nu_faceff);
       cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
@@ -254,6 +309,8 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (o.face_nu < 0 || o.face_nu > 2 || o.cheb_degree < 1 || o.lanczos_steps < 2) return SIPG_ERR_INVALID;
   if (o.krylov_arith != SIPG_F64 && o.krylov_arith != SIPG_F64_FF) return SIPG_ERR_INVALID;
   if (mesh->vertices && o.krylov_arith != SIPG_F64) return SIPG_ERR_INVALID;  // FP64 applies only
+  if (o.mg_cph != 0 && o.mg_cph != 1) return SIPG_ERR_INVALID;
+  if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
   sipg_ctx* ctx = new sipg_ctx();
   ctx->mesh = *mesh;
   ctx->mesh.vertices = nullptr;  // the caller's array is copied below, not kept
@@ -356,6 +413,21 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
   sipg_ctx* ctx = this;
   const Hier& H = hier[op];
   const Level& L = H.L[l];
+  if (L.cg) {  // P^T A_DG P: gather, DG operator of the twin (same mesh and degree), sum the copies
+    constexpr int p = sizeof(T) == 8 ? 0 : 1;
+    T* a = static_cast<T*>(L.tdg[p][0]);
+    T* b = static_cast<T*>(L.tdg[p][1]);
+    const T* nc = nullptr;
+    const T* nf = nullptr;
+    if (op == SIPG_OP_VISCOUS) {
+      if constexpr (sizeof(T) == 8) { nc = (const T*)L.nu_cell64; nf = (const T*)L.nu_face64; }
+      else { nc = (const T*)L.nu_cell32; nf = (const T*)L.nu_face32; }
+    }
+    CK(launch_cg_map<T>(CG_GATHER, L.cgg, x, a, 1, st));
+    CK((launch_apply<T>(L.n, H.ncomp, L.g, tabs[L.n], a, b, nc, nf, T(mass), 1, st)));
+    CK(launch_cg_map<T>(CG_SCATTER_SUM, L.cgg, b, y, 1, st));
+    return SIPG_OK;
+  }
   if (mapped) {
     if constexpr (sizeof(T) == 8) {
       CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam, op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
@@ -442,10 +514,15 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   Level& L = H.L[l];
   const double* nc = op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr;
   const double* nf = op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr;
-  if (mapped)
+  if (mapped) {
     CK(launch_mapped_diagonal(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam, nc, nf, mass, L.diag64, st));
-  else
+  } else if (L.cg) {  // sum over the copies of the cell and wall terms (jumps vanish)
+    double* t = static_cast<double*>(L.tdg[0][0]);
+    CK(launch_diagonal(L.n, H.ncomp, L.g, tabs[L.n], nc, nf, mass, t, st, false));
+    CK(launch_cg_map<double>(CG_SCATTER_SUM, L.cgg, t, L.diag64, 1, st));
+  } else {
     CK(launch_diagonal(L.n, H.ncomp, L.g, tabs[L.n], nc, nf, mass, L.diag64, st));
+  }
   CK(launch_reciprocal(L.ndofs, L.diag64, L.dinv64, st));
   CK((launch_cast<double, float>(L.ndofs, L.dinv64, L.dinv32, st)));
   if (l + 1 == (int)H.L.size()) return SIPG_OK;
@@ -527,10 +604,30 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   CK(launch_unit_columns(N, 0, N, C.Atmp, st));
   const double* nc = op == SIPG_OP_VISCOUS ? C.nu_cell64 : nullptr;
   const double* nf = op == SIPG_OP_VISCOUS ? C.nu_face64 : nullptr;
-  if (mapped)
+  if (mapped) {
     CK(launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.verts, C.lam, nc, nf, mass, C.Atmp, C.Ainv, N, st));
-  else
+  } else if (C.cg) {
+    // continuous coarse level: columns P^T A_DG P e_j in chunks of columns (gather,
+    // batched DG apply, batched sum over copies)
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)(64 << 20) / (16 * C.ndg)));
+    double *ga = nullptr, *gb = nullptr;
+    CK(cudaMalloc(&ga, sizeof(double) * (size_t)C.ndg * chunk));
+    CK(cudaMalloc(&gb, sizeof(double) * (size_t)C.ndg * chunk));
+    cudaError_t ce = cudaSuccess;
+    for (int j0 = 0; j0 < N && ce == cudaSuccess; j0 += chunk) {
+      const int nb = std::min(chunk, N - j0);
+      ce = launch_cg_map<double>(CG_GATHER, C.cgg, C.Atmp + (size_t)j0 * N, ga, nb, st);
+      if (ce == cudaSuccess)
+        ce = launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], ga, gb, nc, nf, mass, nb, st);
+      if (ce == cudaSuccess) ce = launch_cg_map<double>(CG_SCATTER_SUM, C.cgg, gb, C.Ainv + (size_t)j0 * N, nb, st);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(ga);
+    cudaFree(gb);
+    CK(ce);
+  } else {
     CK((launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, N, st)));
+  }
   (void)l;
   // column j of A is stored contiguously: that is A^T row-major = A (symmetric)
   if (H.singular && op == SIPG_OP_POISSON && mass == 0.0) {
@@ -621,14 +718,15 @@ int sipg_ctx::parse_rheology(const sipg_rheology* rh, const double* u_lin, Rheol
 // smoother or coarse setup; the hierarchy is marked stale)
 int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
   Hier& H = hier[SIPG_OP_VISCOUS];
-  for (size_t l = 0; l < H.L.size(); ++l) {
-    Level& L = H.L[l];
+  std::vector<Level>& DL = H.cph ? H.T : H.L;  // the DG sequence holds the viscosity storage
+  for (size_t l = 0; l < DL.size(); ++l) {
+    Level& L = DL[l];
     const double* u = nullptr;
     if (r.law == SIPG_LAW_CARREAU) {
       if (l == 0) {
         u = u_lin;
       } else {
-        Level& F = H.L[l - 1];
+        Level& F = DL[l - 1];
         const double* uf = l == 1 ? u_lin : F.ulin;
         cudaError_t e = F.next_kind == 1
                             ? launch_p_interp_down(F.n, L.n, 3, L.g.ncells, F.interp, uf, L.ulin, st)
@@ -640,7 +738,7 @@ int sipg_ctx::eval_viscosity(const RheologyDev& r, const double* u_lin) {
     cudaError_t e;
     if (r.law == SIPG_LAW_SINKER && l > 0) {
       // cellwise-constant field: carried down by the transfer of piecewise constants
-      const Level& F = H.L[l - 1];
+      const Level& F = DL[l - 1];
       e = launch_cell_nu_transfer(F.g, L.g, F.next_kind, F.n, L.n, F.nu_cell64, L.nu_cell64, L.nu_face64, st);
     } else if (mapped) {
       e = launch_mapped_viscosity(L.n, L.g, stabs[L.n], L.verts, r, u, L.nu_cell64, L.nu_face64, st);

@@ -45,6 +45,12 @@ struct SplitTab {
   double gw[kMaxN], gp[kMaxN];  // Gauss weights and points on [0, 1]
 };
 
+// Global Gauss-Lobatto node grid of a continuous (cph) level on the box.
+struct CgGrid {
+  int nx, ny, nz, k, Gx, Gy, Gz, ncomp;
+};
+enum { CG_GATHER = 0, CG_SCATTER_SUM = 1, CG_PICK = 2, CG_PICK_T = 3 };
+
 // Embedding matrices of the transfers (prolongation = interpolation of the
 // coarse polynomial at the fine Gauss-Lobatto nodes), row-major [nf][nc].
 struct TransferTab {

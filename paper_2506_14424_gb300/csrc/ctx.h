@@ -34,10 +34,20 @@ struct Level {
   double* verts = nullptr;   // trilinear cells: this level's vertices (device)
   bool own_verts = false;    //   allocated for this level (h-levels); p-levels share the finer one's
   double* lam = nullptr;     // trilinear cells: Lambda_e per cell with this level's Gauss rule
+  // continuous (cph) levels: values on the global node grid; the operator is
+  // P^T A_DG P with the DG data (viscosity) of the twin level of the same mesh/degree
+  bool cg = false;
+  bool alias = false;        // shallow copy of a DG level (owns nothing)
+  int twin = -1;
+  CgGrid cgg{};
+  int64_t ndg = 0;           // DoFs of the twin DG level
+  void* tdg[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [prec][2] DG-sized temporaries
 };
 
 struct Hier {
   int op = 0, ncomp = 0;
+  bool cph = false;          // L = [DG level 0, continuous twins of T[0..]]; T: the DG sequence
+  std::vector<Level> T;
   bool singular = false;
   bool ready = false;
   double setup_mass = 0.0;

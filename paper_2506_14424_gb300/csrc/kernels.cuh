@@ -81,9 +81,16 @@ cudaError_t launch_mapped_viscosity(int n, const LevelGeom& g, const SplitTab& t
                                     const RheologyDev& rh, const double* u, double* nu_cell, double* nu_face,
                                     cudaStream_t st);
 
+// ---- continuous (cph) levels (cph.cu): P (gather), P^T (scatter-sum), R (pick), R^T
+template <typename T>
+cudaError_t launch_cg_map(int kind, const CgGrid& cg, const T* x, T* y, int nbatch, cudaStream_t st);
+
 // ---- multigrid and vector kernels (mg.cu)
+// interior_faces = false: without the interior-face terms (the diagonal of a continuous
+// level is the sum over the copies of the cell and wall terms)
 cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
-                            const double* nu_face, double mass, double* diag, cudaStream_t st);
+                            const double* nu_face, double mass, double* diag, cudaStream_t st,
+                            bool interior_faces = true);
 template <typename T>
 cudaError_t launch_p_transfer(int nf, int nc, int ncomp, int ncells, const TransferTab& tt, int dir,
                               const T* in, T* out, cudaStream_t st);

@@ -30,7 +30,8 @@ inline int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + kBS - 1) /
 // One CTA per cell.
 template <int N, int NC>
 __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__ nu_cell,
-                                const double* __restrict__ nu_face, double mass, double* __restrict__ diag) {
+                                const double* __restrict__ nu_face, double mass, double* __restrict__ diag,
+                                bool interior_faces) {
   constexpr int N2 = N * N, N3 = N2 * N;
   __shared__ double F[N3], Fm[N3], T1[N3], T2[N3], C[4][N3];
   __shared__ double S2[N2], D2[N2], FD[6][N2];
@@ -81,7 +82,8 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     const int nb = cell_neighbor(g, e, f);
-    const bool skip = nb < 0 && g.bc[f] == 1;  // homogeneous Neumann: no face term
+    const bool skip = (nb < 0 && g.bc[f] == 1)      // homogeneous Neumann: no face term
+                      || (nb >= 0 && !interior_faces);  // continuous level: jumps vanish
     const double sigma = s ? 1.0 : -1.0;
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
     const double lam = nb >= 0 ? fmax(lam_e, penalty_lambda(g, nb)) : lam_e;
@@ -143,14 +145,15 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
 }
 
 cudaError_t launch_diagonal(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* nu_cell,
-                            const double* nu_face, double mass, double* diag, cudaStream_t st) {
+                            const double* nu_face, double mass, double* diag, cudaStream_t st,
+                            bool interior_faces) {
   if (g.ncells == 0) return cudaSuccess;
 #define SIPG_DIAG(NN)                                                                              \
   case NN:                                                                                         \
     if (ncomp == 3)                                                                                \
-      diagonal_kernel<NN, 3><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);      \
+      diagonal_kernel<NN, 3><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag, interior_faces); \
     else                                                                                           \
-      diagonal_kernel<NN, 1><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag);      \
+      diagonal_kernel<NN, 1><<<g.ncells, 128, 0, st>>>(g, tab, nu_cell, nu_face, mass, diag, interior_faces); \
     break;
   switch (n) {
     SIPG_DIAG(2) SIPG_DIAG(3) SIPG_DIAG(4) SIPG_DIAG(5) SIPG_DIAG(6)

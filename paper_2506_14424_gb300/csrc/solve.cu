@@ -34,6 +34,32 @@ int sipg_ctx::transfer(int op, int l, int dir, const T* in, T* out) {
   const Hier& H = hier[op];
   const Level& F = H.L[l];
   const Level& C = H.L[l + 1];
+  constexpr int pr = sizeof(T) == 8 ? 0 : 1;
+  if (F.next_kind == 3) {  // DG level 0 -> continuous level of the same mesh and degree: P / P^T
+    CK(launch_cg_map<T>(dir > 0 ? CG_GATHER : CG_SCATTER_SUM, C.cgg, in, out, 1, st));
+    return SIPG_OK;
+  }
+  if (F.cg) {
+    // continuous -> continuous: prolongation R_f Pdg P_c, restriction its transpose
+    T* tf = static_cast<T*>(F.tdg[pr][0]);
+    T* tc = static_cast<T*>(C.tdg[pr][0]);
+    if (dir > 0) {
+      CK(launch_cg_map<T>(CG_GATHER, C.cgg, in, tc, 1, st));
+      if (F.next_kind == 1)
+        CK(launch_p_transfer<T>(F.n, C.n, H.ncomp, F.g.ncells, F.tt, dir, tc, tf, st));
+      else
+        CK(launch_h_transfer<T>(F.n, H.ncomp, F.g, C.g, F.tt, dir, tc, tf, st));
+      CK(launch_cg_map<T>(CG_PICK, F.cgg, tf, out, 1, st));
+    } else {
+      CK(launch_cg_map<T>(CG_PICK_T, F.cgg, in, tf, 1, st));
+      if (F.next_kind == 1)
+        CK(launch_p_transfer<T>(F.n, C.n, H.ncomp, F.g.ncells, F.tt, dir, tf, tc, st));
+      else
+        CK(launch_h_transfer<T>(F.n, H.ncomp, F.g, C.g, F.tt, dir, tf, tc, st));
+      CK(launch_cg_map<T>(CG_SCATTER_SUM, C.cgg, tc, out, 1, st));
+    }
+    return SIPG_OK;
+  }
   if (F.next_kind == 1)
     CK(launch_p_transfer<T>(F.n, C.n, H.ncomp, F.g.ncells, F.tt, dir, in, out, st));
   else
@@ -320,6 +346,7 @@ extern "C" int sipg_node_points(const sipg_ctx* cctx, int op, int level, double*
   const Hier& H = ctx->hier[op];
   if (level < 0 || level >= (int)H.L.size()) return SIPG_ERR_INVALID;
   const Level& L = H.L[level];
+  if (L.cg) return ctx->fail(SIPG_ERR_INVALID, "node points of a continuous level: the global Gauss-Lobatto grid");
   const int64_t total = (int64_t)L.g.ncells * L.n * L.n * L.n * 3;
   double* d = nullptr;
   CK(cudaMalloc(&d, sizeof(double) * total));
