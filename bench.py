@@ -333,6 +333,17 @@ def gpu_extras(ctx, xs, ys, stream):
                          "rel_residual": st["rel_residual"], "status": st["status"], "rel_error_vs_ustar": err}
             c3.close()
         row["mixed_speedup"] = row["f64"]["seconds"] / row["f32"]["seconds"]
+        # the cph hierarchy (continuous levels below the DG level), FP32 V-cycle
+        c3 = Context(16, 16, 16, 4, mg_precision="f32", mg_cph=True)
+        c3.set_viscosity(sink)
+        nn = c3.n_dofs("viscous")
+        ustar = torch.tensor(inputs.uniform_vector(nn, seed=3), device="cuda")
+        b = c3.apply("viscous", ustar)
+        c3.solve("viscous", b, rtol=1e-8, precond="mg", maxit=1000, check=False)
+        x, st = c3.solve("viscous", b, rtol=1e-8, precond="mg", maxit=1000, check=False)
+        row["cph_f32"] = {"seconds": st["seconds"], "iterations": st["iterations"], "status": st["status"],
+                          "rel_error_vs_ustar": (torch.linalg.norm(x - ustar) / torch.linalg.norm(ustar)).item()}
+        c3.close()
         solves.append(row)
     out["cfg3_mg_solves_16cubed_k4"] = solves
     out["mass_32cubed_k3"] = mass_timings(ctx, xs, ys, stream)
