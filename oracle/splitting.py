@@ -56,6 +56,14 @@ with explicit basis functions at the Gauss points, as written in the paper:
   symmetric - and the right-hand side sum_i beta_i c_h(v, u^{n-i}; u^{n-i})
   (``convective_blocks``, ``convective_wall_rhs``).
 * Time step, Eq. (CFL_timestep_selection): dt = Cr / k^1.5 / max_{e,q} |J^-1 u|.
+* Divergence and continuity penalty step, Eq. (penalty_step), after the viscous
+  step: (v, u~) + (div v, tau_div div u~) + (v.n, tau_cont [u~].n) = (v, u^{n+1}).
+  READING ("chosen according to Fehn2018b", formulas not printed):
+  tau_div,e = ubar_e h_e/(k+1) dt, tau_cont,e = ubar_e dt (factors 1), ubar_e the
+  cell mean of |u^{n+1}|, h_e = |Omega_e|^(1/3); tau_cont averaged over the two
+  cells of an interior face; the jump of the normal component only; on Dirichlet
+  walls the exterior state is the wall data g (the paper: the oriented jump
+  incorporates the boundary data).
 
 The oracle solves every linear system exactly (sparse LU; the pressure with a
 rank-one term that fixes the mean). Pins: tests/test_oracle_splitting.py.
@@ -349,6 +357,92 @@ def cfl_dt(S, u, Cr):
     return Cr / S.k ** 1.5 / vmax
 
 
+def penalty_parameters(S, u, dt, zeta_div=1.0, zeta_cont=1.0):
+    """tau_div,e = zeta ubar_e h_e / (k+1) dt, tau_cont,e = zeta ubar_e dt per cell, with
+    ubar_e the cell mean of |u| and h_e = |Omega_e|^(1/3) (READING of "chosen according
+    to Fehn2018b", Eq. penalty_step)."""
+    C = S.mesh.n_cells
+    vol = S.mesh.volume()
+    W = S.cell_w * vol
+    tdiv, tcon = np.zeros(C), np.zeros(C)
+    for e in range(C):
+        uq = _values(S.cell_phi, _cell(S, u, e))
+        ubar = float(np.sum(W * np.linalg.norm(uq, axis=1)) / vol)
+        tdiv[e] = zeta_div * ubar * vol ** (1.0 / 3.0) / (S.k + 1) * dt
+        tcon[e] = zeta_cont * ubar * dt
+    return tdiv, tcon
+
+
+def penalty_blocks(S, tdiv, tcon):
+    """Sparse matrix of the divergence and continuity penalty step, Eq. (penalty_step):
+        (v, u)_e + (div v, tau_div,e div u)_e + (v.n, tau_F (u^- - u^+).n)_de
+    with tau_F the mean of the two cells' tau_cont on interior faces and the cell's on a
+    Dirichlet wall, where the exterior state is the wall data (its part goes to the
+    right-hand side, ``penalty_wall_rhs``); nothing on Neumann walls."""
+    mesh = S.mesh
+    C = mesh.n_cells
+    m = S.n_dofs_cell
+    W = S.cell_w * mesh.volume()
+    V, G = S._vector_basis(S.cell_phi, S._phys_grad(S.cell_dphi))
+    div = np.einsum('qakk->qa', G)
+    rows, cols, vals = [], [], []
+    ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing='ij')
+
+    def put(er, ec, blk):
+        rows.append(er * m + ii.ravel())
+        cols.append(ec * m + jj.ravel())
+        vals.append(blk.ravel())
+
+    for e in range(C):
+        own = np.einsum('q,qak,qbk->ab', W, V, V) + tdiv[e] * np.einsum('q,qa,qb->ab', W, div, div)
+        for f in range(6):
+            d, s, nvec = face_normal(f)
+            bt = mesh.boundary_type(e, f)
+            if bt == 'N':
+                continue
+            Wf = S.face_w2 * mesh.face_area(d)
+            Vt, _ = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
+            vn = np.einsum('qak,k->qa', Vt, nvec)
+            if bt == 'I':
+                nb = mesh.neighbor(e, f)
+                fo = 2 * d + (1 - s)
+                tau = 0.5 * (tcon[e] + tcon[nb])
+                Vn, _ = S._vector_basis(S.face_phi[fo], S._phys_grad(S.face_dphi[fo]))
+                vnn = np.einsum('qak,k->qa', Vn, nvec)
+                own += tau * np.einsum('q,qa,qb->ab', Wf, vn, vn)
+                put(e, nb, -tau * np.einsum('q,qa,qb->ab', Wf, vn, vnn))
+            else:
+                own += tcon[e] * np.einsum('q,qa,qb->ab', Wf, vn, vn)
+        put(e, e, own)
+    N = S.n_dofs
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N)).tocsr()
+
+
+def penalty_wall_rhs(S, tcon, g_faces):
+    """(v.n, tau_cont,e g.n) over Dirichlet walls (the wall data of the oriented jump)."""
+    mesh = S.mesh
+    out = np.zeros((mesh.n_cells, 3 * S.n ** 3))
+    for e in range(mesh.n_cells):
+        for f in range(6):
+            if mesh.boundary_type(e, f) != 'D':
+                continue
+            d, s, nvec = face_normal(f)
+            g = wall_data(S, g_faces, e, f)
+            Wf = S.face_w2 * mesh.face_area(d)
+            Vt, _ = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
+            out[e] += tcon[e] * np.einsum('q,qak,k,q->a', Wf, Vt, nvec, g @ nvec)
+    return out.reshape(-1)
+
+
+def penalty_step(S, u, dt, g_faces, zeta_div=1.0, zeta_cont=1.0):
+    """The post-processed velocity of Eq. (penalty_step) (exact sparse solve)."""
+    tdiv, tcon = penalty_parameters(S, u, dt, zeta_div, zeta_cont)
+    K = penalty_blocks(S, tdiv, tcon)
+    b = omass.apply_mass(S, u) + penalty_wall_rhs(S, tcon, g_faces)
+    return spla.spsolve(K.tocsc(), b), tdiv, tcon
+
+
 def pressure_solve(Sp_op, rhs):
     """Mean-free solution of the all-Neumann SIPG Laplacian with a mean-free right-hand side."""
     A = Sp_op.assemble().tocsc()
@@ -387,7 +481,7 @@ class Splitting:
         self.p = np.zeros(self.Sp_op.n_dofs) if p0 is None else np.array(p0, dtype=np.float64)
         self.steps = 0
 
-    def step(self, dt, picard=None):
+    def step(self, dt, picard=None, penalty=False):
         Su, Sp = self.Su, self.Sp
         order = min(2, len(self.hist))
         gamma0, alpha, beta = BDF[order]
@@ -434,6 +528,8 @@ class Splitting:
                 raise ValueError("the implicit-viscosity step is built for zero wall velocity")
             info = nonlinear.viscous_step_picard(Su, self.rheology, b, u_sharp, m, **picard)
             u_new = info['u']
+        if penalty:  # Alg. 1: post-process with the divergence and continuity penalty step
+            u_new = penalty_step(Su, u_new, dt, self.g_faces)[0]
         self.hist = [u_new] + hist[:1]
         self.p = p
         self.steps += 1

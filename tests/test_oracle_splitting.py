@@ -208,3 +208,26 @@ def test_linearly_implicit_convective_step_preserves_uniform_flow():
     for _ in range(2):
         out = sp.step(0.05)
         assert np.abs(out['u'] - u0).max() <= 1e-12
+
+
+def test_penalty_step_properties():
+    """Eq. (penalty_step): symmetric positive definite; a continuous divergence-free field
+    with matching wall data is its own post-processed velocity (both penalties vanish);
+    a divergence-carrying discontinuous field loses divergence and normal jumps."""
+    mesh = BoxMesh(3, 2, 2)
+    k = 2
+    S = SIPG(mesh, k, 3)
+    ufn = lambda x: np.stack([x[:, 1] * (1 - x[:, 2]), x[:, 2] - x[:, 0] * 0.5, 0.3 * x[:, 0] * x[:, 1]], axis=1)
+    u = S.interpolate(ufn)
+    tdiv, tcon = osp.penalty_parameters(S, u, 0.1)
+    K = osp.penalty_blocks(S, tdiv, tcon).toarray()
+    assert np.abs(K - K.T).max() <= 1e-14 * np.abs(K).max()
+    assert np.linalg.eigvalsh(K).min() > 0
+    ut, _, _ = osp.penalty_step(S, u, 0.1, [ufn] * 6)
+    assert np.abs(ut - u).max() <= 1e-12
+    # a discontinuous, divergent field: both penalty energies drop
+    rng = np.random.default_rng(7)
+    w = u + 0.3 * rng.standard_normal(S.n_dofs)
+    wt, tdiv, tcon = osp.penalty_step(S, w, 0.5, [ufn] * 6)
+    D = osp.penalty_blocks(S, tdiv, tcon) - osp.penalty_blocks(S, 0 * tdiv, 0 * tcon)
+    assert wt @ (D @ wt) < w @ (D @ w)
