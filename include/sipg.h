@@ -308,6 +308,9 @@ typedef struct {
   double visc_rtol;          /* viscous CG (linear implicit) [1e-8] */
   int maxit;                 /* CG iteration limit of both [1000] */
   sipg_picard_opts picard;   /* SIPG_VISC_IMPLICIT: mass_coeff is set by the step */
+  int penalty;               /* 1: end the step with the divergence and continuity penalty
+                                step (sipg_penalty_step, factors 1) [0] */
+  double penalty_rtol;       /* its CG tolerance [1e-10] */
 } sipg_step_opts;
 
 typedef struct {
@@ -317,6 +320,8 @@ typedef struct {
   double ppe_rel_residual, visc_rel_residual; /* final relative residuals (Picard: ||r||/||r0||) */
   double t_convective, t_pressure, t_projection, t_viscous, seconds; /* host clock, synchronised */
   int status;
+  int penalty_iterations;                     /* CG iterations of the penalty step (0 without) */
+  double t_penalty;                           /* its host-clock seconds (within seconds) */
 } sipg_step_stats;
 
 void sipg_default_step_opts(sipg_step_opts* o);
@@ -363,6 +368,33 @@ int sipg_viscous_wall_rhs(sipg_ctx* ctx, const double* wall_g, double* y);
  * velocity. The first call allocates restart + 4 fine-level vectors. (sync) */
 int sipg_solve_convective(sipg_ctx* ctx, const double* w, const double* wall_w, const double* b, double* x,
                           const sipg_solve_opts* so, int restart, sipg_solve_stats* stats);
+
+/* ------------------------------------ divergence and continuity penalty step
+ * Sec. 3.2, Eq. (penalty_step), the last sub-step of Alg. 1: the velocity u of
+ * the viscous step becomes u~, the solution of
+ *   (v, u~) + (div v, tau_div,e div u~) + (v.n, tau_F (u~^- - u~^+).n) = (v, u)
+ * for all v, tau_F the mean of the two cells' tau_cont,e on interior faces and
+ * tau_cont,e on a Dirichlet wall, where u~^+ is the wall velocity (18 host
+ * doubles, sides -x,+x,-y,+y,-z,+z, NULL = 0). The paper takes the penalty
+ * parameters from Fehn et al. (2018) without printing them; this library uses
+ *   tau_div,e = zeta_div ubar_e h_e / (k+1) dt,  tau_cont,e = zeta_cont ubar_e dt,
+ * ubar_e the cell mean of |u|, h_e = |Omega_e|^(1/3) (zeta = 1 in sipg_step).
+ * Box meshes, velocity degree 2..5; all vectors DEVICE, fine velocity level.
+ *
+ * sipg_penalty_tau: tau_div, tau_cont (n_cells doubles each) from u.
+ * sipg_penalty_apply: y = K x, K the left-hand side above (x != y).
+ * sipg_penalty_wall_rhs: y = the wall-data part of the right-hand side.
+ * sipg_penalty_step: u_out = u~ by CG preconditioned with the inverse cell mass
+ *   matrix, started from u, ||b - K u_out|| <= rtol ||b||; u_out may equal u.
+ *   SIPG_ERR_MAXIT when maxit iterations do not reach rtol. The first call
+ *   allocates five velocity vectors. (sync) */
+int sipg_penalty_tau(sipg_ctx* ctx, const double* u, double dt, double zeta_div, double zeta_cont,
+                     double* tau_div, double* tau_cont);
+int sipg_penalty_apply(sipg_ctx* ctx, const double* tau_div, const double* tau_cont, const double* x, double* y);
+int sipg_penalty_wall_rhs(sipg_ctx* ctx, const double* wall_g, const double* tau_cont, double* y);
+int sipg_penalty_step(sipg_ctx* ctx, const double* wall_g, const double* u, double dt, double zeta_div,
+                      double zeta_cont, double rtol, int maxit, double* u_out, int* iterations,
+                      double* rel_residual);
 
 /* ------------------------------------------------ multigrid pieces (tests) */
 /* Test hook for the float-float conversions of the SIPG_F64_FF kernels' loads

@@ -32,6 +32,7 @@ EXPORTS = [
     "sipg_default_picard_opts", "sipg_picard_solve", "sipg_ff_convert", "sipg_default_step_opts",
     "sipg_step_init", "sipg_step", "sipg_step_field", "sipg_cfl_dt", "sipg_convective_apply",
     "sipg_projection_rhs", "sipg_viscous_wall_rhs", "sipg_solve_convective", "sipg_convective_lin_apply",
+    "sipg_penalty_tau", "sipg_penalty_apply", "sipg_penalty_wall_rhs", "sipg_penalty_step",
 ]
 FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
 VISC_MODE = {"linear": 0, "implicit": 1}
@@ -89,7 +90,8 @@ class StepOpts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("wall_velocity", ctypes.c_double * 18),
                 ("body", ctypes.c_void_p), ("viscosity_mode", ctypes.c_int), ("convective_mode", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("ppe_rtol", ctypes.c_double),
-                ("visc_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("picard", PicardOpts)]
+                ("visc_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("picard", PicardOpts),
+                ("penalty", ctypes.c_int), ("penalty_rtol", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
@@ -97,7 +99,8 @@ class StepStats(ctypes.Structure):
                 ("picard_updates", ctypes.c_int), ("ppe_rel_residual", ctypes.c_double),
                 ("visc_rel_residual", ctypes.c_double), ("t_convective", ctypes.c_double),
                 ("t_pressure", ctypes.c_double), ("t_projection", ctypes.c_double),
-                ("t_viscous", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("t_viscous", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("penalty_iterations", ctypes.c_int), ("t_penalty", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -174,6 +177,10 @@ def load(path=None):
         "sipg_viscous_wall_rhs": (i, [vp, vp, vp]),
         "sipg_solve_convective": (i, [vp, vp, vp, vp, vp, P(SolveOpts), i, P(SolveStats)]),
         "sipg_convective_lin_apply": (i, [vp, vp, vp, vp, vp, vp]),
+        "sipg_penalty_tau": (i, [vp, vp, d, d, d, vp, vp]),
+        "sipg_penalty_apply": (i, [vp, vp, vp, vp, vp]),
+        "sipg_penalty_wall_rhs": (i, [vp, vp, vp, vp]),
+        "sipg_penalty_step": (i, [vp, vp, vp, d, d, d, d, i, vp, P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -257,6 +257,44 @@ class Context:
         self._check(self._lib.sipg_cfl_dt(self._h, _ptr(u), float(courant), ctypes.byref(dt)))
         return dt.value
 
+    def penalty_tau(self, u, dt, zeta_div=1.0, zeta_cont=1.0):
+        """(tau_div, tau_cont) per cell of the penalty step (see sipg_penalty_tau)."""
+        _need_cuda(u, torch.float64)
+        nc = self.cells[0] * self.cells[1] * self.cells[2]
+        td = torch.empty(nc, dtype=torch.float64, device=u.device)
+        tc = torch.empty(nc, dtype=torch.float64, device=u.device)
+        self._check(self._lib.sipg_penalty_tau(self._h, _ptr(u), float(dt), float(zeta_div), float(zeta_cont),
+                                               _ptr(td), _ptr(tc)))
+        return td, tc
+
+    def penalty_apply(self, tau_div, tau_cont, x):
+        """y = K x, the penalty step's operator (see sipg_penalty_apply)."""
+        for t in (tau_div, tau_cont, x):
+            _need_cuda(t, torch.float64)
+        y = torch.empty_like(x)
+        self._check(self._lib.sipg_penalty_apply(self._h, _ptr(tau_div), _ptr(tau_cont), _ptr(x), _ptr(y)))
+        return y
+
+    def penalty_wall_rhs(self, wall, tau_cont):
+        _need_cuda(tau_cont, torch.float64)
+        y = torch.empty(self.n_dofs("viscous"), dtype=torch.float64, device=tau_cont.device)
+        w = self._wall(wall)
+        wp = w.ctypes.data_as(ctypes.c_void_p) if w is not None else None
+        self._check(self._lib.sipg_penalty_wall_rhs(self._h, wp, _ptr(tau_cont), _ptr(y)))
+        return y
+
+    def penalty_step(self, u, dt, wall=None, zeta_div=1.0, zeta_cont=1.0, rtol=1e-10, maxit=500, out=None):
+        """The divergence and continuity penalty step of Eq. (penalty_step) (see sipg_penalty_step)."""
+        _need_cuda(u, torch.float64)
+        out = torch.empty_like(u) if out is None else out
+        w = self._wall(wall)
+        wp = w.ctypes.data_as(ctypes.c_void_p) if w is not None else None
+        its, res = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.sipg_penalty_step(self._h, wp, _ptr(u), float(dt), float(zeta_div), float(zeta_cont),
+                                                float(rtol), int(maxit), _ptr(out), ctypes.byref(its),
+                                                ctypes.byref(res)))
+        return out, {"iterations": its.value, "rel_residual": res.value}
+
     def step_init(self, u0, p0=None):
         _need_cuda(u0, torch.float64)
         self._check(self._lib.sipg_step_init(self._h, _ptr(u0), _ptr(p0)))
@@ -280,7 +318,8 @@ class Context:
                    "status": rc}
 
     def step(self, rheology, dt, wall=None, body=None, viscosity_mode="linear", ppe_rtol=1e-8, visc_rtol=1e-8,
-             maxit=1000, picard=None, convective_mode="explicit", gmres_restart=30):
+             maxit=1000, picard=None, convective_mode="explicit", gmres_restart=30, penalty=False,
+             penalty_rtol=1e-10):
         """One step of the projection scheme (see include/sipg.h, sipg_step)."""
         r, keep = rheology_struct(rheology)
         o = L.StepOpts()
@@ -296,6 +335,7 @@ class Context:
         o.convective_mode = L.CONV_MODE[convective_mode]
         o.gmres_restart = int(gmres_restart)
         o.ppe_rtol, o.visc_rtol, o.maxit = float(ppe_rtol), float(visc_rtol), int(maxit)
+        o.penalty, o.penalty_rtol = int(bool(penalty)), float(penalty_rtol)
         for key, val in (picard or {}).items():
             setattr(o.picard, key, val)
         st = L.StepStats()

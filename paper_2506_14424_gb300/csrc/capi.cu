@@ -265,6 +265,7 @@ sipg_ctx::~sipg_ctx() {
   cudaFree(ss.vmax);
   for (double* p : gm.V) cudaFree(p);
   cudaFree(gm.z); cudaFree(gm.tmp); cudaFree(gm.r);
+  for (double* p : {pw.tdiv, pw.tcon, pw.b, pw.r, pw.z, pw.p, pw.q}) cudaFree(p);
   cudaFree(dverts);
   if (hscal) cudaFreeHost(hscal);
 }

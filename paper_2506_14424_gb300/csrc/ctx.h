@@ -91,6 +91,12 @@ struct sipg_ctx {
     bool conv1 = false;   // conv[1] holds C(u^{n-1})
     int64_t steps = 0;
   } ss;
+  // divergence and continuity penalty step: tau per cell, right-hand side, CG vectors
+  struct PenaltyWork {
+    double *tdiv = nullptr, *tcon = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
+           *q = nullptr;
+    int64_t n = 0;
+  } pw;
   bool mapped = false;          // trilinear cells from a vertex array (fine level only)
   double* dverts = nullptr;     // device copy of the vertices
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
@@ -125,6 +131,9 @@ struct sipg_ctx {
   int eval_viscosity(const sipg::RheologyDev& r, const double* u_lin);
   int mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse);
   int convective_apply_total(const double* w, const double* wall_w, const double* x, double* y, double mass);
+  int penalty_work();
+  int penalty_solve(const double* wall_g, const double* u, double dt, double zeta_div, double zeta_cont,
+                    double rtol, int maxit, double* x, int* iterations, double* rel_residual);
   int gmres_solve(const double* w, const double* wall_w, const double* b, double* x, const sipg_solve_opts& so,
                   int restart, sipg_solve_stats* stats);
 };

@@ -66,6 +66,15 @@ cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& t
 cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
                            unsigned long long* vmax_bits, cudaStream_t st);
 
+// ---- divergence and continuity penalty step (penalty.cu); n = velocity degree + 1
+cudaError_t launch_penalty_tau(int n, const LevelGeom& g, const SplitTab& tab, const double* u, double zeta_div,
+                               double zeta_cont, double dt, double* tdiv, double* tcon, cudaStream_t st);
+cudaError_t launch_penalty_apply(int n, const LevelGeom& g, const SplitTab& tab, const double* tdiv,
+                                 const double* tcon, const double* x, double* y, cudaStream_t st);
+// y += wall-data terms (nothing for NULL or zero wall velocity)
+cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+                                const double* tcon, double* y, cudaStream_t st);
+
 // ---- operators on trilinear cells (mapped.cu); n = degree + 1 (2..6)
 cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                 const double* lam, const double* nu_cell, const double* nu_face, double mass,

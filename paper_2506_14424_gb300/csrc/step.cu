@@ -2,7 +2,7 @@
 // 5.1, Alg. 1, the convective term explicit (alpha_c = 0) or linearly implicit
 // in the viscous step (alpha_c = 1, u* = u#, GMRES): host sequence of library
 // kernels (split.cu forms, cell mass operators, MG-CG / GMRES solves, the
-// Picard loop).
+// Picard loop, the optional divergence and continuity penalty step).
 //
 // State between steps: u^n, u^{n-1}, C(u^{n-1}) (the convective vector of the
 // previous step is reused), p^n (initial guess of the next pressure solve).
@@ -55,6 +55,8 @@ extern "C" void sipg_default_step_opts(sipg_step_opts* o) {
   o->visc_rtol = 1e-8;
   o->maxit = 1000;
   sipg_default_picard_opts(&o->picard);
+  o->penalty = 0;
+  o->penalty_rtol = 1e-10;
 }
 
 extern "C" int sipg_convective_apply(sipg_ctx* ctx, const double* wall_g, const double* u, double* y) {
@@ -292,9 +294,18 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
     updates = pst2.iterations;
     visc_res = pst2.res0 > 0 ? pst2.res / pst2.res0 : 0.0;
   }
-  std::swap(S.u[0], S.u[1]);  // u^{n+1} -> u[0], u^n -> u[1]
   CK(cudaStreamSynchronize(st));
   const auto t4 = Clock::now();
+  // ---- 5 divergence and continuity penalty step (in place)
+  int pen_its = 0;
+  if (so.penalty) {
+    double pres = 0.0;
+    rc = ctx->penalty_solve(wall, S.u[1], dt, 1.0, 1.0, so.penalty_rtol, so.maxit, S.u[1], &pen_its, &pres);
+    if (rc != SIPG_OK) return rc;
+  }
+  std::swap(S.u[0], S.u[1]);  // u^{n+1} -> u[0], u^n -> u[1]
+  CK(cudaStreamSynchronize(st));
+  const auto t5 = Clock::now();
   S.n_hist = 2;
   S.steps += 1;
   if (stats) {
@@ -308,7 +319,9 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
     stats->t_pressure = secs(t1, t2);
     stats->t_projection = secs(t2, t3);
     stats->t_viscous = secs(t3, t4);
-    stats->seconds = secs(t0, t4);
+    stats->t_penalty = secs(t4, t5);
+    stats->penalty_iterations = pen_its;
+    stats->seconds = secs(t0, t5);
     stats->status = SIPG_OK;
   }
   return SIPG_OK;
