@@ -467,6 +467,19 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
         "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
         "mean_t_viscous": float(np.mean([r["t_viscous"] for r in rows])),
         "gmres_iterations": [r["visc_iterations"] for r in rows]}
+    # explicit convection, ending each step with the divergence and continuity penalty step
+    ctx.step_init(u0)
+    rows = []
+    for i in range(warm + steps):
+        st = ctx.step(rh, dt, wall=wall, ppe_rtol=1e-8, visc_rtol=1e-8, penalty=True)
+        if i >= warm:
+            rows.append(st)
+    out["with_penalty_step"] = {
+        "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
+        "mean_t_penalty": float(np.mean([r["t_penalty"] for r in rows])),
+        "penalty_iterations": [r["penalty_iterations"] for r in rows]}
+    td, tc = ctx.penalty_tau(u0, dt)
+    out["penalty_apply_ms"] = ev(lambda: ctx.penalty_apply(td, tc, u0))
     ctx.close()
     return out
 
