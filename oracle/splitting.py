@@ -104,9 +104,11 @@ def _grads(S, dphi, U):
 
 
 def wall_data(S, g_faces, e, f):
-    """Dirichlet datum g at the face points of (e, f): a constant vector per box face, or a
-    callable of the points (used by the consistency pins)."""
-    g = g_faces[f] if g_faces is not None else np.zeros(3)
+    """Dirichlet datum g at the face points of (e, f): per boundary id (the box sides 0..5,
+    faces against removed cells 6; a missing id is no-slip) a constant vector or a callable
+    of the points (the inflow profile, the consistency pins)."""
+    b = S.mesh.boundary_id(e, f)
+    g = g_faces[b] if g_faces is not None and b < len(g_faces) else np.zeros(3)
     if callable(g):
         return np.asarray(g(S.face_points(e, f)), dtype=np.float64)
     return np.broadcast_to(np.asarray(g, dtype=np.float64), (S.nq ** 2, 3))
@@ -461,13 +463,13 @@ class Splitting:
                  convective='explicit'):
         self.mesh, self.k = mesh, int(k)
         self.rheology = rheology
-        self.g_faces = [np.zeros(3) if g_faces is None else
-                        (g_faces[f] if callable(g_faces[f]) else np.asarray(g_faces[f], float)) for f in range(6)]
+        self.g_faces = [np.zeros(3) if g_faces is None or f >= len(g_faces) else
+                        (g_faces[f] if callable(g_faces[f]) else np.asarray(g_faces[f], float)) for f in range(7)]
         self.Su = SIPG(mesh, k, 3, penalty_factor=penalty_factor)
         self.Sp = SIPG(mesh, k - 1, 1, penalty_factor=penalty_factor, n_quad=k + 1)   # mixed forms
         # the pressure is Neumann where the velocity is Dirichlet and vice versa (Sec. 3.2)
         pbc = tuple('N' if b == 'D' else 'D' for b in mesh.bc)
-        self.pmesh = BoxMesh(*mesh.n_cells_dir, extent=mesh.extent, bc=pbc)
+        self.pmesh = mesh.with_bc(pbc)
         self.Sp_op = SIPG(self.pmesh, k - 1, 1, penalty_factor=penalty_factor)      # PPE operator
         self.body = None if body is None else np.asarray(body, dtype=np.float64)
         self.mode = viscosity_mode

@@ -13,6 +13,8 @@ takes an explicit seed and uses numpy's ``default_rng``.
                         c_m = (k_m x a_m) / |k_m x a_m|, a_m ~ N(0, I),
                         phi_m ~ U(0, 2 pi): unit amplitude per mode and
                         exactly divergence-free because c_m . k_m = 0.
+* ``bfs_channel``     - the grid and active-cell flags of the backward-facing
+                        step channel (geometry only).
 """
 import numpy as np
 
@@ -66,3 +68,21 @@ def fourier_field_gradient(points, modes):
     pts = np.asarray(points, dtype=np.float64)
     arg = 2.0 * np.pi * pts @ ks.T + phis
     return -2.0 * np.pi * np.einsum('pm,mi,mj->pij', np.sin(arg), cs, ks)
+
+
+def bfs_channel(cells_per_unit, inlet_length=5.0, outlet_length=30.0, step=1.0, height=2.0, depth=4.0):
+    """Grid of the backward-facing-step channel: the inlet [-inlet_length, 0] x [step, height]
+    feeds the outlet [0, outlet_length] x [0, height] (expansion ratio height / (height - step)),
+    z in [0, depth] periodic; cubes of side 1 / cells_per_unit. Returns the grid over the
+    bounding box and its active flags (nz, ny, nx): the block [-inlet_length, 0] x [0, step]
+    is removed. Boundary ids of the grid: -x the inflow, +x the outflow, -y / +y and the faces
+    against the removed block no-slip walls."""
+    m = int(cells_per_unit)
+    nx, ny, nz = round((inlet_length + outlet_length) * m), round(height * m), round(depth * m)
+    lo = (-float(inlet_length), 0.0, 0.0)
+    xc = lo[0] + (np.arange(nx) + 0.5) / m
+    yc = (np.arange(ny) + 0.5) / m
+    removed = (xc[None, :] < 0.0) & (yc[:, None] < step)
+    active = np.broadcast_to(~removed, (nz, ny, nx)).copy()
+    return {"dims": (nx, ny, nz), "extent": (inlet_length + outlet_length, float(height), float(depth)),
+            "lo": lo, "active": active, "periodic": (False, False, True)}
