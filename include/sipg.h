@@ -81,6 +81,25 @@ typedef struct {
    * reference-cell embeddings); float-float and FP32 applies, mass operators,
    * the splitting step and serving return SIPG_ERR_INVALID. */
   const double* vertices;
+  /* Topology beyond the plain box (zero-initialised fields keep the box):
+   * active   HOST, optional: nx*ny*nz flags, x fastest, 0 = the grid cell is
+   *          removed (the solid block below a backward-facing step, say); NULL =
+   *          every cell. The cells of the mesh are the active cells, numbered in
+   *          grid order; every vector is laid out over them.
+   * bc_removed_velocity, bc_removed_pressure: condition on faces against a
+   *          removed cell (velocity Dirichlet with zero wall velocity and
+   *          pressure Neumann for a wall).
+   * periodic[3]: 1 = direction d is periodic (each direction needs >= 2 cells;
+   *          the bc of its two sides is unused); the first and last cell layers
+   *          are face neighbours.
+   * origin[3]: the grid's lower corner (positions of nodes, viscosity laws).
+   * Removed cells or periodic directions: boxes only (no vertices), no cph
+   * hierarchy; multigrid h-levels coarsen while every 2x2x2 block of cells is
+   * all active or all removed. */
+  const unsigned char* active;
+  int bc_removed_velocity, bc_removed_pressure;
+  int periodic[3];
+  double origin[3];
 } sipg_mesh_desc;
 
 /* Discretisation and solver options. Zero-initialised fields take the

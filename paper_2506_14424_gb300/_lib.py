@@ -43,7 +43,9 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
                 ("bc_velocity", ctypes.c_int * 6), ("bc_pressure", ctypes.c_int * 6),
-                ("vertices", ctypes.c_void_p)]
+                ("vertices", ctypes.c_void_p), ("active", ctypes.c_void_p),
+                ("bc_removed_velocity", ctypes.c_int), ("bc_removed_pressure", ctypes.c_int),
+                ("periodic", ctypes.c_int * 3), ("origin", ctypes.c_double * 3)]
 
 
 class Opts(ctypes.Structure):

@@ -55,9 +55,14 @@ class Context:
     def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
                  penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
                  cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, krylov_arith="f64",
-                 stream=None, vertices=None, mg_cph=False):
+                 stream=None, vertices=None, mg_cph=False, active=None, periodic=(False, False, False),
+                 origin=(0.0, 0.0, 0.0), bc_removed="DN"):
         """vertices: optional (nz+1, ny+1, nx+1, 3) host array of vertex positions
-        (trilinear cells; fine level only, see include/sipg.h)."""
+        (trilinear cells; fine level only, see include/sipg.h).
+        active: optional (nz, ny, nx) flags of the grid cells (False = removed, e.g. the
+        block below a backward-facing step); periodic: per direction; origin: lower
+        corner of the grid; bc_removed: velocity and pressure condition on faces
+        against removed cells (see sipg_mesh_desc)."""
         self._lib = L.load()
         m = L.MeshDesc()
         m.nx, m.ny, m.nz = int(nx), int(ny), int(nz)
@@ -65,6 +70,17 @@ class Context:
         for i in range(6):
             m.bc_velocity[i] = L.BC[bc_velocity[i]]
             m.bc_pressure[i] = L.BC[bc_pressure[i]]
+        act = None
+        if active is not None:
+            act = np.ascontiguousarray(np.asarray(active, dtype=np.uint8).reshape(-1))
+            if act.size != int(nx) * int(ny) * int(nz):
+                raise ValueError("active: (nz, ny, nx) flags expected")
+            m.active = act.ctypes.data
+        m.bc_removed_velocity = L.BC[bc_removed[0]]
+        m.bc_removed_pressure = L.BC[bc_removed[1]]
+        for d in range(3):
+            m.periodic[d] = int(bool(periodic[d]))
+            m.origin[d] = float(origin[d])
         verts = None
         if vertices is not None:
             verts = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
@@ -88,12 +104,13 @@ class Context:
         h = ctypes.c_void_p()
         rc = self._lib.sipg_create(ctypes.byref(m), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))
-        del verts  # copied by sipg_create
+        del verts, act  # copied by sipg_create
         if rc != L.SIPG_OK:
             raise SipgError(rc, "sipg_create failed (see stderr)")
         self._h = h
         self.k_u = int(k_u)
         self.cells = (int(nx), int(ny), int(nz))
+        self.n_cells = self.n_dofs("poisson") // self.k_u ** 3
 
     def close(self):
         if getattr(self, "_h", None):
@@ -136,9 +153,9 @@ class Context:
         del keep
 
     def get_viscosity(self, level=0):
-        (nx, ny, nz), k, _ = self.level_info("viscous", level)
+        _, k, _ = self.level_info("viscous", level)
         n = k + 1
-        C = nx * ny * nz
+        C = self.level_cells("viscous", level)
         dev = torch.device("cuda")
         nc = torch.empty(C * n ** 3, dtype=torch.float64, device=dev)
         nf = torch.empty(C * 6 * n * n, dtype=torch.float64, device=dev)
@@ -260,7 +277,7 @@ class Context:
     def penalty_tau(self, u, dt, zeta_div=1.0, zeta_cont=1.0):
         """(tau_div, tau_cont) per cell of the penalty step (see sipg_penalty_tau)."""
         _need_cuda(u, torch.float64)
-        nc = self.cells[0] * self.cells[1] * self.cells[2]
+        nc = self.n_cells
         td = torch.empty(nc, dtype=torch.float64, device=u.device)
         tc = torch.empty(nc, dtype=torch.float64, device=u.device)
         self._check(self._lib.sipg_penalty_tau(self._h, _ptr(u), float(dt), float(zeta_div), float(zeta_cont),
@@ -424,10 +441,15 @@ class Context:
         self._check(self._lib.sipg_vcycle(self._h, L.OP[op], _ptr(b), _ptr(x)))
         return x
 
+    def level_cells(self, op="viscous", level=0):
+        """Active cells of a level (the grid's cells on a plain box)."""
+        _, k, nd = self.level_info(op, level)
+        return nd // ((3 if op == "viscous" else 1) * (k + 1) ** 3)
+
     def node_points(self, op="viscous", level=0):
-        (nx, ny, nz), k, _ = self.level_info(op, level)
+        _, k, _ = self.level_info(op, level)
         n = k + 1
-        out = np.empty((nx * ny * nz, n ** 3, 3))
+        out = np.empty((self.level_cells(op, level), n ** 3, 3))
         self._check(self._lib.sipg_node_points(self._h, L.OP[op], level, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 

@@ -52,6 +52,79 @@ bool valid_bc(const int* bc) {
   return true;
 }
 
+// Topology tables of an nx x ny x nz grid with active flags act (NULL: every
+// cell) and periodic directions (see LevelGeom): boundary faces are numbered in
+// cell order, faces -x,+x,-y,+y,-z,+z within a cell. used_ids: bit i set when
+// some boundary face carries boundary id i.
+struct HostTopo {
+  int ncells = 0, nbf = 0, used_ids = 0;
+  std::vector<int> nbr, cgrid, gcell, bface;
+};
+
+HostTopo host_topology(int nx, int ny, int nz, const unsigned char* act, const int* periodic) {
+  HostTopo t;
+  const int G = nx * ny * nz;
+  t.gcell.assign(G, -1);
+  for (int i = 0; i < G; ++i)
+    if (!act || act[i]) {
+      t.gcell[i] = (int)t.cgrid.size();
+      t.cgrid.push_back(i);
+    }
+  t.ncells = (int)t.cgrid.size();
+  t.nbr.assign((size_t)t.ncells * 6, 0);
+  const int dims[3] = {nx, ny, nz};
+  for (int e = 0; e < t.ncells; ++e) {
+    const int gi = t.cgrid[e];
+    const int ijk[3] = {gi % nx, (gi / nx) % ny, gi / (nx * ny)};
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, s = f & 1;
+      int q[3] = {ijk[0], ijk[1], ijk[2]};
+      q[d] += s ? 1 : -1;
+      int bid = -1;
+      if (q[d] < 0 || q[d] >= dims[d]) {
+        if (periodic[d])
+          q[d] = (q[d] + dims[d]) % dims[d];
+        else
+          bid = f;
+      }
+      if (bid < 0) {
+        const int nb = t.gcell[(q[2] * ny + q[1]) * nx + q[0]];
+        if (nb >= 0) {
+          t.nbr[(size_t)e * 6 + f] = nb;
+          continue;
+        }
+        bid = 6;
+      }
+      t.nbr[(size_t)e * 6 + f] = -1 - (bid + 8 * t.nbf);
+      t.bface.push_back(e * 6 + f);
+      t.used_ids |= 1 << bid;
+      ++t.nbf;
+    }
+  }
+  return t;
+}
+
+bool mesh_topology(const sipg_mesh_desc* m) {
+  return m->active != nullptr || m->periodic[0] || m->periodic[1] || m->periodic[2];
+}
+
+// Active flags of the once-coarsened grid; false if a 2x2x2 block mixes active
+// and removed cells (the mesh cannot be coarsened).
+bool coarsen_mask(int nx, int ny, int nz, const std::vector<unsigned char>& fine, std::vector<unsigned char>* coarse) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  coarse->assign((size_t)cx * cy * cz, 0);
+  for (int k = 0; k < cz; ++k)
+    for (int j = 0; j < cy; ++j)
+      for (int i = 0; i < cx; ++i) {
+        int cnt = 0;
+        for (int ch = 0; ch < 8; ++ch)
+          cnt += fine[((size_t)(2 * k + (ch >> 2)) * ny + 2 * j + ((ch >> 1) & 1)) * nx + 2 * i + (ch & 1)] != 0;
+        if (cnt != 0 && cnt != 8) return false;
+        (*coarse)[((size_t)k * cy + j) * cx + i] = cnt == 8;
+      }
+  return true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ construction
@@ -75,7 +148,49 @@ int sipg_ctx::build_hierarchy(int op) {
   std::vector<int> ks{k0};
   if (k0 > 2) ks.push_back(2);
   if (k0 > 1) ks.push_back(1);
+  const int bc_removed = op == SIPG_OP_VISCOUS ? mesh.bc_removed_velocity : mesh.bc_removed_pressure;
   int nx = mesh.nx, ny = mesh.ny, nz = mesh.nz;
+  std::vector<unsigned char> lmask = mask;  // active flags of the current grid (topology meshes)
+  if (topo && lmask.empty()) lmask.assign((size_t)nx * ny * nz, 1);
+  int used_ids = 0x3f;                      // boundary ids on the fine level (plain box: the 6 sides)
+  cudaError_t e = cudaSuccess;
+  // topology tables of the current grid, shared by its levels and by both hierarchies
+  using Cached = TopoEntry;
+  auto fill = [&](const Cached& c, LevelGeom& g) {
+    g.ncells = c.ncells;
+    g.nbf = c.nbf;
+    if (c.dev) {
+      g.nbr = c.dev;
+      g.cgrid = c.dev + (size_t)6 * c.ncells;
+      g.gcell = g.cgrid + c.ncells;
+      g.bface = g.gcell + (size_t)g.nx * g.ny * g.nz;
+    }
+    if (g.nx == mesh.nx && g.ny == mesh.ny && g.nz == mesh.nz) used_ids = c.used;
+  };
+  auto topology = [&](LevelGeom& g) -> int {
+    for (const Cached& c : topo_cache)
+      if (c.nx == g.nx && c.ny == g.ny && c.nz == g.nz) {
+        fill(c, g);
+        return SIPG_OK;
+      }
+    const HostTopo t = host_topology(g.nx, g.ny, g.nz, lmask.data(), mesh.periodic);
+    if (t.ncells == 0) return fail(SIPG_ERR_INVALID, "no active cell");
+    const size_t cnt = t.nbr.size() + t.cgrid.size() + t.gcell.size() + t.bface.size();
+    int* dev = alloc<int>((int64_t)cnt, &e);
+    if (e) return fail(SIPG_ERR_NOMEM, "alloc topology", e);
+    if (dev) {
+      std::vector<int> all;
+      all.reserve(cnt);
+      for (const std::vector<int>* v : {&t.nbr, &t.cgrid, &t.gcell, &t.bface}) all.insert(all.end(), v->begin(), v->end());
+      e = cudaMemcpy(dev, all.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice);
+      if (e) return fail(SIPG_ERR_CUDA, "upload topology", e);
+      topo_dev.push_back(dev);
+    }
+    topo_cache.push_back(Cached{g.nx, g.ny, g.nz, t.ncells, t.nbf, t.used_ids, dev});
+    fill(topo_cache.back(), g);
+    return SIPG_OK;
+  };
+  int rc_level = SIPG_OK;
   auto make_level = [&](int k, int lnx, int lny, int lnz) {
     Level L{};
     L.k = k;
@@ -88,20 +203,32 @@ int sipg_ctx::build_hierarchy(int op) {
     L.g.h[1] = mesh.ly / lny;
     L.g.h[2] = mesh.lz / lnz;
     for (int d = 0; d < 3; ++d) L.g.ih[d] = 1.0 / L.g.h[d];
+    for (int d = 0; d < 3; ++d) L.g.x0[d] = mesh.origin[d];
     for (int i = 0; i < 6; ++i) L.g.bc[i] = bc[i];
+    L.g.bc[6] = bc_removed;
     L.g.cip = opts.penalty_factor;
     L.g.face_nu = opts.face_nu;
+    if (topo && rc_level == SIPG_OK) rc_level = topology(L.g);
     L.ndofs = (int64_t)L.g.ncells * H.ncomp * L.n * L.n * L.n;
     return L;
   };
   H.L.clear();
   for (int k : ks) H.L.push_back(make_level(k, nx, ny, nz));
   while (H.L.back().ndofs >= opts.coarse_max_dofs && nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0) {
+    if (topo) {
+      bool ok = true;
+      const int cd[3] = {nx / 2, ny / 2, nz / 2};
+      for (int d = 0; d < 3; ++d) ok = ok && (!mesh.periodic[d] || cd[d] >= 2);
+      std::vector<unsigned char> cm;
+      if (!ok || !coarsen_mask(nx, ny, nz, lmask, &cm)) break;
+      lmask.swap(cm);
+    }
     nx /= 2;
     ny /= 2;
     nz /= 2;
     H.L.push_back(make_level(H.L.back().k, nx, ny, nz));
   }
+  if (rc_level != SIPG_OK) return rc_level;
   for (size_t l = 0; l + 1 < H.L.size(); ++l) {
     Level& F = H.L[l];
     Level& C = H.L[l + 1];
@@ -116,10 +243,9 @@ int sipg_ctx::build_hierarchy(int op) {
     }
   }
   H.singular = true;  // all-Neumann operator: constants (Poisson) / rigid modes (viscous)
-  for (int i = 0; i < 6; ++i)
-    if (bc[i] == SIPG_BC_DIRICHLET) H.singular = false;
+  for (int i = 0; i < 7; ++i)
+    if ((used_ids >> i & 1) && H.L[0].g.bc[i] == SIPG_BC_DIRICHLET) H.singular = false;
   // storage
-  cudaError_t e = cudaSuccess;
   for (size_t l = 0; l < H.L.size(); ++l) {
     Level& L = H.L[l];
     const int64_t C = L.g.ncells, n3 = (int64_t)L.n * L.n * L.n, n2 = (int64_t)L.n * L.n;
@@ -266,6 +392,7 @@ sipg_ctx::~sipg_ctx() {
   for (double* p : gm.V) cudaFree(p);
   cudaFree(gm.z); cudaFree(gm.tmp); cudaFree(gm.r);
   for (double* p : {pw.tdiv, pw.tcon, pw.b, pw.r, pw.z, pw.p, pw.q}) cudaFree(p);
+  for (int* p : topo_dev) cudaFree(p);
   cudaFree(dverts);
   if (hscal) cudaFreeHost(hscal);
 }
@@ -312,8 +439,21 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (mesh->vertices && o.krylov_arith != SIPG_F64) return SIPG_ERR_INVALID;  // FP64 applies only
   if (o.mg_cph != 0 && o.mg_cph != 1) return SIPG_ERR_INVALID;
   if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
+  const bool topo = mesh_topology(mesh);
+  if (topo) {
+    if (mesh->vertices || o.mg_cph) return SIPG_ERR_INVALID;
+    const int dims[3] = {mesh->nx, mesh->ny, mesh->nz};
+    for (int d = 0; d < 3; ++d)
+      if ((mesh->periodic[d] != 0 && mesh->periodic[d] != 1) || (mesh->periodic[d] && dims[d] < 2))
+        return SIPG_ERR_INVALID;
+    for (int b : {mesh->bc_removed_velocity, mesh->bc_removed_pressure})
+      if (b != SIPG_BC_DIRICHLET && b != SIPG_BC_NEUMANN) return SIPG_ERR_INVALID;
+  }
   sipg_ctx* ctx = new sipg_ctx();
   ctx->mesh = *mesh;
+  ctx->topo = topo;
+  if (mesh->active) ctx->mask.assign(mesh->active, mesh->active + (size_t)mesh->nx * mesh->ny * mesh->nz);
+  ctx->mesh.active = nullptr;  // copied above
   ctx->mesh.vertices = nullptr;  // the caller's array is copied below, not kept
   ctx->mapped = mesh->vertices != nullptr;
   ctx->opts = o;
@@ -369,6 +509,9 @@ extern "C" int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* 
   probe.dry = true;
   probe.mesh = *mesh;
   probe.opts = o;
+  probe.topo = mesh_topology(mesh);
+  if (mesh->active) probe.mask.assign(mesh->active, mesh->active + (size_t)mesh->nx * mesh->ny * mesh->nz);
+  probe.mesh.active = nullptr;
   for (int op = 0; op < 2; ++op) {
     int rc = probe.build_hierarchy(op);
     if (rc) return rc;

@@ -60,17 +60,55 @@ struct TransferTab {
 };
 
 // Geometry and discretisation of one level, passed by value to kernels.
+// The cells are the active cells of an nx x ny x nz grid of equal boxes over
+// [x0, x0 + extent]. The plain box (every cell active, no periodic direction)
+// has no tables (nbr == nullptr): cell e is grid cell e and neighbours follow
+// from the grid indices. Otherwise (cells removed, e.g. the channel behind a
+// backward-facing step, or periodic directions) three device tables describe
+// the topology:
+//   nbr[e*6 + f]  >= 0: the cell across face f (periodic directions wrap);
+//                 <  0: a boundary face, v = -1 - nbr with boundary id v & 7
+//                       (0..5 the grid's sides -x,+x,-y,+y,-z,+z, 6 a face
+//                       against a removed cell) and boundary-face number v >> 3
+//   cgrid[e]      grid index (ix + nx (iy + ny iz)) of active cell e
+//   gcell[i]      active index of grid cell i, or -1 for a removed cell
+//   bface[b]      e*6 + f of boundary face b
+// Boundary faces of the plain box are numbered side by side (-x first), each
+// side lexicographic over its tangential cell indices t1 < t2.
 struct LevelGeom {
   int nx, ny, nz;
   int ncells;
   double h[3];
   double ih[3];     // 1 / h, precomputed on the host (no FP64 division on the device)
-  int bc[6];        // 0 = Dirichlet, 1 = Neumann, per box face -x,+x,-y,+y,-z,+z
+  int bc[7];        // 0 = Dirichlet, 1 = Neumann, per boundary id
   double cip;       // penalty factor C_IP
   int face_nu;      // 0 max, 1 arithmetic, 2 harmonic
+  double x0[3];     // lower corner of the grid
+  int nbf;          // boundary faces
+  const int* nbr;   // topology tables (nullptr: the plain box)
+  const int* cgrid;
+  const int* gcell;
+  const int* bface;
 };
 
+__host__ __device__ inline void cell_ijk(const LevelGeom& g, int e, int* ijk) {
+  const int i = g.cgrid ? g.cgrid[e] : e;
+  ijk[0] = i % g.nx;
+  ijk[1] = (i / g.nx) % g.ny;
+  ijk[2] = i / (g.nx * g.ny);
+}
+
+// active index of grid cell (i, j, k) (in range), -1 if removed
+__host__ __device__ inline int grid_cell(const LevelGeom& g, int i, int j, int k) {
+  const int gi = (k * g.ny + j) * g.nx + i;
+  return g.gcell ? g.gcell[gi] : gi;
+}
+
 __host__ __device__ inline int cell_neighbor(const LevelGeom& g, int e, int f) {
+  if (g.nbr) {
+    const int v = g.nbr[e * 6 + f];
+    return v >= 0 ? v : -1;
+  }
   const int d = f >> 1, s = f & 1;
   int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
   const int dims[3] = {g.nx, g.ny, g.nz};
@@ -78,6 +116,14 @@ __host__ __device__ inline int cell_neighbor(const LevelGeom& g, int e, int f) {
   if (ijk[d] < 0 || ijk[d] >= dims[d]) return -1;
   return (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
 }
+
+// boundary id of the boundary face (e, f) (the grid side f on the plain box)
+__host__ __device__ inline int boundary_id(const LevelGeom& g, int e, int f) {
+  return g.nbr ? ((-1 - g.nbr[e * 6 + f]) & 7) : f;
+}
+
+// boundary condition (0 Dirichlet, 1 Neumann) of the boundary face (e, f)
+__host__ __device__ inline int face_bc(const LevelGeom& g, int e, int f) { return g.bc[boundary_id(g, e, f)]; }
 
 // Penalty geometry factor Lambda_e = sum_f w_f |f| / |Omega_e| with w_f = 1/2
 // on interior and 1 on boundary faces (box cells: |f| / |Omega_e| = 1 / h_d).

@@ -59,6 +59,14 @@ struct Hier {
 
 struct sipg_ctx {
   sipg_mesh_desc mesh{};
+  std::vector<unsigned char> mask;  // active flags of the fine grid (empty: every cell)
+  bool topo = false;                // removed cells or periodic directions: topology tables
+  std::vector<int*> topo_dev;       // device topology tables (one allocation per mesh)
+  struct TopoEntry {
+    int nx, ny, nz, ncells, nbf, used;
+    int* dev;
+  };
+  std::vector<TopoEntry> topo_cache;
   sipg_opts opts{};
   cudaStream_t st = nullptr;
   sipg::Tab tabs[sipg::kMaxN + 1]{};

@@ -39,6 +39,16 @@ cudaError_t launch_viscosity(int n, const LevelGeom& g, const Tab& tab, const Rh
 cudaError_t launch_cell_nu_transfer(const LevelGeom& fine, const LevelGeom& coarse, int kind, int nf, int nc,
                                     const double* fine_cell, double* nu_cell, double* nu_face, cudaStream_t st);
 
+// Wall velocity handed to the form launchers: `side`, 18 HOST doubles (a constant
+// vector per grid side -x,+x,-y,+y,-z,+z; faces against removed cells take zero)
+// or NULL (zero), and optionally `pts`, DEVICE values at the Gauss points of every
+// boundary face ([nbf][n^2][3], see LevelGeom), which take precedence.
+struct WallArg {
+  const double* side;
+  const double* pts;
+  WallArg(const double* s = nullptr, const double* p = nullptr) : side(s), pts(p) {}
+};
+
 // ---- forms of the splitting step (split.cu); n = velocity degree + 1 (3..6)
 struct PpeBndArgs {
   int n_hist;        // m: velocity histories entering the convective terms
@@ -47,21 +57,21 @@ struct PpeBndArgs {
   double betabar[2]; // extrapolation of order m_p
   double gn_coef;    // -(gamma0/dt)
 };
-cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                               const double* u, double* y, cudaStream_t st);
 // y = sum_e c_h(phi, u; w), walls u^+ = -u^- + 2 wall_u, w^+ = -w^- + 2 wall_w (NULL = 0)
-cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_w,
-                                  const double* wall_u, const double* w, const double* u, double* y,
+cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_w,
+                                  const WallArg& wall_u, const double* w, const double* u, double* y,
                                   cudaStream_t st);
-int n_wall_faces(const LevelGeom& g);
-cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+int n_wall_faces(const LevelGeom& g);  // boundary faces (g.nbf with topology tables)
+cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                 const PpeBndArgs& a, const RheologyDev& rh, const double* u0, const double* u1,
                                 double* sb, cudaStream_t st);
 cudaError_t launch_ppe_rhs(int n, const LevelGeom& g, const SplitTab& tab, double coef, const double* uhat,
                            const double* sb, double* r, cudaStream_t st);
 cudaError_t launch_projection_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* p, double* y,
                                   cudaStream_t st);
-cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                     const double* nu_face, double* y, cudaStream_t st);
 cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
                            unsigned long long* vmax_bits, cudaStream_t st);
@@ -72,7 +82,7 @@ cudaError_t launch_penalty_tau(int n, const LevelGeom& g, const SplitTab& tab, c
 cudaError_t launch_penalty_apply(int n, const LevelGeom& g, const SplitTab& tab, const double* tdiv,
                                  const double* tcon, const double* x, double* y, cudaStream_t st);
 // y += wall-data terms (nothing for NULL or zero wall velocity)
-cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                 const double* tcon, double* y, cudaStream_t st);
 
 // ---- operators on trilinear cells (mapped.cu); n = degree + 1 (2..6)

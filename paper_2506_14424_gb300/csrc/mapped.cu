@@ -30,7 +30,9 @@ using namespace sweeps;
 
 __device__ __forceinline__ void load_cell_vertices(const LevelGeom& g, const double* __restrict__ verts, int e,
                                                    double (*X)[3]) {
-  const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
   for (int t = threadIdx.x; t < 24; t += blockDim.x) {
     const int v = t / 3, c = t % 3;
     const int a = v & 1, b = (v >> 1) & 1, cc = (v >> 2) & 1;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
     int t1, t2;
     face_dirs(d, &t1, &t2);
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] == 1) continue;  // homogeneous Neumann: no term
+    if (nb < 0 && face_bc(g, e, f) == 1) continue;  // homogeneous Neumann: no term
     const int fo = 2 * d + (1 - s);
     for (int c = 0; c < NC; ++c) face_eval<N>(U[c], d, s, T, FM[c], SC);
     if (nb >= 0) {
@@ -318,7 +320,9 @@ __global__ void mapped_lambda_kernel(LevelGeom g, SplitTab tab, int n, const dou
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ncells) return;
   double X[8][3];
-  const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
   for (int v = 0; v < 8; ++v) {
     const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
     const size_t idx = ((size_t)(k + c) * (g.ny + 1) + (j + b)) * (g.nx + 1) + (i + a);
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_diagonal_kernel(LevelGeo
     int t1, t2;
     face_dirs(d, &t1, &t2);
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] == 1) continue;
+    if (nb < 0 && face_bc(g, e, f) == 1) continue;
     const int fo = 2 * d + (1 - s);
     const double orient = (2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0);
     const double lam_p = nb >= 0 ? lam[nb] : lam_e;

@@ -82,7 +82,7 @@ __global__ void diagonal_kernel(LevelGeom g, Tab tab, const double* __restrict__
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     const int nb = cell_neighbor(g, e, f);
-    const bool skip = (nb < 0 && g.bc[f] == 1)      // homogeneous Neumann: no face term
+    const bool skip = (nb < 0 && face_bc(g, e, f) == 1)      // homogeneous Neumann: no face term
                       || (nb >= 0 && !interior_faces);  // continuous level: jumps vanish
     const double sigma = s ? 1.0 : -1.0;
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
@@ -224,8 +224,10 @@ __global__ void h_prolong_kernel(int n, int ncomp, LevelGeom fine, LevelGeom coa
   const int ef = (int)(idx / (ncomp * n3));
   const int rem = (int)(idx % (ncomp * n3));
   const int comp = rem / n3, r = rem % n3;
-  const int fx = ef % fine.nx, fy = (ef / fine.nx) % fine.ny, fz = ef / (fine.nx * fine.ny);
-  const int ec = ((fz / 2) * coarse.ny + fy / 2) * coarse.nx + fx / 2;
+  int fi[3];
+  cell_ijk(fine, ef, fi);
+  const int fx = fi[0], fy = fi[1], fz = fi[2];
+  const int ec = grid_cell(coarse, fx / 2, fy / 2, fz / 2);
   const T* Ex = (fx & 1) ? E1 : E0;
   const T* Ey = (fy & 1) ? E1 : E0;
   const T* Ez = (fz & 1) ? E1 : E0;
@@ -257,12 +259,14 @@ __global__ void h_restrict_kernel(int n, int ncomp, LevelGeom fine, LevelGeom co
   const int ec = (int)(idx / (ncomp * n3));
   const int rem = (int)(idx % (ncomp * n3));
   const int comp = rem / n3, r = rem % n3;
-  const int cx = ec % coarse.nx, cy = (ec / coarse.nx) % coarse.ny, cz = ec / (coarse.nx * coarse.ny);
+  int ci[3];
+  cell_ijk(coarse, ec, ci);
+  const int cx = ci[0], cy = ci[1], cz = ci[2];
   const int o[3] = {r % n, (r / n) % n, r / (n * n)};
   T acc = T(0);
   for (int ch = 0; ch < 8; ++ch) {
     const int bx = ch & 1, by = (ch >> 1) & 1, bz = ch >> 2;
-    const int ef = ((2 * cz + bz) * fine.ny + 2 * cy + by) * fine.nx + 2 * cx + bx;
+    const int ef = grid_cell(fine, 2 * cx + bx, 2 * cy + by, 2 * cz + bz);
     const T* Ex = bx ? E1 : E0;
     const T* Ey = by ? E1 : E0;
     const T* Ez = bz ? E1 : E0;
@@ -328,9 +332,10 @@ __global__ void h_interp_down_kernel(int n, int ncomp, LevelGeom fine, LevelGeom
   const int ec = (int)(idx / (ncomp * n3));
   const int rem = (int)(idx % (ncomp * n3));
   const int comp = rem / n3, r = rem % n3;
-  const int cx = ec % coarse.nx, cy = (ec / coarse.nx) % coarse.ny, cz = ec / (coarse.nx * coarse.ny);
+  int ci[3];
+  cell_ijk(coarse, ec, ci);
   const int o[3] = {r % n, (r / n) % n, r / (n * n)};
-  const int ef = ((2 * cz + cm.c[o[2]]) * fine.ny + 2 * cy + cm.c[o[1]]) * fine.nx + 2 * cx + cm.c[o[0]];
+  const int ef = grid_cell(fine, 2 * ci[0] + cm.c[o[0]], 2 * ci[1] + cm.c[o[1]], 2 * ci[2] + cm.c[o[2]]);
   const double* src = in + ((size_t)ef * ncomp + comp) * n3;
   double acc = 0.0;
   for (int k = 0; k < n; ++k)

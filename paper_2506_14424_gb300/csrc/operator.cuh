@@ -199,7 +199,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
     T* gT1 = F + (s * 8 + 5) * FS;
     const T* gT2p = F + (s * 8 + 6) * FS;
     const T* gT1p = F + (s * 8 + 7) * FS;
-    if (nb < 0 && g.bc[f] == 1) {  // homogeneous Neumann: no face term
+    if (nb < 0 && face_bc(g, e, f) == 1) {  // homogeneous Neumann: no face term
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const int j = (c * NC + k) * N2 + p;

@@ -32,10 +32,6 @@ namespace {
 
 using namespace sweeps;
 
-struct PenWall {
-  double g[6][3];
-};
-
 template <int N>
 __global__ void __launch_bounds__(kSplitThreads) pen_tau_kernel(LevelGeom g, SplitTab tab,
                                                                 const double* __restrict__ u, double zeta_div,
@@ -118,7 +114,7 @@ __global__ void __launch_bounds__(kSplitThreads) pen_apply_kernel(LevelGeom g, S
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] != 0) continue;  // Neumann wall
+    if (nb < 0 && face_bc(g, e, f) != 0) continue;  // Neumann wall
     int t1, t2;
     face_dirs(d, &t1, &t2);
     const double tau = nb >= 0 ? 0.5 * (tc + tcon[nb]) : tc;
@@ -145,7 +141,7 @@ __global__ void __launch_bounds__(kSplitThreads) pen_apply_kernel(LevelGeom g, S
 }
 
 template <int N>
-__global__ void __launch_bounds__(kSplitThreads) pen_wall_kernel(LevelGeom g, SplitTab tab, PenWall wall,
+__global__ void __launch_bounds__(kSplitThreads) pen_wall_kernel(LevelGeom g, SplitTab tab, Wall wall,
                                                                  const double* __restrict__ tcon,
                                                                  double* __restrict__ y) {
   constexpr int N3 = N * N * N, N2 = N * N;
@@ -155,14 +151,13 @@ __global__ void __launch_bounds__(kSplitThreads) pen_wall_kernel(LevelGeom g, Sp
   load_tab(tab, T);
   __syncthreads();
   for (int f = 0; f < 6; ++f) {
-    if (cell_neighbor(g, e, f) >= 0 || g.bc[f] != 0) continue;
+    if (cell_neighbor(g, e, f) >= 0 || face_bc(g, e, f) != 0) continue;
     const int d = f >> 1, s = f & 1;
-    const double gd = wall.g[f][d];
-    if (gd == 0.0) continue;
     int t1, t2;
     face_dirs(d, &t1, &t2);
-    const double c = tcon[e] * gd * g.h[t1] * g.h[t2];
-    for (int q = threadIdx.x; q < N2; q += blockDim.x) FA[q] = c * T.gw[q % N] * T.gw[q / N];
+    const double c = tcon[e] * g.h[t1] * g.h[t2];
+    for (int q = threadIdx.x; q < N2; q += blockDim.x)
+      FA[q] = c * wall_val(wall, g, e, f, q, d, N2) * T.gw[q % N] * T.gw[q / N];
     __syncthreads();
     sweep<N, N, 1, 0, N, true>(T.S, N, FA, FT);
     __syncthreads();
@@ -200,15 +195,16 @@ cudaError_t launch_penalty_apply(int n, const LevelGeom& g, const SplitTab& tab,
   return cudaGetLastError();
 }
 
-cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                 const double* tcon, double* y, cudaStream_t st) {
-  if (!wall_g || g.ncells == 0) return cudaSuccess;
-  PenWall w;
-  bool any = false;
+  if ((!wall_g.side && !wall_g.pts) || g.ncells == 0) return cudaSuccess;
+  Wall w{};
+  bool any = wall_g.pts != nullptr;
   for (int i = 0; i < 18; ++i) {
-    w.g[i / 3][i % 3] = wall_g[i];
-    any |= wall_g[i] != 0.0;
+    w.g[i / 3][i % 3] = wall_g.side ? wall_g.side[i] : 0.0;
+    any |= w.g[i / 3][i % 3] != 0.0;
   }
+  w.pts = wall_g.pts;
   if (!any) return cudaSuccess;
   SIPG_PEN_DISPATCH(n, (pen_wall_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, tcon, y)));
   return cudaGetLastError();

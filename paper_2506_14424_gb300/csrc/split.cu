@@ -29,10 +29,6 @@ namespace {
 
 using namespace sweeps;
 
-struct Wall {
-  double g[6][3];
-};
-
 // --------------------------------------------------------------- convective
 template <int N>
 __global__ void __launch_bounds__(kSplitThreads) conv_kernel(LevelGeom g, SplitTab tab, Wall wall,
@@ -89,7 +85,7 @@ __global__ void __launch_bounds__(kSplitThreads) conv_kernel(LevelGeom g, SplitT
       double um[3], up[3];
       for (int c = 0; c < 3; ++c) {
         um[c] = UM[c][p];
-        up[c] = nb >= 0 ? UP[c][p] : (g.bc[f] == 0 ? -um[c] + 2.0 * wall.g[f][c] : um[c]);
+        up[c] = nb >= 0 ? UP[c][p] : (face_bc(g, e, f) == 0 ? -um[c] + 2.0 * wall_val(wall, g, e, f, p, c, N2) : um[c]);
       }
       const double wn = 0.5 * (um[d] + up[d]) * nd;
       const double sg = wn > 0.0 ? 1.0 : (wn < 0.0 ? -1.0 : 0.0);
@@ -152,7 +148,7 @@ __global__ void __launch_bounds__(kSplitThreads) conv_lin_kernel(LevelGeom g, Sp
     face_dirs(d, &t1, &t2);
     const double nd = 2.0 * s - 1.0;
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] != 0) continue;  // Neumann: u^+ = u^-, w^+ = w^-: no flux
+    if (nb < 0 && face_bc(g, e, f) != 0) continue;  // Neumann: u^+ = u^-, w^+ = w^-: no flux
     // face nodes: own u, own w, neighbour u, neighbour w (in Q as scratch)
     for (int i = threadIdx.x; i < 3 * N2; i += blockDim.x) {
       const int c = i / N2, p = i % N2;
@@ -191,10 +187,10 @@ __global__ void __launch_bounds__(kSplitThreads) conv_lin_kernel(LevelGeom g, Sp
       double um[3], up[3], wm, wp;
       for (int c = 0; c < 3; ++c) {
         um[c] = UM[c][p];
-        up[c] = nb >= 0 ? UP[c][p] : -um[c] + 2.0 * wall_u.g[f][c];
+        up[c] = nb >= 0 ? UP[c][p] : -um[c] + 2.0 * wall_val(wall_u, g, e, f, p, c, N2);
       }
       wm = WM[d][p];
-      wp = nb >= 0 ? WP[d][p] : -wm + 2.0 * wall_w.g[f][d];
+      wp = nb >= 0 ? WP[d][p] : -wm + 2.0 * wall_val(wall_w, g, e, f, p, d, N2);
       const double wn = 0.5 * (wm + wp) * nd;
       const double sg = wn > 0.0 ? 1.0 : (wn < 0.0 ? -1.0 : 0.0);
       const double wt = T.gw[p % N] * T.gw[p / N] * area;
@@ -243,25 +239,19 @@ __global__ void __launch_bounds__(kSplitThreads) ppe_bnd_kernel(LevelGeom g, Spl
   __shared__ STabSm T;
   __shared__ double U[3][N3], Q[3][N3], G[3][3][N3], T0[N3], T1[N3], W3[3][N3];
   __shared__ double TR[12][N2], ACC[N2];
-  // decode the wall face
-  int bf = blockIdx.x, f = 0;
-  const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
-  while (bf >= side[f >> 1]) {
-    bf -= side[f >> 1];
-    ++f;
+  // the wall face: cell e, face f
+  int e, f;
+  bface_cell(g, blockIdx.x, &e, &f);
+  if (face_bc(g, e, f) != 0) {  // velocity Neumann (pressure Dirichlet): no datum
+    for (int p = threadIdx.x; p < N2; p += blockDim.x) sb[(size_t)blockIdx.x * N2 + p] = 0.0;
+    return;
   }
   const int d = f >> 1, s = f & 1;
   int t1, t2;
   face_dirs(d, &t1, &t2);
-  const int dims[3] = {g.nx, g.ny, g.nz};
-  int ijk[3];
-  ijk[d] = s ? dims[d] - 1 : 0;
-  ijk[t1] = bf % dims[t1];
-  ijk[t2] = bf / dims[t1];
-  const int e = (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
   const double nd = 2.0 * s - 1.0;
   load_tab(tab, T);
-  for (int p = threadIdx.x; p < N2; p += blockDim.x) ACC[p] = pb.a.gn_coef * wall.g[f][d] * nd;
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) ACC[p] = pb.a.gn_coef * wall_val(wall, g, e, f, p, d, N2) * nd;
   __syncthreads();
   // convective terms: n.(u.grad)u of each history, weight beta_i - betabar_i
   for (int h = 0; h < pb.a.n_hist; ++h) {
@@ -390,7 +380,7 @@ __global__ void __launch_bounds__(kSplitThreads) ppe_rhs_kernel(LevelGeom g, Spl
     face_dirs(d, &t1, &t2);
     const double nd = 2.0 * s - 1.0;
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] != 0) continue;  // velocity Neumann: not used on the box
+    if (nb < 0 && face_bc(g, e, f) != 0) continue;  // velocity Neumann: u^+ = u^- handled below
     const double area = g.h[t1] * g.h[t2];
     if (nb >= 0) {
       for (int p = threadIdx.x; p < N2; p += blockDim.x) {
@@ -463,7 +453,7 @@ __global__ void __launch_bounds__(kSplitThreads) proj_rhs_kernel(LevelGeom g, Sp
     face_dirs(d, &t1, &t2);
     const double nd = 2.0 * s - 1.0;
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && g.bc[f] != 0) continue;
+    if (nb < 0 && face_bc(g, e, f) != 0) continue;  // pressure Dirichlet, datum 0: {{p}} = 0
     for (int q = threadIdx.x; q < NP2; q += blockDim.x) {
       FA[q] = P[fnode(d, s, q % NP, q / NP, NP)];
       FB[q] = nb >= 0 ? p[(size_t)nb * NP3 + fnode(d, 1 - s, q % NP, q / NP, NP)] : FA[q];
@@ -505,9 +495,11 @@ __global__ void __launch_bounds__(kSplitThreads) visc_dir_kernel(LevelGeom g, Sp
   __syncthreads();
   const double lam = penalty_lambda(g, e);
   for (int f = 0; f < 6; ++f) {
-    if (cell_neighbor(g, e, f) >= 0 || g.bc[f] != 0) continue;
-    const double* gv = wall.g[f];
-    if (gv[0] == 0.0 && gv[1] == 0.0 && gv[2] == 0.0) continue;
+    if (cell_neighbor(g, e, f) >= 0 || face_bc(g, e, f) != 0) continue;
+    if (!wall.pts) {
+      const double* gc = wall.g[boundary_id(g, e, f)];
+      if (gc[0] == 0.0 && gc[1] == 0.0 && gc[2] == 0.0) continue;
+    }
     const int d = f >> 1, s = f & 1;
     int t1, t2;
     face_dirs(d, &t1, &t2);
@@ -519,6 +511,8 @@ __global__ void __launch_bounds__(kSplitThreads) visc_dir_kernel(LevelGeom g, Sp
         const double w = T.gw[p % N] * T.gw[p / N] * area;
         const double nu = nu_face[((size_t)e * 6 + f) * N2 + p];
         const double tau = g.cip * (double)(N * N) * lam * nu;
+        double gv[3];
+        for (int j = 0; j < 3; ++j) gv[j] = wall_val(wall, g, e, f, p, j, N2);
         CA[p] = -nu * w * (gv[c] * nd + nc * gv[d]) * g.ih[d];
         CB[p] = -nu * w * nc * gv[t1] * g.ih[t1];
         CC[p] = -nu * w * nc * gv[t2] * g.ih[t2];
@@ -586,6 +580,13 @@ __global__ void __launch_bounds__(kSplitThreads) cfl_kernel(LevelGeom g, SplitTa
 
 }  // namespace
 
+Wall make_wall(const WallArg& a) {
+  Wall w{};
+  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = a.side ? a.side[i] : 0.0;
+  w.pts = a.pts;
+  return w;
+}
+
 #define SIPG_SPLIT_DISPATCH(NN, CALL) \
   switch (NN) {                       \
     case 3: { constexpr int N = 3; CALL; break; } \
@@ -595,35 +596,29 @@ __global__ void __launch_bounds__(kSplitThreads) cfl_kernel(LevelGeom g, SplitTa
     default: return cudaErrorInvalidValue;        \
   }
 
-cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_convective(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                               const double* u, double* y, cudaStream_t st) {
-  Wall w;
-  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  const Wall w = make_wall(wall_g);
   if (g.ncells == 0) return cudaSuccess;
   SIPG_SPLIT_DISPATCH(n, (conv_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, u, y)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_w,
-                                  const double* wall_u, const double* w, const double* u, double* y,
+cudaError_t launch_convective_lin(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_w,
+                                  const WallArg& wall_u, const double* w, const double* u, double* y,
                                   cudaStream_t st) {
-  Wall ww, wu;
-  for (int i = 0; i < 18; ++i) {
-    ww.g[i / 3][i % 3] = wall_w ? wall_w[i] : 0.0;
-    wu.g[i / 3][i % 3] = wall_u ? wall_u[i] : 0.0;
-  }
+  const Wall ww = make_wall(wall_w), wu = make_wall(wall_u);
   if (g.ncells == 0) return cudaSuccess;
   SIPG_SPLIT_DISPATCH(n, (conv_lin_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, ww, wu, w, u, y)));
   return cudaGetLastError();
 }
 
-int n_wall_faces(const LevelGeom& g) { return 2 * (g.ny * g.nz + g.nx * g.nz + g.nx * g.ny); }
+int n_wall_faces(const LevelGeom& g) { return g.nbr ? g.nbf : 2 * (g.ny * g.nz + g.nx * g.nz + g.nx * g.ny); }
 
-cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                 const PpeBndArgs& a, const RheologyDev& rh, const double* u0, const double* u1,
                                 double* sb, cudaStream_t st) {
-  Wall w;
-  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  const Wall w = make_wall(wall_g);
   PpeBnd pb{};
   pb.a = a;
   pb.rh = rh;
@@ -647,10 +642,9 @@ cudaError_t launch_projection_rhs(int n, const LevelGeom& g, const SplitTab& tab
   return cudaGetLastError();
 }
 
-cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* wall_g,
+cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const WallArg& wall_g,
                                     const double* nu_face, double* y, cudaStream_t st) {
-  Wall w;
-  for (int i = 0; i < 18; ++i) w.g[i / 3][i % 3] = wall_g ? wall_g[i] : 0.0;
+  const Wall w = make_wall(wall_g);
   if (g.ncells == 0) return cudaSuccess;
   SIPG_SPLIT_DISPATCH(n, (visc_dir_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, w, nu_face, y)));
   return cudaGetLastError();

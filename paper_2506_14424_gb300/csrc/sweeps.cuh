@@ -64,9 +64,9 @@ __device__ __forceinline__ int fnode(int d, int s, int a, int b, int n) {
   return (i[2] * n + i[1]) * n + i[0];
 }
 
-// index of the wall face of box side f holding cell e (sides in order, faces
-// lexicographic over the tangential cell indices t1 < t2)
+// boundary-face number of the boundary face (e, f) (see LevelGeom)
 __device__ __forceinline__ int bface_index(const LevelGeom& g, int e, int f) {
+  if (g.nbr) return (-1 - g.nbr[e * 6 + f]) >> 3;
   const int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
   const int dims[3] = {g.nx, g.ny, g.nz};
   const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
@@ -76,6 +76,45 @@ __device__ __forceinline__ int bface_index(const LevelGeom& g, int e, int f) {
   int t1, t2;
   face_dirs(d, &t1, &t2);
   return off + ijk[t2] * dims[t1] + ijk[t1];
+}
+
+// cell and face of boundary face b (inverse of bface_index)
+__device__ __forceinline__ void bface_cell(const LevelGeom& g, int b, int* e, int* f) {
+  if (g.bface) {
+    const int v = g.bface[b];
+    *e = v / 6;
+    *f = v % 6;
+    return;
+  }
+  int bf = b, ff = 0;
+  const int side[3] = {g.ny * g.nz, g.nx * g.nz, g.nx * g.ny};
+  while (bf >= side[ff >> 1]) {
+    bf -= side[ff >> 1];
+    ++ff;
+  }
+  const int d = ff >> 1, s = ff & 1;
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  int ijk[3];
+  ijk[d] = s ? dims[d] - 1 : 0;
+  ijk[t1] = bf % dims[t1];
+  ijk[t2] = bf / dims[t1];
+  *e = (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+  *f = ff;
+}
+
+// Wall velocity on the Dirichlet boundary faces: a constant vector per boundary
+// id (g[6] for faces against removed cells), or, with pts != nullptr, values at
+// the n^2 Gauss points of every boundary face, [nbf][n^2][3] (face point
+// a + n b over the face's tangential directions t1 < t2).
+struct Wall {
+  double g[7][3];
+  const double* pts;
+};
+__device__ __forceinline__ double wall_val(const Wall& w, const LevelGeom& g, int e, int f, int p, int c, int n2) {
+  if (w.pts) return w.pts[((size_t)bface_index(g, e, f) * n2 + p) * 3 + c];
+  return w.g[boundary_id(g, e, f)][c];
 }
 
 // load the split tables into shared memory

@@ -49,8 +49,9 @@ __global__ void viscosity_position_kernel(LevelGeom g, Tab tab, RheologyDev rh, 
   constexpr int N2 = N * N, N3 = N2 * N;
   const int e = blockIdx.x;
   if (e >= g.ncells) return;
-  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
-  const double o[3] = {ex * g.h[0], ey * g.h[1], ez * g.h[2]};
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  const double o[3] = {g.x0[0] + ijk[0] * g.h[0], g.x0[1] + ijk[1] * g.h[1], g.x0[2] + ijk[2] * g.h[2]};
   __shared__ double part[N3];
   for (int q = threadIdx.x; q < N3; q += blockDim.x) {
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
@@ -181,10 +182,11 @@ __global__ void node_points_kernel(LevelGeom g, Tab tab, double* xyz) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= (int64_t)g.ncells * N3) return;
   const int e = (int)(i / N3), r = (int)(i % N3);
-  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
-  xyz[3 * i + 0] = (ex + tab.gll[r % N]) * g.h[0];
-  xyz[3 * i + 1] = (ey + tab.gll[(r / N) % N]) * g.h[1];
-  xyz[3 * i + 2] = (ez + tab.gll[r / (N * N)]) * g.h[2];
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  xyz[3 * i + 0] = g.x0[0] + (ijk[0] + tab.gll[r % N]) * g.h[0];
+  xyz[3 * i + 1] = g.x0[1] + (ijk[1] + tab.gll[(r / N) % N]) * g.h[1];
+  xyz[3 * i + 2] = g.x0[2] + (ijk[2] + tab.gll[r / (N * N)]) * g.h[2];
 }
 
 cudaError_t launch_node_points(int n, const LevelGeom& g, const Tab& tab, double* xyz, cudaStream_t st) {
@@ -219,10 +221,11 @@ __global__ void cell_nu_transfer_kernel(LevelGeom fine, LevelGeom coarse, int ki
   if (kind == 1) {
     v = fine_cell[(size_t)ec * nf3];
   } else {
-    const int cx = ec % coarse.nx, cy = (ec / coarse.nx) % coarse.ny, cz = ec / (coarse.nx * coarse.ny);
+    int ci[3];
+    cell_ijk(coarse, ec, ci);
     v = 0.0;
     for (int ch = 0; ch < 8; ++ch) {
-      const int ef = ((2 * cz + (ch >> 2)) * fine.ny + 2 * cy + ((ch >> 1) & 1)) * fine.nx + 2 * cx + (ch & 1);
+      const int ef = grid_cell(fine, 2 * ci[0] + (ch & 1), 2 * ci[1] + ((ch >> 1) & 1), 2 * ci[2] + (ch >> 2));
       v += fine_cell[(size_t)ef * nf3];
     }
     v *= 0.125;

@@ -1,0 +1,177 @@
+"""GPU parity on grids with removed cells and periodic directions (the
+backward-facing-step channel: inflow at -x, outflow at +x, walls at +-y and
+around the removed block, z periodic) against the oracle.
+
+* node positions (the grid's origin), the viscosity at the points (position
+  law and Carreau-Yasuda of a velocity), the viscous operator in FP64,
+  float-float and FP32 and the Poisson operator (pressure Dirichlet at the
+  outflow) on the channel, degrees 2..4, several CTAs with a ragged tail;
+* the multigrid hierarchy: level sizes follow the masked coarsening, the
+  transfers and the inverse diagonals equal the oracle's on every level;
+* MG-CG solves of the viscous and the (non-singular) pressure problem reach the
+  oracle's discrete solution;
+* a box periodic in two directions (no removed cell) with the constants in
+  the Poisson kernel.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import multigrid as omg  # noqa: E402
+from oracle.mesh import BoxMesh  # noqa: E402
+from oracle.sipg import SIPG  # noqa: E402
+from paper_2506_14424_gb300 import Context, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+TOL32 = 2e-5
+VEL, PRE = "DNDDDD", "NDNNNN"
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+def _channel(m):
+    return inputs.bfs_channel(m, inlet_length=1.0, outlet_length=3.0, depth=1.0)
+
+
+def _ctx(c, k, **kw):
+    return Context(*c["dims"], k, extent=c["extent"], origin=c["lo"], active=c["active"], periodic=c["periodic"],
+                   bc_velocity=VEL, bc_pressure=PRE, bc_removed="DN", **kw)
+
+
+def _mesh(c, op):
+    bc = tuple(VEL) + ('D',) if op == "viscous" else tuple(PRE) + ('N',)
+    return BoxMesh(*c["dims"], extent=c["extent"], lo=c["lo"], active=c["active"], periodic=c["periodic"], bc=bc)
+
+
+def _levels(ctx, op, mesh):
+    out = []
+    for level in range(ctx.num_levels(op)):
+        dims, k, _ = ctx.level_info(op, level)
+        if out and tuple(dims) != out[-1][0].n_cells_dir:
+            m = out[-1][0].coarsen()
+            assert m.n_cells_dir == tuple(dims)
+        else:
+            m = out[-1][0] if out else mesh
+        out.append((m, k))
+    return out
+
+
+def _velocity(S):
+    modes = inputs.fourier_modes(1)
+    return S.interpolate(lambda p: inputs.fourier_field(p, modes))
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_channel_viscous_apply(k):
+    c = _channel(2)
+    mesh = _mesh(c, "viscous")
+    S = SIPG(mesh, k, 3)
+    ctx = _ctx(c, k)
+    assert ctx.n_dofs("viscous") == S.n_dofs
+    pts = ctx.node_points("viscous", 0)
+    assert np.abs(pts - np.stack([S.node_points(e) for e in range(mesh.n_cells)])).max() <= 1e-14
+    x = inputs.uniform_vector(S.n_dofs, seed=11)
+    for rheo, u in (({'law': 'analytic'}, None), (inputs.carreau_blood_like(), _velocity(S))):
+        ctx.set_viscosity(rheo, None if u is None else _dev(u))
+        nc, nf = ctx.get_viscosity(0)
+        rc, rf = S.viscosity_at_points(rheo, u)
+        assert _rel(nc.cpu().numpy(), rc) <= 1e-13
+        assert _rel(nf.cpu().numpy(), rf) <= 1e-13
+        ref = S.apply(x, rc, rf)
+        for arith in ("f64", "f64ff"):
+            assert _rel(ctx.apply("viscous", _dev(x), arith=arith).cpu().numpy(), ref) <= TOL64, arith
+        ref_m = S.apply(x, rc, rf, mass=25.0)
+        assert _rel(ctx.apply("viscous", _dev(x), mass=25.0, arith="f64ff").cpu().numpy(), ref_m) <= TOL64
+        y32 = ctx.apply("viscous", _dev(x, torch.float32)).double().cpu().numpy()
+        assert _rel(y32, ref) <= TOL32
+    ctx.close()
+
+
+@pytest.mark.parametrize("kp", [1, 2, 3])
+def test_channel_poisson_apply(kp):
+    c = _channel(2)
+    P = SIPG(_mesh(c, "poisson"), kp, 1)
+    ctx = _ctx(c, kp + 1)
+    x = inputs.uniform_vector(P.n_dofs, seed=12)
+    for arith in ("f64", "f64ff"):
+        assert _rel(ctx.apply("poisson", _dev(x), arith=arith).cpu().numpy(), P.apply(x)) <= TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("op", ["viscous", "poisson"])
+def test_channel_hierarchy_transfers_and_diagonals(op):
+    c = _channel(4)   # 16 x 8 x 4 grid, 448 cells; h-levels down to 8 x 4 x 2
+    k = 2 if op == "viscous" else 3
+    ctx = _ctx(c, k, coarse_max_dofs=500)
+    rheo = {'law': 'analytic'}
+    ctx.set_viscosity(rheo)
+    levels = _levels(ctx, op, _mesh(c, op))
+    assert [m.n_cells for m, _ in levels][-1] == _mesh(_channel(2), op).n_cells
+    nc = 3 if op == "viscous" else 1
+    nus = omg.level_viscosity(levels, rheo) if op == "viscous" else None
+    for level, (m, kl) in enumerate(levels):
+        S = SIPG(m, kl, nc)
+        A = S.assemble(*nus[level]) if op == "viscous" else S.assemble()
+        dinv = ctx.inverse_diagonal(op, level).cpu().numpy()
+        assert _rel(1.0 / dinv, A.diagonal()) <= TOL64, level
+        if level == 0:
+            continue
+        F, kf = levels[level - 1]
+        P = (omg.prolongation_p(m, kf, kl, nc) if F.n_cells == m.n_cells
+             else omg.prolongation_h(F, m, kl, nc))
+        xc = inputs.uniform_vector(P.shape[1], seed=30 + level)
+        xf = inputs.uniform_vector(P.shape[0], seed=40 + level)
+        assert _rel(ctx.transfer(op, level - 1, +1, _dev(xc)).cpu().numpy(), P @ xc) <= 1e-14
+        assert _rel(ctx.transfer(op, level - 1, -1, _dev(xf)).cpu().numpy(), P.T @ xf) <= 1e-14
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_channel_mg_solves(prec):
+    c = _channel(2)
+    k = 3
+    ctx = _ctx(c, k, mg_precision=prec, coarse_max_dofs=2000)
+    S = SIPG(_mesh(c, "viscous"), k, 3)
+    rheo = inputs.carreau_blood_like()
+    u = _velocity(S)
+    ctx.set_viscosity(rheo, _dev(u))
+    A = S.assemble(*S.viscosity_at_points(rheo, u), mass=40.0)
+    u_star = inputs.uniform_vector(S.n_dofs, seed=80)
+    b = A @ u_star
+    x, st = ctx.solve("viscous", _dev(b), rtol=1e-10, precond="mg", maxit=300, mass=40.0)
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-10 * (1 + 1e-6) * np.linalg.norm(b)
+    assert st["iterations"] < 60, st
+    P = SIPG(_mesh(c, "poisson"), k - 1, 1)
+    Ap = P.assemble()
+    p_star = inputs.uniform_vector(P.n_dofs, seed=81)
+    bp = Ap @ p_star
+    xp, st = ctx.solve("poisson", _dev(bp), rtol=1e-10, precond="mg", maxit=300)
+    assert _rel(xp.cpu().numpy(), p_star) <= 1e-7
+    assert st["iterations"] < 60, st
+    ctx.close()
+
+
+def test_periodic_box():
+    """x and z periodic, walls at +-y (velocity Dirichlet, pressure Neumann)."""
+    dims, k = (4, 2, 3), 3
+    ctx = Context(*dims, k, periodic=(True, False, True))
+    mesh = BoxMesh(*dims, periodic=(True, False, True), bc=('N',) * 6)
+    P = SIPG(mesh, k - 1, 1)
+    x = inputs.uniform_vector(P.n_dofs, seed=5)
+    assert _rel(ctx.apply("poisson", _dev(x), arith="f64ff").cpu().numpy(), P.apply(x)) <= TOL64
+    ones = torch.ones(P.n_dofs, dtype=torch.float64, device="cuda")
+    assert ctx.apply("poisson", ones).abs().max().item() <= 1e-12
+    S = SIPG(mesh.with_bc(('D',) * 6), k, 3)
+    ctx.set_viscosity({'law': 'analytic'})
+    xv = inputs.uniform_vector(S.n_dofs, seed=6)
+    ref = S.apply(xv, *S.viscosity_at_points({'law': 'analytic'}))
+    assert _rel(ctx.apply("viscous", _dev(xv)).cpu().numpy(), ref) <= TOL64
+    ctx.close()
