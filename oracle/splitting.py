@@ -254,10 +254,13 @@ def viscous_boundary_terms(S, e, f, u_dd, rheology):
     return -nu_f * (curl_omega @ nvec) + 2.0 * np.einsum('l,plk,pk->p', nvec, eps, grad_nu)
 
 
-def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology):
+def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology, g_hist=None):
     """h_p - (gamma0/dt) g_uhat.n at the face points of the Dirichlet face (e, f).
 
-    hist: [u^n, u^{n-1}, ...] (velocity DoF vectors), body: b_h DoF vector or None."""
+    hist: [u^n, u^{n-1}, ...] (velocity DoF vectors), body: b_h DoF vector or None,
+    g_faces: the wall data at t_{n+1}; g_hist: the wall data at t_n, t_{n-1}, ... (None:
+    steady data, g_faces at every time). d_t g(t_{n+1}) is the BDF-m approximation
+    (gamma0 g(t_{n+1}) - sum_i alpha_i g(t_{n-i})) / dt (Sec. 3.2: g approximated by BDF-m)."""
     gamma0, alpha, beta = BDF[order]
     m_p = min(order - 1, 2)
     betabar = EXTRAP[m_p]
@@ -266,15 +269,17 @@ def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology):
     nb = np.zeros(P)
     if body is not None:
         nb = _values(S.face_phi[f], _cell(S, body, e)) @ nvec
-    g = wall_data(S, g_faces, e, f)
+    g_new = wall_data(S, g_faces, e, f) @ nvec
+    g_old = [wall_data(S, g_faces if g_hist is None else g_hist[i], e, f) @ nvec for i in range(order)]
+    dtg = (gamma0 * g_new - sum(alpha[i] * g_old[i] for i in range(order))) / dt
     conv_m = sum(beta[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(order))
     conv_mp = sum((betabar[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(m_p)), np.zeros(P))
     visc = np.zeros(P)
     if m_p > 0:
         u_dd = sum(betabar[i] * np.asarray(hist[i]) for i in range(m_p))
         visc = viscous_boundary_terms(S, e, f, u_dd, rheology)
-    h_p = nb - 0.0 - conv_mp + visc   # d_t g = 0 for steady data
-    g_uhat_n = dt / gamma0 * nb - dt / gamma0 * conv_m + sum(alpha[i] / gamma0 for i in range(order)) * (g @ nvec)
+    h_p = nb - dtg - conv_mp + visc
+    g_uhat_n = dt / gamma0 * nb - dt / gamma0 * conv_m + sum(alpha[i] / gamma0 * g_old[i] for i in range(order))
     return h_p - gamma0 / dt * g_uhat_n
 
 
@@ -292,7 +297,7 @@ def ppe_rhs(Su, Sp, uhat, coef, boundary):
             d, s, nvec = face_normal(f)
             Wf = Su.face_w2 * mesh.face_area(d)
             bt = mesh.boundary_type(e, f)
-            if bt == 'I':
+            if bt in ('I', 'N'):   # velocity Neumann (outflow): uhat^+ = uhat^-
                 um, _, up, _, _ = _exterior(Su, uhat, e, f, None)
                 out[e] -= coef * np.einsum('p,pi,p->i', Wf, Sp.face_phi[f], 0.5 * (um + up) @ nvec)
             elif bt == 'D':
@@ -446,8 +451,12 @@ def penalty_step(S, u, dt, g_faces, zeta_div=1.0, zeta_cont=1.0):
 
 
 def pressure_solve(Sp_op, rhs):
-    """Mean-free solution of the all-Neumann SIPG Laplacian with a mean-free right-hand side."""
+    """The SIPG Laplacian's solution; with no pressure-Dirichlet face (all-Neumann) the
+    mean-free solution for the mean-free right-hand side (Sec. 3.2)."""
     A = Sp_op.assemble().tocsc()
+    m = Sp_op.mesh
+    if any(m.boundary_type(e, f) == 'D' for e, f in m.boundary_faces()):
+        return spla.spsolve(A, rhs)
     N = A.shape[0]
     r = rhs - rhs.mean()
     c = float(A.diagonal().mean()) / N
@@ -460,8 +469,14 @@ class Splitting:
     """State and one-step driver of the projection scheme on a box."""
 
     def __init__(self, mesh, k, rheology, g_faces=None, body=None, viscosity_mode='linear', penalty_factor=1.0,
-                 convective='explicit'):
+                 convective='explicit', ramp=None, t0=0.0):
+        """g_faces: wall data per boundary id (constant vectors or callables of the points);
+        ramp: optional scalar function of time, the wall data at time t being ramp(t) g_faces
+        (the ramped inflow of the backward-facing-step benchmark)."""
         self.mesh, self.k = mesh, int(k)
+        self.ramp = ramp
+        self.t = float(t0)
+        self.times = []
         self.rheology = rheology
         self.g_faces = [np.zeros(3) if g_faces is None or f >= len(g_faces) else
                         (g_faces[f] if callable(g_faces[f]) else np.asarray(g_faces[f], float)) for f in range(7)]
@@ -478,8 +493,16 @@ class Splitting:
         self.p = None
         self.steps = 0
 
+    def walls(self, t):
+        """Wall data at time t (per boundary id)."""
+        if self.ramp is None:
+            return self.g_faces
+        r = float(self.ramp(t))
+        return [(lambda x, g=g: r * np.asarray(g(x))) if callable(g) else r * g for g in self.g_faces]
+
     def set_initial(self, u0, p0=None):
         self.hist = [np.array(u0, dtype=np.float64)]
+        self.times = [self.t]
         self.p = np.zeros(self.Sp_op.n_dofs) if p0 is None else np.array(p0, dtype=np.float64)
         self.steps = 0
 
@@ -492,7 +515,10 @@ class Splitting:
         rhs = sum(alpha[i] / dt * omass.apply_mass(Su, hist[i]) for i in range(order))
         if self.body is not None:
             rhs = rhs + omass.apply_mass(Su, self.body)
-        conv = [convective_vector(Su, hist[i], self.g_faces) for i in range(order)]
+        t_new = self.times[0] + dt
+        g_new = self.walls(t_new)
+        g_hist = [self.walls(self.times[i]) for i in range(order)]
+        conv = [convective_vector(Su, hist[i], g_hist[i]) for i in range(order)]
         rhs = rhs - sum(beta[i] * conv[i] for i in range(order))
         uhat = omass.apply_inverse_mass(Su, rhs, gamma0 / dt)
         # pressure step
@@ -500,8 +526,8 @@ class Splitting:
         for e in range(self.mesh.n_cells):
             for f in range(6):
                 if self.mesh.boundary_type(e, f) == 'D':
-                    bnd[(e, f)] = ppe_boundary_datum(Su, e, f, hist, order, dt, self.body, self.g_faces,
-                                                     self.rheology)
+                    bnd[(e, f)] = ppe_boundary_datum(Su, e, f, hist, order, dt, self.body, g_new,
+                                                     self.rheology, g_hist)
         rp = ppe_rhs(Su, Sp, uhat, gamma0 / dt, bnd)
         p = pressure_solve(self.Sp_op, rp)
         # projection step
@@ -516,23 +542,24 @@ class Splitting:
             # on the right (Eq. viscous_step_weak); wall data of both terms on the right
             if picard is not None:
                 raise ValueError("the linearly implicit convective step takes the linear-implicit viscosity")
-            b = b + viscous_dirichlet_rhs(Su, nf, self.g_faces) + sum(beta[i] * conv[i] for i in range(order))
-            b = b + convective_wall_rhs(Su, u_sharp, self.g_faces, self.g_faces)
-            K = Su.assemble(nc, nf, mass=m) + convective_blocks(Su, u_sharp, self.g_faces)
+            b = b + viscous_dirichlet_rhs(Su, nf, g_new) + sum(beta[i] * conv[i] for i in range(order))
+            b = b + convective_wall_rhs(Su, u_sharp, g_new, g_new)
+            K = Su.assemble(nc, nf, mass=m) + convective_blocks(Su, u_sharp, g_new)
             u_new = spla.spsolve(K.tocsc(), b)
             info = None
         elif picard is None:
-            b = b + viscous_dirichlet_rhs(Su, nf, self.g_faces)
+            b = b + viscous_dirichlet_rhs(Su, nf, g_new)
             u_new = spla.spsolve(Su.assemble(nc, nf, mass=m).tocsc(), b)
             info = None
         else:
-            if any(callable(g) or np.any(g) for g in self.g_faces):
+            if any(callable(g) or np.any(g) for g in g_new):
                 raise ValueError("the implicit-viscosity step is built for zero wall velocity")
             info = nonlinear.viscous_step_picard(Su, self.rheology, b, u_sharp, m, **picard)
             u_new = info['u']
         if penalty:  # Alg. 1: post-process with the divergence and continuity penalty step
-            u_new = penalty_step(Su, u_new, dt, self.g_faces)[0]
+            u_new = penalty_step(Su, u_new, dt, g_new)[0]
         self.hist = [u_new] + hist[:1]
+        self.times = [t_new] + self.times[:1]
         self.p = p
         self.steps += 1
         return {'uhat': uhat, 'p': p, 'uhathat': uhh, 'u': u_new, 'order': order, 'picard': info,

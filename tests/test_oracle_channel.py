@@ -133,3 +133,45 @@ def test_channel_multigrid_transfer():
     uc = SIPG(coarse, k, 1).interpolate(poly)
     uf = SIPG(mesh, k, 1).interpolate(poly)
     assert np.abs(P @ uc - uf).max() <= 1e-13
+
+
+def test_channel_hydrostatic_with_outflow():
+    """u0 = 0 under a uniform body force b = c e_x, no-slip walls and step, zero inflow,
+    outflow traction-free with p = 0: BDF1 and BDF2 steps keep u = 0 and give p = c (x - x_out)
+    (the PPE's outflow face term (q, uhat.n) with uhat = dt/gamma0 b, the pressure Dirichlet
+    condition and the non-singular pressure solve)."""
+    mesh = small_channel(2)
+    k = 2
+    S = SIPG(mesh, k, 3)
+    c = 0.8
+    body = S.interpolate(lambda x: np.stack([c + 0 * x[:, 0], 0 * x[:, 0], 0 * x[:, 0]], axis=1))
+    ref = osp.Splitting(mesh, k, {'law': 'constant', 'nu': 0.1}, body=body)
+    ref.set_initial(np.zeros(S.n_dofs))
+    Sp = SIPG(mesh.with_bc(PRE_BC), k - 1, 1)
+    x_out = mesh.lo[0] + mesh.extent[0]
+    p_exact = Sp.interpolate(lambda x: c * (x[:, 0] - x_out))
+    for _ in range(2):
+        r = ref.step(0.05)
+        assert np.abs(r['u']).max() <= 1e-12
+        assert np.abs(r['p'] - p_exact).max() <= 1e-12 * np.abs(p_exact).max()
+
+
+def test_ppe_datum_depends_on_the_newest_wall_data_only():
+    """h_p - (gamma0/dt) g_uhat.n with the BDF approximation of d_t g: the older wall data
+    cancel (-(gamma0/dt) n.g(t_{n+1}) is the only wall term)."""
+    mesh = small_channel(2)
+    S = SIPG(mesh, 2, 3)
+    rng = np.random.default_rng(3)
+    hist = [rng.uniform(-1, 1, S.n_dofs) for _ in range(2)]
+    g_new = [rng.uniform(-1, 1, 3) for _ in range(7)]
+    g_old = [[rng.uniform(-1, 1, 3) for _ in range(7)] for _ in range(2)]
+    e, f = [(e, f) for e, f in mesh.boundary_faces() if mesh.boundary_type(e, f) == 'D'][0]
+    rh = {'law': 'constant', 'nu': 0.3}
+    a = osp.ppe_boundary_datum(S, e, f, hist, 2, 0.1, None, g_new, rh, g_old)
+    b = osp.ppe_boundary_datum(S, e, f, hist, 2, 0.1, None, g_new, rh, None)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    zero = [np.zeros(3)] * 7
+    c0 = osp.ppe_boundary_datum(S, e, f, hist, 2, 0.1, None, zero, rh, None)
+    _, _, nvec = osp.face_normal(f)
+    gn = g_new[mesh.boundary_id(e, f)] @ nvec
+    assert np.abs(b - (c0 - 1.5 / 0.1 * gn)).max() <= 1e-12 * np.abs(b).max()
