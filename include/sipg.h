@@ -308,7 +308,13 @@ int sipg_picard_solve(sipg_ctx* ctx, const sipg_rheology* rh, const double* b, d
  *    implicit), or the Picard/Aitken loop of sipg_picard_solve (implicit; zero
  *    wall velocity only).
  * BDF1 for the first step after sipg_step_init, BDF2 afterwards (gamma0 = 3/2,
- * alpha = (2, -1/2), beta = (2, -1)). Laws: SIPG_LAW_CONSTANT or SIPG_LAW_CARREAU. */
+ * alpha = (2, -1/2), beta = (2, -1)). Laws: SIPG_LAW_CONSTANT or SIPG_LAW_CARREAU.
+ * Walls: every boundary id present is velocity Dirichlet with pressure Neumann
+ * (walls, inflow) or velocity Neumann with pressure Dirichlet (outflow, p = 0,
+ * traction free); periodic directions and removed cells (the channel behind a
+ * backward-facing step) are allowed. With time-dependent wall data d_t g is the
+ * BDF approximation of the step, which leaves g(t_{n+1}) alone in the pressure
+ * datum. */
 enum { SIPG_VISC_LINEAR_IMPLICIT = 0, SIPG_VISC_IMPLICIT = 1 };
 enum { SIPG_CONV_EXPLICIT = 0, SIPG_CONV_LINEAR_IMPLICIT = 1 };
 enum { SIPG_FIELD_U = 0, SIPG_FIELD_P = 1, SIPG_FIELD_UHAT = 2, SIPG_FIELD_UHATHAT = 3, SIPG_FIELD_PPE_RHS = 4,
@@ -330,6 +336,11 @@ typedef struct {
   int penalty;               /* 1: end the step with the divergence and continuity penalty
                                 step (sipg_penalty_step, factors 1) [0] */
   double penalty_rtol;       /* its CG tolerance [1e-10] */
+  const double* wall_points;      /* DEVICE or NULL: wall velocity g(t_{n+1}) at the Gauss points of
+                                     every boundary face, [nbf][n^2][3] (sipg_boundary_points gives
+                                     the positions); replaces wall_velocity [NULL] */
+  const double* wall_points_prev; /* DEVICE or NULL: g(t_n) likewise, for the convective term of
+                                     u^n (NULL: wall_points, steady data) [NULL] */
 } sipg_step_opts;
 
 typedef struct {
@@ -357,6 +368,14 @@ int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step_opts* so, 
  * U (u^n), U_PREV (u^{n-1}), P (p^n), UHAT, UHATHAT, PPE_RHS (the pressure
  * step's right-hand side before the mean is removed). */
 int sipg_step_field(sipg_ctx* ctx, int which, double* out);
+
+/* Boundary faces of the velocity mesh (fine level): *nbf their number; with
+ * cell_face_id (HOST, 3 ints per face) their cell, face (-x,+x,-y,+y,-z,+z) and
+ * boundary id (0..5 the grid's sides, 6 faces against removed cells), in the
+ * order of the wall_points arrays; with xyz (DEVICE, nbf * n^2 * 3 doubles) the
+ * positions of their n^2 Gauss points (point a + n b over the face's
+ * tangential directions t1 < t2). Either pointer may be NULL. (sync) */
+int sipg_boundary_faces(sipg_ctx* ctx, int* nbf, int* cell_face_id, double* xyz);
 
 /* dt = courant / k_u^1.5 / max over cells and Gauss points of |J^-1 u|
  * (Eq. CFL_timestep_selection); u: DEVICE velocity. Returns SIPG_ERR_INVALID

@@ -312,6 +312,25 @@ class Context:
                                                 ctypes.byref(res)))
         return out, {"iterations": its.value, "rel_residual": res.value}
 
+    def boundary_faces(self):
+        """(cell, face, boundary id) of every boundary face of the velocity mesh, (nbf, 3) ints,
+        in the order of the step's wall_points arrays."""
+        nbf = ctypes.c_int()
+        self._check(self._lib.sipg_boundary_faces(self._h, ctypes.byref(nbf), None, None))
+        out = np.zeros((nbf.value, 3), dtype=np.int32)
+        self._check(self._lib.sipg_boundary_faces(self._h, ctypes.byref(nbf),
+                                                  out.ctypes.data_as(ctypes.c_void_p), None))
+        return out
+
+    def boundary_points(self):
+        """Positions of the Gauss points of every boundary face, (nbf, n^2, 3) on the device."""
+        nbf = ctypes.c_int()
+        self._check(self._lib.sipg_boundary_faces(self._h, ctypes.byref(nbf), None, None))
+        n = self.k_u + 1
+        out = torch.empty((nbf.value, n * n, 3), dtype=torch.float64, device="cuda")
+        self._check(self._lib.sipg_boundary_faces(self._h, ctypes.byref(nbf), None, _ptr(out)))
+        return out
+
     def step_init(self, u0, p0=None):
         _need_cuda(u0, torch.float64)
         self._check(self._lib.sipg_step_init(self._h, _ptr(u0), _ptr(p0)))
@@ -336,7 +355,7 @@ class Context:
 
     def step(self, rheology, dt, wall=None, body=None, viscosity_mode="linear", ppe_rtol=1e-8, visc_rtol=1e-8,
              maxit=1000, picard=None, convective_mode="explicit", gmres_restart=30, penalty=False,
-             penalty_rtol=1e-10):
+             penalty_rtol=1e-10, wall_points=None, wall_points_prev=None):
         """One step of the projection scheme (see include/sipg.h, sipg_step)."""
         r, keep = rheology_struct(rheology)
         o = L.StepOpts()
@@ -353,6 +372,10 @@ class Context:
         o.gmres_restart = int(gmres_restart)
         o.ppe_rtol, o.visc_rtol, o.maxit = float(ppe_rtol), float(visc_rtol), int(maxit)
         o.penalty, o.penalty_rtol = int(bool(penalty)), float(penalty_rtol)
+        for name, wp in (("wall_points", wall_points), ("wall_points_prev", wall_points_prev)):
+            if wp is not None:
+                _need_cuda(wp, torch.float64)
+                setattr(o, name, wp.data_ptr())
         for key, val in (picard or {}).items():
             setattr(o.picard, key, val)
         st = L.StepStats()

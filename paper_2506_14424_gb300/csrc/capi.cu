@@ -242,6 +242,7 @@ int sipg_ctx::build_hierarchy(int op) {
       F.interp = make_h_interp_down(F.n, F.child);
     }
   }
+  this->used_ids = used_ids;
   H.singular = true;  // all-Neumann operator: constants (Poisson) / rigid modes (viscous)
   for (int i = 0; i < 7; ++i)
     if ((used_ids >> i & 1) && H.L[0].g.bc[i] == SIPG_BC_DIRICHLET) H.singular = false;

@@ -125,6 +125,16 @@ __host__ __device__ inline int boundary_id(const LevelGeom& g, int e, int f) {
 // boundary condition (0 Dirichlet, 1 Neumann) of the boundary face (e, f)
 __host__ __device__ inline int face_bc(const LevelGeom& g, int e, int f) { return g.bc[boundary_id(g, e, f)]; }
 
+// Wall velocity handed to the form launchers: `side`, 18 HOST doubles (a constant
+// vector per grid side -x,+x,-y,+y,-z,+z; faces against removed cells take zero)
+// or NULL (zero), and optionally `pts`, DEVICE values at the Gauss points of every
+// boundary face ([nbf][n^2][3], see LevelGeom), which take precedence.
+struct WallArg {
+  const double* side;
+  const double* pts;
+  WallArg(const double* s = nullptr, const double* p = nullptr) : side(s), pts(p) {}
+};
+
 // Penalty geometry factor Lambda_e = sum_f w_f |f| / |Omega_e| with w_f = 1/2
 // on interior and 1 on boundary faces (box cells: |f| / |Omega_e| = 1 / h_d).
 __host__ __device__ inline double penalty_lambda(const LevelGeom& g, int e) {

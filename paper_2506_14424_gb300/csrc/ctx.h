@@ -67,6 +67,7 @@ struct sipg_ctx {
     int* dev;
   };
   std::vector<TopoEntry> topo_cache;
+  int used_ids = 0x3f;              // boundary ids present on the fine level (bit i: id i)
   sipg_opts opts{};
   cudaStream_t st = nullptr;
   sipg::Tab tabs[sipg::kMaxN + 1]{};
@@ -138,10 +139,10 @@ struct sipg_ctx {
   int parse_rheology(const sipg_rheology* rh, const double* u_lin, sipg::RheologyDev* out);
   int eval_viscosity(const sipg::RheologyDev& r, const double* u_lin);
   int mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse);
-  int convective_apply_total(const double* w, const double* wall_w, const double* x, double* y, double mass);
+  int convective_apply_total(const double* w, const sipg::WallArg& wall_w, const double* x, double* y, double mass);
   int penalty_work();
-  int penalty_solve(const double* wall_g, const double* u, double dt, double zeta_div, double zeta_cont,
+  int penalty_solve(const sipg::WallArg& wall_g, const double* u, double dt, double zeta_div, double zeta_cont,
                     double rtol, int maxit, double* x, int* iterations, double* rel_residual);
-  int gmres_solve(const double* w, const double* wall_w, const double* b, double* x, const sipg_solve_opts& so,
+  int gmres_solve(const double* w, const sipg::WallArg& wall_w, const double* b, double* x, const sipg_solve_opts& so,
                   int restart, sipg_solve_stats* stats);
 };

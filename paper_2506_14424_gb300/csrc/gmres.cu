@@ -25,7 +25,7 @@ using namespace sipg;
   } while (0)
 
 // y = K x
-int sipg_ctx::convective_apply_total(const double* w, const double* wall_w, const double* x, double* y,
+int sipg_ctx::convective_apply_total(const double* w, const WallArg& wall_w, const double* x, double* y,
                                      double mass) {
   sipg_ctx* ctx = this;
   int rc = krylov_apply(SIPG_OP_VISCOUS, x, y, mass);
@@ -38,7 +38,7 @@ int sipg_ctx::convective_apply_total(const double* w, const double* wall_w, cons
   return SIPG_OK;
 }
 
-int sipg_ctx::gmres_solve(const double* w, const double* wall_w, const double* b, double* x,
+int sipg_ctx::gmres_solve(const double* w, const WallArg& wall_w, const double* b, double* x,
                           const sipg_solve_opts& so, int restart, sipg_solve_stats* stats) {
   sipg_ctx* ctx = this;
   Hier& H = hier[SIPG_OP_VISCOUS];

@@ -39,16 +39,6 @@ cudaError_t launch_viscosity(int n, const LevelGeom& g, const Tab& tab, const Rh
 cudaError_t launch_cell_nu_transfer(const LevelGeom& fine, const LevelGeom& coarse, int kind, int nf, int nc,
                                     const double* fine_cell, double* nu_cell, double* nu_face, cudaStream_t st);
 
-// Wall velocity handed to the form launchers: `side`, 18 HOST doubles (a constant
-// vector per grid side -x,+x,-y,+y,-z,+z; faces against removed cells take zero)
-// or NULL (zero), and optionally `pts`, DEVICE values at the Gauss points of every
-// boundary face ([nbf][n^2][3], see LevelGeom), which take precedence.
-struct WallArg {
-  const double* side;
-  const double* pts;
-  WallArg(const double* s = nullptr, const double* p = nullptr) : side(s), pts(p) {}
-};
-
 // ---- forms of the splitting step (split.cu); n = velocity degree + 1 (3..6)
 struct PpeBndArgs {
   int n_hist;        // m: velocity histories entering the convective terms
@@ -75,6 +65,7 @@ cudaError_t launch_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& t
                                     const double* nu_face, double* y, cudaStream_t st);
 cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* u,
                            unsigned long long* vmax_bits, cudaStream_t st);
+cudaError_t launch_boundary_points(int n, const LevelGeom& g, const SplitTab& tab, double* xyz, cudaStream_t st);
 
 // ---- divergence and continuity penalty step (penalty.cu); n = velocity degree + 1
 cudaError_t launch_penalty_tau(int n, const LevelGeom& g, const SplitTab& tab, const double* u, double zeta_div,

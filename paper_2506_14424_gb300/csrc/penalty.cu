@@ -243,7 +243,7 @@ int sipg_ctx::penalty_work() {
   return SIPG_OK;
 }
 
-int sipg_ctx::penalty_solve(const double* wall_g, const double* u, double dt, double zeta_div, double zeta_cont,
+int sipg_ctx::penalty_solve(const WallArg& wall_g, const double* u, double dt, double zeta_div, double zeta_cont,
                             double rtol, int maxit, double* x, int* iterations, double* rel_residual) {
   sipg_ctx* ctx = this;
   int rc = penalty_work();

@@ -5,7 +5,8 @@
 //   ppe_bnd_kernel    h_p - (gamma0/dt) g_uhat.n at the Gauss points of every
 //                     wall face, Eqs. (pressure_Neumann_BC), (guhat_consistent_BC)
 //   ppe_rhs_kernel    (gamma0/dt)[(grad q, uhat) - (q, {{uhat}}.n)] with the wall
-//                     datum above on Dirichlet faces, Eq. (pressure_step_weak)
+//                     datum above on Dirichlet faces and uhat^+ = uhat^- on
+//                     outflow (velocity Neumann) faces, Eq. (pressure_step_weak)
 //   proj_rhs_kernel   (div v, p) - (v, {{p}} n), Eq. (projection_step_weak)
 //   visc_dir_kernel   Dirichlet wall-data terms of the SIPG viscous form (mirror
 //                     u^+ = -u^- + 2g) for the viscous step's right-hand side
@@ -380,12 +381,13 @@ __global__ void __launch_bounds__(kSplitThreads) ppe_rhs_kernel(LevelGeom g, Spl
     face_dirs(d, &t1, &t2);
     const double nd = 2.0 * s - 1.0;
     const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && face_bc(g, e, f) != 0) continue;  // velocity Neumann: u^+ = u^- handled below
+    // velocity Neumann (outflow): uhat^+ = uhat^-, so {{uhat}}.n = uhat^-.n
+    const bool outflow = nb < 0 && face_bc(g, e, f) != 0;
     const double area = g.h[t1] * g.h[t2];
-    if (nb >= 0) {
+    if (nb >= 0 || outflow) {
       for (int p = threadIdx.x; p < N2; p += blockDim.x) {
         FA[p] = U[d][fnode(d, s, p % N, p / N, N)];
-        FB[p] = uh[(size_t)nb * 3 * N3 + d * N3 + fnode(d, 1 - s, p % N, p / N, N)];
+        FB[p] = outflow ? FA[p] : uh[(size_t)nb * 3 * N3 + d * N3 + fnode(d, 1 - s, p % N, p / N, N)];
       }
       __syncthreads();
       sweep<N, N, 1, 0, N, false>(T.S, N, FA, FT);
@@ -578,6 +580,26 @@ __global__ void __launch_bounds__(kSplitThreads) cfl_kernel(LevelGeom g, SplitTa
   if (threadIdx.x == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(red[0]));
 }
 
+// positions of the Gauss points of every boundary face, [nbf][n^2][3]
+template <int N>
+__global__ void bpoints_kernel(LevelGeom g, SplitTab tab, int nbf, double* __restrict__ xyz) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nbf * N * N) return;
+  const int b = (int)(i / (N * N)), p = (int)(i % (N * N));
+  int e, f;
+  bface_cell(g, b, &e, &f);
+  const int d = f >> 1, s = f & 1;
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  double xi[3];
+  xi[d] = s;
+  xi[t1] = tab.gp[p % N];
+  xi[t2] = tab.gp[p / N];
+  for (int c = 0; c < 3; ++c) xyz[3 * i + c] = g.x0[c] + (ijk[c] + xi[c]) * g.h[c];
+}
+
 }  // namespace
 
 Wall make_wall(const WallArg& a) {
@@ -655,6 +677,15 @@ cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const
   cudaError_t e = cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess || g.ncells == 0) return e;
   SIPG_SPLIT_DISPATCH(n, (cfl_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, u, vmax_bits)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_points(int n, const LevelGeom& g, const SplitTab& tab, double* xyz, cudaStream_t st) {
+  const int nbf = n_wall_faces(g);
+  const int64_t total = (int64_t)nbf * n * n;
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)((total + 127) / 128);
+  SIPG_SPLIT_DISPATCH(n, (bpoints_kernel<N><<<blocks, 128, 0, st>>>(g, tab, nbf, xyz)));
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <utility>
+#include <vector>
 
 using namespace sipg;
 
@@ -29,9 +30,17 @@ using Clock = std::chrono::steady_clock;
 
 double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
-bool box_walls_ok(const sipg_ctx* ctx) {
-  for (int f = 0; f < 6; ++f)
-    if (ctx->mesh.bc_velocity[f] != SIPG_BC_DIRICHLET || ctx->mesh.bc_pressure[f] != SIPG_BC_NEUMANN) return false;
+// every boundary id present: velocity Dirichlet + pressure Neumann (wall, inflow) or
+// velocity Neumann + pressure Dirichlet (outflow)
+bool walls_ok(const sipg_ctx* ctx) {
+  const LevelGeom& gu = ctx->hier[SIPG_OP_VISCOUS].L[0].g;
+  const LevelGeom& gp = ctx->hier[SIPG_OP_POISSON].L[0].g;
+  for (int i = 0; i < 7; ++i) {
+    if (!(ctx->used_ids >> i & 1)) continue;
+    const bool wall = gu.bc[i] == SIPG_BC_DIRICHLET && gp.bc[i] == SIPG_BC_NEUMANN;
+    const bool outflow = gu.bc[i] == SIPG_BC_NEUMANN && gp.bc[i] == SIPG_BC_DIRICHLET;
+    if (!wall && !outflow) return false;
+  }
   return true;
 }
 
@@ -115,12 +124,57 @@ extern "C" int sipg_cfl_dt(sipg_ctx* ctx, const double* u, double courant, doubl
   return SIPG_OK;
 }
 
+extern "C" int sipg_boundary_faces(sipg_ctx* ctx, int* nbf, int* cell_face_id, double* xyz) {
+  if (!ctx) return SIPG_ERR_INVALID;
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "boundary faces of box grids only");
+  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
+  const LevelGeom& g = L.g;
+  const int nb = n_wall_faces(g);
+  if (nbf) *nbf = nb;
+  if (cell_face_id) {
+    if (g.nbr) {
+      std::vector<int> bf(nb), nbr((size_t)g.ncells * 6);
+      CK(cudaMemcpy(bf.data(), g.bface, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(nbr.data(), g.nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost));
+      for (int b = 0; b < nb; ++b) {
+        cell_face_id[3 * b + 0] = bf[b] / 6;
+        cell_face_id[3 * b + 1] = bf[b] % 6;
+        cell_face_id[3 * b + 2] = (-1 - nbr[bf[b]]) & 7;
+      }
+    } else {  // the plain box: side by side, each lexicographic over t1 < t2
+      const int dims[3] = {g.nx, g.ny, g.nz};
+      int b = 0;
+      for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1, s = f & 1;
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        for (int j2 = 0; j2 < dims[t2]; ++j2)
+          for (int j1 = 0; j1 < dims[t1]; ++j1, ++b) {
+            int ijk[3];
+            ijk[d] = s ? dims[d] - 1 : 0;
+            ijk[t1] = j1;
+            ijk[t2] = j2;
+            cell_face_id[3 * b + 0] = (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+            cell_face_id[3 * b + 1] = f;
+            cell_face_id[3 * b + 2] = f;
+          }
+      }
+    }
+  }
+  if (xyz) {
+    CK(launch_boundary_points(L.n, g, ctx->stabs[L.n], xyz, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return SIPG_OK;
+}
+
 extern "C" int sipg_step_init(sipg_ctx* ctx, const double* u0, const double* p0) {
   if (!ctx || !u0) return SIPG_ERR_INVALID;
   int rc = check_forms(ctx);
   if (rc) return rc;
-  if (!box_walls_ok(ctx))
-    return ctx->fail(SIPG_ERR_INVALID, "the splitting step needs velocity-Dirichlet (pressure-Neumann) walls");
+  if (!walls_ok(ctx))
+    return ctx->fail(SIPG_ERR_INVALID,
+                     "the splitting step needs velocity-Dirichlet / pressure-Neumann walls or "
+                     "velocity-Neumann / pressure-Dirichlet outflow faces");
   auto& S = ctx->ss;
   const int64_t nu = ctx->hier[SIPG_OP_VISCOUS].L[0].ndofs;
   const int64_t np = ctx->hier[SIPG_OP_POISSON].L[0].ndofs;
@@ -181,7 +235,7 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   if (!(so.dt > 0) || !std::isfinite(so.dt)) return ctx->fail(SIPG_ERR_INVALID, "time step must be positive");
   if (rh->law != SIPG_LAW_CONSTANT && rh->law != SIPG_LAW_CARREAU)
     return ctx->fail(SIPG_ERR_INVALID, "the splitting step takes a constant or Carreau-Yasuda viscosity");
-  bool wall_moving = false;
+  bool wall_moving = so.wall_points != nullptr;
   for (double v : so.wall_velocity) wall_moving |= v != 0.0;
   if (so.viscosity_mode == SIPG_VISC_IMPLICIT && wall_moving)
     return ctx->fail(SIPG_ERR_INVALID, "the implicit-viscosity step is built for zero wall velocity");
@@ -207,13 +261,15 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   const double beta[2] = {m == 2 ? 2.0 : 1.0, m == 2 ? -1.0 : 0.0};
   const int m_p = m - 1 < 2 ? m - 1 : 2;
   const double betabar[2] = {m_p >= 1 ? (m_p == 2 ? 2.0 : 1.0) : 0.0, m_p == 2 ? -1.0 : 0.0};
-  const double* wall = so.wall_velocity;
+  // wall data at t_{n+1} (pressure datum, viscous and penalty steps) and at t_n (C(u^n))
+  const WallArg wall(so.wall_velocity, so.wall_points);
+  const WallArg wall_n(so.wall_velocity, so.wall_points_prev ? so.wall_points_prev : so.wall_points);
 
   // ---- 1 convective step: C(u^n) (C(u^{n-1}) kept from the previous step)
   std::swap(S.conv[0], S.conv[1]);
   S.conv1 = S.steps > 0;
-  CK(launch_convective(Lu.n, Lu.g, tab, wall, S.u[0], S.conv[0], st));
-  if (m == 2 && !S.conv1) CK(launch_convective(Lu.n, Lu.g, tab, wall, S.u[1], S.conv[1], st));
+  CK(launch_convective(Lu.n, Lu.g, tab, wall_n, S.u[0], S.conv[0], st));
+  if (m == 2 && !S.conv1) CK(launch_convective(Lu.n, Lu.g, tab, wall_n, S.u[1], S.conv[1], st));
   // tmp = sum_i alpha_i/dt u^{n-i} + b ; bv = M tmp - sum_i beta_i C_i ; uhat = (gamma0/dt M)^-1 bv
   CK(launch_scale(nu, alpha[0] / dt, S.u[0], S.tmp, st));
   if (m == 2) CK(launch_add_scaled_f64(nu, alpha[1] / dt, S.u[1], S.tmp, st));

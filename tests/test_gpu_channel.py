@@ -11,7 +11,12 @@ around the removed block, z periodic) against the oracle.
 * MG-CG solves of the viscous and the (non-singular) pressure problem reach the
   oracle's discrete solution;
 * a box periodic in two directions (no removed cell) with the constants in
-  the Poisson kernel.
+  the Poisson kernel;
+* the splitting step on the channel: boundary faces and their Gauss points;
+  BDF1/BDF2 steps with the ramped parabolic inflow (time-dependent wall data
+  at the boundary points), the outflow and the Carreau-Yasuda law, with and
+  without the penalty step, equal the oracle's; a hydrostatic state with the
+  outflow at p = 0 at 448 cells.
 """
 import numpy as np
 import pytest
@@ -19,6 +24,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import multigrid as omg  # noqa: E402
+from oracle import splitting as osp  # noqa: E402
 from oracle.mesh import BoxMesh  # noqa: E402
 from oracle.sipg import SIPG  # noqa: E402
 from paper_2506_14424_gb300 import Context, inputs  # noqa: E402
@@ -174,4 +180,87 @@ def test_periodic_box():
     xv = inputs.uniform_vector(S.n_dofs, seed=6)
     ref = S.apply(xv, *S.viscosity_at_points({'law': 'analytic'}))
     assert _rel(ctx.apply("viscous", _dev(xv)).cpu().numpy(), ref) <= TOL64
+    ctx.close()
+
+
+CARREAU = {'law': 'carreau', 'eta0': 1.0, 'eta_inf': 1e-3, 'kappa': 1.0, 'lam': 1.0, 'a': 2.0, 'b': 0.5}
+
+
+def _inflow(x):
+    """Parabolic inflow on the inlet y in [1, 2] (maximum 1 on its centre line)."""
+    return np.stack([1 - ((x[:, 1] - 1.5) / 0.5) ** 2, 0 * x[:, 0], 0 * x[:, 0]], axis=1)
+
+
+def _ramp(t, t_ramp=0.1):
+    return np.sin(np.pi * t / (2 * t_ramp)) ** 2 if t < t_ramp else 1.0
+
+
+def _wall_points(ctx, t):
+    ids = ctx.boundary_faces()[:, 2]
+    pts = ctx.boundary_points().cpu().numpy()
+    g = np.zeros_like(pts)
+    inlet = ids == 0
+    g[inlet] = _ramp(t) * _inflow(pts[inlet].reshape(-1, 3)).reshape(pts[inlet].shape)
+    return _dev(g)
+
+
+def test_channel_boundary_faces():
+    c = _channel(2)
+    k = 2
+    ctx = _ctx(c, k)
+    mesh = _mesh(c, "viscous")
+    ref = mesh.boundary_faces()
+    got = ctx.boundary_faces()
+    assert [(int(e), int(f)) for e, f, _ in got] == ref
+    assert [int(b) for b in got[:, 2]] == [mesh.boundary_id(e, f) for e, f in ref]
+    S = SIPG(mesh, k, 3)
+    pts = ctx.boundary_points().cpu().numpy()
+    for i, (e, f) in enumerate(ref):
+        assert np.abs(pts[i] - S.face_points(e, f)).max() <= 1e-14
+    ctx.close()
+
+
+@pytest.mark.parametrize("penalty", [False, True])
+def test_channel_steps_match_oracle(penalty):
+    """Ramped parabolic inflow, outflow, no-slip walls and step, z periodic, Carreau-Yasuda:
+    BDF1 then BDF2 steps equal the oracle's exactly-solved steps."""
+    c = _channel(2)
+    k = 2
+    mesh = _mesh(c, "viscous")
+    ref = osp.Splitting(mesh, k, CARREAU, g_faces=[_inflow] + [np.zeros(3)] * 6, ramp=_ramp)
+    ref.set_initial(np.zeros(ref.Su.n_dofs))
+    ctx = _ctx(c, k)
+    ctx.step_init(torch.zeros(ref.Su.n_dofs, dtype=torch.float64, device="cuda"))
+    dt, t = 0.02, 0.0
+    for n in range(3):
+        r = ref.step(dt, penalty=penalty)
+        st = ctx.step(CARREAU, dt, wall_points=_wall_points(ctx, t + dt), wall_points_prev=_wall_points(ctx, t),
+                      ppe_rtol=1e-13, visc_rtol=1e-13, maxit=3000, penalty=penalty, penalty_rtol=1e-13)
+        t += dt
+        assert st["order"] == r["order"]
+        assert _rel(ctx.step_field("uhat").cpu().numpy(), r["uhat"]) <= 1e-10
+        assert _rel(ctx.step_field("p").cpu().numpy(), r["p"]) <= 1e-8
+        assert _rel(ctx.step_field("u").cpu().numpy(), r["u"]) <= 1e-8
+    ctx.close()
+
+
+def test_channel_hydrostatic_outflow_at_448_cells():
+    """u0 = 0 under b = c e_x with the outflow at p = 0: u stays 0, p = c (x - x_out)
+    (the property the oracle's pin establishes), 16 x 8 x 4 grid, k = 3."""
+    c = _channel(4)
+    k = 3
+    ctx = _ctx(c, k)
+    n = ctx.n_dofs("viscous")
+    cb = 0.8
+    body = torch.zeros(n, dtype=torch.float64, device="cuda").view(-1, 3, (k + 1) ** 3)
+    body[:, 0] = cb
+    ctx.step_init(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    pp = ctx.node_points("poisson", 0).reshape(-1, 3)
+    x_out = c["lo"][0] + c["extent"][0]
+    p_exact = cb * (pp[:, 0] - x_out)
+    for _ in range(2):
+        ctx.step({'law': 'constant', 'nu': 0.1}, 0.05, body=body.reshape(-1), ppe_rtol=1e-13, visc_rtol=1e-13,
+                 maxit=3000)
+        assert ctx.step_field("u").abs().max().item() <= 1e-10
+        assert _rel(ctx.step_field("p").cpu().numpy(), p_exact) <= 1e-10
     ctx.close()

@@ -176,7 +176,13 @@ def test_step_status_codes():
     with pytest.raises(SipgError):
         ctx.step({'law': 'analytic'}, 0.01)
     ctx.close()
-    c2 = Context(2, 2, 2, 2, bc_velocity="DDDDDN", bc_pressure="NNNNND")
-    with pytest.raises(SipgError):
-        c2.step_init(torch.zeros(c2.n_dofs("viscous"), dtype=torch.float64, device="cuda"))
-    c2.close()
+    # a side that is velocity Neumann needs the pressure Dirichlet there (outflow), and a
+    # velocity-Dirichlet side the pressure Neumann
+    for bv, bp in (("DDDDDN", "NNNNNN"), ("DDDDDD", "NNNNND")):
+        c2 = Context(2, 2, 2, 2, bc_velocity=bv, bc_pressure=bp)
+        with pytest.raises(SipgError):
+            c2.step_init(torch.zeros(c2.n_dofs("viscous"), dtype=torch.float64, device="cuda"))
+        c2.close()
+    c3 = Context(2, 2, 2, 2, bc_velocity="DDDDDN", bc_pressure="NNNNND")   # outflow at +z
+    c3.step_init(torch.zeros(c3.n_dofs("viscous"), dtype=torch.float64, device="cuda"))
+    c3.close()
