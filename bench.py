@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     p.add_argument("--arith", default="f64ff", choices=["f64", "f64ff"],
                    help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
-    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear"],
+    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear", "channel"],
                    help="run one extra workload alone and print its JSON (profiling runs)")
     return p.parse_args()
 
@@ -53,6 +53,8 @@ def run_extra(name):
         out = step_extras()
     elif name == "trilinear":
         out = trilinear_extras()
+    elif name == "channel":
+        out = channel_extras()
     else:
         ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U, krylov_arith="f64ff")
         n = ctx.n_dofs("viscous")
@@ -350,6 +352,7 @@ def gpu_extras(ctx, xs, ys, stream):
     out["picard_viscous_step_32cubed_k3"] = picard_extras(ctx)
     out["splitting_step_32cubed_k3"] = step_extras()
     out["trilinear_cells_32cubed_k3"] = trilinear_extras()
+    out["bfs_channel_steps"] = channel_extras()
     out["components_16cubed_k4"] = component_timings(stream)
     out["serving"] = serving_extras()
     return out
@@ -480,6 +483,58 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
         "penalty_iterations": [r["penalty_iterations"] for r in rows]}
     td, tc = ctx.penalty_tau(u0, dt)
     out["penalty_apply_ms"] = ev(lambda: ctx.penalty_apply(td, tc, u0))
+    ctx.close()
+    return out
+
+
+def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=1.0):
+    """Projection-scheme steps on the backward-facing-step channel (inlet [-5, 0] x [1, 2],
+    outlet [0, 30] x [0, 2], z in [0, 4] periodic, step height 1, expansion ratio 2), cubes
+    of side 1/8: 133,120 affine hexes, k = 3 velocity / k = 2 pressure. Parabolic inflow
+    of maximum 1 ramped by sin^2(pi t / (2 t_ramp)), traction-free outflow at p = 0, no-slip
+    walls and step, Carreau-Yasuda viscosity linear implicit, fluid at rest at t = 0,
+    dt from the CFL rule (Cr = 0.3) at the full inflow velocity, CG to 1e-8 with the FP32
+    hp-multigrid (p: 3 -> 2 -> 1, then h down to cubes of side 1). The wall data of every
+    step are evaluated before the timed steps. Host-clock step times (the step synchronises)."""
+    import numpy as np
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+    c = inputs.bfs_channel(cells_per_unit)
+    t0 = time.perf_counter()
+    ctx = Context(*c["dims"], k, extent=c["extent"], origin=c["lo"], active=c["active"], periodic=c["periodic"],
+                  bc_velocity="DNDDDD", bc_pressure="NDNNNN", bc_removed="DN", krylov_arith="f64ff",
+                  coarse_max_dofs=8000)
+    t_create = time.perf_counter() - t0
+    rh = inputs.carreau_blood_like()
+    n = ctx.n_dofs("viscous")
+    ids = torch.tensor(ctx.boundary_faces()[:, 2], device="cuda")
+    pts = ctx.boundary_points()
+    shape = torch.zeros_like(pts)
+    inlet = ids == 0
+    shape[inlet, :, 0] = 1.0 - ((pts[inlet, :, 1] - 1.5) / 0.5) ** 2
+    dt = courant / k ** 1.5 / (1.0 * cells_per_unit)
+    ramp = [float(np.sin(np.pi * (i * dt) / (2 * t_ramp)) ** 2) if i * dt < t_ramp else 1.0
+            for i in range(warm + steps + 1)]
+    walls = [r * shape for r in ramp]
+    ctx.step_init(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    rows = []
+    for i in range(warm + steps):
+        st = ctx.step(rh, dt, wall_points=walls[i + 1], wall_points_prev=walls[i], ppe_rtol=1e-8, visc_rtol=1e-8)
+        if i >= warm:
+            rows.append(st)
+    u = ctx.step_field("u")
+    levels = [(tuple(ctx.level_info("viscous", l)[0]), ctx.level_info("viscous", l)[1], ctx.level_info("viscous", l)[2])
+              for l in range(ctx.num_levels("viscous"))]
+    out = {"cells": ctx.n_cells, "n_dofs_velocity": n, "n_dofs_pressure": ctx.n_dofs("poisson"), "dt": dt,
+           "steps_timed": steps, "create_seconds": t_create, "viscous_levels": levels,
+           "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
+           "mean_t_pressure": float(np.mean([r["t_pressure"] for r in rows])),
+           "mean_t_viscous": float(np.mean([r["t_viscous"] for r in rows])),
+           "ppe_iterations": [r["ppe_iterations"] for r in rows],
+           "visc_iterations": [r["visc_iterations"] for r in rows],
+           "max_u": u.abs().max().item()}
+    out["dof_steps_per_s"] = n / out["mean_seconds"]
     ctx.close()
     return out
 
