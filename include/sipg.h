@@ -93,9 +93,11 @@ typedef struct {
    *          the bc of its two sides is unused); the first and last cell layers
    *          are face neighbours.
    * origin[3]: the grid's lower corner (positions of nodes, viscosity laws).
-   * Removed cells or periodic directions: boxes only (no vertices), no cph
-   * hierarchy; multigrid h-levels coarsen while every 2x2x2 block of cells is
-   * all active or all removed. */
+   * Removed cells or periodic directions: no cph hierarchy; with vertices the
+   * active cells are trilinear (the jittered channel; the vertex array covers the
+   * whole grid and the vertices of a periodic direction's end layers must agree
+   * up to the period); multigrid h-levels coarsen while every 2x2x2 block of
+   * cells is all active or all removed. */
   const unsigned char* active;
   int bc_removed_velocity, bc_removed_pressure;
   int periodic[3];

@@ -35,13 +35,16 @@ from .sipg import _sym
 
 
 class MappedMesh:
-    """Structured hexahedral mesh; vertex (i, j, k) at X[k, j, i] (shape (nz+1, ny+1, nx+1, 3))."""
+    """Structured hexahedral mesh; vertex (i, j, k) at X[k, j, i] (shape (nz+1, ny+1, nx+1, 3)).
+    The topology is that of oracle.mesh.BoxMesh: optional removed cells (``active``) and
+    periodic directions (the vertices of the first and last layers of a periodic direction
+    must then agree up to the period)."""
 
-    def __init__(self, nx, ny, nz, vertices, bc=('D',) * 6):
-        self.topo = BoxMesh(nx, ny, nz, bc=bc)
+    def __init__(self, nx, ny, nz, vertices, bc=('D',) * 6, active=None, periodic=(False, False, False)):
+        self.topo = BoxMesh(nx, ny, nz, bc=bc, active=active, periodic=periodic)
         self.X = np.asarray(vertices, dtype=np.float64).reshape(nz + 1, ny + 1, nx + 1, 3)
         self.n_cells_dir = (nx, ny, nz)
-        self.bc = tuple(bc)
+        self.bc = self.topo.bc
 
     @property
     def n_cells(self):

@@ -442,7 +442,7 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
   const bool topo = mesh_topology(mesh);
   if (topo) {
-    if (mesh->vertices || o.mg_cph) return SIPG_ERR_INVALID;
+    if (o.mg_cph) return SIPG_ERR_INVALID;  // continuous levels: plain boxes only
     const int dims[3] = {mesh->nx, mesh->ny, mesh->nz};
     for (int d = 0; d < 3; ++d)
       if ((mesh->periodic[d] != 0 && mesh->periodic[d] != 1) || (mesh->periodic[d] && dims[d] < 2))

@@ -14,7 +14,8 @@ takes an explicit seed and uses numpy's ``default_rng``.
                         phi_m ~ U(0, 2 pi): unit amplitude per mode and
                         exactly divergence-free because c_m . k_m = 0.
 * ``bfs_channel``     - the grid and active-cell flags of the backward-facing
-                        step channel (geometry only).
+                        step channel (geometry only); ``bfs_vertices`` its
+                        vertices with the 5 % seeded jitter inside the fluid.
 """
 import numpy as np
 
@@ -86,3 +87,26 @@ def bfs_channel(cells_per_unit, inlet_length=5.0, outlet_length=30.0, step=1.0, 
     active = np.broadcast_to(~removed, (nz, ny, nx)).copy()
     return {"dims": (nx, ny, nz), "extent": (inlet_length + outlet_length, float(height), float(depth)),
             "lo": lo, "active": active, "periodic": (False, False, True)}
+
+
+def bfs_vertices(channel, amp=0.05, seed=4):
+    """Vertices (nz+1, ny+1, nx+1, 3) of the channel grid with the vertices inside the fluid
+    moved by U(-amp h, amp h) per direction (seed 4): a vertex moves when all 8 cells around
+    it are active and it is not on the grid's outer surface, so the walls, the step, the
+    inflow and outflow planes and the periodic end planes stay planar."""
+    nx, ny, nz = channel["dims"]
+    ext, lo = channel["extent"], channel["lo"]
+    h = np.array([ext[0] / nx, ext[1] / ny, ext[2] / nz])
+    xs = [lo[d] + h[d] * np.arange(n + 1) for d, n in enumerate((nx, ny, nz))]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing='ij')
+    V = np.stack([X, Y, Z], axis=-1)
+    act = np.asarray(channel["active"], dtype=bool)
+    free = np.zeros((nz + 1, ny + 1, nx + 1), dtype=bool)
+    inner = np.ones((nz - 1, ny - 1, nx - 1), dtype=bool)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                inner &= act[dz:dz + nz - 1, dy:dy + ny - 1, dx:dx + nx - 1]
+    free[1:nz, 1:ny, 1:nx] = inner
+    J = np.random.default_rng(seed).uniform(-amp, amp, size=V.shape) * h
+    return V + J * free[..., None]

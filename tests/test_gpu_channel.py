@@ -16,7 +16,9 @@ around the removed block, z periodic) against the oracle.
   BDF1/BDF2 steps with the ramped parabolic inflow (time-dependent wall data
   at the boundary points), the outflow and the Carreau-Yasuda law, with and
   without the penalty step, equal the oracle's; a hydrostatic state with the
-  outflow at p = 0 at 448 cells.
+  outflow at p = 0 at 448 cells;
+* the jittered channel (trilinear cells, 5 % jitter inside the fluid): viscous
+  and Poisson applies, the diagonal and the FP64 multigrid solve.
 """
 import numpy as np
 import pytest
@@ -263,4 +265,57 @@ def test_channel_hydrostatic_outflow_at_448_cells():
                  maxit=3000)
         assert ctx.step_field("u").abs().max().item() <= 1e-10
         assert _rel(ctx.step_field("p").cpu().numpy(), p_exact) <= 1e-10
+    ctx.close()
+
+
+def _mapped_ctx(c, V, k, **kw):
+    return Context(*c["dims"], k, extent=c["extent"], origin=c["lo"], active=c["active"], periodic=c["periodic"],
+                   bc_velocity=VEL, bc_pressure=PRE, bc_removed="DN", vertices=V, **kw)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_jittered_channel_applies_and_diagonal(k):
+    """The channel with 5 % vertex jitter inside the fluid (trilinear cells): viscous
+    (Carreau-Yasuda) and Poisson applies and the viscous diagonal equal the oracle's."""
+    from oracle.mapped import MappedMesh, MappedSIPG
+    c = _channel(2)
+    V = inputs.bfs_vertices(c)
+    vm = MappedMesh(*c["dims"], V, bc=tuple(VEL) + ('D',), active=c["active"], periodic=c["periodic"])
+    S = MappedSIPG(vm, k, 3)
+    u = S.interpolate(lambda p: inputs.fourier_field(p, inputs.fourier_modes(1)))
+    nc, nf = S.viscosity_at_points(CARREAU, u)
+    ctx = _mapped_ctx(c, V, k)
+    ctx.set_viscosity(CARREAU, _dev(u))
+    x = inputs.uniform_vector(S.n_dofs, seed=21)
+    A = S.assemble(nc, nf)
+    assert _rel(ctx.apply("viscous", _dev(x)).cpu().numpy(), A @ x) <= TOL64
+    assert _rel(ctx.inverse_diagonal("viscous", 0).cpu().numpy(), 1.0 / A.diagonal()) <= TOL64
+    pm = MappedMesh(*c["dims"], V, bc=tuple(PRE) + ('N',), active=c["active"], periodic=c["periodic"])
+    P = MappedSIPG(pm, k - 1, 1)
+    xp = inputs.uniform_vector(P.n_dofs, seed=22)
+    assert _rel(ctx.apply("poisson", _dev(xp)).cpu().numpy(), P.assemble() @ xp) <= TOL64
+    ctx.close()
+
+
+def test_jittered_channel_multigrid_solve():
+    """FP64 hp-multigrid on the jittered channel (p-levels on the fine vertices, an h-level
+    from every other vertex) preconditions CG to the oracle's sparse-LU solution."""
+    import scipy.sparse.linalg as spla
+
+    from oracle.mapped import MappedMesh, MappedSIPG
+    c = inputs.bfs_channel(2, inlet_length=1.0, outlet_length=3.0, depth=2.0)   # 8 x 4 x 4 grid, 112 cells
+    V = inputs.bfs_vertices(c)
+    k, m = 2, 5.0
+    vm = MappedMesh(*c["dims"], V, bc=tuple(VEL) + ('D',), active=c["active"], periodic=c["periodic"])
+    S = MappedSIPG(vm, k, 3)
+    u = S.interpolate(lambda p: inputs.fourier_field(p, inputs.fourier_modes(1)))
+    nc, nf = S.viscosity_at_points(CARREAU, u)
+    b = inputs.uniform_vector(S.n_dofs, 23)
+    ref = spla.spsolve(S.assemble(nc, nf, mass=m).tocsc(), b)
+    ctx = _mapped_ctx(c, V, k, coarse_max_dofs=2000)
+    assert ctx.num_levels("viscous") >= 3
+    ctx.set_viscosity(CARREAU, _dev(u))
+    xs, st = ctx.solve("viscous", _dev(b), rtol=1e-12, maxit=300, precond="mg", mass=m)
+    assert _rel(xs.cpu().numpy(), ref) <= 1e-9
+    assert st["iterations"] <= 60, st
     ctx.close()

@@ -175,3 +175,24 @@ def test_ppe_datum_depends_on_the_newest_wall_data_only():
     _, _, nvec = osp.face_normal(f)
     gn = g_new[mesh.boundary_id(e, f)] @ nvec
     assert np.abs(b - (c0 - 1.5 / 0.1 * gn)).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_jittered_channel_operators():
+    """Trilinear cells on the channel (vertices inside the fluid jittered): symmetric,
+    definite with the channel's walls, and equal to the affine channel without jitter."""
+    from oracle.mapped import MappedMesh, MappedSIPG
+    c = inputs.bfs_channel(2, inlet_length=1.0, outlet_length=3.0, depth=1.0)
+    V = inputs.bfs_vertices(c)
+    flat = inputs.bfs_vertices(c, amp=0.0)
+    assert np.abs(V - flat).max() > 0.01 / 2
+    mm = MappedMesh(*c["dims"], V, bc=VEL_BC, active=c["active"], periodic=c["periodic"])
+    S = MappedSIPG(mm, 2, 3)
+    A = S.assemble(*S.viscosity_at_points({'law': 'constant', 'nu': 0.4})).toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+    m0 = MappedMesh(*c["dims"], flat, bc=VEL_BC, active=c["active"], periodic=c["periodic"])
+    S0 = MappedSIPG(m0, 2, 3)
+    A0 = S0.assemble(*S0.viscosity_at_points({'law': 'constant', 'nu': 0.4}))
+    Sa = SIPG(small_channel(2), 2, 3)
+    Aa = Sa.assemble(*Sa.viscosity_at_points({'law': 'constant', 'nu': 0.4}))
+    assert np.abs((A0 - Aa).toarray()).max() <= 1e-12 * np.abs(Aa.toarray()).max()
