@@ -526,7 +526,8 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
     u = ctx.step_field("u")
     levels = [(tuple(ctx.level_info("viscous", l)[0]), ctx.level_info("viscous", l)[1], ctx.level_info("viscous", l)[2])
               for l in range(ctx.num_levels("viscous"))]
-    out = {"cells": ctx.n_cells, "n_dofs_velocity": n, "n_dofs_pressure": ctx.n_dofs("poisson"), "dt": dt,
+    out = {"geometry": "affine cells (no vertex jitter)", "cells": ctx.n_cells, "n_dofs_velocity": n,
+           "n_dofs_pressure": ctx.n_dofs("poisson"), "dt": dt,
            "steps_timed": steps, "create_seconds": t_create, "viscous_levels": levels,
            "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
            "mean_t_pressure": float(np.mean([r["t_pressure"] for r in rows])),
