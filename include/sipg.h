@@ -409,6 +409,21 @@ int sipg_viscous_wall_rhs(sipg_ctx* ctx, const double* wall_g, double* y);
 int sipg_solve_convective(sipg_ctx* ctx, const double* w, const double* wall_w, const double* b, double* x,
                           const sipg_solve_opts* so, int restart, sipg_solve_stats* stats);
 
+/* ------------------------------------------------- manufactured solutions
+ * Load vectors of the manufactured solutions that verify the operators (Sec. 7.1
+ * checks convergence with manufactured solutions; here the steady operators):
+ * b_i = integral of phi_i f over each cell, over-integrated with k+4 Gauss points
+ * per direction, on the fine level of the viscous (SIPG_MMS_VELOCITY) or Poisson
+ * (SIPG_MMS_PRESSURE) space; b: DEVICE vector of that space.
+ *   SIPG_MMS_VELOCITY: u = s(x) (1, -1, 2), s = sin(pi x) sin(pi y) sin(pi z), with
+ *     the analytic viscosity nu = 1 + 9 s^2 (SIPG_LAW_ANALYTIC): f = -div(2 nu eps(u));
+ *     u = 0 on the walls of the unit cube.
+ *   SIPG_MMS_PRESSURE: p = cos(pi x) cos(pi y) cos(pi z), f = -lap p = 3 pi^2 p;
+ *     zero normal derivative on the walls of the unit cube, zero mean.
+ * Affine cells only (SIPG_ERR_INVALID with vertices). (sync) */
+enum { SIPG_MMS_VELOCITY = 0, SIPG_MMS_PRESSURE = 1 };
+int sipg_rhs_manufactured(sipg_ctx* ctx, int case_id, double* b);
+
 /* ------------------------------------ divergence and continuity penalty step
  * Sec. 3.2, Eq. (penalty_step), the last sub-step of Alg. 1: the velocity u of
  * the viscous step becomes u~, the solution of

@@ -312,6 +312,13 @@ class Context:
                                                 ctypes.byref(res)))
         return out, {"iterations": its.value, "rel_residual": res.value}
 
+    def rhs_manufactured(self, case="velocity"):
+        """Load vector of a manufactured solution (see sipg_rhs_manufactured)."""
+        op = "viscous" if case == "velocity" else "poisson"
+        b = torch.empty(self.n_dofs(op), dtype=torch.float64, device="cuda")
+        self._check(self._lib.sipg_rhs_manufactured(self._h, 0 if case == "velocity" else 1, _ptr(b)))
+        return b
+
     def boundary_faces(self):
         """(cell, face, boundary id) of every boundary face of the velocity mesh, (nbf, 3) ints,
         in the order of the step's wall_points arrays."""

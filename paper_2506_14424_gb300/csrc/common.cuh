@@ -45,6 +45,15 @@ struct SplitTab {
   double gw[kMaxN], gp[kMaxN];  // Gauss weights and points on [0, 1]
 };
 
+// Over-integration rule of the manufactured loads: nq Gauss points on [0, 1]
+// (nq = n + 3) and the Gauss-Lobatto basis there, S[q*n + j] = l_j(gp_q).
+constexpr int kMaxNQ = kMaxN + 3;
+struct LoadTab {
+  int n, nq;
+  double S[kMaxN * kMaxNQ];
+  double gw[kMaxNQ], gp[kMaxNQ];
+};
+
 // Global Gauss-Lobatto node grid of a continuous (cph) level on the box.
 struct CgGrid {
   int nx, ny, nz, k, Gx, Gy, Gz, ncomp;

@@ -67,6 +67,9 @@ cudaError_t launch_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const
                            unsigned long long* vmax_bits, cudaStream_t st);
 cudaError_t launch_boundary_points(int n, const LevelGeom& g, const SplitTab& tab, double* xyz, cudaStream_t st);
 
+// ---- manufactured-solution loads (manufactured.cu); which 0 velocity, 1 pressure
+cudaError_t launch_manufactured_load(int n, const LevelGeom& g, int which, double* b, cudaStream_t st);
+
 // ---- divergence and continuity penalty step (penalty.cu); n = velocity degree + 1
 cudaError_t launch_penalty_tau(int n, const LevelGeom& g, const SplitTab& tab, const double* u, double zeta_div,
                                double zeta_cont, double dt, double* tdiv, double* tcon, cudaStream_t st);

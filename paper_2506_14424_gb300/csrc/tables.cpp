@@ -252,4 +252,18 @@ TransferTab make_h_interp_down(int n, int* child) {
   return T;
 }
 
+LoadTab make_load_tab(int n) {
+  LoadTab T{};
+  T.n = n;
+  T.nq = n + 3;
+  std::vector<double> gll(n), gllw(n);
+  gauss_lobatto(n, gll.data(), gllw.data());
+  gauss_legendre(T.nq, T.gp, T.gw);
+  for (int q = 0; q < T.nq; ++q) {
+    const auto v = lagrange_values(gll, T.gp[q]);
+    for (int j = 0; j < n; ++j) T.S[q * n + j] = v[j];
+  }
+  return T;
+}
+
 }  // namespace sipg

@@ -10,4 +10,5 @@ TransferTab make_p_transfer(int nf, int nc);
 TransferTab make_h_transfer(int n);
 TransferTab make_p_interp_down(int nf, int nc);
 TransferTab make_h_interp_down(int n, int* child);
+LoadTab make_load_tab(int n);
 }  // namespace sipg
