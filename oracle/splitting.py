@@ -1,9 +1,11 @@
-"""One time step of the dual splitting (projection) scheme on a box (oracle, test infrastructure).
+"""One time step of the dual splitting (projection) scheme on affine grids (oracle, test infrastructure).
 
 Sec. 3.2 / 5.1 / 5.4, Alg. 1 of the paper, with the convective term explicit
-(alpha_c = 0), on a box of affine hexahedra whose six walls carry steady
-Dirichlet velocity data g (one constant vector per box face: no-slip walls, or
-the moving lid of a cavity). Every form below is evaluated element by element
+(alpha_c = 0), on grids of affine hexahedra (oracle.mesh: the box, the
+backward-facing-step channel) whose Dirichlet faces carry velocity data g per
+boundary id (constant vectors: no-slip walls, the moving lid of a cavity; or
+functions of the position: the inflow profile, optionally ramped in time), and
+whose outflow faces are velocity Neumann (traction free) with p = 0. Every form below is evaluated element by element
 with explicit basis functions at the Gauss points, as written in the paper:
 
 * BDF-m and extrapolation coefficients (textbook values, "see Hairer1993";
@@ -466,7 +468,7 @@ def pressure_solve(Sp_op, rhs):
 
 
 class Splitting:
-    """State and one-step driver of the projection scheme on a box."""
+    """State and one-step driver of the projection scheme."""
 
     def __init__(self, mesh, k, rheology, g_faces=None, body=None, viscosity_mode='linear', penalty_factor=1.0,
                  convective='explicit', ramp=None, t0=0.0):

@@ -14,7 +14,7 @@
 //   pen_tau_kernel    ubar_e by Gauss quadrature -> tau_div,e, tau_cont,e
 //   pen_apply_kernel  y = K x (cell mass + div-div + normal-jump terms)
 //   pen_wall_kernel   y += (v.n, tau_cont,e g.n) over Dirichlet walls
-// On the box the face normal is +-e_d, so the jump term acts on component d
+// On affine grid cells the face normal is +-e_d, so the jump term acts on component d
 // only, on the face layer of Gauss-Lobatto coefficients (the trace of the
 // nodal basis). The system is symmetric positive definite and close to the
 // mass matrix (the penalties scale with the Courant number), so it is solved
@@ -224,7 +224,7 @@ namespace {
 
 int check_penalty(sipg_ctx* ctx) {
   if (ctx->opts.k_u < 2 || ctx->opts.k_u > 5) return ctx->fail(SIPG_ERR_INVALID, "velocity degree 2..5");
-  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the penalty step is built for the box only");
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the penalty step is built for affine cells only");
   return SIPG_OK;
 }
 

@@ -1,4 +1,5 @@
-// Forms of one step of the projection scheme on a box (Sec. 3.2 / 5.1, Alg. 1),
+// Forms of one step of the projection scheme on affine grids (the box, the
+// backward-facing-step channel; Sec. 3.2 / 5.1, Alg. 1),
 // convective term explicit:
 //   conv_kernel       C_a = c_h(phi_a, u; u), Eq. (convective_term_weak), upwind flux,
 //                     mirror principle on Dirichlet walls

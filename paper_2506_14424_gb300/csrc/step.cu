@@ -1,4 +1,5 @@
-// One time step of the projection (dual splitting) scheme on a box, Sec. 3.2 /
+// One time step of the projection (dual splitting) scheme on affine grids (the
+// box, the backward-facing-step channel), Sec. 3.2 /
 // 5.1, Alg. 1, the convective term explicit (alpha_c = 0) or linearly implicit
 // in the viscous step (alpha_c = 1, u* = u#, GMRES): host sequence of library
 // kernels (split.cu forms, cell mass operators, MG-CG / GMRES solves, the
@@ -46,7 +47,7 @@ bool walls_ok(const sipg_ctx* ctx) {
 
 int check_forms(sipg_ctx* ctx) {
   if (ctx->opts.k_u < 2 || ctx->opts.k_u > 5) return ctx->fail(SIPG_ERR_INVALID, "velocity degree 2..5");
-  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the splitting-step forms are built for the box only");
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the splitting-step forms are built for affine cells only");
   return SIPG_OK;
 }
 
