@@ -32,14 +32,14 @@ CTab<T> make_ctab(const Tab& t) {
   return c;
 }
 
-template <int N, int NC, typename TS, typename TN, typename TC>
-cudaError_t launch_apply_n(const LevelGeom& g, const Tab& tab, const TS* x, TS* y, const TN* nu_cell,
+template <int N, int NC, typename TS, typename TN, typename TC, bool TOPO>
+cudaError_t launch_apply_g(const LevelGeom& g, const Tab& tab, const TS* x, TS* y, const TN* nu_cell,
                            const TN* nu_face, double mass, int nbatch, cudaStream_t st) {
   using Cfg = OpCfg<N, NC>;
   const size_t smem = sizeof(TC) * op_smem_elems<N, NC>();
   static bool attr_set = false;  // per instantiation, per process (single device)
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, NC, TS, TN, TC>,
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<N, NC, TS, TN, TC, TOPO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -47,9 +47,17 @@ cudaError_t launch_apply_n(const LevelGeom& g, const Tab& tab, const TS* x, TS* 
   const int grid = (g.ncells + Cfg::CPB - 1) / Cfg::CPB;
   if (grid == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
-  apply_kernel<N, NC, TS, TN, TC><<<dim3(grid, nbatch), Cfg::NT, smem, st>>>(g, make_ctab<TC>(tab), x, y, nu_cell,
-                                                                             nu_face, mass, stride);
+  apply_kernel<N, NC, TS, TN, TC, TOPO><<<dim3(grid, nbatch), Cfg::NT, smem, st>>>(g, make_ctab<TC>(tab), x, y,
+                                                                                   nu_cell, nu_face, mass, stride);
   return cudaGetLastError();
+}
+
+// the plain box (no topology tables) keeps the arithmetic neighbour path
+template <int N, int NC, typename TS, typename TN, typename TC>
+cudaError_t launch_apply_n(const LevelGeom& g, const Tab& tab, const TS* x, TS* y, const TN* nu_cell,
+                           const TN* nu_face, double mass, int nbatch, cudaStream_t st) {
+  return g.nbr ? launch_apply_g<N, NC, TS, TN, TC, true>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st)
+               : launch_apply_g<N, NC, TS, TN, TC, false>(g, tab, x, y, nu_cell, nu_face, mass, nbatch, st);
 }
 
 template <typename TS, typename TN, typename TC>

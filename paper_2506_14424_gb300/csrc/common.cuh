@@ -126,6 +126,26 @@ __host__ __device__ inline int cell_neighbor(const LevelGeom& g, int e, int f) {
   return (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
 }
 
+// Compile-time variants for kernels instantiated per kind of grid (TOPO: the
+// topology tables are present); the plain box keeps its arithmetic path.
+template <bool TOPO>
+__host__ __device__ inline int cell_neighbor_t(const LevelGeom& g, int e, int f) {
+  if (TOPO) {
+    const int v = g.nbr[e * 6 + f];
+    return v >= 0 ? v : -1;
+  }
+  const int d = f >> 1, s = f & 1;
+  int ijk[3] = {e % g.nx, (e / g.nx) % g.ny, e / (g.nx * g.ny)};
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  ijk[d] += s ? 1 : -1;
+  if (ijk[d] < 0 || ijk[d] >= dims[d]) return -1;
+  return (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+}
+template <bool TOPO>
+__host__ __device__ inline int face_bc_t(const LevelGeom& g, int e, int f) {
+  return TOPO ? g.bc[(-1 - g.nbr[e * 6 + f]) & 7] : g.bc[f];
+}
+
 // boundary id of the boundary face (e, f) (the grid side f on the plain box)
 __host__ __device__ inline int boundary_id(const LevelGeom& g, int e, int f) {
   return g.nbr ? ((-1 - g.nbr[e * 6 + f]) & 7) : f;
@@ -150,6 +170,16 @@ __host__ __device__ inline double penalty_lambda(const LevelGeom& g, int e) {
   double lam = 0.0;
   for (int f = 0; f < 6; ++f) {
     const double w = cell_neighbor(g, e, f) >= 0 ? 0.5 : 1.0;
+    lam += w * g.ih[f >> 1];
+  }
+  return lam;
+}
+
+template <bool TOPO>
+__host__ __device__ inline double penalty_lambda_t(const LevelGeom& g, int e) {
+  double lam = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    const double w = cell_neighbor_t<TOPO>(g, e, f) >= 0 ? 0.5 : 1.0;
     lam += w * g.ih[f >> 1];
   }
   return lam;

@@ -175,7 +175,7 @@ __device__ __forceinline__ void load_tables(const CTab<T>& ct, T* dS0, T* dS1, T
 template <typename T>
 __device__ __forceinline__ T sel3(const T* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
 
-template <int N, int NC, typename TN, typename T>
+template <int N, int NC, typename TN, typename T, bool TOPO>
 __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int cell0, int ncell, int FS, int CPB,
                                                const T* ih, const T* gw, const T* pen,
                                                const TN* __restrict__ nu_face, T* F) {
@@ -190,7 +190,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
     const int a = p % N, b = p / N;
     const int e = cell0 + c;
     const int f = 2 * D + s;
-    const int nb = cell_neighbor(g, e, f);
+    const int nb = cell_neighbor_t<TOPO>(g, e, f);
     T* gV = F + (s * 8 + 0) * FS;
     T* gN = F + (s * 8 + 1) * FS;
     const T* gVp = F + (s * 8 + 2) * FS;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
     T* gT1 = F + (s * 8 + 5) * FS;
     const T* gT2p = F + (s * 8 + 6) * FS;
     const T* gT1p = F + (s * 8 + 7) * FS;
-    if (nb < 0 && face_bc(g, e, f) == 1) {  // homogeneous Neumann: no face term
+    if (nb < 0 && face_bc_t<TOPO>(g, e, f) == 1) {  // homogeneous Neumann: no face term
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const int j = (c * NC + k) * N2 + p;
@@ -294,7 +294,7 @@ __device__ __forceinline__ T line_dot(const T* M, const T* v, int o) {
 // serves the three directions (the direction only changes indices), which
 // keeps the unrolled float-float code within the instruction cache.
 // S and Dg point to shared-memory copies of the 1D matrices.
-template <int N, int NC, typename TS, typename TN, typename T>
+template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
 __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, const T* Dg, int cell0, int ncell,
                                        int CPB, const TS* __restrict__ x, const TN* __restrict__ nu_face,
                                        const T* Xs, T* Y, T* F, T* pen, const T* ih, const T* gw,
@@ -321,7 +321,7 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     T* Fs = F + s * 8 * FS;
     Fs[rem] = xs[(s ? N - 1 : 0) * STD];
     Fs[FS + rem] = dn.get();
-    const int nb = cell_neighbor(g, e, 2 * D + s);
+    const int nb = cell_neighbor_t<TOPO>(g, e, 2 * D + s);
     if (nb >= 0) {
       const TS* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
       T v[N];
@@ -340,9 +340,9 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
   for (int i = threadIdx.x; i < 2 * ncell; i += blockDim.x) {
     const int s = i / ncell, c = i - s * ncell;
     const int e = cell0 + c;
-    const int nb = cell_neighbor(g, e, 2 * D + s);
-    const double lm = penalty_lambda(g, e);
-    const double lp = nb >= 0 ? penalty_lambda(g, nb) : lm;
+    const int nb = cell_neighbor_t<TOPO>(g, e, 2 * D + s);
+    const double lm = penalty_lambda_t<TOPO>(g, e);
+    const double lp = nb >= 0 ? penalty_lambda_t<TOPO>(g, nb) : lm;
     pen[s * CPB + c] = from_double<T>(g.cip * double(N * N) * (lm > lp ? lm : lp));
   }
   __syncthreads();
@@ -415,7 +415,7 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     __syncthreads();
   }
   // (E) numerical flux
-  face_flux_pair<N, NC, TN, T>(D, g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
+  face_flux_pair<N, NC, TN, T, TOPO>(D, g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
   __syncthreads();
   // (F) test side, along a: slot 2 = gV + Dg_a^T gT1
   for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
@@ -496,7 +496,7 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
 // NC = 1: Poisson operator (nu pointers unused).
 // TS is the storage type of x and y, TN that of nu, T the arithmetic type
 // (double, float, or ff = float-float with double x/y and pre-split nu).
-template <int N, int NC, typename TS, typename TN, typename T>
+template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
 __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const TS* __restrict__ x,
                                             TS* __restrict__ y, const TN* __restrict__ nu_cell,
                                             const TN* __restrict__ nu_face, double mass_d, int cell0, T* sm) {
@@ -604,27 +604,30 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
 
   // ---- face terms, both faces of one direction at a time (work region reused)
   for (int d = 0; d < 3; ++d)
-    face_pair<N, NC, TS, TN, T>(d, g, Ssh, Dsh, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0, dS1);
+    face_pair<N, NC, TS, TN, T, TOPO>(d, g, Ssh, Dsh, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0,
+                                      dS1);
   for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(Y[i]);
 }
 
 // One CTA per CPB consecutive cells of one level; blockIdx.y selects one of
-// several vectors applied in the same launch (columns of a batch).
-template <int N, int NC, typename TS, typename TN, typename T>
+// several vectors applied in the same launch (columns of a batch). TOPO: the
+// level has topology tables (removed cells or periodic directions).
+template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
 __global__ void __launch_bounds__(OpCfg<N, NC>::NT, (OccCfg<N, NC, T>::MIN))
 apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
              const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
-  apply_cells<N, NC, TS, TN, T>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
-                                reinterpret_cast<T*>(smem_raw));
+  apply_cells<N, NC, TS, TN, T, TOPO>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
+                                      reinterpret_cast<T*>(smem_raw));
 }
 
 // Operator applies of several problems of the same degree in one persistent
 // launch: tile i = (problem, first cell) of tiles[]; CTAs stride over the
 // tile list (static round robin, deterministic: every tile is computed by
 // exactly the same code as in apply_kernel, so results are bitwise equal).
+// The served problems are plain boxes (no topology tables).
 template <typename TS, typename TN>
 struct ApplyDesc {
   LevelGeom g;
@@ -643,8 +646,8 @@ apply_multi_kernel(const ApplyDesc<TS, TN>* __restrict__ descs, const int2* __re
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int2 tl = tiles[tile];
     const ApplyDesc<TS, TN> d = descs[tl.x];
-    apply_cells<N, NC, TS, TN, T>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y,
-                                  reinterpret_cast<T*>(smem_raw));
+    apply_cells<N, NC, TS, TN, T, false>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y,
+                                         reinterpret_cast<T*>(smem_raw));
     __syncthreads();  // the next tile reuses the shared memory
   }
 }
