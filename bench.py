@@ -348,13 +348,19 @@ def gpu_extras(ctx, xs, ys, stream):
         c3.close()
         solves.append(row)
     out["cfg3_mg_solves_16cubed_k4"] = solves
-    out["mass_32cubed_k3"] = mass_timings(ctx, xs, ys, stream)
-    out["picard_viscous_step_32cubed_k3"] = picard_extras(ctx)
-    out["splitting_step_32cubed_k3"] = step_extras()
-    out["trilinear_cells_32cubed_k3"] = trilinear_extras()
-    out["bfs_channel_steps"] = channel_extras()
-    out["components_16cubed_k4"] = component_timings(stream)
-    out["serving"] = serving_extras()
+    # each further workload on its own: a failure is recorded in its entry, the line still prints
+    for key, fn in (("mass_32cubed_k3", lambda: mass_timings(ctx, xs, ys, stream)),
+                    ("picard_viscous_step_32cubed_k3", lambda: picard_extras(ctx)),
+                    ("splitting_step_32cubed_k3", step_extras),
+                    ("trilinear_cells_32cubed_k3", trilinear_extras),
+                    ("bfs_channel_steps", channel_extras),
+                    ("components_16cubed_k4", lambda: component_timings(stream)),
+                    ("serving", serving_extras)):
+        try:
+            out[key] = fn()
+        except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+            out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.synchronize()
     return out
 
 
