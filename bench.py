@@ -360,7 +360,6 @@ def gpu_extras(ctx, xs, ys, stream):
             out[key] = fn()
         except Exception as exc:  # noqa: BLE001 - reported in the JSON line
             out[key] = {"error": f"{type(exc).__name__}: {exc}"}
-            torch.cuda.synchronize()
     return out
 
 
