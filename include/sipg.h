@@ -458,6 +458,18 @@ int sipg_penalty_step(sipg_ctx* ctx, const double* wall_g, const double* u, doub
  * floats and n doubles, on the context's stream (sync). */
 int sipg_ff_convert(sipg_ctx* ctx, const double* x, float* hilo, double* back, int64_t n);
 
+/* Host-only test hooks of the grid topology (no GPU needed): for an nx x ny x nz
+ * grid with active flags (HOST, x fastest, NULL = every cell) and periodic[3],
+ * sipg_topology_tables sets *ncells and *nbf and, where the pointers are not NULL,
+ * fills nbr (6 * ncells ints: the cell across each face, or -1 - (boundary id +
+ * 8 * boundary-face number)) and bface (nbf ints: cell * 6 + face), the tables the
+ * kernels read. sipg_coarsen_mask writes the active flags of the once-coarsened
+ * grid (nx/2 x ny/2 x nz/2) and returns 1, or returns 0 when a 2x2x2 block mixes
+ * active and removed cells. */
+int sipg_topology_tables(int nx, int ny, int nz, const unsigned char* active, const int* periodic, int* ncells,
+                         int* nbf, int* nbr, int* bface);
+int sipg_coarsen_mask(int nx, int ny, int nz, const unsigned char* fine, unsigned char* coarse);
+
 /* Copy the stored viscosity of a level to DEVICE buffers: nu_cell
  * [cells][n^3] and nu_face [cells][6][n^2] (the cell's own side of each face;
  * faces -x,+x,-y,+y,-z,+z; face point a + n b over the face's tangential

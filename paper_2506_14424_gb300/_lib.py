@@ -33,7 +33,7 @@ EXPORTS = [
     "sipg_step_init", "sipg_step", "sipg_step_field", "sipg_cfl_dt", "sipg_convective_apply",
     "sipg_projection_rhs", "sipg_viscous_wall_rhs", "sipg_solve_convective", "sipg_convective_lin_apply",
     "sipg_penalty_tau", "sipg_penalty_apply", "sipg_penalty_wall_rhs", "sipg_penalty_step",
-    "sipg_boundary_faces", "sipg_rhs_manufactured",
+    "sipg_boundary_faces", "sipg_rhs_manufactured", "sipg_topology_tables", "sipg_coarsen_mask",
 ]
 FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
 VISC_MODE = {"linear": 0, "implicit": 1}
@@ -187,6 +187,8 @@ def load(path=None):
         "sipg_penalty_step": (i, [vp, vp, vp, d, d, d, d, i, vp, P(i), P(d)]),
         "sipg_boundary_faces": (i, [vp, P(i), vp, vp]),
         "sipg_rhs_manufactured": (i, [vp, i, vp]),
+        "sipg_topology_tables": (i, [i, i, i, vp, vp, P(i), P(i), vp, vp]),
+        "sipg_coarsen_mask": (i, [i, i, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

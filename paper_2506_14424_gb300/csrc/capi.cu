@@ -15,6 +15,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <algorithm>
 
 using namespace sipg;
 
@@ -491,6 +492,26 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   }
   *out = ctx;
   return SIPG_OK;
+}
+
+extern "C" int sipg_topology_tables(int nx, int ny, int nz, const unsigned char* active, const int* periodic,
+                                    int* ncells, int* nbf, int* nbr, int* bface) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || !periodic || !ncells || !nbf) return SIPG_ERR_INVALID;
+  if ((int64_t)nx * ny * nz > (int64_t)1 << 28) return SIPG_ERR_INVALID;
+  const HostTopo t = host_topology(nx, ny, nz, active, periodic);
+  *ncells = t.ncells;
+  *nbf = t.nbf;
+  if (nbr) std::copy(t.nbr.begin(), t.nbr.end(), nbr);
+  if (bface) std::copy(t.bface.begin(), t.bface.end(), bface);
+  return SIPG_OK;
+}
+
+extern "C" int sipg_coarsen_mask(int nx, int ny, int nz, const unsigned char* fine, unsigned char* coarse) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 2 || ny % 2 || nz % 2 || !fine || !coarse) return SIPG_ERR_INVALID;
+  std::vector<unsigned char> f(fine, fine + (size_t)nx * ny * nz), c;
+  if (!coarsen_mask(nx, ny, nz, f, &c)) return 0;
+  std::copy(c.begin(), c.end(), coarse);
+  return 1;
 }
 
 // Device bytes a context of this mesh and options allocates (no allocation).

@@ -1,0 +1,111 @@
+"""Host logic of the grid topology (no GPU): the tables the kernels read for grids with
+removed cells and periodic directions, and the masked coarsening of the multigrid
+hierarchy, computed by the C library's host code, equal the oracle's mesh.
+
+* neighbour of every face (periodic wrap, removed cells), boundary id and
+  boundary-face number of every boundary face, the boundary-face list;
+* coarsened active flags, and the refusal when a 2x2x2 block mixes active and
+  removed cells;
+* the dry run of the hierarchy allocation (sipg_estimate_bytes) on the cfg-4
+  channel grid.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle.mesh import BoxMesh
+from paper_2506_14424_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_14424_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def _tables(lib, dims, active, periodic):
+    act = None if active is None else np.ascontiguousarray(np.asarray(active, dtype=np.uint8).reshape(-1))
+    ap = None if act is None else act.ctypes.data_as(ctypes.c_void_p)
+    per = (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+    nc, nb = ctypes.c_int(), ctypes.c_int()
+    assert lib.sipg_topology_tables(*dims, ap, per, ctypes.byref(nc), ctypes.byref(nb), None, None) == 0
+    nbr = np.zeros(6 * nc.value, dtype=np.int32)
+    bface = np.zeros(max(nb.value, 1), dtype=np.int32)
+    assert lib.sipg_topology_tables(*dims, ap, per, ctypes.byref(nc), ctypes.byref(nb),
+                                    nbr.ctypes.data_as(ctypes.c_void_p), bface.ctypes.data_as(ctypes.c_void_p)) == 0
+    return nc.value, nb.value, nbr, bface[:nb.value]
+
+
+CASES = [
+    ("channel m=2", lambda: inputs.bfs_channel(2, inlet_length=1.0, outlet_length=3.0, depth=1.0)),
+    ("channel m=4", lambda: inputs.bfs_channel(4, inlet_length=1.0, outlet_length=3.0, depth=1.0)),
+    ("periodic box", lambda: {"dims": (3, 4, 2), "extent": (1.0, 1.0, 1.0), "lo": (0.0, 0.0, 0.0), "active": None,
+                              "periodic": (True, False, True)}),
+    ("holes", lambda: {"dims": (4, 3, 3), "extent": (1.0, 1.0, 1.0), "lo": (0.0, 0.0, 0.0),
+                       "active": np.random.default_rng(5).uniform(size=(3, 3, 4)) > 0.3,
+                       "periodic": (False, True, False)}),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_topology_tables_match_oracle(lib, name, make):
+    c = make()
+    mesh = BoxMesh(*c["dims"], extent=c["extent"], lo=c["lo"], active=c["active"], periodic=c["periodic"])
+    ncells, nbf, nbr, bface = _tables(lib, c["dims"], c["active"], c["periodic"])
+    assert ncells == mesh.n_cells
+    faces = mesh.boundary_faces()
+    assert nbf == len(faces)
+    assert list(bface) == [e * 6 + f for e, f in faces]
+    number = {ef: i for i, ef in enumerate(faces)}
+    for e in range(mesh.n_cells):
+        for f in range(6):
+            v = int(nbr[e * 6 + f])
+            nb = mesh.neighbor(e, f)
+            if nb is not None:
+                assert v == nb, (e, f)
+            else:
+                w = -1 - v
+                assert v < 0 and (w & 7) == mesh.boundary_id(e, f) and (w >> 3) == number[(e, f)], (e, f)
+
+
+def test_coarsen_mask_matches_oracle(lib):
+    c = inputs.bfs_channel(4, inlet_length=1.0, outlet_length=3.0, depth=1.0)
+    fine = np.ascontiguousarray(c["active"].astype(np.uint8).reshape(-1))
+    nx, ny, nz = c["dims"]
+    out = np.zeros(fine.size // 8, dtype=np.uint8)
+    assert lib.sipg_coarsen_mask(nx, ny, nz, fine.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p)) == 1
+    ref = BoxMesh(*c["dims"], extent=c["extent"], lo=c["lo"], active=c["active"], periodic=c["periodic"]).coarsen()
+    assert np.array_equal(out.astype(bool), ref.active)
+    bad = fine.copy()
+    bad[0] = 1 - bad[0]   # one cell of a block flipped
+    assert lib.sipg_coarsen_mask(nx, ny, nz, bad.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p)) == 0
+
+
+def test_estimate_bytes_of_the_channel(lib):
+    from paper_2506_14424_gb300 import _lib
+    c = inputs.bfs_channel(8)
+    m = _lib.MeshDesc()
+    m.nx, m.ny, m.nz = c["dims"]
+    m.lx, m.ly, m.lz = c["extent"]
+    for i, b in enumerate("DNDDDD"):
+        m.bc_velocity[i] = _lib.BC[b]
+    for i, b in enumerate("NDNNNN"):
+        m.bc_pressure[i] = _lib.BC[b]
+    act = np.ascontiguousarray(c["active"].astype(np.uint8).reshape(-1))
+    m.active = act.ctypes.data
+    m.bc_removed_velocity, m.bc_removed_pressure = 0, 1
+    m.periodic[2] = 1
+    for d in range(3):
+        m.origin[d] = c["lo"][d]
+    o = _lib.Opts()
+    lib.sipg_default_opts(ctypes.byref(o))
+    o.coarse_max_dofs = 8000
+    nbytes = ctypes.c_int64()
+    assert lib.sipg_estimate_bytes(ctypes.byref(m), ctypes.byref(o), ctypes.byref(nbytes)) == 0
+    n_vel = 133120 * 3 * 64
+    # at least the fine-level work vectors; well below the GPU's memory
+    assert 10 * 8 * n_vel < nbytes.value < 60e9
