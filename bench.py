@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -81,7 +82,9 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples (the summary goes into the JSON line); SIPG_BENCH_DIR keeps them
+        out_dir = os.environ.get("SIPG_BENCH_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -121,7 +124,7 @@ class Clocks:
 
 
 # ------------------------------------------------------------ shared input
-def cfg2_velocity(node_points):
+def fourier_velocity(node_points):
     from paper_2506_14424_gb300 import inputs
     modes = inputs.fourier_modes(1)
     C = N_CELLS ** 3
@@ -152,11 +155,11 @@ def traffic_record(kernel_key):
     return rec["dram_bytes_per_launch"]
 
 
-# FP64 peak of this machine's GB300: own FMA-chain micro-benchmark.
+# FP64 peak of the GB300: own FMA-chain micro-benchmark (1.01 TFLOP/s measured).
 FP64_PEAK_TFLOPS = 1.01
 # FP64-equivalent peak of float-float arithmetic on the FP32 pipe: 128 FP32 lanes x
 # 152 SMs x 2.07 GHz = 40.3e12 instructions/s, 12 instructions per float-float
-# multiply-add (2 flops) -> 6.71 TFLOP/s (derivation in the design doc).
+# multiply-add (exact product 4, TwoSum 6, low-word adds 2; 2 flops) -> 6.71 TFLOP/s.
 FF_PEAK_TFLOPS = 128 * 152 * 2.07e9 / 12 * 2 / 1e12
 # Algorithmic flops per DoF of the k=3 viscous apply (minimal sum-factorised count).
 FLOP_PER_DOF = 250.0
@@ -198,7 +201,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U, krylov_arith=args.arith)  # e2e uses the same arithmetic
     n = ctx.n_dofs("viscous")
-    u = torch.tensor(cfg2_velocity(ctx.node_points("viscous", 0)), device="cuda")
+    u = torch.tensor(fourier_velocity(ctx.node_points("viscous", 0)), device="cuda")
     ctx.set_viscosity(inputs.carreau_blood_like(), u)
     del u
     pairs = 4
@@ -347,7 +350,7 @@ def gpu_extras(ctx, xs, ys, stream):
                           "rel_error_vs_ustar": (torch.linalg.norm(x - ustar) / torch.linalg.norm(ustar)).item()}
         c3.close()
         solves.append(row)
-    out["cfg3_mg_solves_16cubed_k4"] = solves
+    out["sinker_mg_solves_16cubed_k4"] = solves
     # each further workload on its own: a failure is recorded in its entry, the line still prints
     for key, fn in (("mass_32cubed_k3", lambda: mass_timings(ctx, xs, ys, stream)),
                     ("picard_viscous_step_32cubed_k3", lambda: picard_extras(ctx)),
@@ -417,7 +420,7 @@ def picard_extras(ctx, dt=1e-2):
 def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
     """Projection-scheme time steps on a lid-driven box (lid velocity (1, 0, 0)
     on +z, no-slip elsewhere), Carreau-Yasuda viscosity linear implicit, the
-    cfg-2 Fourier field as initial velocity, dt from the CFL rule (Cr = 0.3),
+    seeded Fourier field as initial velocity, dt from the CFL rule (Cr = 0.3),
     pressure and viscous CG to 1e-8. Host-clock step times (the step
     synchronises); CUDA-event times of the step's form kernels."""
     import numpy as np

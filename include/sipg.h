@@ -498,7 +498,7 @@ int sipg_node_points(const sipg_ctx* ctx, int op, int level, double* xyz_host);
 int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* opts, int64_t* bytes);
 
 /* ------------------------------------------------------------- serving
- * Continuous-batching solve server (spec systems pattern; the paper's
+ * Continuous-batching solve server (a systems pattern around the solver; the paper's
  * solver is Sec. 5.4): requests are admitted when a slot is free and their
  * context fits the HBM budget, every active request advances one FP64 CG
  * iteration (float-float operator, FP32 hp-multigrid V-cycle) per round, the

@@ -1,9 +1,9 @@
 """GPU parity of the manufactured-solution loads (sipg_rhs_manufactured) against the
-oracle's over-integrated load vectors, and the cfg-1 manufactured solve end to end.
+oracle's over-integrated load vectors, and the 4^3, k = 2 manufactured solve end to end.
 
 * velocity case (u = s(x) (1, -1, 2), analytic viscosity) and pressure case
   (p = cos cos cos, -lap p = 3 pi^2 p), degrees 2..5, boxes of unequal sides;
-* the viscous MG-CG solve of the cfg-1 problem (4^3 cells, k = 2) from the GPU load
+* the viscous MG-CG solve of the 4^3-cell, k = 2 problem from the GPU load
   reaches the oracle's sparse-LU solution, whose L2 error against u the oracle's
   convergence pin bounds.
 """
@@ -39,7 +39,7 @@ def test_manufactured_loads_match_oracle(dims, k, ext):
     ctx.close()
 
 
-def test_cfg1_manufactured_solve():
+def test_4cubed_k2_manufactured_solve():
     dims, k = (4, 4, 4), 2
     ctx = Context(*dims, k)
     ctx.set_viscosity({'law': 'analytic'})

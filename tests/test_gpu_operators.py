@@ -135,7 +135,7 @@ def test_symmetry_of_gpu_applies():
     assert abs(a - b) <= 1e-12 * abs(a)
 
 
-def test_cfg2_full_size_sampled_rows():
+def test_full_size_32cubed_sampled_rows():
     """32^3 cells, k = 3, Carreau-Yasuda from the Fourier field: sampled rows."""
     N, k = 32, 3
     mesh = BoxMesh(N, N, N)

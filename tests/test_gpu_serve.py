@@ -1,4 +1,4 @@
-"""Continuous-batching server on the GPU (spec serving pattern).
+"""Continuous-batching server on the GPU (the serving pattern of the solver).
 
 * every request converges to rtol 1e-8 (true residual), in the mix as alone;
 * a request's solution is bitwise the same alone and batched with others of

@@ -129,7 +129,7 @@ def test_vcycle_f64_matches_oracle_vcycle(op, bc):
     assert _rel(x, ref) <= 1e-10
 
 
-def test_cfg1_jacobi_cg_matches_oracle():
+def test_4cubed_k2_jacobi_cg_matches_oracle():
     """4^3 cells, k = 2, analytic viscosity, Dirichlet walls, manufactured load."""
     mesh = BoxMesh(4, 4, 4)
     S = SIPG(mesh, 2, 3)

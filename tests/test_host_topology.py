@@ -6,8 +6,8 @@ hierarchy, computed by the C library's host code, equal the oracle's mesh.
   boundary-face number of every boundary face, the boundary-face list;
 * coarsened active flags, and the refusal when a 2x2x2 block mixes active and
   removed cells;
-* the dry run of the hierarchy allocation (sipg_estimate_bytes) on the cfg-4
-  channel grid.
+* the dry run of the hierarchy allocation (sipg_estimate_bytes) on the
+  133,120-cell channel grid.
 """
 import ctypes
 

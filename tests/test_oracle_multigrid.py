@@ -45,7 +45,7 @@ def test_h_prolongation_exact(k):
                   - Sc.interpolate(_poly)).max() < 1e-13
 
 
-def test_level_sequence_cfg3_shape():
+def test_level_sequence_16cubed_k4_shape():
     levels = mg.level_sequence(BoxMesh(16, 16, 16), 4, 3)
     desc = [(m.n_cells_dir[0], k) for m, k in levels]
     assert desc == [(16, 4), (16, 2), (16, 1), (8, 1), (4, 1)]
