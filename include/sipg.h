@@ -470,6 +470,14 @@ int sipg_topology_tables(int nx, int ny, int nz, const unsigned char* active, co
                          int* nbf, int* nbr, int* bface);
 int sipg_coarsen_mask(int nx, int ny, int nz, const unsigned char* fine, unsigned char* coarse);
 
+/* Host-only test hook: the multigrid level sequence sipg_create would build for this
+ * mesh and these options, without allocating (a dry run of the hierarchy):
+ * *nlevels levels of operator op; with info (HOST, 6 ints per level, at most
+ * max_levels) the grid nx, ny, nz, the degree, the active cells and the DoFs
+ * (clamped to INT_MAX) of each level, finest first. */
+int sipg_level_plan(const sipg_mesh_desc* mesh, const sipg_opts* opts, int op, int max_levels, int* nlevels,
+                    int* info);
+
 /* Copy the stored viscosity of a level to DEVICE buffers: nu_cell
  * [cells][n^3] and nu_face [cells][6][n^2] (the cell's own side of each face;
  * faces -x,+x,-y,+y,-z,+z; face point a + n b over the face's tangential

@@ -34,6 +34,7 @@ EXPORTS = [
     "sipg_projection_rhs", "sipg_viscous_wall_rhs", "sipg_solve_convective", "sipg_convective_lin_apply",
     "sipg_penalty_tau", "sipg_penalty_apply", "sipg_penalty_wall_rhs", "sipg_penalty_step",
     "sipg_boundary_faces", "sipg_rhs_manufactured", "sipg_topology_tables", "sipg_coarsen_mask",
+    "sipg_level_plan",
 ]
 FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
 VISC_MODE = {"linear": 0, "implicit": 1}
@@ -189,6 +190,7 @@ def load(path=None):
         "sipg_rhs_manufactured": (i, [vp, i, vp]),
         "sipg_topology_tables": (i, [i, i, i, vp, vp, P(i), P(i), vp, vp]),
         "sipg_coarsen_mask": (i, [i, i, i, vp, vp]),
+        "sipg_level_plan": (i, [P(MeshDesc), P(Opts), i, i, P(i), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

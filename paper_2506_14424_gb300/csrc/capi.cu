@@ -547,6 +547,48 @@ extern "C" int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* 
   return SIPG_OK;
 }
 
+extern "C" int sipg_level_plan(const sipg_mesh_desc* mesh, const sipg_opts* opts_in, int op, int max_levels,
+                               int* nlevels, int* info) {
+  if (!mesh || !nlevels || (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) || max_levels < 0) return SIPG_ERR_INVALID;
+  sipg_opts o;
+  sipg_default_opts(&o);
+  if (opts_in) {
+    o = *opts_in;
+    sipg_opts d;
+    sipg_default_opts(&d);
+    if (o.coarse_max_dofs == 0) o.coarse_max_dofs = d.coarse_max_dofs;
+    if (o.k_u == 0) o.k_u = d.k_u;
+  }
+  if (o.k_u < 2 || o.k_u > 5 || mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return SIPG_ERR_INVALID;
+  sipg_ctx probe;
+  probe.dry = true;
+  probe.mesh = *mesh;
+  probe.opts = o;
+  probe.mapped = mesh->vertices != nullptr;
+  probe.topo = mesh_topology(mesh);
+  if (mesh->active) probe.mask.assign(mesh->active, mesh->active + (size_t)mesh->nx * mesh->ny * mesh->nz);
+  probe.mesh.active = nullptr;
+  probe.mesh.vertices = nullptr;
+  int rc = probe.build_hierarchy(op);
+  if (rc) return rc;
+  const std::vector<Level>& L = probe.hier[op].L;
+  *nlevels = (int)L.size();
+  for (int l = 0; info && l < (int)L.size() && l < max_levels; ++l) {
+    int* r = info + 6 * l;
+    r[0] = L[l].g.nx;
+    r[1] = L[l].g.ny;
+    r[2] = L[l].g.nz;
+    r[3] = L[l].k;
+    r[4] = L[l].g.ncells;
+    r[5] = (int)std::min<int64_t>(L[l].ndofs, 2147483647);
+  }
+  for (sipg::Hier& H : probe.hier)
+    for (sipg::Level& Lv : H.L)
+      for (int p = 0; p < 2; ++p)
+        for (int v = 0; v < 4; ++v) Lv.w[p][v] = nullptr;
+  return SIPG_OK;
+}
+
 extern "C" int sipg_destroy(sipg_ctx* ctx) {
   if (!ctx) return SIPG_ERR_INVALID;
   cudaStreamSynchronize(ctx->st);

@@ -7,7 +7,10 @@ hierarchy, computed by the C library's host code, equal the oracle's mesh.
 * coarsened active flags, and the refusal when a 2x2x2 block mixes active and
   removed cells;
 * the dry run of the hierarchy allocation (sipg_estimate_bytes) on the
-  133,120-cell channel grid.
+  133,120-cell channel grid;
+* the multigrid level sequence of a dry hierarchy build (sipg_level_plan) equals
+  the oracle's level sequence (p-levels, masked h-coarsening, periodic minimum,
+  coarse-size threshold) for the channel, a box and a periodic grid.
 """
 import ctypes
 
@@ -109,3 +112,52 @@ def test_estimate_bytes_of_the_channel(lib):
     n_vel = 133120 * 3 * 64
     # at least the fine-level work vectors; well below the GPU's memory
     assert 10 * 8 * n_vel < nbytes.value < 60e9
+
+
+def _plan(lib, c, k, op, bc_v="DNDDDD", bc_p="NDNNNN", coarse=2000):
+    from paper_2506_14424_gb300 import _lib
+    m = _lib.MeshDesc()
+    m.nx, m.ny, m.nz = c["dims"]
+    m.lx, m.ly, m.lz = c["extent"]
+    for i in range(6):
+        m.bc_velocity[i] = _lib.BC[bc_v[i]]
+        m.bc_pressure[i] = _lib.BC[bc_p[i]]
+    act = None
+    if c["active"] is not None:
+        act = np.ascontiguousarray(np.asarray(c["active"], dtype=np.uint8).reshape(-1))
+        m.active = act.ctypes.data
+    m.bc_removed_velocity, m.bc_removed_pressure = 0, 1
+    for d in range(3):
+        m.periodic[d] = int(bool(c["periodic"][d]))
+        m.origin[d] = c["lo"][d]
+    o = _lib.Opts()
+    lib.sipg_default_opts(ctypes.byref(o))
+    o.k_u = k
+    o.coarse_max_dofs = coarse
+    nl = ctypes.c_int()
+    info = np.zeros(6 * 16, dtype=np.int32)
+    assert lib.sipg_level_plan(ctypes.byref(m), ctypes.byref(o), 0 if op == "viscous" else 1, 16,
+                               ctypes.byref(nl), info.ctypes.data_as(ctypes.c_void_p)) == 0
+    return info[:6 * nl.value].reshape(-1, 6)
+
+
+@pytest.mark.parametrize("name,make,k,coarse", [
+    ("channel m=8", lambda: inputs.bfs_channel(8), 3, 8000),
+    ("channel m=4 small", lambda: inputs.bfs_channel(4, inlet_length=1.0, outlet_length=3.0, depth=1.0), 2, 500),
+    ("box 16^3", lambda: {"dims": (16, 16, 16), "extent": (1.0, 1.0, 1.0), "lo": (0.0, 0.0, 0.0), "active": None,
+                          "periodic": (False, False, False)}, 4, 2000),
+    ("periodic 8x4x8", lambda: {"dims": (8, 4, 8), "extent": (1.0, 1.0, 1.0), "lo": (0.0, 0.0, 0.0), "active": None,
+                                "periodic": (True, False, True)}, 3, 300),
+])
+@pytest.mark.parametrize("op", ["viscous", "poisson"])
+def test_level_plan_matches_oracle_sequence(lib, name, make, k, coarse, op):
+    from oracle import multigrid as omg
+    c = make()
+    mesh = BoxMesh(*c["dims"], extent=c["extent"], lo=c["lo"], active=c["active"], periodic=c["periodic"])
+    ncomp, kk = (3, k) if op == "viscous" else (1, k - 1)
+    ref = omg.level_sequence(mesh, kk, ncomp, coarse_threshold=coarse)
+    plan = _plan(lib, c, k, op, coarse=coarse)
+    assert len(plan) == len(ref)
+    for row, (m, kl) in zip(plan, ref):
+        assert tuple(row[:3]) == m.n_cells_dir and row[3] == kl and row[4] == m.n_cells
+        assert row[5] == m.n_cells * ncomp * (kl + 1) ** 3
