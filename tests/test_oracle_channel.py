@@ -196,3 +196,16 @@ def test_jittered_channel_operators():
     Sa = SIPG(small_channel(2), 2, 3)
     Aa = Sa.assemble(*Sa.viscosity_at_points({'law': 'constant', 'nu': 0.4}))
     assert np.abs((A0 - Aa).toarray()).max() <= 1e-12 * np.abs(Aa.toarray()).max()
+
+
+def test_channel_penalty_step_keeps_a_compatible_field():
+    """Eq. (penalty_step) on the channel: u = (0, 0, c y) is continuous, divergence free and
+    periodic in z; with its own values as wall data on inflow, walls and step (the
+    outflow is Neumann: no term) both penalties vanish and the step returns u."""
+    mesh = small_channel(2)
+    S = SIPG(mesh, 2, 3)
+    ufn = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], 0.6 * x[:, 1]], axis=1)
+    u = S.interpolate(ufn)
+    ut, tdiv, tcon = osp.penalty_step(S, u, 0.2, [ufn] * 7)
+    assert np.all(tdiv > 0) and np.all(tcon > 0)
+    assert np.abs(ut - u).max() <= 1e-12
