@@ -7,9 +7,14 @@
 * Analytic field nu(x) = 1 + 9 sin^2(pi x) sin^2(pi y) sin^2(pi z) (contrast 10).
 * Sphere ("sinker") field: nu_max inside any sphere |x - c_i| <= r, nu_matrix
   elsewhere; a point on a sphere surface counts as inside.
-Pinned in tests by the law's limits (gdot = 0 gives eta_0, gdot -> infinity
-gives eta_inf, eta_0 = eta_inf gives a constant) and by simple shear, whose
-shear rate is the shear gradient itself.
+Pinned in tests/test_oracle_viscosity.py by the law's limits (gdot = 0 gives
+eta_0, the excess over eta_inf decays like (lambda gdot)^(b-1), eta_0 = eta_inf
+gives a constant), the closed-form value at lambda gdot = 1 (kappa = 1, a = 2,
+b = 1/2: eta_inf + (eta_0 - eta_inf) 2^(-1/4)), the power law at kappa = 0 for
+any a, the shear rates of simple shear (|gamma|), planar extension (2|e|) and a
+rigid rotation (0), frame invariance, closed-form values of the analytic field,
+the sphere test on a surface point, and the law evaluated from interpolated
+simple-shear and extension flows at every cell and face point.
 
 A rheology is a dict: {'law': 'constant', 'nu': v}, {'law': 'analytic'},
 {'law': 'sinker', 'centers': (m,3), 'radius': r, 'nu_max': a, 'nu_matrix': b,
