@@ -219,7 +219,8 @@ int sipg_apply_host(sipg_ctx* ctx, int op, const double* x_host, double* y_host,
  * fine level is rejected with SIPG_ERR_INVALID. All calls on a device share
  * that array, so calls that overlap on the GPU race: serialise them. The
  * first call on a device looks up the array's device address; make it before
- * any stream capture. (sync) */
+ * any stream capture. The device that was current at sipg_create must be
+ * current at the call, else SIPG_ERR_INVALID (nothing is copied). (sync) */
 int sipg_apply_host_static(sipg_ctx* ctx, int op, const double* x_host, double* y_host, double mass_coeff);
 
 /* Level-operator apply on multigrid level `level` (level 0 = fine). */
@@ -505,39 +506,63 @@ int sipg_node_points(const sipg_ctx* ctx, int op, int level, double* xyz_host);
  * (no allocation; used for admission by HBM budget). */
 int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* opts, int64_t* bytes);
 
+/* ---------------------------------------------------------- measurement
+ * FMA throughput of the current device's FP64 (prec SIPG_F64) or FP32
+ * (SIPG_F32) pipe in TFLOP/s (2 flops per multiply-add): independent FMA
+ * chains on every SM, timed with CUDA events after a warm-up launch. It is the
+ * ALU denominator of the benchmark's roofline fractions (the paper has no
+ * counterpart: it measures on CPUs). Allocates a few KB and a private stream
+ * for the call. (sync) */
+int sipg_alu_peak(int prec, double* tflops);
+
 /* ------------------------------------------------------------- serving
  * Continuous-batching solve server (a systems pattern around the solver; the paper's
  * solver is Sec. 5.4): requests are admitted when a slot is free and their
- * context fits the HBM budget, every active request advances one FP64 CG
- * iteration (float-float operator, FP32 hp-multigrid V-cycle) per round, the
- * fine-level operator applies of all active requests of a degree run in one
- * persistent launch, and requests join and leave between rounds. Each request
- * solves the viscous system on the unit cube (Dirichlet walls, sphere
- * viscosity) with b = A u*, u* uniform(-1,1) from its seed. One worker
- * thread drives the GPU; submit/poll/drain are thread-safe. */
+ * context fits the HBM budget, every active request advances one CG iteration
+ * (FP64 CG with the FP64 operator by default, or the float-float operator;
+ * FP32 or FP64 hp-multigrid V-cycle) per round, the fine-level operator
+ * applies of all active requests of a degree run in one persistent launch, and
+ * requests join and leave between rounds. Each request solves the viscous
+ * system A(nu) x = b on the unit cube (n^3 cells, Dirichlet walls) with its
+ * own viscosity field and right-hand side. One worker thread drives the GPU;
+ * submit/poll/drain are thread-safe. */
 typedef struct sipg_server sipg_server;
 typedef struct {
   uint64_t hbm_budget_bytes; /* device bytes the server's contexts may hold */
   int max_slots;             /* requests served concurrently */
   int mg_precision;          /* SIPG_F32 (default for serving) or SIPG_F64 */
   int cheb_degree;           /* 0 = 3 */
+  int krylov_arith;          /* operator of the CG iterations and the final residual:
+                                SIPG_F64 [0, default] or SIPG_F64_FF */
 } sipg_server_opts;
+/* Right-hand side of a request:
+ *  MANUFACTURED  b = A u* with u* uniform(-1, 1) drawn on the device from `seed`
+ *                (the result also reports ||x - u*|| / ||u*||)
+ *  BUOYANCY      b = M f, M the cell mass matrix, f the nodal interpolant of
+ *                -e_z chi(x), chi = 1 inside any sphere of a SINKER rheology
+ *                (|x - c| <= r) and 0 elsewhere (a sinking-sphere load)
+ *  HOST          b given in HOST memory (n_dofs doubles), copied by submit
+ *  DEVICE        b given in DEVICE memory of the server's device (n_dofs
+ *                doubles), copied at admission: keep it valid and unchanged
+ *                until sipg_server_poll reports the request done */
+enum { SIPG_RHS_MANUFACTURED = 0, SIPG_RHS_BUOYANCY = 1, SIPG_RHS_HOST = 2, SIPG_RHS_DEVICE = 3 };
 typedef struct {
   int n_cells;               /* n^3 cells on the unit cube */
   int k_u;                   /* degree 2..5 */
-  int n_spheres;
-  const double* centers;     /* HOST, 3*n_spheres, copied by submit */
-  double radius, nu_max, nu_matrix;
-  double rtol;               /* relative residual target */
+  const sipg_rheology* rheology; /* HOST, copied by submit (sphere centers too):
+                                SIPG_LAW_CONSTANT, ANALYTIC or SINKER */
+  int rhs;                   /* SIPG_RHS_* */
+  const double* b;           /* HOST or DEVICE right-hand side (rhs HOST / DEVICE) */
+  double rtol;               /* relative residual target ||b - A x|| <= rtol ||b|| */
   int maxit;
-  uint64_t seed;             /* of u* */
+  uint64_t seed;             /* of u* (rhs MANUFACTURED) */
   int keep_solution;         /* keep x for sipg_server_poll */
 } sipg_request;
 typedef struct {
   int status;                /* SIPG_OK, SIPG_ERR_MAXIT, SIPG_ERR_BREAKDOWN, SIPG_ERR_NOMEM, ... */
   int iterations;
-  double rel_residual;       /* true ||b - A x|| / ||b|| of the returned x */
-  double err_vs_ustar;       /* ||x - u*|| / ||u*|| */
+  double rel_residual;       /* true ||b - A x|| / ||b|| of the returned x (krylov_arith operator) */
+  double err_vs_ustar;       /* ||x - u*|| / ||u*|| (rhs MANUFACTURED; NaN otherwise) */
   int64_t n_dofs;
   double queue_s, solve_s, latency_s;  /* submit->admit, admit->done, submit->done */
 } sipg_result;

@@ -15,7 +15,7 @@ used without loading torch.
 
 
 def __getattr__(name):
-    if name in ("Context", "SipgError", "Server", "estimate_bytes"):
+    if name in ("Context", "SipgError", "Server", "estimate_bytes", "alu_peak"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

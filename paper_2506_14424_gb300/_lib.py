@@ -34,7 +34,7 @@ EXPORTS = [
     "sipg_projection_rhs", "sipg_viscous_wall_rhs", "sipg_solve_convective", "sipg_convective_lin_apply",
     "sipg_penalty_tau", "sipg_penalty_apply", "sipg_penalty_wall_rhs", "sipg_penalty_step",
     "sipg_boundary_faces", "sipg_rhs_manufactured", "sipg_topology_tables", "sipg_coarsen_mask",
-    "sipg_level_plan",
+    "sipg_level_plan", "sipg_alu_peak",
 ]
 FIELD = {"u": 0, "p": 1, "uhat": 2, "uhathat": 3, "ppe_rhs": 4, "u_prev": 5}
 VISC_MODE = {"linear": 0, "implicit": 1}
@@ -110,13 +110,15 @@ class StepStats(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int), ("mg_precision", ctypes.c_int),
-                ("cheb_degree", ctypes.c_int)]
+                ("cheb_degree", ctypes.c_int), ("krylov_arith", ctypes.c_int)]
+
+
+RHS = {"manufactured": 0, "buoyancy": 1, "host": 2, "device": 3}
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("n_cells", ctypes.c_int), ("k_u", ctypes.c_int), ("n_spheres", ctypes.c_int),
-                ("centers", ctypes.POINTER(ctypes.c_double)), ("radius", ctypes.c_double),
-                ("nu_max", ctypes.c_double), ("nu_matrix", ctypes.c_double), ("rtol", ctypes.c_double),
+    _fields_ = [("n_cells", ctypes.c_int), ("k_u", ctypes.c_int), ("rheology", ctypes.POINTER(Rheology)),
+                ("rhs", ctypes.c_int), ("b", ctypes.c_void_p), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("seed", ctypes.c_uint64), ("keep_solution", ctypes.c_int)]
 
 
@@ -191,6 +193,7 @@ def load(path=None):
         "sipg_topology_tables": (i, [i, i, i, vp, vp, P(i), P(i), vp, vp]),
         "sipg_coarsen_mask": (i, [i, i, i, vp, vp]),
         "sipg_level_plan": (i, [P(MeshDesc), P(Opts), i, i, P(i), vp]),
+        "sipg_alu_peak": (i, [i, P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

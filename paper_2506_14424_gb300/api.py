@@ -487,9 +487,10 @@ class Context:
 class Server:
     """Continuous-batching solve server (see include/sipg.h, sipg_server_*)."""
 
-    def __init__(self, hbm_budget_bytes, max_slots=8, mg_precision="f32", cheb_degree=3):
+    def __init__(self, hbm_budget_bytes, max_slots=8, mg_precision="f32", cheb_degree=3, krylov_arith="f64"):
         self._lib = L.load()
-        o = L.ServerOpts(int(hbm_budget_bytes), int(max_slots), L.PREC[mg_precision], int(cheb_degree))
+        o = L.ServerOpts(int(hbm_budget_bytes), int(max_slots), L.PREC[mg_precision], int(cheb_degree),
+                         L.PREC[krylov_arith])
         h = ctypes.c_void_p()
         rc = self._lib.sipg_server_create(ctypes.byref(o), ctypes.byref(h))
         if rc != L.SIPG_OK:
@@ -497,13 +498,29 @@ class Server:
         self._h = h
         self._sizes = {}
 
-    def submit(self, n_cells, k_u, sinker, rtol=1e-8, maxit=300, seed=0, keep_solution=False):
-        c = np.ascontiguousarray(np.asarray(sinker["centers"], dtype=np.float64).reshape(-1))
-        r = L.Request(int(n_cells), int(k_u), len(c) // 3, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                      float(sinker["radius"]), float(sinker["nu_max"]), float(sinker["nu_matrix"]), float(rtol),
-                      int(maxit), int(seed), int(bool(keep_solution)))
+    def submit(self, n_cells, k_u, rheology, rtol=1e-8, maxit=300, seed=0, keep_solution=False,
+               rhs="manufactured"):
+        """Queue a viscous solve on the n^3 unit cube. rheology: a constant, analytic or
+        sinker dict; rhs: "manufactured" (b = A u*, u* from seed), "buoyancy" (b = M f of the
+        spheres), a host numpy array (copied now) or a CUDA torch tensor (read at admission:
+        keep it alive and unchanged until the request is done)."""
+        r_struct, keep = rheology_struct(rheology)
+        b_ptr = None
+        if isinstance(rhs, str):
+            kind = L.RHS[rhs]
+        elif isinstance(rhs, np.ndarray):
+            kind = L.RHS["host"]
+            b_host = np.ascontiguousarray(rhs, dtype=np.float64)
+            b_ptr = b_host.ctypes.data
+        else:  # a device tensor
+            kind = L.RHS["device"]
+            assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.is_contiguous()
+            b_ptr = rhs.data_ptr()
+        r = L.Request(int(n_cells), int(k_u), ctypes.pointer(r_struct), kind, b_ptr, float(rtol), int(maxit),
+                      int(seed), int(bool(keep_solution)))
         rid = ctypes.c_uint64()
         rc = self._lib.sipg_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid))
+        del keep
         if rc != L.SIPG_OK:
             raise SipgError(rc, "sipg_server_submit failed")
         self._sizes[rid.value] = (int(n_cells) ** 3 * 3 * (int(k_u) + 1) ** 3, bool(keep_solution))
@@ -538,6 +555,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def alu_peak(prec):
+    """FMA throughput of the current device in TFLOP/s: prec "f64" or "f32" (sipg_alu_peak)."""
+    lib = L.load()
+    t = ctypes.c_double()
+    rc = lib.sipg_alu_peak(L.PREC[prec], ctypes.byref(t))
+    if rc != L.SIPG_OK:
+        raise SipgError(rc, "sipg_alu_peak failed")
+    return t.value
 
 
 def estimate_bytes(n_cells, k_u):

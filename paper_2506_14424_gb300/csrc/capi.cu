@@ -453,6 +453,7 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   }
   sipg_ctx* ctx = new sipg_ctx();
   ctx->mesh = *mesh;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) ctx->device = -1;
   ctx->topo = topo;
   if (mesh->active) ctx->mask.assign(mesh->active, mesh->active + (size_t)mesh->nx * mesh->ny * mesh->nz);
   ctx->mesh.active = nullptr;  // copied above

@@ -109,6 +109,7 @@ struct sipg_ctx {
   bool mapped = false;          // trilinear cells from a vertex array (fine level only)
   double* dverts = nullptr;     // device copy of the vertices
   bool dry = false;     // size accounting only (sipg_estimate_bytes)
+  int device = -1;      // CUDA device current at sipg_create (the context's device)
   int64_t bytes = 0;    // device bytes allocated by the hierarchy
 
   ~sipg_ctx();

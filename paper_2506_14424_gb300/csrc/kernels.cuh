@@ -18,6 +18,8 @@ cudaError_t launch_ff_convert(int64_t n, const double* in, float2* hilo, double*
 // descs: device array of ApplyDesc<double, ff> (operator.cuh), tiles: (problem, cell0)
 cudaError_t launch_apply_multi_ff(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
                                   const Tab& tab, cudaStream_t st);
+cudaError_t launch_apply_multi_f64(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
+                                   const Tab& tab, cudaStream_t st);
 int op_cells_per_cta(int n, int ncomp);
 
 // ---- cell mass matrix and its inverse (mass.cu): y = scale (M1 (x) M1 (x) M1) x per

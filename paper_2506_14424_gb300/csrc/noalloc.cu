@@ -19,7 +19,10 @@
 //    caller. The staging halves are fully overwritten by each call (x by the
 //    host-to-device copy, y by the operator), so nothing needs clearing;
 //  * the first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress; make that first call before any stream capture.
+//    cudaGetSymbolAddress; make that first call before any stream capture;
+//  * the device that was current at sipg_create must be current at the call
+//    (the array and the context's stream both belong to it); otherwise the
+//    call returns SIPG_ERR_INVALID without touching any memory.
 #include "../../include/sipg.h"
 #include "ctx.h"
 
@@ -36,17 +39,15 @@ __device__ __align__(256) double g_apply_staging[2 * kStaticMaxDofs];
 std::mutex g_mu;
 double* g_staging_addr[kMaxDevices] = {nullptr};
 
-// Device address of the staging array on the current device (looked up once
-// per device; in host code the symbol itself is only a host-side stand-in).
-cudaError_t staging_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the staging array on device `dev`, which must be the
+// current device (looked up once per device; in host code the symbol itself is
+// only a host-side stand-in).
+cudaError_t staging_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_staging_addr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_apply_staging);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_apply_staging);
     if (e != cudaSuccess) return e;
     g_staging_addr[dev] = static_cast<double*>(p);
   }
@@ -65,8 +66,15 @@ extern "C" int sipg_apply_host_static(sipg_ctx* ctx, int op, const double* x_hos
   if (n > kStaticMaxDofs)
     return ctx->fail(SIPG_ERR_INVALID,
                      "sipg_apply_host_static: vector larger than the static staging area (524288 values)");
+  // The staging array is per device and the context's stream belongs to its
+  // device: a call made while another device is current is refused.
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return ctx->fail(SIPG_ERR_CUDA, "cudaGetDevice", e);
+  if (cur != ctx->device)
+    return ctx->fail(SIPG_ERR_INVALID, "sipg_apply_host_static: the current device is not the context's device");
   double* dx = nullptr;
-  cudaError_t e = staging_address(&dx);
+  e = staging_address(cur, &dx);
   if (e != cudaSuccess) return ctx->fail(SIPG_ERR_CUDA, "cudaGetSymbolAddress(staging)", e);
   double* dy = dx + kStaticMaxDofs;
   e = cudaMemcpyAsync(dx, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st);
