@@ -155,12 +155,24 @@ def traffic_record(kernel_key):
     return rec["dram_bytes_per_launch"]
 
 
-# FP64 peak of the GB300: own FMA-chain micro-benchmark (1.01 TFLOP/s measured).
-FP64_PEAK_TFLOPS = 1.01
-# FP64-equivalent peak of float-float arithmetic on the FP32 pipe: 128 FP32 lanes x
-# 152 SMs x 2.07 GHz = 40.3e12 instructions/s, 12 instructions per float-float
-# multiply-add (exact product 4, TwoSum 6, low-word adds 2; 2 flops) -> 6.71 TFLOP/s.
-FF_PEAK_TFLOPS = 128 * 152 * 2.07e9 / 12 * 2 / 1e12
+# ALU peaks of the GPU, measured at start-up by the library's FMA-chain kernel
+# (sipg_alu_peak): FP64 and FP32 TFLOP/s. The FP64-equivalent peak of float-float
+# arithmetic on the FP32 pipe is the FP32 multiply-add rate over 12 instructions per
+# float-float multiply-add (exact product 4, TwoSum 6, low-word adds 2), 2 flops each.
+FF_INSTR_PER_MA = 12
+_PEAKS = {}
+
+
+def alu_peaks():
+    """{'f64': TFLOP/s, 'f32': TFLOP/s, 'f64ff': TFLOP/s}, measured once per process."""
+    if not _PEAKS:
+        from paper_2506_14424_gb300 import alu_peak
+        f64 = max(alu_peak("f64") for _ in range(3))
+        f32 = max(alu_peak("f32") for _ in range(3))
+        _PEAKS.update({"f64": f64, "f32": f32, "f64ff": f32 / FF_INSTR_PER_MA})
+    return _PEAKS
+
+
 # Algorithmic flops per DoF of the k=3 viscous apply (minimal sum-factorised count).
 FLOP_PER_DOF = 250.0
 
@@ -246,21 +258,14 @@ def run_gpu(args):
     C = N_CELLS ** 3
     nb = K_U + 1
     alg_bytes = algorithmic_bytes(n, C, nb)
-    flops = FLOP_PER_DOF * n
-    achieved_tflops = flops / (ms_step * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS if args.arith == "f64" else FF_PEAK_TFLOPS
+    pk = alu_peaks()
     key = "apply_kernel<4,3,double>" if args.arith == "f64" else "apply_kernel<4,3,ff>"
-    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak, "traffic": traffic_record(key),
-            "kernel": key,
-            "peak_source": ("measured FP64 FMA rate (own micro-benchmark); MEASURED_PEAKS.json has no FP64 figure"
-                            if args.arith == "f64" else
-                            "FP64-equivalent float-float peak derived from the FP32 pipe (128 lanes x 152 SMs x "
-                            "2.07 GHz / 12 instructions per multiply-add)"),
-            "hbm_achieved_gbs": alg_bytes / (ms_step * 1e-3) / 1e9,
-            "hbm_peak_gbs": peaks().get("hbm_gbs", 6686.1),
-            "hbm_frac": alg_bytes / (ms_step * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6686.1),
-            "algorithmic_bytes_per_launch": alg_bytes, "algorithmic_flops_per_launch": flops}
+    roof = roofline(ms_step, n, alg_bytes, args.arith, pk, key)
+    # the binary64 kernel on the same inputs, as its own field
+    ms64 = time_apply(ctx, "viscous", xs[0], ys[0], max(10, min(args.steps, 50)), stream, arith="f64",
+                      rotate=(xs, ys))
+    binary64 = {"value": n / ms64 / 1e6, "unit": "GDoF/s", "ms_per_apply": ms64, "dtype": "f64",
+                "roofline": roofline(ms64, n, alg_bytes, "f64", pk, "apply_kernel<4,3,double>")}
     extras = {}
     if not args.no_extras and rank == 0:
         extras = gpu_extras(ctx, xs, ys, stream)
@@ -271,7 +276,9 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "cells": [N_CELLS] * 3, "k_u": K_U, "n_dofs": n, "arith": args.arith,
                        "l2": "inputs larger than L2: 4 rotating x/y pairs (403 MB) + 42 MB stored nu",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roof}
+            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps * (2 if args.arith == "f64ff" else 1),
+            "roofline": roof, "binary64": binary64,
+            "alu_peaks_tflops": {k: round(v, 3) for k, v in pk.items()}}
     if rank == 0:
         line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(sample_cells=1024)
         line["extras"] = extras
@@ -281,14 +288,32 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def time_apply(ctx, op, x, y, reps, stream, warm=3, arith=None):
+def roofline(ms, n, alg_bytes, arith, pk, key):
+    """ALU roofline of one viscous apply (the bound of these kernels) with the HBM fraction beside it."""
+    flops = FLOP_PER_DOF * n
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = pk[arith]
+    hbm = peaks().get("hbm_gbs", 6686.1)
+    src = {"f64": "measured FP64 FMA rate (sipg_alu_peak)", "f32": "measured FP32 FMA rate (sipg_alu_peak)",
+           "f64ff": "FP64-equivalent float-float peak: measured FP32 FMA rate / 12 instructions per "
+                    "float-float multiply-add"}[arith]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_record(key), "kernel": key, "peak_source": src,
+            "hbm_achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
+            "hbm_frac": alg_bytes / (ms * 1e-3) / 1e9 / hbm,
+            "algorithmic_bytes_per_launch": alg_bytes, "algorithmic_flops_per_launch": flops}
+
+
+def time_apply(ctx, op, x, y, reps, stream, warm=3, arith=None, rotate=None):
+    """CUDA-event time of one apply (ms); rotate=(xs, ys) cycles through vectors larger than L2."""
     import torch
-    for _ in range(warm):
-        ctx.apply(op, x, y, arith=arith)
+    X, Y = rotate if rotate else ([x], [y])
+    for i in range(warm):
+        ctx.apply(op, X[i % len(X)], Y[i % len(Y)], arith=arith)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(reps):
-        ctx.apply(op, x, y, arith=arith)
+    for i in range(reps):
+        ctx.apply(op, X[i % len(X)], Y[i % len(Y)], arith=arith)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
@@ -303,15 +328,26 @@ def gpu_extras(ctx, xs, ys, stream):
     out = {}
     n = ctx.n_dofs("viscous")
     yref = ctx.apply("viscous", xs[0])
-    for arith, peak in (("f64", FP64_PEAK_TFLOPS), ("f64ff", FF_PEAK_TFLOPS)):
-        ms = time_apply(ctx, "viscous", xs[0], ys[0], 20, stream, arith=arith)
+    pk = alu_peaks()
+    for arith in ("f64", "f64ff"):
+        ms = time_apply(ctx, "viscous", xs[0], ys[0], 20, stream, arith=arith, rotate=(xs, ys))
+        ctx.apply("viscous", xs[0], ys[0], arith=arith)
         diff = ((ys[0] - yref).abs().max() / yref.abs().max()).item()
         tf = FLOP_PER_DOF * n / (ms * 1e-3) / 1e12
         out[f"viscous_{arith}_apply"] = {"ms": ms, "gdofs": n / ms / 1e6, "rel_diff_vs_f64": diff,
-                                         "alu_frac": tf / peak, "alu_peak_tflops": peak}
-    x32, y32 = xs[0].float(), ys[0].float()
-    ms = time_apply(ctx, "viscous", x32, y32, 20, stream)
-    out["viscous_f32_apply"] = {"ms": ms, "gdofs": n / ms / 1e6}
+                                         "alu_frac": tf / pk[arith], "alu_peak_tflops": pk[arith]}
+    # FP32 multigrid-level apply (the V-cycle's operator), rotating vectors larger than L2
+    x32 = [x.float() for x in xs]
+    y32 = [y.float() for y in ys]
+    ms = time_apply(ctx, "viscous", x32[0], y32[0], 40, stream, rotate=(x32, y32))
+    ctx.apply("viscous", x32[0], y32[0])
+    d32 = ((y32[0].double() - yref).abs().max() / yref.abs().max()).item()
+    tf = FLOP_PER_DOF * n / (ms * 1e-3) / 1e12
+    out["viscous_f32_apply"] = {"ms": ms, "gdofs": n / ms / 1e6, "rel_diff_vs_f64": d32,
+                                "alu_frac": tf / pk["f32"], "alu_peak_tflops": pk["f32"],
+                                "hbm_frac": 12.0 * n / (ms * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6686.1),
+                                "kernel": "apply_tpc_kernel<4,3> (register-tiled)"}
+    del x32, y32
     npr = ctx.n_dofs("poisson")
     xp = torch.tensor(inputs.uniform_vector(npr, seed=300), device="cuda")
     yp = torch.empty_like(xp)

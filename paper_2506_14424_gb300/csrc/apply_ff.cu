@@ -4,10 +4,11 @@
 
 #include <algorithm>
 namespace sipg {
-cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
+cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const float2* x, double* y,
                             const float2* nu_cell, const float2* nu_face, double mass, int nbatch, cudaStream_t st) {
-  return launch_apply_t<double, ff, ff>(n, ncomp, g, tab, x, y, reinterpret_cast<const ff*>(nu_cell),
-                                        reinterpret_cast<const ff*>(nu_face), mass, nbatch, st);
+  return launch_apply_t<ff, double, ff, ff>(n, ncomp, g, tab, reinterpret_cast<const ff*>(x), y,
+                                            reinterpret_cast<const ff*>(nu_cell),
+                                            reinterpret_cast<const ff*>(nu_face), mass, nbatch, st);
 }
 
 cudaError_t launch_apply_multi_ff(int n, int ncomp, const void* descs, const int2* tiles, int ntiles,
@@ -47,6 +48,21 @@ cudaError_t launch_ff_convert(int64_t n, const double* in, float2* hilo, double*
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
   ff_convert_kernel<<<blocks, 256, 0, st>>>(n, in, hilo, back);
+  return cudaGetLastError();
+}
+
+// x of the float-float operator, split once per apply with the integer
+// conversion (no FP64-pipe instructions; the same bits as the hardware split)
+__global__ void split_ff_int_kernel(int64_t n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const ff v = split_double(in[i]);
+    out[i] = make_float2(v.hi, v.lo);
+  }
+}
+cudaError_t launch_split_ff_int(int64_t n, const double* in, float2* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  split_ff_int_kernel<<<blocks, 256, 0, st>>>(n, in, out);
   return cudaGetLastError();
 }
 

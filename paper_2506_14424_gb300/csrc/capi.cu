@@ -262,6 +262,9 @@ int sipg_ctx::build_hierarchy(int op) {
       }
       if (l > 0) { L.ulin = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc ulin", e); }
     }
+    if (l == 0 && !mapped) {
+      L.xff = alloc<float2>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc split x", e);
+    }
     L.diag64 = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
     L.dinv64 = alloc<double>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
     L.dinv32 = alloc<float>(L.ndofs, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc diag", e);
@@ -376,7 +379,7 @@ sipg_ctx::~sipg_ctx() {
     }
     for (Level& L : (H.cph ? H.T : H.L)) {
       cudaFree(L.nu_cell64); cudaFree(L.nu_face64); cudaFree(L.nu_cell32); cudaFree(L.nu_face32);
-      cudaFree(L.nu_cellff); cudaFree(L.nu_faceff);
+      cudaFree(L.nu_cellff); cudaFree(L.nu_faceff); cudaFree(L.xff);
       cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
       cudaFree(L.lam);
       if (L.own_verts) cudaFree(L.verts);
@@ -664,7 +667,9 @@ int sipg_ctx::level_apply_ff(int op, int l, const double* x, double* y, double m
   if (op == SIPG_OP_VISCOUS && !L.nu_cellff) return fail(SIPG_ERR_INVALID, "float-float apply on level 0 only");
   const float2* nc = op == SIPG_OP_VISCOUS ? L.nu_cellff : nullptr;
   const float2* nf = op == SIPG_OP_VISCOUS ? L.nu_faceff : nullptr;
-  CK(launch_apply_ff(L.n, H.ncomp, L.g, tabs[L.n], x, y, nc, nf, mass, 1, st));
+  if (!L.xff) return fail(SIPG_ERR_INVALID, "float-float apply on level 0 only");
+  CK(launch_split_ff_int(L.ndofs, x, L.xff, st));
+  CK(launch_apply_ff(L.n, H.ncomp, L.g, tabs[L.n], L.xff, y, nc, nf, mass, 1, st));
   return SIPG_OK;
 }
 

@@ -21,6 +21,7 @@ struct Level {
   double *nu_cell64 = nullptr, *nu_face64 = nullptr;
   float *nu_cell32 = nullptr, *nu_face32 = nullptr;
   float2 *nu_cellff = nullptr, *nu_faceff = nullptr;  // (hi, lo) split for float-float
+  float2* xff = nullptr;     // level 0: x of the float-float apply split into (hi, lo) pairs
   double* ulin = nullptr;    // linearization velocity on this level (l > 0)
   double* diag64 = nullptr;
   double* dinv64 = nullptr;

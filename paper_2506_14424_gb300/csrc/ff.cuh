@@ -15,7 +15,7 @@
 
 namespace sipg {
 
-struct ff {
+struct __align__(8) ff {  // the layout of float2: (hi, lo)
   float hi, lo;
   ff() = default;
   __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}

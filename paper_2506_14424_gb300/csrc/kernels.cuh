@@ -10,8 +10,14 @@ cudaError_t launch_apply(int n, int ncomp, const LevelGeom& g, const Tab& tab, c
                          const T* nu_cell, const T* nu_face, T mass, int nbatch, cudaStream_t st);
 // FP64-accurate apply with float-float arithmetic (double storage)
 // (nu given as (hi, lo) float pairs, see launch_split_ff)
-cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const double* x, double* y,
+// register-tiled FP32 operator (n = 2..4)
+bool tpc_supported(int n);
+cudaError_t launch_apply_tpc(int n, int ncomp, const LevelGeom& g, const Tab& tab, const float* x, float* y,
+                             const float* nu_cell, const float* nu_face, float mass, int nbatch, cudaStream_t st);
+cudaError_t launch_apply_ff(int n, int ncomp, const LevelGeom& g, const Tab& tab, const float2* x, double* y,
                             const float2* nu_cell, const float2* nu_face, double mass, int nbatch, cudaStream_t st);
+// x of the float-float operator as (hi, lo) pairs (integer split, bit-identical to the hardware one)
+cudaError_t launch_split_ff_int(int64_t n, const double* in, float2* out, cudaStream_t st);
 cudaError_t launch_split_ff(int64_t n, const double* in, float2* out, cudaStream_t st);
 cudaError_t launch_ff_convert(int64_t n, const double* in, float2* hilo, double* back, cudaStream_t st);
 // float-float applies of several problems of one degree in one persistent launch;

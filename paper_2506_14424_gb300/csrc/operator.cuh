@@ -18,7 +18,11 @@
 // ("according to Hillewaert 2013", formula not printed; nubar = 1 for Poisson).
 //
 // Design: each CTA owns CPB consecutive cells and writes only their rows of y,
-// so there are no atomics and the result is deterministic. Per cell:
+// so there are no atomics and the result is deterministic. Every loop runs a
+// compile-time count (CPB cells, also in the last CTA of a level, whose cells
+// beyond the level's end repeat its last cell and are never stored), and the
+// neighbour, boundary kind and penalty of each of the CTA's faces are looked
+// up once per CTA into shared tables. Per cell:
 //   1. stage x (own cell) in shared memory (contiguous, coalesced),
 //   2. interpolate nodes -> Gauss points (3 sweeps), collocation gradient
 //      (3 sweeps), quadrature-point flux, transposed sweeps back (6 sweeps),
@@ -152,8 +156,15 @@ __host__ __device__ constexpr int op_work_elems() {
 }
 template <int N, int NC>
 __host__ __device__ constexpr int op_smem_elems() {
-  return 2 * N * N + 4 * N + 2 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
+  return 2 * N * N + 4 * N + 6 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
 }
+// bytes: the T region above, then the per-CTA face table (int, 6 per cell):
+// the neighbour across each face, or kBndDirichlet / kBndNeumann
+template <int N, int NC, typename T>
+__host__ __device__ constexpr size_t op_smem_bytes() {
+  return ((sizeof(T) * op_smem_elems<N, NC>() + 15) / 16) * 16 + sizeof(int) * 6 * OpCfg<N, NC>::CPB;
+}
+constexpr int kBndDirichlet = -1, kBndNeumann = -2;
 
 template <int N, typename T>
 __device__ __forceinline__ void load_tables(const CTab<T>& ct, T* dS0, T* dS1, T* gw) {
@@ -175,22 +186,23 @@ __device__ __forceinline__ void load_tables(const CTab<T>& ct, T* dS0, T* dS1, T
 template <typename T>
 __device__ __forceinline__ T sel3(const T* v, int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
 
-template <int N, int NC, typename TN, typename T, bool TOPO>
-__device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int cell0, int ncell, int FS, int CPB,
-                                               const T* ih, const T* gw, const T* pen,
+template <int N, int NC, typename TN, typename T>
+__device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int cell0, int FS, const T* ih,
+                                               const T* gw, const T* pen, const int* nbt,
                                                const TN* __restrict__ nu_face, T* F) {
-  constexpr int N2 = N * N;
+  constexpr int N2 = N * N, CPB = OpCfg<N, NC>::CPB;
   const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
   const T ihd = sel3(ih, D), iht1 = sel3(ih, T1), iht2 = sel3(ih, T2);
   const T area = from_double<T>(g.h[T1] * g.h[T2]);
-  for (int i = threadIdx.x; i < 2 * ncell * N2; i += blockDim.x) {
-    const int s = i / (ncell * N2);
-    const int rem = i - s * ncell * N2;
+  const int last = g.ncells - 1;
+  for (int i = threadIdx.x; i < 2 * CPB * N2; i += blockDim.x) {
+    const int s = i / (CPB * N2);
+    const int rem = i - s * CPB * N2;
     const int c = rem / N2, p = rem - c * N2;
     const int a = p % N, b = p / N;
-    const int e = cell0 + c;
+    const int e = min(cell0 + c, last);
     const int f = 2 * D + s;
-    const int nb = cell_neighbor_t<TOPO>(g, e, f);
+    const int nb = nbt[c * 6 + f];
     T* gV = F + (s * 8 + 0) * FS;
     T* gN = F + (s * 8 + 1) * FS;
     const T* gVp = F + (s * 8 + 2) * FS;
@@ -199,7 +211,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
     T* gT1 = F + (s * 8 + 5) * FS;
     const T* gT2p = F + (s * 8 + 6) * FS;
     const T* gT1p = F + (s * 8 + 7) * FS;
-    if (nb < 0 && face_bc_t<TOPO>(g, e, f) == 1) {  // homogeneous Neumann: no face term
+    if (nb == kBndNeumann) {  // homogeneous Neumann: no face term
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const int j = (c * NC + k) * N2 + p;
@@ -211,12 +223,13 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
       }
       continue;
     }
+    const bool inner = nb >= 0;
     const T nsign = s ? T(1) : T(-1);
     const T W = gw[a] * gw[b] * area;
-    const T pe = pen[s * CPB + c];
+    const T pe = pen[c * 6 + f];
     if constexpr (NC == 3) {
       const T num = load_as<T>(nu_face[((size_t)e * 6 + f) * N2 + p]);
-      const T nup = nb >= 0 ? load_as<T>(nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p]) : num;
+      const T nup = inner ? load_as<T>(nu_face[((size_t)nb * 6 + (f ^ 1)) * N2 + p]) : num;
       const T tW = pe * nubar_of<T>(g.face_nu, num, nup) * W;  // tau W
       // Only grad u_D . e_l (l tangential) and d u_k / d x_D enter the flux:
       // P_k = tau ([u]_k + d_kD [u]_D) - sigma (A_kD + A_Dk), A = (nu- G- + nu+ G+)/2;
@@ -230,7 +243,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
         const int j = (c * 3 + k) * N2 + p;
         um[k] = gV[j];
         nm[k] = gN[j];
-        if (nb >= 0) {
+        if (inner) {
           up[k] = gVp[j];
           npd[k] = gNp[j];
         } else {  // Dirichlet mirror: u+ = -u-, grad u+ = grad u-
@@ -240,8 +253,8 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
       }
       const int jd = (c * 3 + D) * N2 + p;
       const T t1m = gT1[jd], t2m = gT2[jd];
-      const T t1p = nb >= 0 ? gT1p[jd] : t1m;
-      const T t2p = nb >= 0 ? gT2p[jd] : t2m;
+      const T t1p = inner ? gT1p[jd] : t1m;
+      const T t2p = inner ? gT2p[jd] : t2m;
       T jmp[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) jmp[k] = um[k] - up[k];
@@ -266,7 +279,7 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
       const T pm = gV[j];
       const T dnm = gN[j] * ihd;
       T pp, dnp;
-      if (nb >= 0) {
+      if (inner) {
         pp = gVp[j];
         dnp = gNp[j] * ihd;
       } else {
@@ -293,24 +306,24 @@ __device__ __forceinline__ T line_dot(const T* M, const T* v, int o) {
 // Face terms of direction D (both sides) added to Y. One non-inlined copy
 // serves the three directions (the direction only changes indices), which
 // keeps the unrolled float-float code within the instruction cache.
-// S and Dg point to shared-memory copies of the 1D matrices.
-template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
-__device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, const T* Dg, int cell0, int ncell,
-                                       int CPB, const TS* __restrict__ x, const TN* __restrict__ nu_face,
-                                       const T* Xs, T* Y, T* F, T* pen, const T* ih, const T* gw,
-                                       const T* dS0, const T* dS1) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+// S and Dg point to shared-memory copies of the 1D matrices; nbt / pen are the
+// CTA's face tables (neighbour or boundary kind, penalty factor).
+template <int N, int NC, typename TX, typename TN, typename T>
+__device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, const T* Dg, int cell0,
+                                       const TX* __restrict__ x, const TN* __restrict__ nu_face, const T* Xs, T* Y,
+                                       T* F, const T* pen, const int* nbt, const T* ih, const T* gw, const T* dS0,
+                                       const T* dS1) {
+  constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
+  constexpr int nt = CPB * NC;
+  constexpr int FS = CPB * NC * N2;
   const int STD = D == 0 ? 1 : (D == 1 ? N : N2);
-  const int nt = ncell * NC;
-  const int FS = CPB * NC * N2;
   // (A) traces and normal derivatives at the face Gauss-Lobatto nodes of both
-  // sides (neighbour data straight from global memory); penalty per cell/side
+  // sides (neighbour data straight from global memory)
   for (int i = threadIdx.x; i < 2 * nt * N2; i += blockDim.x) {
     const int s = i / (nt * N2);
     const int rem = i - s * nt * N2;
     const int t = rem / N2, p = rem - t * N2;
     const int c = t / NC, comp = t - c * NC;
-    const int e = cell0 + c;
     const int off0 = face_node<N>(D, 0, p % N, p / N);
     const T* dS = s ? dS1 : dS0;
     const T* dSn = s ? dS0 : dS1;
@@ -321,9 +334,9 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     T* Fs = F + s * 8 * FS;
     Fs[rem] = xs[(s ? N - 1 : 0) * STD];
     Fs[FS + rem] = dn.get();
-    const int nb = cell_neighbor_t<TOPO>(g, e, 2 * D + s);
+    const int nb = nbt[c * 6 + 2 * D + s];
     if (nb >= 0) {
-      const TS* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
+      const TX* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
       T v[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = load_as<T>(xn[j * STD]);
@@ -337,16 +350,8 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
       Fs[3 * FS + rem] = T(0);
     }
   }
-  for (int i = threadIdx.x; i < 2 * ncell; i += blockDim.x) {
-    const int s = i / ncell, c = i - s * ncell;
-    const int e = cell0 + c;
-    const int nb = cell_neighbor_t<TOPO>(g, e, 2 * D + s);
-    const double lm = penalty_lambda_t<TOPO>(g, e);
-    const double lp = nb >= 0 ? penalty_lambda_t<TOPO>(g, nb) : lm;
-    pen[s * CPB + c] = from_double<T>(g.cip * double(N * N) * (lm > lp ? lm : lp));
-  }
   __syncthreads();
-  // (B) interpolate the four node quantities of each side along a
+// (B) interpolate the four node quantities of each side along a
   for (int line = threadIdx.x; line < 2 * 4 * nt * N; line += blockDim.x) {
     const int s = line / (4 * nt * N);
     const int rem = line - s * 4 * nt * N;
@@ -398,10 +403,10 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
   // (D) along a: tangential a-derivatives of the own and neighbour traces of
   // velocity component D (no tangential derivative enters the Poisson flux)
   if (NC == 3) {
-    for (int line = threadIdx.x; line < 2 * 2 * ncell * N; line += blockDim.x) {
-      const int s = line / (2 * ncell * N);
-      const int rem = line - s * 2 * ncell * N;
-      const int q = rem / (ncell * N), lc = rem - q * ncell * N;  // q = 0 own, 1 neighbour
+    for (int line = threadIdx.x; line < 2 * 2 * CPB * N; line += blockDim.x) {
+      const int s = line / (2 * CPB * N);
+      const int rem = line - s * 2 * CPB * N;
+      const int q = rem / (CPB * N), lc = rem - q * CPB * N;  // q = 0 own, 1 neighbour
       const int c = lc / N, r = lc - c * N;
       const int t = c * 3 + D;
       const T* in = F + (s * 8 + 2 * q) * FS + t * N2 + r * N;
@@ -415,7 +420,7 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     __syncthreads();
   }
   // (E) numerical flux
-  face_flux_pair<N, NC, TN, T, TOPO>(D, g, cell0, ncell, FS, CPB, ih, gw, pen, nu_face, F);
+  face_flux_pair<N, NC, TN, T>(D, g, cell0, FS, ih, gw, pen, nbt, nu_face, F);
   __syncthreads();
   // (F) test side, along a: slot 2 = gV + Dg_a^T gT1
   for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
@@ -491,23 +496,28 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
 }
 
 // y = (m M + A) x on the cells [cell0, cell0 + CPB) of a level, executed by
-// one CTA with shared memory sm (op_smem_elems<N, NC>() elements of T).
+// one CTA with shared memory sm (op_smem_bytes<N, NC, T>() bytes).
 // NC = 3: viscous operator (nu_cell [C][N^3], nu_face [C][6][N^2]);
 // NC = 1: Poisson operator (nu pointers unused).
-// TS is the storage type of x and y, TN that of nu, T the arithmetic type
-// (double, float, or ff = float-float with double x/y and pre-split nu).
-template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
-__device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const TS* __restrict__ x,
+// TX is the storage type of x, TS that of y, TN that of nu, T the arithmetic
+// type (double, float, or ff = float-float: x and nu pre-split into (hi, lo)
+// pairs, y stored as binary64).
+template <int N, int NC, typename TX, typename TS, typename TN, typename T, bool TOPO>
+__device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const TX* __restrict__ x,
                                             TS* __restrict__ y, const TN* __restrict__ nu_cell,
-                                            const TN* __restrict__ nu_face, double mass_d, int cell0, T* sm) {
+                                            const TN* __restrict__ nu_face, double mass_d, int cell0,
+                                            unsigned char* smraw) {
   constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
+  constexpr int nt = CPB * NC;
+  T* sm = reinterpret_cast<T*>(smraw);
+  int* nbt = reinterpret_cast<int*>(smraw + ((sizeof(T) * op_smem_elems<N, NC>() + 15) / 16) * 16);
   T* Ssh = sm;                     // N2, copies of the 1D matrices for the face routine
   T* Dsh = Ssh + N2;               // N2
   T* dS0 = Dsh + N2;
   T* dS1 = dS0 + N;
   T* gw = dS1 + N;
-  T* pen = gw + 2 * N;             // 2 * CPB
-  T* Xs = pen + 2 * CPB;           // CPB * NC * N3
+  T* pen = gw + 2 * N;             // 6 * CPB: C_IP N^2 max(Lambda-, Lambda+) per face
+  T* Xs = pen + 6 * CPB;           // CPB * NC * N3
   T* Y = Xs + CPB * NC * N3;       // CPB * NC * N3
   T* Wk = Y + CPB * NC * N3;       // CPB * op_work_elems
   T* W0 = Wk;
@@ -521,11 +531,24 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
     Ssh[i] = ct.S[i];
     Dsh[i] = ct.Dg[i];
   }
+  const int last = g.ncells - 1;
+  // face tables: neighbour (or boundary kind) and penalty of each face
+  for (int i = threadIdx.x; i < 6 * CPB; i += blockDim.x) {
+    const int c = i / 6, f = i - 6 * c;
+    const int e = min(cell0 + c, last);
+    const int nb = cell_neighbor_t<TOPO>(g, e, f);
+    nbt[i] = nb >= 0 ? nb : (face_bc_t<TOPO>(g, e, f) == 1 ? kBndNeumann : kBndDirichlet);
+    const double lm = penalty_lambda_t<TOPO>(g, e);
+    const double lp = nb >= 0 ? penalty_lambda_t<TOPO>(g, nb) : lm;
+    pen[i] = from_double<T>(g.cip * double(N * N) * (lm > lp ? lm : lp));
+  }
   const T mass = from_double<T>(mass_d);
-  const int ncell = min(CPB, g.ncells - cell0);
-  const int nt = ncell * NC;
-  const size_t base0 = (size_t)cell0 * NC * N3;
-  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) Xs[i] = load_as<T>(x[base0 + i]);
+  const int ncell = min(CPB, g.ncells - cell0);  // cells stored by this CTA
+  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) {
+    const int c = i / (NC * N3);
+    const int e = min(cell0 + c, last);
+    Xs[i] = load_as<T>(x[(size_t)e * NC * N3 + (i - c * NC * N3)]);
+  }
   __syncthreads();
 
   // ---- cell term: nodes -> Gauss points along x, y; the z pass also forms
@@ -554,7 +577,7 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
   __syncthreads();
   const T ih[3] = {from_double<T>(g.ih[0]), from_double<T>(g.ih[1]), from_double<T>(g.ih[2])};
   const T detJ = from_double<T>(g.h[0] * g.h[1] * g.h[2]);
-  for (int i = threadIdx.x; i < ncell * N3; i += blockDim.x) {
+  for (int i = threadIdx.x; i < CPB * N3; i += blockDim.x) {
     const int c = i / N3, q = i - c * N3;
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
     const T W = gw[qx] * gw[qy] * gw[qz] * detJ;
@@ -565,7 +588,7 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
       for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l) G[k][l] = Bl[l][(c * 3 + k) * N3 + q] * ih[l];
-      const T nu2W = T(2) * load_as<T>(nu_cell[(size_t)(cell0 + c) * N3 + q]) * W;
+      const T nu2W = T(2) * load_as<T>(nu_cell[(size_t)min(cell0 + c, last) * N3 + q]) * W;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
 #pragma unroll
@@ -604,30 +627,30 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
 
   // ---- face terms, both faces of one direction at a time (work region reused)
   for (int d = 0; d < 3; ++d)
-    face_pair<N, NC, TS, TN, T, TOPO>(d, g, Ssh, Dsh, cell0, ncell, CPB, x, nu_face, Xs, Y, Wk, pen, ih, gw, dS0,
-                                      dS1);
-  for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) y[base0 + i] = store_as<TS>(Y[i]);
+    face_pair<N, NC, TX, TN, T>(d, g, Ssh, Dsh, cell0, x, nu_face, Xs, Y, Wk, pen, nbt, ih, gw, dS0, dS1);
+  const size_t base0 = (size_t)cell0 * NC * N3;
+  for (int i = threadIdx.x; i < ncell * NC * N3; i += blockDim.x) y[base0 + i] = stream_store<TS>(Y[i]);
 }
 
 // One CTA per CPB consecutive cells of one level; blockIdx.y selects one of
 // several vectors applied in the same launch (columns of a batch). TOPO: the
 // level has topology tables (removed cells or periodic directions).
-template <int N, int NC, typename TS, typename TN, typename T, bool TOPO>
+template <int N, int NC, typename TX, typename TS, typename TN, typename T, bool TOPO>
 __global__ void __launch_bounds__(OpCfg<N, NC>::NT, (OccCfg<N, NC, T>::MIN))
-apply_kernel(LevelGeom g, CTab<T> ct, const TS* __restrict__ x, TS* __restrict__ y,
+apply_kernel(LevelGeom g, CTab<T> ct, const TX* __restrict__ x, TS* __restrict__ y,
              const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
-  apply_cells<N, NC, TS, TN, T, TOPO>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
-                                      reinterpret_cast<T*>(smem_raw));
+  apply_cells<N, NC, TX, TS, TN, T, TOPO>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
+                                          smem_raw);
 }
 
 // Operator applies of several problems of the same degree in one persistent
 // launch: tile i = (problem, first cell) of tiles[]; CTAs stride over the
 // tile list (static round robin, deterministic: every tile is computed by
 // exactly the same code as in apply_kernel, so results are bitwise equal).
-// The served problems are plain boxes (no topology tables).
+// The served problems are plain boxes (no topology tables) with binary64 x.
 template <typename TS, typename TN>
 struct ApplyDesc {
   LevelGeom g;
@@ -646,8 +669,7 @@ apply_multi_kernel(const ApplyDesc<TS, TN>* __restrict__ descs, const int2* __re
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int2 tl = tiles[tile];
     const ApplyDesc<TS, TN> d = descs[tl.x];
-    apply_cells<N, NC, TS, TN, T, false>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y,
-                                         reinterpret_cast<T*>(smem_raw));
+    apply_cells<N, NC, TS, TS, TN, T, false>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y, smem_raw);
     __syncthreads();  // the next tile reuses the shared memory
   }
 }

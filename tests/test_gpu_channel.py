@@ -109,8 +109,10 @@ def test_channel_poisson_apply(kp):
     P = SIPG(_mesh(c, "poisson"), kp, 1)
     ctx = _ctx(c, kp + 1)
     x = inputs.uniform_vector(P.n_dofs, seed=12)
+    ref = P.apply(x)
     for arith in ("f64", "f64ff"):
-        assert _rel(ctx.apply("poisson", _dev(x), arith=arith).cpu().numpy(), P.apply(x)) <= TOL64
+        assert _rel(ctx.apply("poisson", _dev(x), arith=arith).cpu().numpy(), ref) <= TOL64
+    assert _rel(ctx.apply("poisson", _dev(x, torch.float32)).double().cpu().numpy(), ref) <= TOL32
     ctx.close()
 
 

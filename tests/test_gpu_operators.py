@@ -79,6 +79,32 @@ def test_viscous_apply_f32_close_to_oracle(dims, k):
     assert _rel(y, S.apply(x, *S.viscosity_at_points(rheo))) <= TOL32
 
 
+@pytest.mark.parametrize("op", ["viscous", "poisson"])
+@pytest.mark.parametrize("dims,k_u", [((7, 3, 2), 3), ((11, 2, 1), 4), ((3, 5, 3), 2)])
+def test_f32_level_applies_close_to_oracle(op, dims, k_u):
+    """FP32 applies on every p-level of the fine mesh (degrees 1..4 of both
+    operators: the register-tiled kernel for degrees 1..3, the shared-memory
+    kernel above), anisotropic cells, mixed walls, the mass term; cell counts
+    (42, 22, 45) leave ragged warps of 10 and 32 cells."""
+    extent = (1.3, 0.7, 2.1)
+    bcv, bcp = "DNDDND", "NDNNDN"
+    ctx = Context(*dims, k_u, extent=extent, bc_velocity=bcv, bc_pressure=bcp)
+    rheo = {'law': 'analytic'}
+    ctx.set_viscosity(rheo)
+    nc = 3 if op == "viscous" else 1
+    bc = bcv if op == "viscous" else bcp
+    for level in range(ctx.num_levels(op)):
+        cells, deg, nd = ctx.level_info(op, level)
+        if tuple(cells) != tuple(dims):
+            break
+        S = SIPG(BoxMesh(*dims, extent=extent, bc=_bc(bc)), deg, nc)
+        nu = S.viscosity_at_points(rheo) if nc == 3 else (None, None)
+        x = inputs.uniform_vector(S.n_dofs, seed=31 + level)
+        for mass in (0.0, 7.5):
+            y = ctx.apply(op, _dev(x, torch.float32), mass=mass, level=level).double().cpu().numpy()
+            assert _rel(y, S.apply(x, *nu, mass=mass)) <= TOL32, (level, deg, mass)
+
+
 @pytest.mark.parametrize("rheo_name", ["analytic", "sinker", "carreau"])
 def test_viscosity_at_points_matches_oracle(rheo_name):
     dims, k = (4, 3, 3), 3
