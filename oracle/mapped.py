@@ -56,6 +56,20 @@ class MappedMesh:
     def boundary_type(self, e, f):
         return self.topo.boundary_type(e, f)
 
+    def boundary_id(self, e, f):
+        return self.topo.boundary_id(e, f)
+
+    def boundary_faces(self):
+        return self.topo.boundary_faces()
+
+    def cell_ijk(self, e):
+        return self.topo.cell_ijk(e)
+
+    def with_bc(self, bc):
+        """The same cells and vertices with other boundary types."""
+        nx, ny, nz = self.n_cells_dir
+        return MappedMesh(nx, ny, nz, self.X, bc=bc, active=self.topo.active, periodic=self.topo.periodic)
+
     def cell_vertices(self, e):
         """(8, 3), vertex (a, b, c) in {0,1}^3 at index a + 2 b + 4 c."""
         i, j, k = self.topo.cell_ijk(e)
@@ -182,6 +196,12 @@ class MappedSIPG:
             w = 0.5 if self.mesh.boundary_type(e, f) == 'I' else 1.0
             lam += w * self.face_area(e, f)
         return lam / self.volume(e)
+
+    def cell_points(self, e):
+        return self.cell_geometry(e)[0]
+
+    def face_points(self, e, f):
+        return self.face_geometry(e, f)[0]
 
     def node_points(self, e):
         n = self.n

@@ -25,12 +25,16 @@ import numpy as np
 
 
 def mass_block(sipg, e=0):
-    """M_e of operator ``sipg`` (SIPG instance; its ncomp picks vector or scalar)."""
-    W = sipg.cell_w * sipg.mesh.volume()
+    """M_e of operator ``sipg`` (an affine SIPG or a trilinear MappedSIPG space; its
+    ncomp picks vector or scalar). On trilinear cells the weights are w_q det J(xi_q)."""
+    if hasattr(sipg, 'cell_geometry'):
+        W = sipg.cell_geometry(e)[2]
+    else:
+        W = sipg.cell_w * sipg.mesh.volume()
     phi = sipg.cell_phi
     if sipg.ncomp == 1:
         return np.einsum('q,qa,qb->ab', W, phi, phi)
-    V, _ = sipg._vector_basis(phi, sipg._phys_grad(sipg.cell_dphi))
+    V, _ = sipg._vector_basis(phi, np.zeros(phi.shape + (3,)))
     return np.einsum('q,qak,qbk->ab', W, V, V)
 
 

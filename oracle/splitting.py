@@ -1,4 +1,4 @@
-"""One time step of the dual splitting (projection) scheme on affine grids (oracle, test infrastructure).
+"""One time step of the dual splitting (projection) scheme (oracle, test infrastructure).
 
 Sec. 3.2 / 5.1 / 5.4, Alg. 1 of the paper, with the convective term explicit
 (alpha_c = 0), on grids of affine hexahedra (oracle.mesh: the box, the
@@ -67,8 +67,17 @@ with explicit basis functions at the Gauss points, as written in the paper:
   walls the exterior state is the wall data g (the paper: the oriented jump
   incorporates the boundary data).
 
+Cells are affine (oracle.mesh / oracle.sipg: the box, the channel) or trilinear
+(oracle.mapped: the jittered channel); every form reads its geometry through
+``cell_geo`` / ``face_geo`` - quadrature weights w det J, physical basis
+gradients J^-T grad_xi phi, J^-1 and the outward unit normal per point - which
+are constant per cell on affine grids. The element-local L2 projection onto
+Q_k and the mass matrix then carry det J per point, so the same code is the
+form of Sec. 5 on general hexahedra.
+
 The oracle solves every linear system exactly (sparse LU; the pressure with a
-rank-one term that fixes the mean). Pins: tests/test_oracle_splitting.py.
+rank-one term that fixes the mean). Pins: tests/test_oracle_splitting.py,
+tests/test_oracle_channel.py.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -77,6 +86,7 @@ import scipy.sparse.linalg as spla
 from . import mass as omass
 from . import nonlinear
 from . import viscosity
+from .mapped import MappedMesh, MappedSIPG
 from .mesh import BoxMesh
 from .sipg import SIPG, _sym
 
@@ -91,6 +101,28 @@ def face_normal(f):
     return d, s, n
 
 
+def cell_geo(S, e):
+    """Gauss-point weights w det J (P,), physical basis gradients (P, n^3, 3) and
+    J^-1 (P, 3, 3) of cell e (per point on trilinear cells)."""
+    if hasattr(S, 'cell_geometry'):
+        _, J, W, Jinv = S.cell_geometry(e)
+        return W, S._grad(S.cell_dphi, J), Jinv
+    P = len(S.cell_w)
+    return (S.cell_w * S.mesh.volume(), S._phys_grad(S.cell_dphi),
+            np.broadcast_to(np.diag(1.0 / np.asarray(S.mesh.h)), (P, 3, 3)))
+
+
+def face_geo(S, e, f):
+    """Surface weights (P,), outward unit normals (P, 3) and physical basis gradients
+    (P, n^3, 3) of cell e at the Gauss points of its face f."""
+    if hasattr(S, 'face_geometry'):
+        _, J, nvec, Wf = S.face_geometry(e, f)
+        return Wf, nvec, S._grad(S.face_dphi[f], J)
+    d, s, n = face_normal(f)
+    P = len(S.face_w2)
+    return S.face_w2 * S.mesh.face_area(d), np.broadcast_to(n, (P, 3)), S._phys_grad(S.face_dphi[f])
+
+
 def _cell(S, x, e):
     return np.asarray(x).reshape(S.mesh.n_cells, S.ncomp, S.n ** 3)[e]
 
@@ -100,9 +132,9 @@ def _values(phi, U):
     return np.einsum('pi,ci->pc', phi, U)
 
 
-def _grads(S, dphi, U):
-    """gradients G[p, c, l] = d u_c / d x_l."""
-    return np.einsum('pil,ci->pcl', S._phys_grad(dphi), U)
+def _grads(gphys, U):
+    """gradients G[p, c, l] = d u_c / d x_l from the physical basis gradients (P, n^3, 3)."""
+    return np.einsum('pil,ci->pcl', gphys, U)
 
 
 def wall_data(S, g_faces, e, f):
@@ -119,15 +151,15 @@ def wall_data(S, g_faces, e, f):
 def _exterior(S, x, e, f, g_faces):
     """Trace values and gradients of the exterior state at the face points of (e, f)."""
     mesh = S.mesh
-    d, s, nvec = face_normal(f)
+    d, s = divmod(f, 2)
     U = _cell(S, x, e)
-    um, Gm = _values(S.face_phi[f], U), _grads(S, S.face_dphi[f], U)
+    um, Gm = _values(S.face_phi[f], U), _grads(face_geo(S, e, f)[2], U)
     bt = mesh.boundary_type(e, f)
     if bt == 'I':
         nb = mesh.neighbor(e, f)
         fo = 2 * d + (1 - s)
         Un = _cell(S, x, nb)
-        return um, Gm, _values(S.face_phi[fo], Un), _grads(S, S.face_dphi[fo], Un), bt
+        return um, Gm, _values(S.face_phi[fo], Un), _grads(face_geo(S, nb, fo)[2], Un), bt
     if bt == 'D':
         g = wall_data(S, g_faces, e, f)
         return um, Gm, -um + 2.0 * g, Gm, bt
@@ -138,19 +170,18 @@ def convective_vector(S, u, g_faces):
     """C_a = sum_e c_h(phi_a, u; u) (velocity space S, ncomp = 3)."""
     C = S.mesh.n_cells
     out = np.zeros((C, 3, S.n ** 3))
-    W = S.cell_w * S.mesh.volume()
     for e in range(C):
+        W, gphys, _ = cell_geo(S, e)
         U = _cell(S, u, e)
-        uq, Gq = _values(S.cell_phi, U), _grads(S, S.cell_dphi, U)
+        uq, Gq = _values(S.cell_phi, U), _grads(gphys, U)
         conv = np.einsum('pl,pcl->pc', uq, Gq)
         out[e] += np.einsum('p,pi,pc->ci', W, S.cell_phi, conv)
         for f in range(6):
-            d, s, nvec = face_normal(f)
+            Wf, nvec, _ = face_geo(S, e, f)
             um, _, up, _, bt = _exterior(S, u, e, f, g_faces)
-            wn = 0.5 * (um + up) @ nvec
+            wn = np.einsum('pk,pk->p', 0.5 * (um + up), nvec)
             udag = 0.5 * (um + up) + 0.5 * np.sign(wn)[:, None] * (um - up)
             flux = wn[:, None] * (udag - um)
-            Wf = S.face_w2 * S.mesh.face_area(d)
             out[e] += np.einsum('p,pi,pc->ci', Wf, S.face_phi[f], flux)
     return out.reshape(-1)
 
@@ -164,7 +195,6 @@ def convective_blocks(S, w, g_w):
     C = mesh.n_cells
     m = S.n_dofs_cell
     n3 = S.n ** 3
-    W = S.cell_w * mesh.volume()
     rows, cols, vals = [], [], []
     ii, jj = np.meshgrid(np.arange(n3), np.arange(n3), indexing='ij')
 
@@ -175,17 +205,17 @@ def convective_blocks(S, w, g_w):
             vals.append(blk.ravel())
 
     for e in range(C):
+        W, dphi, _ = cell_geo(S, e)
         wq = _values(S.cell_phi, _cell(S, w, e))
-        dphi = S._phys_grad(S.cell_dphi)
         put(e, e, np.einsum('p,pi,pl,pjl->ij', W, S.cell_phi, wq, dphi))
         for f in range(6):
-            d, s, nvec = face_normal(f)
+            d, s = divmod(f, 2)
             wm, _, wp, _, bt = _exterior(S, w, e, f, g_w)
             if bt == 'N':
                 continue
-            wn = 0.5 * (wm + wp) @ nvec
+            Wf, nvec, _ = face_geo(S, e, f)
+            wn = np.einsum('pk,pk->p', 0.5 * (wm + wp), nvec)
             up_fac = 0.5 * (1.0 - np.sign(wn)) * wn      # coefficient of (u^+ - u^-)
-            Wf = S.face_w2 * mesh.face_area(d)
             phi = S.face_phi[f]
             if bt == 'I':
                 nb = mesh.neighbor(e, f)
@@ -207,12 +237,11 @@ def convective_wall_rhs(S, w, g_w, g_u):
         for f in range(6):
             if mesh.boundary_type(e, f) != 'D':
                 continue
-            d, s, nvec = face_normal(f)
+            Wf, nvec, _ = face_geo(S, e, f)
             wm, _, wp, _, _ = _exterior(S, w, e, f, g_w)
-            wn = 0.5 * (wm + wp) @ nvec
+            wn = np.einsum('pk,pk->p', 0.5 * (wm + wp), nvec)
             up_fac = 0.5 * (1.0 - np.sign(wn)) * wn
             g = wall_data(S, g_u, e, f)
-            Wf = S.face_w2 * mesh.face_area(d)
             out[e] -= np.einsum('p,pi,pc->ci', Wf * up_fac * 2.0, S.face_phi[f], g)
     return out.reshape(-1)
 
@@ -220,12 +249,13 @@ def convective_wall_rhs(S, w, g_w, g_u):
 def convective_at_face(S, u, e, f):
     """(u.grad) u at the face points of (e, f) from the cell's own trace."""
     U = _cell(S, u, e)
-    return np.einsum('pl,pcl->pc', _values(S.face_phi[f], U), _grads(S, S.face_dphi[f], U))
+    return np.einsum('pl,pcl->pc', _values(S.face_phi[f], U), _grads(face_geo(S, e, f)[2], U))
 
 
 def l2_project_cell(S, e, values):
-    """Element-local L2 projection onto Q_k of point values (P,) or (P, c) at the cell Gauss points."""
-    W = S.cell_w * S.mesh.volume()
+    """Element-local L2 projection onto Q_k of point values (P,) or (P, c) at the cell Gauss
+    points, with the weights w det J of the cell."""
+    W = cell_geo(S, e)[0]
     phi = S.cell_phi
     Ms = np.einsum('p,pi,pj->ij', W, phi, phi)
     v = values if values.ndim == 2 else values[:, None]
@@ -240,20 +270,20 @@ def _curl(G):
 
 def viscous_boundary_terms(S, e, f, u_dd, rheology):
     """-nu n.(curl omega) + 2 n.(eps(u) grad nu) at the face points of (e, f) for the field u_dd."""
-    d, s, nvec = face_normal(f)
+    _, nvec, gface = face_geo(S, e, f)
     U = _cell(S, u_dd, e)
-    Gc = _grads(S, S.cell_dphi, U)
+    Gc = _grads(cell_geo(S, e)[1], U)
     omega = l2_project_cell(S, e, _curl(Gc))                       # (3, n^3)
-    Gw = _grads(S, S.face_dphi[f], omega)
+    Gw = _grads(gface, omega)
     curl_omega = _curl(Gw)
-    Gf = _grads(S, S.face_dphi[f], U)
+    Gf = _grads(gface, U)
     pts_f = S.face_points(e, f)
     nu_f = viscosity.evaluate(rheology, pts_f, Gf)
     nu_c = viscosity.evaluate(rheology, S.cell_points(e), Gc)
     nu_coef = l2_project_cell(S, e, nu_c)                          # (n^3,)
-    grad_nu = np.einsum('pil,i->pl', S._phys_grad(S.face_dphi[f]), nu_coef)
+    grad_nu = np.einsum('pil,i->pl', gface, nu_coef)
     eps = viscosity.strain_rate(Gf)
-    return -nu_f * (curl_omega @ nvec) + 2.0 * np.einsum('l,plk,pk->p', nvec, eps, grad_nu)
+    return -nu_f * np.einsum('pk,pk->p', curl_omega, nvec) + 2.0 * np.einsum('pl,plk,pk->p', nvec, eps, grad_nu)
 
 
 def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology, g_hist=None):
@@ -266,16 +296,20 @@ def ppe_boundary_datum(S, e, f, hist, order, dt, body, g_faces, rheology, g_hist
     gamma0, alpha, beta = BDF[order]
     m_p = min(order - 1, 2)
     betabar = EXTRAP[m_p]
-    d, s, nvec = face_normal(f)
+    nvec = face_geo(S, e, f)[1]
     P = S.nq ** 2
+
+    def dn(v):  # normal component per point
+        return np.einsum('pk,pk->p', v, nvec)
+
     nb = np.zeros(P)
     if body is not None:
-        nb = _values(S.face_phi[f], _cell(S, body, e)) @ nvec
-    g_new = wall_data(S, g_faces, e, f) @ nvec
-    g_old = [wall_data(S, g_faces if g_hist is None else g_hist[i], e, f) @ nvec for i in range(order)]
+        nb = dn(_values(S.face_phi[f], _cell(S, body, e)))
+    g_new = dn(wall_data(S, g_faces, e, f))
+    g_old = [dn(wall_data(S, g_faces if g_hist is None else g_hist[i], e, f)) for i in range(order)]
     dtg = (gamma0 * g_new - sum(alpha[i] * g_old[i] for i in range(order))) / dt
-    conv_m = sum(beta[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(order))
-    conv_mp = sum((betabar[i] * convective_at_face(S, hist[i], e, f) @ nvec for i in range(m_p)), np.zeros(P))
+    conv_m = sum(beta[i] * dn(convective_at_face(S, hist[i], e, f)) for i in range(order))
+    conv_mp = sum((betabar[i] * dn(convective_at_face(S, hist[i], e, f)) for i in range(m_p)), np.zeros(P))
     visc = np.zeros(P)
     if m_p > 0:
         u_dd = sum(betabar[i] * np.asarray(hist[i]) for i in range(m_p))
@@ -291,17 +325,17 @@ def ppe_rhs(Su, Sp, uhat, coef, boundary):
     mesh = Su.mesh
     C = mesh.n_cells
     out = np.zeros((C, Sp.n ** 3))
-    W = Su.cell_w * mesh.volume()
     for e in range(C):
+        W = cell_geo(Su, e)[0]
         uq = _values(Su.cell_phi, _cell(Su, uhat, e))
-        out[e] += coef * np.einsum('p,pil,pl->i', W, Sp._phys_grad(Sp.cell_dphi), uq)
+        out[e] += coef * np.einsum('p,pil,pl->i', W, cell_geo(Sp, e)[1], uq)
         for f in range(6):
-            d, s, nvec = face_normal(f)
-            Wf = Su.face_w2 * mesh.face_area(d)
+            Wf, nvec, _ = face_geo(Su, e, f)
             bt = mesh.boundary_type(e, f)
             if bt in ('I', 'N'):   # velocity Neumann (outflow): uhat^+ = uhat^-
                 um, _, up, _, _ = _exterior(Su, uhat, e, f, None)
-                out[e] -= coef * np.einsum('p,pi,p->i', Wf, Sp.face_phi[f], 0.5 * (um + up) @ nvec)
+                out[e] -= coef * np.einsum('p,pi,p->i', Wf, Sp.face_phi[f],
+                                           np.einsum('pk,pk->p', 0.5 * (um + up), nvec))
             elif bt == 'D':
                 out[e] += np.einsum('p,pi,p->i', Wf, Sp.face_phi[f], boundary[(e, f)])
     return out.reshape(-1)
@@ -312,13 +346,13 @@ def projection_rhs(Su, Sp, p):
     mesh = Su.mesh
     C = mesh.n_cells
     out = np.zeros((C, 3, Su.n ** 3))
-    W = Su.cell_w * mesh.volume()
     for e in range(C):
+        W, gphys, _ = cell_geo(Su, e)
         pq = Sp.cell_phi @ _cell(Sp, p, e)[0]
-        out[e] += np.einsum('p,pic,p->ci', W, Su._phys_grad(Su.cell_dphi), pq)
+        out[e] += np.einsum('p,pic,p->ci', W, gphys, pq)
         for f in range(6):
-            d, s, nvec = face_normal(f)
-            Wf = Su.face_w2 * mesh.face_area(d)
+            d, s = divmod(f, 2)
+            Wf, nvec, _ = face_geo(Su, e, f)
             pm = Sp.face_phi[f] @ _cell(Sp, p, e)[0]
             bt = mesh.boundary_type(e, f)
             if bt == 'I':
@@ -329,7 +363,7 @@ def projection_rhs(Su, Sp, p):
                 pavg = pm
             else:
                 continue
-            out[e] -= np.einsum('p,pi,p,c->ci', Wf, Su.face_phi[f], pavg, nvec)
+            out[e] -= np.einsum('p,pi,p,pc->ci', Wf, Su.face_phi[f], pavg, nvec)
     return out.reshape(-1)
 
 
@@ -345,15 +379,15 @@ def viscous_dirichlet_rhs(S, nu_face, g_faces):
             g = wall_data(S, g_faces, e, f)
             if not np.any(g):
                 continue
-            d, s, nvec = face_normal(f)
-            Wf = S.face_w2 * mesh.face_area(d)
-            Vt, Gt = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
+            Wf, nvec, gface = face_geo(S, e, f)
+            Vt, Gt = S._vector_basis(S.face_phi[f], gface)
             num = nu_face[e, f]
             tau = S._tau(e, None, num, num)
-            epsn = np.einsum('pakl,l->pak', _sym(Gt), nvec)
+            epsn = np.einsum('pakl,pl->pak', _sym(Gt), nvec)
+            gn = np.einsum('pk,pk->p', g, nvec)
             out[e] -= np.einsum('p,p,pak,pk->a', Wf, 2.0 * num, epsn, g)
             out[e] += np.einsum('p,p,pa->a', Wf, 2.0 * tau, np.einsum('pak,pk->pa', Vt, g)
-                                + np.einsum('pak,k->pa', Vt, nvec) * (g @ nvec)[:, None])
+                                + np.einsum('pak,pk->pa', Vt, nvec) * gn[:, None])
     return out.reshape(-1)
 
 
@@ -361,7 +395,8 @@ def cfl_dt(S, u, Cr):
     """Eq. (CFL_timestep_selection): Cr / k^1.5 / max_{e,q} |J^-1 u|."""
     vmax = 0.0
     for e in range(S.mesh.n_cells):
-        uq = _values(S.cell_phi, _cell(S, u, e)) / S.mesh.h[None, :]
+        Jinv = cell_geo(S, e)[2]
+        uq = np.einsum('pkl,pl->pk', Jinv, _values(S.cell_phi, _cell(S, u, e)))
         vmax = max(vmax, float(np.sqrt((uq ** 2).sum(axis=1)).max()))
     return Cr / S.k ** 1.5 / vmax
 
@@ -371,10 +406,10 @@ def penalty_parameters(S, u, dt, zeta_div=1.0, zeta_cont=1.0):
     ubar_e the cell mean of |u| and h_e = |Omega_e|^(1/3) (READING of "chosen according
     to Fehn2018b", Eq. penalty_step)."""
     C = S.mesh.n_cells
-    vol = S.mesh.volume()
-    W = S.cell_w * vol
     tdiv, tcon = np.zeros(C), np.zeros(C)
     for e in range(C):
+        W = cell_geo(S, e)[0]
+        vol = float(np.sum(W))
         uq = _values(S.cell_phi, _cell(S, u, e))
         ubar = float(np.sum(W * np.linalg.norm(uq, axis=1)) / vol)
         tdiv[e] = zeta_div * ubar * vol ** (1.0 / 3.0) / (S.k + 1) * dt
@@ -391,9 +426,6 @@ def penalty_blocks(S, tdiv, tcon):
     mesh = S.mesh
     C = mesh.n_cells
     m = S.n_dofs_cell
-    W = S.cell_w * mesh.volume()
-    V, G = S._vector_basis(S.cell_phi, S._phys_grad(S.cell_dphi))
-    div = np.einsum('qakk->qa', G)
     rows, cols, vals = [], [], []
     ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing='ij')
 
@@ -403,21 +435,24 @@ def penalty_blocks(S, tdiv, tcon):
         vals.append(blk.ravel())
 
     for e in range(C):
+        W, gphys, _ = cell_geo(S, e)
+        V, G = S._vector_basis(S.cell_phi, gphys)
+        div = np.einsum('qakk->qa', G)
         own = np.einsum('q,qak,qbk->ab', W, V, V) + tdiv[e] * np.einsum('q,qa,qb->ab', W, div, div)
         for f in range(6):
-            d, s, nvec = face_normal(f)
+            d, s = divmod(f, 2)
             bt = mesh.boundary_type(e, f)
             if bt == 'N':
                 continue
-            Wf = S.face_w2 * mesh.face_area(d)
-            Vt, _ = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
-            vn = np.einsum('qak,k->qa', Vt, nvec)
+            Wf, nvec, gface = face_geo(S, e, f)
+            Vt, _ = S._vector_basis(S.face_phi[f], gface)
+            vn = np.einsum('qak,qk->qa', Vt, nvec)
             if bt == 'I':
                 nb = mesh.neighbor(e, f)
                 fo = 2 * d + (1 - s)
                 tau = 0.5 * (tcon[e] + tcon[nb])
-                Vn, _ = S._vector_basis(S.face_phi[fo], S._phys_grad(S.face_dphi[fo]))
-                vnn = np.einsum('qak,k->qa', Vn, nvec)
+                Vn, _ = S._vector_basis(S.face_phi[fo], face_geo(S, nb, fo)[2])
+                vnn = np.einsum('qak,qk->qa', Vn, nvec)
                 own += tau * np.einsum('q,qa,qb->ab', Wf, vn, vn)
                 put(e, nb, -tau * np.einsum('q,qa,qb->ab', Wf, vn, vnn))
             else:
@@ -436,11 +471,10 @@ def penalty_wall_rhs(S, tcon, g_faces):
         for f in range(6):
             if mesh.boundary_type(e, f) != 'D':
                 continue
-            d, s, nvec = face_normal(f)
+            Wf, nvec, gface = face_geo(S, e, f)
             g = wall_data(S, g_faces, e, f)
-            Wf = S.face_w2 * mesh.face_area(d)
-            Vt, _ = S._vector_basis(S.face_phi[f], S._phys_grad(S.face_dphi[f]))
-            out[e] += tcon[e] * np.einsum('q,qak,k,q->a', Wf, Vt, nvec, g @ nvec)
+            Vt, _ = S._vector_basis(S.face_phi[f], gface)
+            out[e] += tcon[e] * np.einsum('q,qak,qk,q->a', Wf, Vt, nvec, np.einsum('pk,pk->p', g, nvec))
     return out.reshape(-1)
 
 
@@ -482,12 +516,13 @@ class Splitting:
         self.rheology = rheology
         self.g_faces = [np.zeros(3) if g_faces is None or f >= len(g_faces) else
                         (g_faces[f] if callable(g_faces[f]) else np.asarray(g_faces[f], float)) for f in range(7)]
-        self.Su = SIPG(mesh, k, 3, penalty_factor=penalty_factor)
-        self.Sp = SIPG(mesh, k - 1, 1, penalty_factor=penalty_factor, n_quad=k + 1)   # mixed forms
+        space = MappedSIPG if isinstance(mesh, MappedMesh) else SIPG   # trilinear or affine cells
+        self.Su = space(mesh, k, 3, penalty_factor=penalty_factor)
+        self.Sp = space(mesh, k - 1, 1, penalty_factor=penalty_factor, n_quad=k + 1)   # mixed forms
         # the pressure is Neumann where the velocity is Dirichlet and vice versa (Sec. 3.2)
         pbc = tuple('N' if b == 'D' else 'D' for b in mesh.bc)
         self.pmesh = mesh.with_bc(pbc)
-        self.Sp_op = SIPG(self.pmesh, k - 1, 1, penalty_factor=penalty_factor)      # PPE operator
+        self.Sp_op = space(self.pmesh, k - 1, 1, penalty_factor=penalty_factor)      # PPE operator
         self.body = None if body is None else np.asarray(body, dtype=np.float64)
         self.mode = viscosity_mode
         self.convective = convective   # 'explicit' (alpha_c = 0) or 'linear_implicit' (alpha_c = 1, u* = u#)
