@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     p.add_argument("--arith", default="f64ff", choices=["f64", "f64ff"],
                    help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
-    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear", "channel"],
+    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear", "channel", "f32apply"],
                    help="run one extra workload alone and print its JSON (profiling runs)")
     return p.parse_args()
 
@@ -56,6 +56,8 @@ def run_extra(name):
         out = trilinear_extras()
     elif name == "channel":
         out = channel_extras()
+    elif name == "f32apply":
+        out = f32_apply_extra()
     else:
         ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U, krylov_arith="f64ff")
         n = ctx.n_dofs("viscous")
@@ -67,6 +69,23 @@ def run_extra(name):
             out = picard_extras(ctx)
         ctx.close()
     print(json.dumps({"extra": name, "result": out}), flush=True)
+
+
+def f32_apply_extra(reps=40):
+    """FP32 viscous apply (the multigrid level operator) on the 32^3, k = 3 workload,
+    rotating four vector pairs larger than L2 together."""
+    import torch
+
+    from paper_2506_14424_gb300 import Context, inputs
+    ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U)
+    n = ctx.n_dofs("viscous")
+    u = torch.tensor(fourier_velocity(ctx.node_points("viscous", 0)), device="cuda")
+    ctx.set_viscosity(inputs.carreau_blood_like(), u)
+    xs = [torch.tensor(inputs.uniform_vector(n, seed=100 + i), device="cuda", dtype=torch.float32) for i in range(4)]
+    ys = [torch.empty_like(xs[0]) for _ in range(4)]
+    ms = time_apply(ctx, "viscous", xs[0], ys[0], reps, torch.cuda.current_stream(), rotate=(xs, ys))
+    ctx.close()
+    return {"ms": ms, "gdofs": n / ms / 1e6, "n_dofs": n}
 
 
 def dist_env():

@@ -38,12 +38,24 @@ struct TpcCfg {
   static constexpr int CW = NC == 3 ? 10 : 32;  // cells per warp
 };
 
-// Shared floats per warp: the gradient exchange of the cell term (9 tiles per
-// cell) or the face exchange (5 face tensors per cell and component).
+// Strides of the warp's shared exchange regions, padded so that the lanes of a
+// warp hit distinct banks (at most 2-way conflicts; found by enumerating the
+// access patterns below for 10 cells x 3 components and 32 cells):
+//   gradient tiles  G[cw*GC + (dir*3 + comp)*GT + q]   (cell term, viscous)
+//   face data       E[(cw*3 + comp)*EC + slot*ES + p]  (faces, viscous; 5 slots)
+//   scalar values   U[cw*UC + q]                       (cell term, Poisson)
+template <int N> struct TpcPad;
+template <> struct TpcPad<2> { static constexpr int GT = 8, GC = 73, ES = 4, EC = 21, UC = 9; };
+template <> struct TpcPad<3> { static constexpr int GT = 27, GC = 243, ES = 9, EC = 45, UC = 27; };
+template <> struct TpcPad<4> { static constexpr int GT = 65, GC = 585, ES = 16, EC = 81, UC = 65; };
+
+// Shared floats per warp.
 template <int N, int NC>
 __host__ __device__ constexpr int tpc_smem_floats() {
-  return NC == 3 ? (9 * N * N * N > 15 * N * N ? 9 * N * N * N : 15 * N * N) * TpcCfg<NC>::CW
-                 : N * N * N * TpcCfg<NC>::CW;
+  return NC == 3 ? (TpcPad<N>::GC * TpcCfg<NC>::CW > 3 * TpcPad<N>::EC * TpcCfg<NC>::CW
+                        ? TpcPad<N>::GC * TpcCfg<NC>::CW
+                        : 3 * TpcPad<N>::EC * TpcCfg<NC>::CW)
+                 : TpcPad<N>::UC * TpcCfg<NC>::CW;
 }
 
 // ---- register sweeps on an N^3 tile t[(iz*N + iy)*N + ix]
@@ -142,7 +154,7 @@ __device__ __forceinline__ void load_row(const float* __restrict__ src, float (&
 // direction t1, b along t2 (the node order of face_node in operator.cuh),
 // streamed row by row.
 template <int N, int D>
-__device__ __forceinline__ void face_trace(const float* __restrict__ src, int layer, const float* dS,
+__device__ __forceinline__ void face_trace(const float* __restrict__ src, bool last, const float (&dS)[N],
                                            float (&tr)[N * N], float (&nd)[N * N]) {
   constexpr int N2 = N * N;
   if constexpr (D == 0) {  // lines along x are rows (a = iy, b = iz)
@@ -156,7 +168,7 @@ __device__ __forceinline__ void face_trace(const float* __restrict__ src, int la
 #pragma unroll
         for (int j = 0; j < N; ++j) sd = fmaf(dS[j], r[j], sd);
         nd[b * N + a] = sd;
-        tr[b * N + a] = layer == 0 ? r[0] : r[N - 1];
+        tr[b * N + a] = last ? r[N - 1] : r[0];
       }
   } else {  // D = 1: a = ix, b = iz, rows (iy = j, iz = b); D = 2: a = ix, b = iy, rows (iy = b, iz = j)
 #pragma unroll
@@ -170,8 +182,8 @@ __device__ __forceinline__ void face_trace(const float* __restrict__ src, int la
 #pragma unroll
         for (int a = 0; a < N; ++a) {
           nd[b * N + a] = fmaf(dS[j], r[a], nd[b * N + a]);
-          if (j == 0 && layer == 0) tr[b * N + a] = r[a];
-          if (j == N - 1 && layer != 0) tr[b * N + a] = r[a];
+          if (j == 0 && !last) tr[b * N + a] = r[a];
+          if (j == N - 1 && last) tr[b * N + a] = r[a];
         }
       }
   }
@@ -207,7 +219,7 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
   const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
   const float ihd = ihf[D], iht1 = ihf[T1], iht2 = ihf[T2];
   const float area = (float)(g.h[T1] * g.h[T2]);
-#pragma unroll
+#pragma unroll 1
   for (int s = 0; s < 2; ++s) {
     const int f = 2 * D + s;
     int nb;
@@ -221,12 +233,21 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
       nb = bnd ? -1 : e + (s ? step : -step);
     }
     const bool inner = nb >= 0;
-    const bool neumann = !inner && face_bc_t<TOPO>(g, e, f) == 1;
+    const int bcf = TOPO ? face_bc_t<TOPO>(g, e, f) : (s ? g.bc[2 * D + 1] : g.bc[2 * D]);
+    const bool neumann = !inner && bcf == 1;
+    // normal-derivative rows of the own side and of the neighbour's side (registers:
+    // the side index is a loop variable)
+    float dso[N], dsn[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      dso[j] = s ? tb.dS1[j] : tb.dS0[j];
+      dsn[j] = s ? tb.dS0[j] : tb.dS1[j];
+    }
     // own and neighbour traces / normal derivatives at the face nodes
     float tm[N2], nm[N2], tp[N2], np[N2];
-    face_trace<N, D>(xe, s ? N - 1 : 0, s ? tb.dS1 : tb.dS0, tm, nm);
+    face_trace<N, D>(xe, s != 0, dso, tm, nm);
     if (inner) {
-      face_trace<N, D>(x + ((size_t)nb * NC + kk) * N3, s ? 0 : N - 1, s ? tb.dS0 : tb.dS1, tp, np);
+      face_trace<N, D>(x + ((size_t)nb * NC + kk) * N3, s == 0, dsn, tp, np);
     }
     // to the face Gauss points (a then b)
     rsweep2<N, 0, false>(tm, tb.S);
@@ -259,7 +280,8 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
     float gV[N2], gN[N2];
     if constexpr (NC == 3) {
       // publish the jump and the tangential derivatives (own, neighbour)
-      float* EX = tsm + (cw * 3 + kk) * 5 * N2;
+      constexpr int ES = TpcPad<N>::ES, EC = TpcPad<N>::EC;
+      float* EX = tsm + (cw * 3 + kk) * EC;
       float d1[N2], d2[N2];
       rderiv2<N, 0>(tm, d1, tb.Dg);
       rderiv2<N, 1>(tm, d2, tb.Dg);
@@ -267,8 +289,8 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
 #pragma unroll
         for (int p = 0; p < N2; ++p) {
           EX[p] = tm[p] - tp[p];
-          EX[N2 + p] = d1[p] * iht1;
-          EX[2 * N2 + p] = d2[p] * iht2;
+          EX[ES + p] = d1[p] * iht1;
+          EX[2 * ES + p] = d2[p] * iht2;
         }
       }
       if (inner) {
@@ -278,14 +300,14 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
       if (active) {
 #pragma unroll
         for (int p = 0; p < N2; ++p) {
-          EX[3 * N2 + p] = d1[p] * iht1;
-          EX[4 * N2 + p] = d2[p] * iht2;
+          EX[3 * ES + p] = d1[p] * iht1;
+          EX[4 * ES + p] = d2[p] * iht2;
         }
       }
       __syncwarp();
-      const float* ED = tsm + (cw * 3 + D) * 5 * N2;     // the normal component's data
-      const float* E1 = tsm + (cw * 3 + T1) * 5 * N2;
-      const float* E2 = tsm + (cw * 3 + T2) * 5 * N2;
+      const float* ED = tsm + (cw * 3 + D) * EC;     // the normal component's data
+      const float* E1 = tsm + (cw * 3 + T1) * EC;
+      const float* E2 = tsm + (cw * 3 + T2) * EC;
       const bool isD = kk == D;
       const int tsel = kk == T1 ? 1 : 2;                 // tangential direction of this component
       const float* nuf = nu_face + ((size_t)e * 6 + f) * N2;
@@ -308,8 +330,8 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
           gT1[p] = cq * E1[p] * iht1;
           gT2[p] = cq * E2[p] * iht2;
         } else {
-          const float tmk = ED[tsel * N2 + p];
-          const float tpk = inner ? ED[(tsel + 2) * N2 + p] : tmk;
+          const float tmk = ED[tsel * ES + p];
+          const float tpk = inner ? ED[(tsel + 2) * ES + p] : tmk;
           gV[p] = tW * jmp - (am * (nm[p] * ihd + tmk) + ap * (np[p] * ihd + tpk));
           gN[p] = cq * jmp * ihd;
           gT1[p] = 0.f;
@@ -346,7 +368,6 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
     rsweep2<N, 1, true>(gN, tb.S);
     rsweep2<N, 0, true>(gN, tb.S);
     if (!neumann) {
-      const float* dS = s ? tb.dS1 : tb.dS0;
       constexpr int STR = D == 0 ? 1 : (D == 1 ? N : N2);
 #pragma unroll
       for (int b = 0; b < N; ++b)
@@ -354,8 +375,10 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
         for (int a = 0; a < N; ++a) {
           const int base = D == 0 ? (a * N + b * N2) : (D == 1 ? (a + b * N2) : (a + b * N));
 #pragma unroll
-          for (int j = 0; j < N; ++j) t[base + j * STR] = fmaf(dS[j], gN[b * N + a], t[base + j * STR]);
-          t[base + (s ? N - 1 : 0) * STR] += gV[b * N + a];
+          for (int j = 0; j < N; ++j) t[base + j * STR] = fmaf(dso[j], gN[b * N + a], t[base + j * STR]);
+          const float vlast = s ? gV[b * N + a] : 0.f;
+          t[base] += gV[b * N + a] - vlast;
+          t[base + (N - 1) * STR] += vlast;
         }
     }
   }
@@ -395,8 +418,9 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
   rsweep3<N, 1, false>(t, tb.S);
   rsweep3<N, 2, false>(t, tb.S);  // t = u_k at the Gauss points
   if constexpr (NC == 3) {
-    // publish the physical gradient tiles G[cw][k][l][q] = d u_k / d x_l
-    float* G = tsm + (cw * 3 + kk) * 3 * N3;
+    // publish the physical gradient tiles: G(dir l, comp k)[q] = d u_k / d x_l
+    constexpr int GT = TpcPad<N>::GT, GC = TpcPad<N>::GC;
+    float* G = tsm + cw * GC + kk * GT;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       const int STR = l == 0 ? 1 : (l == 1 ? N : N2);
@@ -410,7 +434,7 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
             float s = 0.f;
 #pragma unroll
             for (int j = 0; j < N; ++j) s = fmaf(tb.Dg[o * N + j], t[off + j * STR], s);
-            if (active) G[l * N3 + off + o * STR] = s * ihf[l];
+            if (active) G[l * 3 * GT + off + o * STR] = s * ihf[l];
           }
         }
     }
@@ -421,11 +445,10 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
       const float W = tb.gw[q % N] * tb.gw[(q / N) % N] * tb.gw[q / N2] * detJ;
       t[q] *= mass * W;
     }
-    const float* Gk = tsm + (cw * 3 + kk) * 3 * N3;
+    const float* Gc = tsm + cw * GC;
     const float* nue = nu_cell + (size_t)e * N3;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      const float* Gl = tsm + (cw * 3 + l) * 3 * N3;
       const int STR = l == 0 ? 1 : (l == 1 ? N : N2);
 #pragma unroll
       for (int a = 0; a < N; ++a)
@@ -437,7 +460,7 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
           for (int j = 0; j < N; ++j) {
             const int q = off + j * STR;
             const float W = tb.gw[q % N] * tb.gw[(q / N) % N] * tb.gw[q / N2] * detJ;
-            F[j] = __ldg(nue + q) * W * (Gk[l * N3 + q] + Gl[kk * N3 + q]) * ihf[l];
+            F[j] = __ldg(nue + q) * W * (Gc[(l * 3 + kk) * GT + q] + Gc[(kk * 3 + l) * GT + q]) * ihf[l];
           }
 #pragma unroll
           for (int o = 0; o < N; ++o) {
@@ -451,7 +474,7 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
     __syncwarp();  // the face exchange reuses the shared region
   } else {
     // scalar: u_q kept in shared memory (private to the thread), acc in t
-    float* U = tsm + cw * N3;
+    float* U = tsm + cw * TpcPad<N>::UC;
 #pragma unroll
     for (int q = 0; q < N3; ++q) {
       U[q] = t[q];
