@@ -39,12 +39,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     p.add_argument("--arith", default="f64ff", choices=["f64", "f64ff"],
                    help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
-    p.add_argument("--extra", default=None, choices=["mass", "picard", "step", "trilinear", "channel", "f32apply"],
+    p.add_argument("--channel-steps", type=int, default=10, help="timed steps of the channel extras")
+    p.add_argument("--extra", default=None,
+                   choices=["mass", "picard", "step", "trilinear", "channel", "jchannel", "f32apply", "serve"],
                    help="run one extra workload alone and print its JSON (profiling runs)")
     return p.parse_args()
 
 
-def run_extra(name):
+def run_extra(name, steps=10):
     """One extra workload on its own (the commands of the ncu summaries in profiles/)."""
     import torch
 
@@ -55,9 +57,13 @@ def run_extra(name):
     elif name == "trilinear":
         out = trilinear_extras()
     elif name == "channel":
-        out = channel_extras()
+        out = channel_extras(steps=steps)
+    elif name == "jchannel":
+        out = channel_extras(steps=steps, jitter=True)
     elif name == "f32apply":
         out = f32_apply_extra()
+    elif name == "serve":
+        out = serving_full()
     else:
         ctx = Context(N_CELLS, N_CELLS, N_CELLS, K_U, krylov_arith="f64ff")
         n = ctx.n_dofs("viscous")
@@ -300,6 +306,10 @@ def run_gpu(args):
             "alu_peaks_tflops": {k: round(v, 3) for k, v in pk.items()}}
     if rank == 0:
         line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(sample_cells=1024)
+        if line["cpu_baseline"]:
+            line["cpu_baseline"]["note"] = ("the explicit-block Python oracle (element blocks rebuilt per cell), "
+                                            "not a tuned CPU implementation: a correctness reference, not a "
+                                            "speed baseline")
         line["extras"] = extras
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -373,7 +383,28 @@ def gpu_extras(ctx, xs, ys, stream):
     ms = time_apply(ctx, "poisson", xp, yp, 50, stream)
     out["poisson_f64_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr}
     ms = time_apply(ctx, "poisson", xp, yp, 50, stream, arith="f64ff")
-    out["poisson_f64ff_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr}
+    out["poisson_f64ff_apply_k2"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr,
+                                     "l2": "warm: x, y (14 MB) stay in L2"}
+    # L2-cold: 24 rotating pairs (340 MB) so that every apply reads x from HBM
+    xps = [torch.tensor(inputs.uniform_vector(npr, seed=400 + i), device="cuda") for i in range(24)]
+    yps = [torch.empty_like(xps[0]) for _ in xps]
+    for arith in ("f64", "f64ff"):
+        ms = time_apply(ctx, "poisson", xps[0], yps[0], 48, stream, arith=arith, rotate=(xps, yps))
+        out[f"poisson_{arith}_apply_k2_l2cold"] = {"ms": ms, "gdofs": npr / ms / 1e6, "n_dofs": npr,
+                                                   "l2": "cold: 24 rotating x/y pairs (340 MB)"}
+    del xps, yps
+    # the small FP64 configuration: 4^3 cells, k = 2, analytic viscosity, Jacobi-preconditioned
+    # CG to 1e-8 against the manufactured load (5,184 DoFs)
+    c1 = Context(4, 4, 4, 2, mg_precision="f64")
+    c1.set_viscosity({"law": "analytic"})
+    b1 = c1.rhs_manufactured("velocity")
+    c1.solve("viscous", b1, rtol=1e-8, precond="jacobi", maxit=2000, check=False)
+    torch.cuda.synchronize()
+    x1, st1 = c1.solve("viscous", b1, rtol=1e-8, precond="jacobi", maxit=2000, check=False)
+    out["jacobi_cg_4cubed_k2"] = {"seconds": st1["seconds"], "iterations": st1["iterations"],
+                                  "rel_residual": st1["rel_residual"], "status": st1["status"],
+                                  "n_dofs": c1.n_dofs(), "solves_per_s": 1.0 / st1["seconds"]}
+    c1.close()
     # mixed-precision vs all-FP64 multigrid solve, 16^3 cells, k = 4, sinker viscosity
     solves = []
     sink = inputs.sinker(seed=2, count=8, radius=0.1, nu_max=1.0)
@@ -412,6 +443,7 @@ def gpu_extras(ctx, xs, ys, stream):
                     ("splitting_step_32cubed_k3", step_extras),
                     ("trilinear_cells_32cubed_k3", trilinear_extras),
                     ("bfs_channel_steps", channel_extras),
+                    ("bfs_jittered_channel_steps", lambda: channel_extras(jitter=True)),
                     ("components_16cubed_k4", lambda: component_timings(stream)),
                     ("serving", serving_extras)):
         try:
@@ -550,10 +582,12 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
     return out
 
 
-def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=1.0):
+def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=1.0, jitter=False):
     """Projection-scheme steps on the backward-facing-step channel (inlet [-5, 0] x [1, 2],
     outlet [0, 30] x [0, 2], z in [0, 4] periodic, step height 1, expansion ratio 2), cubes
-    of side 1/8: 133,120 affine hexes, k = 3 velocity / k = 2 pressure. Parabolic inflow
+    of side 1/8: 133,120 hexes, k = 3 velocity / k = 2 pressure; with jitter the vertices
+    inside the fluid move by U(-0.05 h, 0.05 h)^3 (seed 4: trilinear cells, FP64 Krylov
+    operator), else affine cells (float-float Krylov operator). Parabolic inflow
     of maximum 1 ramped by sin^2(pi t / (2 t_ramp)), traction-free outflow at p = 0, no-slip
     walls and step, Carreau-Yasuda viscosity linear implicit, fluid at rest at t = 0,
     dt from the CFL rule (Cr = 0.3) at the full inflow velocity, CG to 1e-8 with the FP32
@@ -566,8 +600,9 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
     c = inputs.bfs_channel(cells_per_unit)
     t0 = time.perf_counter()
     ctx = Context(*c["dims"], k, extent=c["extent"], origin=c["lo"], active=c["active"], periodic=c["periodic"],
-                  bc_velocity="DNDDDD", bc_pressure="NDNNNN", bc_removed="DN", krylov_arith="f64ff",
-                  coarse_max_dofs=8000)
+                  bc_velocity="DNDDDD", bc_pressure="NDNNNN", bc_removed="DN",
+                  krylov_arith="f64" if jitter else "f64ff", coarse_max_dofs=8000, mg_precision="f32",
+                  vertices=inputs.bfs_vertices(c) if jitter else None)
     t_create = time.perf_counter() - t0
     rh = inputs.carreau_blood_like()
     n = ctx.n_dofs("viscous")
@@ -589,7 +624,9 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
     u = ctx.step_field("u")
     levels = [(tuple(ctx.level_info("viscous", l)[0]), ctx.level_info("viscous", l)[1], ctx.level_info("viscous", l)[2])
               for l in range(ctx.num_levels("viscous"))]
-    out = {"geometry": "affine cells (no vertex jitter)", "cells": ctx.n_cells, "n_dofs_velocity": n,
+    out = {"geometry": ("trilinear cells (5 % vertex jitter inside the fluid, seed 4)" if jitter
+                        else "affine cells (no vertex jitter)"),
+           "multigrid": "FP32 V-cycle, FP64 CG", "cells": ctx.n_cells, "n_dofs_velocity": n,
            "n_dofs_pressure": ctx.n_dofs("poisson"), "dt": dt,
            "steps_timed": steps, "create_seconds": t_create, "viscous_levels": levels,
            "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
@@ -709,37 +746,59 @@ def component_timings(stream, contrast=1e2):
     return out
 
 
-def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5):
+def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5, sizes=(8, 12, 16), degrees=(2, 3, 4),
+                   contrasts=(1.0, 1e2, 1e4), rhs="buoyancy", budget_gib=96, slots=8):
     """Served stream: Poisson arrivals, uneven sizes/degrees/contrasts, rtol 1e-8.
 
-    A bounded version of the 256-request stream (n^3 cells with n in {8, 12, 16},
-    k in {2, 3, 4}, contrast in {1, 1e2, 1e4}) so that the bench stays short; the
-    one-at-a-time baseline solves the same requests sequentially with the plain
-    FP64 path (FP64 CG and FP64 multigrid, one context per request) and is
-    queued against the same arrival times."""
+    Each request solves the viscous system on the n^3 unit cube (Dirichlet walls) with
+    the sphere ("sinker") viscosity of its contrast (8 spheres of radius 0.15, seed
+    1000 + i) and the buoyancy load b = M f of those spheres (f = -e_z inside them).
+    The server admits by HBM budget, runs one FP64 CG iteration per request and round
+    (FP64 operator, FP32 hp-multigrid V-cycle) with the fine-level applies of each degree
+    batched into one launch. The one-at-a-time baseline solves the same requests one
+    after another with the plain FP64 path (FP64 CG and FP64 multigrid, one context per
+    request): its service times are measured once and queued against each rate's
+    arrival times (FIFO). Latency = completion - arrival."""
     import numpy as np
+    import torch
 
     from paper_2506_14424_gb300 import Context, Server, inputs
 
     rng = np.random.default_rng(seed)
     specs = []
     for i in range(n_req):
-        specs.append({"n": int(rng.choice([8, 12, 16])), "k": int(rng.choice([2, 3, 4])),
-                      "contrast": float(rng.choice([1.0, 1e2, 1e4])), "seed": 1000 + i})
-    out = {"requests": n_req, "mix": "n^3 cells n in {8,12,16}, k in {2,3,4}, contrast {1,1e2,1e4}, rtol 1e-8"}
+        specs.append({"n": int(rng.choice(sizes)), "k": int(rng.choice(degrees)),
+                      "contrast": float(rng.choice(contrasts)), "seed": 1000 + i})
+    out = {"requests": n_req, "mix": f"n^3 cells n in {list(sizes)}, k in {list(degrees)}, sphere contrast "
+                                     f"{list(contrasts)}, {rhs} right-hand sides, rtol 1e-8",
+           "n_dofs_total": int(sum(3 * sp["n"] ** 3 * (sp["k"] + 1) ** 3 for sp in specs))}
+
+    def sinker(sp):
+        return inputs.sinker(seed=sp["seed"], count=8, radius=0.15, nu_max=sp["contrast"])
+
     # one-at-a-time FP64 service times
     service = []
     for sp in specs:
         t0 = time.perf_counter()
         c = Context(sp["n"], sp["n"], sp["n"], sp["k"], mg_precision="f64", krylov_arith="f64")
-        c.set_viscosity(inputs.sinker(seed=sp["seed"], count=8, radius=0.15, nu_max=sp["contrast"]))
-        import torch
-        u = torch.tensor(inputs.uniform_vector(c.n_dofs(), seed=sp["seed"]), device="cuda")
-        b = c.apply("viscous", u)
+        c.set_viscosity(sinker(sp))
+        nn = c.n_dofs()
+        if rhs == "buoyancy":
+            f = torch.zeros(nn, dtype=torch.float64, device="cuda").view(-1, 3, (sp["k"] + 1) ** 3)
+            pts = c.node_points("viscous", 0).reshape(-1, (sp["k"] + 1) ** 3, 3)
+            cen = np.asarray(sinker(sp)["centers"])
+            d2 = ((pts[:, :, None, :] - cen[None, None, :, :]) ** 2).sum(-1)
+            inside = (d2 <= 0.15 ** 2).any(-1)
+            f[:, 2] = -torch.tensor(inside.astype(np.float64), device="cuda")
+            b = c.mass("viscous", f.reshape(-1))
+        else:
+            b = c.apply("viscous", torch.tensor(inputs.uniform_vector(nn, seed=sp["seed"]), device="cuda"))
         c.solve("viscous", b, rtol=1e-8, precond="mg", maxit=400, check=False)
         torch.cuda.synchronize()
         c.close()
         service.append(time.perf_counter() - t0)
+    out["one_at_a_time_service_s"] = {"total": float(sum(service)), "mean": float(np.mean(service)),
+                                      "max": float(max(service))}
     runs = []
     for rate in rates:
         arr = np.cumsum(np.random.default_rng(seed + int(rate)).exponential(1.0 / rate, n_req))
@@ -748,17 +807,15 @@ def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5):
         for a_t, s_t in zip(arr, service):
             fin = max(fin, a_t) + s_t
             lat_seq.append(fin - a_t)
-        srv = Server(96 << 30, max_slots=8)
+        srv = Server(int(budget_gib) << 30, max_slots=slots)
         t0 = time.perf_counter()
         ids = []
         for sp, a_t in zip(specs, arr):
             dt = t0 + a_t - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            ids.append(srv.submit(sp["n"], sp["k"], inputs.sinker(seed=sp["seed"], count=8, radius=0.15,
-                                                                  nu_max=sp["contrast"]),
-                                  rtol=1e-8, maxit=400, seed=sp["seed"]))
-        srv.drain(600)
+            ids.append(srv.submit(sp["n"], sp["k"], sinker(sp), rtol=1e-8, maxit=400, seed=sp["seed"], rhs=rhs))
+        srv.drain(3600)
         t_end = time.perf_counter()
         res = [srv.poll(i)[0] for i in ids]
         srv.close()
@@ -767,11 +824,20 @@ def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5):
         runs.append({"rate_per_s": rate, "solves_per_s": n_req / (t_end - t0), "p50_s": float(np.percentile(lat, 50)),
                      "p99_s": float(np.percentile(lat, 99)), "converged": ok,
                      "max_rel_residual": max(r["rel_residual"] for r in res),
+                     "makespan_s": t_end - t0,
                      "one_at_a_time_fp64": {"solves_per_s": n_req / max(fin, arr[-1]),
                                             "p50_s": float(np.percentile(lat_seq, 50)),
                                             "p99_s": float(np.percentile(lat_seq, 99))}})
     out["runs"] = runs
     return out
+
+
+def serving_full():
+    """The configured stream: 256 requests, 8^3 .. 48^3 cells, k in {2, 3, 4, 5}, contrast
+    in {1, 1e2, 1e4}, sphere-buoyancy right-hand sides, Poisson arrivals at 10, 20, 50, 100
+    and 200 per second."""
+    return serving_extras(n_req=256, rates=(10.0, 20.0, 50.0, 100.0, 200.0), sizes=(8, 16, 24, 32, 40, 48),
+                          degrees=(2, 3, 4, 5), budget_gib=160, slots=12)
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -860,7 +926,7 @@ def run_reference(args):
 if __name__ == "__main__":
     a = parse()
     if a.extra:
-        run_extra(a.extra)
+        run_extra(a.extra, steps=a.channel_steps)
     elif a.impl == "reference":
         run_reference(a)
     else:

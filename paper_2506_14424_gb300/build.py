@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsipg.so")
-SOURCES = ["apply_f64.cu", "apply_f32.cu", "apply_ff.cu", "apply_tpc.cu", "viscosity.cu", "mg.cu", "capi.cu", "solve.cu", "noalloc.cu", "serve.cu", "mass.cu", "picard.cu", "split.cu", "step.cu", "gmres.cu", "mapped.cu", "cph.cu", "penalty.cu", "manufactured.cu", "peaks.cu", "tables.cpp"]
+SOURCES = ["apply_f64.cu", "apply_f32.cu", "apply_ff.cu", "apply_tpc.cu", "viscosity.cu", "mg.cu", "capi.cu", "solve.cu", "noalloc.cu", "serve.cu", "mass.cu", "picard.cu", "split.cu", "step.cu", "gmres.cu", "mapped.cu", "mapped_split.cu", "cph.cu", "penalty.cu", "manufactured.cu", "peaks.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -469,8 +469,6 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   cudaError_t e = cudaSuccess;
   int rc = SIPG_OK;
   if (ctx->mapped) {
-    // the multigrid of trilinear cells runs in FP64 (the trilinear kernels are FP64)
-    ctx->opts.mg_precision = SIPG_F64;
     const size_t nv = (size_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1) * 3;
     e = cudaMalloc(&ctx->dverts, sizeof(double) * nv);
     if (!e) e = cudaMemcpyAsync(ctx->dverts, mesh->vertices, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->st);
@@ -646,7 +644,11 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
                              op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr, mass, (const double*)x, (double*)y, 1, st));
       return SIPG_OK;
     } else {
-      return fail(SIPG_ERR_INVALID, "trilinear cells: FP64 applies only");
+      CK(launch_mapped_apply_f32(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam,
+                                 op == SIPG_OP_VISCOUS ? L.nu_cell32 : nullptr,
+                                 op == SIPG_OP_VISCOUS ? L.nu_face32 : nullptr, mass, (const float*)x, (float*)y, 1,
+                                 st));
+      return SIPG_OK;
     }
   }
   const T* nc = nullptr;
@@ -1006,13 +1008,17 @@ extern "C" int sipg_apply(sipg_ctx* ctx, int op, int prec, const void* x, void* 
 
 int sipg_ctx::mass_apply(int op, int prec, const void* x, void* y, double coeff, bool inverse) {
   sipg_ctx* ctx = this;
-  if (mapped) return fail(SIPG_ERR_INVALID, "cell mass operators are built for the box only");
   if (op != SIPG_OP_VISCOUS && op != SIPG_OP_POISSON) return fail(SIPG_ERR_INVALID, "unknown operator");
   if (prec != SIPG_F64 && prec != SIPG_F32 && prec != SIPG_F64_FF) return fail(SIPG_ERR_INVALID, "unknown arithmetic");
   if (!x || !y) return fail(SIPG_ERR_INVALID, "null vector");
   if (!std::isfinite(coeff) || (inverse && coeff == 0.0)) return fail(SIPG_ERR_INVALID, "mass coefficient");
   const Hier& H = hier[op];
   const Level& L = H.L[0];
+  if (mapped) {  // trilinear cells: w det J per point (FP64; S^-1 diag S^-T for the inverse)
+    if (prec == SIPG_F32) return fail(SIPG_ERR_INVALID, "trilinear cells: FP64 mass operators");
+    CK(launch_mapped_mass(L.n, H.ncomp, L.g, stabs[L.n], L.verts, coeff, inverse, (const double*)x, (double*)y, st));
+    return SIPG_OK;
+  }
   const double detJ = L.g.h[0] * L.g.h[1] * L.g.h[2];
   const double scale = inverse ? 1.0 / (coeff * detJ) : coeff * detJ;
   CK(launch_cell_mass(L.n, H.ncomp, L.g.ncells, tabs[L.n], prec, inverse, scale, x, y, st));

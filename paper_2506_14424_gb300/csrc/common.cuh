@@ -43,6 +43,8 @@ struct SplitTab {
   double dS0[kMaxN], dS1[kMaxN];
   double lg0[kMaxN], lg1[kMaxN], dlg0[kMaxN], dlg1[kMaxN];
   double gw[kMaxN], gp[kMaxN];  // Gauss weights and points on [0, 1]
+  double Sinv[kMaxN * kMaxN];    // S^-1 [j][q]: the Lagrange basis on the Gauss points at the
+                                 // Gauss-Lobatto nodes (Gauss-point values -> nodal values)
 };
 
 // Over-integration rule of the manufactured loads: nq Gauss points on [0, 1]

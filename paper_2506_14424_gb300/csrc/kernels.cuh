@@ -88,6 +88,28 @@ cudaError_t launch_penalty_wall(int n, const LevelGeom& g, const SplitTab& tab, 
                                 const double* tcon, double* y, cudaStream_t st);
 
 // ---- operators on trilinear cells (mapped.cu); n = degree + 1 (2..6)
+// forms of the splitting step on trilinear cells (mapped_split.cu)
+cudaError_t launch_mapped_convective(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                     const WallArg& wall_g, const double* u, double* y, cudaStream_t st);
+cudaError_t launch_mapped_ppe_boundary(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                       const WallArg& wall_g, const PpeBndArgs& a, const RheologyDev& rh,
+                                       const double* u0, const double* u1, double* sb, cudaStream_t st);
+cudaError_t launch_mapped_ppe_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double coef,
+                                  const double* uhat, const double* sb, double* r, cudaStream_t st);
+cudaError_t launch_mapped_projection_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                         const double* p, double* y, cudaStream_t st);
+cudaError_t launch_mapped_viscous_wall_rhs(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                           const double* lam, const WallArg& wall_g, const double* nu_face,
+                                           double* y, cudaStream_t st);
+cudaError_t launch_mapped_cfl_max(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                  const double* u, unsigned long long* vmax_bits, cudaStream_t st);
+cudaError_t launch_mapped_mass(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                               double coeff, bool inverse, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_mapped_boundary_points(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                          double* xyz, cudaStream_t st);
+cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                    const double* lam, const float* nu_cell, const float* nu_face, double mass,
+                                    const float* x, float* y, int nbatch, cudaStream_t st);
 cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                 const double* lam, const double* nu_cell, const double* nu_face, double mass,
                                 const double* x, double* y, int nbatch, cudaStream_t st);

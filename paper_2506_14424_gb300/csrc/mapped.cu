@@ -15,6 +15,7 @@
 // instead of being stored: per point, reference gradients -> physical ->
 // flux -> back to reference coefficients in one pass.
 #include "kernels.cuh"
+#include "mapped_geom.cuh"
 #include "sweeps.cuh"
 
 // Resident CTAs per SM requested from the compiler for the trilinear apply: the
@@ -27,147 +28,23 @@ template <int N> struct MappedMinBlocks { static constexpr int value = N <= 4 ? 
 namespace sipg {
 namespace {
 using namespace sweeps;
-
-__device__ __forceinline__ void load_cell_vertices(const LevelGeom& g, const double* __restrict__ verts, int e,
-                                                   double (*X)[3]) {
-  int ijk[3];
-  cell_ijk(g, e, ijk);
-  const int i = ijk[0], j = ijk[1], k = ijk[2];
-  for (int t = threadIdx.x; t < 24; t += blockDim.x) {
-    const int v = t / 3, c = t % 3;
-    const int a = v & 1, b = (v >> 1) & 1, cc = (v >> 2) & 1;
-    const size_t idx = ((size_t)(k + cc) * (g.ny + 1) + (j + b)) * (g.nx + 1) + (i + a);
-    X[v][c] = verts[idx * 3 + c];
-  }
-}
-
-// J[k][l] = d x_k / d xi_l of the trilinear map at xi; also x if wanted
-__device__ __forceinline__ void trilinear_jac(const double (*X)[3], double x0, double x1, double x2, double J[3][3],
-                                              double* pos = nullptr) {
-  for (int k = 0; k < 3; ++k) {
-    J[k][0] = J[k][1] = J[k][2] = 0.0;
-    if (pos) pos[k] = 0.0;
-  }
-#pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
-    const double fx = a ? x0 : 1.0 - x0, fy = b ? x1 : 1.0 - x1, fz = c ? x2 : 1.0 - x2;
-    const double sx = a ? 1.0 : -1.0, sy = b ? 1.0 : -1.0, sz = c ? 1.0 : -1.0;
-    const double d0 = sx * fy * fz, d1 = fx * sy * fz, d2 = fx * fy * sz;
-    for (int k = 0; k < 3; ++k) {
-      J[k][0] += X[v][k] * d0;
-      J[k][1] += X[v][k] * d1;
-      J[k][2] += X[v][k] * d2;
-      if (pos) pos[k] += X[v][k] * fx * fy * fz;
-    }
-  }
-}
-
-__device__ __forceinline__ double inverse3(const double J[3][3], double Ji[3][3]) {
-  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-  const double id = 1.0 / det;
-  Ji[0][0] = c00 * id;
-  Ji[1][0] = c01 * id;
-  Ji[2][0] = c02 * id;
-  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-  return det;
-}
-
-// node (layer along d, a along t1, b along t2) of an n^3 tensor
-__device__ __forceinline__ int lnode(int d, int layer, int a, int b, int n) {
-  int i[3];
-  int t1, t2;
-  face_dirs(d, &t1, &t2);
-  i[d] = layer;
-  i[t1] = a;
-  i[t2] = b;
-  return (i[2] * n + i[1]) * n + i[0];
-}
-
-// Values and reference derivatives at the face Gauss points of a nodal field U
-// (n^3): out[0] values, out[1] d/dxi_d, out[2] d/dxi_t1, out[3] d/dxi_t2 (N^2
-// each); scratch: 5 N^2.
-template <int N>
-__device__ void face_eval(const double* U, int d, int s, const STabSm& T, double* out, double* sc) {
-  constexpr int N2 = N * N;
-  double *L = sc, *D = sc + N2, *A = sc + 2 * N2, *B = sc + 3 * N2, *C = sc + 4 * N2;
-  for (int p = threadIdx.x; p < N2; p += blockDim.x) {
-    const int a = p % N, b = p / N;
-    L[p] = U[lnode(d, s ? N - 1 : 0, a, b, N)];
-    double acc = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc += T.dS[s][i] * U[lnode(d, i, a, b, N)];
-    D[p] = acc;
-  }
-  __syncthreads();
-  sweep<N, N, 1, 0, N, false>(T.S, N, L, A);
-  sweep<N, N, 1, 0, N, false>(T.DS, N, L, B);
-  sweep<N, N, 1, 0, N, false>(T.S, N, D, C);
-  __syncthreads();
-  sweep<N, N, 1, 1, N, false>(T.S, N, A, out);            // values
-  sweep<N, N, 1, 1, N, false>(T.S, N, C, out + N2);       // d/dxi_d
-  sweep<N, N, 1, 1, N, false>(T.S, N, B, out + 2 * N2);   // d/dxi_t1
-  sweep<N, N, 1, 1, N, false>(T.DS, N, A, out + 3 * N2);  // d/dxi_t2
-  __syncthreads();
-}
-
-// Transpose of face_eval: add to the nodal tensor Y the test-side contributions
-// of coefficients cf[0] (value), cf[1] (d/dxi_d), cf[2] (d/dxi_t1), cf[3] (d/dxi_t2).
-template <int N>
-__device__ void face_eval_t(const double* cf, int d, int s, const STabSm& T, double* Y, double* sc) {
-  constexpr int N2 = N * N, N3 = N2 * N;
-  double *A = sc, *B = sc + N2, *C = sc + 2 * N2, *L = sc + 3 * N2, *D = sc + 4 * N2;
-  sweep<N, N, 1, 1, N, true>(T.S, N, cf, A);
-  sweep<N, N, 1, 1, N, true>(T.S, N, cf + N2, C);
-  sweep<N, N, 1, 1, N, true>(T.S, N, cf + 2 * N2, B);
-  __syncthreads();
-  sweep<N, N, 1, 0, N, true>(T.S, N, A, L);   // value part
-  sweep<N, N, 1, 0, N, true>(T.S, N, C, D);   // normal part
-  __syncthreads();
-  sweep<N, N, 1, 0, N, true>(T.DS, N, B, A);  // d/dxi_t1 part (A is free again)
-  sweep<N, N, 1, 1, N, true>(T.DS, N, cf + 3 * N2, C);
-  __syncthreads();
-  for (int p = threadIdx.x; p < N2; p += blockDim.x) L[p] += A[p];
-  sweep<N, N, 1, 0, N, true>(T.S, N, C, B);   // d/dxi_t2 part
-  __syncthreads();
-  for (int p = threadIdx.x; p < N2; p += blockDim.x) A[p] = L[p] + B[p];
-  __syncthreads();
-  // layer nodes: values and tangential parts; every node along the normal line: normal part
-  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
-    const int idx[3] = {i % N, (i / N) % N, i / N2};
-    int t1, t2;
-    face_dirs(d, &t1, &t2);
-    const int p = idx[t1] + N * idx[t2];
-    double v = T.dS[s][idx[d]] * D[p];
-    if (idx[d] == (s ? N - 1 : 0)) v += A[p];
-    Y[i] += v;
-  }
-  __syncthreads();
-}
-
-template <int N, int NC>
+using namespace mgeo;
+template <int N, int NC, typename R>
 __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapped_apply_kernel(LevelGeom g, SplitTab tab,
                                                                      const double* __restrict__ verts,
                                                                      const double* __restrict__ lam,
-                                                                     const double* __restrict__ nu_cell,
-                                                                     const double* __restrict__ nu_face, double mass,
-                                                                     const double* __restrict__ x,
-                                                                     double* __restrict__ y, int64_t batch_stride) {
+                                                                     const R* __restrict__ nu_cell,
+                                                                     const R* __restrict__ nu_face, double mass_d,
+                                                                     const R* __restrict__ x,
+                                                                     R* __restrict__ y, int64_t batch_stride) {
   constexpr int N3 = N * N * N, N2 = N * N;
-  __shared__ STabSm T;
-  __shared__ double X[8][3], XN[8][3];
+  __shared__ STabSmT<R> T;
+  __shared__ R X[8][3], XN[8][3];
+  const R mass = (R)mass_d;
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
-  __shared__ double U[NC][N3], Q[NC][N3], G[NC][3][N3], T0[N3], T1[N3], OUT[NC][N3];
-  __shared__ double FM[NC][4 * N2], FP[NC][4 * N2], CF[NC][4 * N2], SC[5 * N2];
+  __shared__ R U[NC][N3], Q[NC][N3], G[NC][3][N3], T0[N3], T1[N3], OUT[NC][N3];
+  __shared__ R FM[NC][4 * N2], FP[NC][4 * N2], CF[NC][4 * N2], SC[5 * N2];
   const int e = blockIdx.x;
   load_tab(tab, T);
   load_cell_vertices(g, verts, e, X);
@@ -180,16 +57,16 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
   __syncthreads();
   for (int q = threadIdx.x; q < N3; q += blockDim.x) {
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
-    double J[3][3], Ji[3][3];
-    trilinear_jac(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J);
-    const double det = inverse3(J, Ji);
-    const double W = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
-    double Gp[NC][3];
+    R J[3][3], Ji[3][3];
+    trilinear_jac<R>(X, (R)tab.gp[qx], (R)tab.gp[qy], (R)tab.gp[qz], J);
+    const R det = inverse3(J, Ji);
+    const R W = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
+    R Gp[NC][3];
     for (int c = 0; c < NC; ++c)
       for (int l = 0; l < 3; ++l) Gp[c][l] = G[c][0][q] * Ji[0][l] + G[c][1][q] * Ji[1][l] + G[c][2][q] * Ji[2][l];
-    double Tf[NC][3];
+    R Tf[NC][3];
     if (NC == 3) {
-      const double nu = nu_cell[(size_t)e * N3 + q];
+      const R nu = nu_cell[(size_t)e * N3 + q];
       for (int c = 0; c < 3; ++c)
         for (int l = 0; l < 3; ++l) Tf[c][l] = nu * (Gp[c][l] + Gp[l][c]);  // 2 nu eps(u)
     } else {
@@ -211,7 +88,7 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
     sweep3<N, N, true>(T.S, N, Q[c], T0, T1, OUT[c]);
   }
   // ---- faces
-  const double lam_e = lam[e];
+  const R lam_e = (R)lam[e];
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     int t1, t2;
@@ -225,35 +102,35 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
       for (int c = 0; c < NC; ++c) face_eval<N>(x + (size_t)nb * NC * N3 + c * N3, d, 1 - s, T, FP[c], SC);
     }
     __syncthreads();
-    const double orient = (2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0);
-    const double lam_p = nb >= 0 ? lam[nb] : lam_e;
-    const double tau0 = g.cip * (double)(N * N) * fmax(lam_e, lam_p);
+    const R orient = R((2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0));
+    const R lam_p = nb >= 0 ? (R)lam[nb] : lam_e;
+    const R tau0 = R(g.cip * (double)(N * N)) * (lam_e > lam_p ? lam_e : lam_p);
     for (int p = threadIdx.x; p < N2; p += blockDim.x) {
-      double xi[3];
-      xi[d] = s ? 1.0 : 0.0;
-      xi[t1] = tab.gp[p % N];
-      xi[t2] = tab.gp[p / N];
-      double Jm[3][3], Jim[3][3], Jp[3][3], Jip[3][3];
-      trilinear_jac(X, xi[0], xi[1], xi[2], Jm);
+      R xi[3];
+      xi[d] = s ? R(1) : R(0);
+      xi[t1] = (R)tab.gp[p % N];
+      xi[t2] = (R)tab.gp[p / N];
+      R Jm[3][3], Jim[3][3], Jp[3][3], Jip[3][3];
+      trilinear_jac<R>(X, xi[0], xi[1], xi[2], Jm);
       inverse3(Jm, Jim);
       if (nb >= 0) {
-        double xo[3] = {xi[0], xi[1], xi[2]};
-        xo[d] = s ? 0.0 : 1.0;
-        trilinear_jac(XN, xo[0], xo[1], xo[2], Jp);
+        R xo[3] = {xi[0], xi[1], xi[2]};
+        xo[d] = s ? R(0) : R(1);
+        trilinear_jac<R>(XN, xo[0], xo[1], xo[2], Jp);
         inverse3(Jp, Jip);
       } else {
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) Jip[a][b] = Jim[a][b];
       }
-      const double ta[3] = {Jm[0][t1], Jm[1][t1], Jm[2][t1]}, tb[3] = {Jm[0][t2], Jm[1][t2], Jm[2][t2]};
-      double n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
-      const double area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      const R ta[3] = {Jm[0][t1], Jm[1][t1], Jm[2][t1]}, tb[3] = {Jm[0][t2], Jm[1][t2], Jm[2][t2]};
+      R n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
+      const R area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
       for (int k = 0; k < 3; ++k) n[k] *= orient / area;
-      const double W = T.gw[p % N] * T.gw[p / N] * area;
+      const R W = T.gw[p % N] * T.gw[p / N] * area;
       // physical traces
-      double um[NC], up[NC], Gm[NC][3], Gq[NC][3];
+      R um[NC], up[NC], Gm[NC][3], Gq[NC][3];
       for (int c = 0; c < NC; ++c) {
-        double rm[3], rp[3];
+        R rm[3], rp[3];
         rm[d] = FM[c][N2 + p];
         rm[t1] = FM[c][2 * N2 + p];
         rm[t2] = FM[c][3 * N2 + p];
@@ -270,42 +147,42 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
           for (int l = 0; l < 3; ++l) Gq[c][l] = Gm[c][l];
         }
       }
-      double cv[NC], S[NC][3];
+      R cv[NC], S[NC][3];
       if (NC == 3) {
-        const double num = nu_face[((size_t)e * 6 + f) * N2 + p];
-        const double nup = nb >= 0 ? nu_face[((size_t)nb * 6 + fo) * N2 + p] : num;
-        double nub = num > nup ? num : nup;
-        if (g.face_nu == 1) nub = 0.5 * (num + nup);
-        if (g.face_nu == 2) nub = 2.0 * num * nup / (num + nup);
-        const double tau = tau0 * nub;
-        double jm[3], jn = 0.0;
+        const R num = nu_face[((size_t)e * 6 + f) * N2 + p];
+        const R nup = nb >= 0 ? nu_face[((size_t)nb * 6 + fo) * N2 + p] : num;
+        R nub = num > nup ? num : nup;
+        if (g.face_nu == 1) nub = R(0.5) * (num + nup);
+        if (g.face_nu == 2) nub = R(2) * num * nup / (num + nup);
+        const R tau = tau0 * nub;
+        R jm[3], jn = R(0);
         for (int c = 0; c < 3; ++c) {
           jm[c] = um[c] - up[c];
           jn += jm[c] * n[c];
         }
         for (int c = 0; c < 3; ++c) {
           // (A + A^T) n, A = (nu- Gm + nu+ Gp)/2
-          double an = 0.0;
+          R an = R(0);
           for (int l = 0; l < 3; ++l)
-            an += 0.5 * (num * (Gm[c][l] + Gm[l][c]) + nup * (Gq[c][l] + Gq[l][c])) * n[l];
+            an += R(0.5) * (num * (Gm[c][l] + Gm[l][c]) + nup * (Gq[c][l] + Gq[l][c])) * n[l];
           cv[c] = W * (-an + tau * (jm[c] + n[c] * jn));
-          for (int l = 0; l < 3; ++l) S[c][l] = -W * num * 0.5 * (jm[c] * n[l] + jm[l] * n[c]);
+          for (int l = 0; l < 3; ++l) S[c][l] = -W * num * R(0.5) * (jm[c] * n[l] + jm[l] * n[c]);
         }
       } else {
-        const double tau = tau0;
-        const double jm = um[0] - up[0];
-        double gn = 0.0;
-        for (int l = 0; l < 3; ++l) gn += 0.5 * (Gm[0][l] + Gq[0][l]) * n[l];
+        const R tau = tau0;
+        const R jm = um[0] - up[0];
+        R gn = R(0);
+        for (int l = 0; l < 3; ++l) gn += R(0.5) * (Gm[0][l] + Gq[0][l]) * n[l];
         cv[0] = W * (-gn + tau * jm);
-        for (int l = 0; l < 3; ++l) S[0][l] = -W * 0.5 * jm * n[l];
+        for (int l = 0; l < 3; ++l) S[0][l] = -W * R(0.5) * jm * n[l];
       }
       for (int c = 0; c < NC; ++c) {
-        double R[3];
-        for (int m = 0; m < 3; ++m) R[m] = S[c][0] * Jim[m][0] + S[c][1] * Jim[m][1] + S[c][2] * Jim[m][2];
+        R Rv[3];
+        for (int m = 0; m < 3; ++m) Rv[m] = S[c][0] * Jim[m][0] + S[c][1] * Jim[m][1] + S[c][2] * Jim[m][2];
         CF[c][p] = cv[c];
-        CF[c][N2 + p] = R[d];
-        CF[c][2 * N2 + p] = R[t1];
-        CF[c][3 * N2 + p] = R[t2];
+        CF[c][N2 + p] = Rv[d];
+        CF[c][2 * N2 + p] = Rv[t1];
+        CF[c][3 * N2 + p] = Rv[t2];
       }
     }
     __syncthreads();
@@ -486,10 +363,27 @@ cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const Spli
   const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
   const dim3 grid(g.ncells, nbatch);
   if (ncomp == 3) {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3><<<grid, kSplitThreads, 0, st>>>(
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, double><<<grid, kSplitThreads, 0, st>>>(
                                 g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
   } else {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1><<<grid, kSplitThreads, 0, st>>>(
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, double><<<grid, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+  }
+  return cudaGetLastError();
+}
+
+// the same operator in FP32 (multigrid levels: geometry, sweeps and flux in binary32)
+cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
+                                    const double* lam, const float* nu_cell, const float* nu_face, double mass,
+                                    const float* x, float* y, int nbatch, cudaStream_t st) {
+  if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
+  const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
+  const dim3 grid(g.ncells, nbatch);
+  if (ncomp == 3) {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, float><<<grid, kSplitThreads, 0, st>>>(
+                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+  } else {
+    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, float><<<grid, kSplitThreads, 0, st>>>(
                                 g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
   }
   return cudaGetLastError();

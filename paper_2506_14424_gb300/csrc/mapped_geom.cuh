@@ -1,0 +1,142 @@
+// Geometry of trilinear (non-affine) hexahedra for the kernels of mapped.cu and
+// mapped_split.cu: cell vertices, the Jacobian of the trilinear map and its
+// inverse at a reference point, and the face evaluation / its transpose of a
+// nodal field (values and reference derivatives at the face Gauss points).
+// Device code only; one CTA per cell (split.cu style, shared-memory tensors).
+#pragma once
+#include "sweeps.cuh"
+
+namespace sipg {
+namespace mgeo {
+using namespace sweeps;
+
+template <typename R>
+__device__ __forceinline__ void load_cell_vertices(const LevelGeom& g, const double* __restrict__ verts, int e,
+                                                   R (*X)[3]) {
+  int ijk[3];
+  cell_ijk(g, e, ijk);
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  for (int t = threadIdx.x; t < 24; t += blockDim.x) {
+    const int v = t / 3, c = t % 3;
+    const int a = v & 1, b = (v >> 1) & 1, cc = (v >> 2) & 1;
+    const size_t idx = ((size_t)(k + cc) * (g.ny + 1) + (j + b)) * (g.nx + 1) + (i + a);
+    X[v][c] = (R)verts[idx * 3 + c];
+  }
+}
+
+// J[k][l] = d x_k / d xi_l of the trilinear map at xi; also x if wanted
+template <typename R>
+__device__ __forceinline__ void trilinear_jac(const R (*X)[3], R x0, R x1, R x2, R J[3][3], R* pos = nullptr) {
+  for (int k = 0; k < 3; ++k) {
+    J[k][0] = J[k][1] = J[k][2] = R(0);
+    if (pos) pos[k] = R(0);
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const int a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
+    const R fx = a ? x0 : R(1) - x0, fy = b ? x1 : R(1) - x1, fz = c ? x2 : R(1) - x2;
+    const R sx = a ? R(1) : R(-1), sy = b ? R(1) : R(-1), sz = c ? R(1) : R(-1);
+    const R d0 = sx * fy * fz, d1 = fx * sy * fz, d2 = fx * fy * sz;
+    for (int k = 0; k < 3; ++k) {
+      J[k][0] += X[v][k] * d0;
+      J[k][1] += X[v][k] * d1;
+      J[k][2] += X[v][k] * d2;
+      if (pos) pos[k] += X[v][k] * fx * fy * fz;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R inverse3(const R J[3][3], R Ji[3][3]) {
+  const R c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const R c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const R c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const R det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  const R id = R(1) / det;
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  return det;
+}
+
+// node (layer along d, a along t1, b along t2) of an n^3 tensor
+__device__ __forceinline__ int lnode(int d, int layer, int a, int b, int n) {
+  int i[3];
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  i[d] = layer;
+  i[t1] = a;
+  i[t2] = b;
+  return (i[2] * n + i[1]) * n + i[0];
+}
+
+// Values and reference derivatives at the face Gauss points of a nodal field U
+// (n^3): out[0] values, out[1] d/dxi_d, out[2] d/dxi_t1, out[3] d/dxi_t2 (N^2
+// each); scratch: 5 N^2.
+template <int N, typename R>
+__device__ void face_eval(const R* U, int d, int s, const STabSmT<R>& T, R* out, R* sc) {
+  constexpr int N2 = N * N;
+  R *L = sc, *D = sc + N2, *A = sc + 2 * N2, *B = sc + 3 * N2, *C = sc + 4 * N2;
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+    const int a = p % N, b = p / N;
+    L[p] = U[lnode(d, s ? N - 1 : 0, a, b, N)];
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc += T.dS[s][i] * U[lnode(d, i, a, b, N)];
+    D[p] = acc;
+  }
+  __syncthreads();
+  sweep<N, N, 1, 0, N, false>(T.S, N, L, A);
+  sweep<N, N, 1, 0, N, false>(T.DS, N, L, B);
+  sweep<N, N, 1, 0, N, false>(T.S, N, D, C);
+  __syncthreads();
+  sweep<N, N, 1, 1, N, false>(T.S, N, A, out);            // values
+  sweep<N, N, 1, 1, N, false>(T.S, N, C, out + N2);       // d/dxi_d
+  sweep<N, N, 1, 1, N, false>(T.S, N, B, out + 2 * N2);   // d/dxi_t1
+  sweep<N, N, 1, 1, N, false>(T.DS, N, A, out + 3 * N2);  // d/dxi_t2
+  __syncthreads();
+}
+
+// Transpose of face_eval: add to the nodal tensor Y the test-side contributions
+// of coefficients cf[0] (value), cf[1] (d/dxi_d), cf[2] (d/dxi_t1), cf[3] (d/dxi_t2).
+template <int N, typename R>
+__device__ void face_eval_t(const R* cf, int d, int s, const STabSmT<R>& T, R* Y, R* sc) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  R *A = sc, *B = sc + N2, *C = sc + 2 * N2, *L = sc + 3 * N2, *D = sc + 4 * N2;
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf, A);
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf + N2, C);
+  sweep<N, N, 1, 1, N, true>(T.S, N, cf + 2 * N2, B);
+  __syncthreads();
+  sweep<N, N, 1, 0, N, true>(T.S, N, A, L);   // value part
+  sweep<N, N, 1, 0, N, true>(T.S, N, C, D);   // normal part
+  __syncthreads();
+  sweep<N, N, 1, 0, N, true>(T.DS, N, B, A);  // d/dxi_t1 part (A is free again)
+  sweep<N, N, 1, 1, N, true>(T.DS, N, cf + 3 * N2, C);
+  __syncthreads();
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) L[p] += A[p];
+  sweep<N, N, 1, 0, N, true>(T.S, N, C, B);   // d/dxi_t2 part
+  __syncthreads();
+  for (int p = threadIdx.x; p < N2; p += blockDim.x) A[p] = L[p] + B[p];
+  __syncthreads();
+  // layer nodes: values and tangential parts; every node along the normal line: normal part
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) {
+    const int idx[3] = {i % N, (i / N) % N, i / N2};
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    const int p = idx[t1] + N * idx[t2];
+    R v = T.dS[s][idx[d]] * D[p];
+    if (idx[d] == (s ? N - 1 : 0)) v += A[p];
+    Y[i] += v;
+  }
+  __syncthreads();
+}
+
+
+}  // namespace mgeo
+}  // namespace sipg

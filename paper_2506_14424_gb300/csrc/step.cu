@@ -1,9 +1,10 @@
 // One time step of the projection (dual splitting) scheme on affine grids (the
-// box, the backward-facing-step channel), Sec. 3.2 /
-// 5.1, Alg. 1, the convective term explicit (alpha_c = 0) or linearly implicit
-// in the viscous step (alpha_c = 1, u* = u#, GMRES): host sequence of library
-// kernels (split.cu forms, cell mass operators, MG-CG / GMRES solves, the
-// Picard loop, the optional divergence and continuity penalty step).
+// box, the backward-facing-step channel) and on trilinear cells (the jittered
+// channel), Sec. 3.2 / 5.1, Alg. 1, the convective term explicit (alpha_c = 0)
+// or, on affine grids, linearly implicit in the viscous step (alpha_c = 1,
+// u* = u#, GMRES): host sequence of library kernels (split.cu / mapped_split.cu
+// forms, cell mass operators, MG-CG / GMRES solves, the Picard loop, the
+// optional divergence and continuity penalty step on affine grids).
 //
 // State between steps: u^n, u^{n-1}, C(u^{n-1}) (the convective vector of the
 // previous step is reused), p^n (initial guess of the next pressure solve).
@@ -47,8 +48,25 @@ bool walls_ok(const sipg_ctx* ctx) {
 
 int check_forms(sipg_ctx* ctx) {
   if (ctx->opts.k_u < 2 || ctx->opts.k_u > 5) return ctx->fail(SIPG_ERR_INVALID, "velocity degree 2..5");
-  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the splitting-step forms are built for affine cells only");
   return SIPG_OK;
+}
+
+// the forms of the fine velocity level, affine (split.cu) or trilinear (mapped_split.cu)
+cudaError_t form_convective(sipg_ctx* ctx, const WallArg& w, const double* u, double* y) {
+  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
+  return ctx->mapped ? launch_mapped_convective(L.n, L.g, ctx->stabs[L.n], L.verts, w, u, y, ctx->st)
+                     : launch_convective(L.n, L.g, ctx->stabs[L.n], w, u, y, ctx->st);
+}
+cudaError_t form_projection(sipg_ctx* ctx, const double* p, double* y) {
+  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
+  return ctx->mapped ? launch_mapped_projection_rhs(L.n, L.g, ctx->stabs[L.n], L.verts, p, y, ctx->st)
+                     : launch_projection_rhs(L.n, L.g, ctx->stabs[L.n], p, y, ctx->st);
+}
+cudaError_t form_viscous_wall(sipg_ctx* ctx, const WallArg& w, double* y) {
+  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
+  return ctx->mapped
+             ? launch_mapped_viscous_wall_rhs(L.n, L.g, ctx->stabs[L.n], L.verts, L.lam, w, L.nu_face64, y, ctx->st)
+             : launch_viscous_wall_rhs(L.n, L.g, ctx->stabs[L.n], w, L.nu_face64, y, ctx->st);
 }
 
 }  // namespace
@@ -73,8 +91,7 @@ extern "C" int sipg_convective_apply(sipg_ctx* ctx, const double* wall_g, const 
   if (!ctx || !u || !y || u == y) return SIPG_ERR_INVALID;
   int rc = check_forms(ctx);
   if (rc) return rc;
-  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
-  CK(launch_convective(L.n, L.g, ctx->stabs[L.n], wall_g, u, y, ctx->st));
+  CK(form_convective(ctx, WallArg(wall_g), u, y));
   return SIPG_OK;
 }
 
@@ -83,6 +100,7 @@ extern "C" int sipg_convective_lin_apply(sipg_ctx* ctx, const double* w, const d
   if (!ctx || !w || !u || !y || u == y || w == y) return SIPG_ERR_INVALID;
   int rc = check_forms(ctx);
   if (rc) return rc;
+  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "the linearised convective form is built for affine cells");
   const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
   CK(launch_convective_lin(L.n, L.g, ctx->stabs[L.n], wall_w, wall_u, w, u, y, ctx->st));
   return SIPG_OK;
@@ -92,8 +110,7 @@ extern "C" int sipg_projection_rhs(sipg_ctx* ctx, const double* p, double* y) {
   if (!ctx || !p || !y) return SIPG_ERR_INVALID;
   int rc = check_forms(ctx);
   if (rc) return rc;
-  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
-  CK(launch_projection_rhs(L.n, L.g, ctx->stabs[L.n], p, y, ctx->st));
+  CK(form_projection(ctx, p, y));
   return SIPG_OK;
 }
 
@@ -102,8 +119,7 @@ extern "C" int sipg_viscous_wall_rhs(sipg_ctx* ctx, const double* wall_g, double
   int rc = check_forms(ctx);
   if (rc) return rc;
   if (!ctx->have_nu) return ctx->fail(SIPG_ERR_STATE, "set the viscosity first");
-  const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
-  CK(launch_viscous_wall_rhs(L.n, L.g, ctx->stabs[L.n], wall_g, L.nu_face64, y, ctx->st));
+  CK(form_viscous_wall(ctx, WallArg(wall_g), y));
   return SIPG_OK;
 }
 
@@ -114,7 +130,10 @@ extern "C" int sipg_cfl_dt(sipg_ctx* ctx, const double* u, double courant, doubl
   auto& S = ctx->ss;
   if (!S.vmax) CK(cudaMalloc(&S.vmax, sizeof(unsigned long long)));
   const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
-  CK(launch_cfl_max(L.n, L.g, ctx->stabs[L.n], u, S.vmax, ctx->st));
+  if (ctx->mapped)
+    CK(launch_mapped_cfl_max(L.n, L.g, ctx->stabs[L.n], L.verts, u, S.vmax, ctx->st));
+  else
+    CK(launch_cfl_max(L.n, L.g, ctx->stabs[L.n], u, S.vmax, ctx->st));
   unsigned long long bits = 0;
   CK(cudaMemcpyAsync(&bits, S.vmax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -127,7 +146,6 @@ extern "C" int sipg_cfl_dt(sipg_ctx* ctx, const double* u, double courant, doubl
 
 extern "C" int sipg_boundary_faces(sipg_ctx* ctx, int* nbf, int* cell_face_id, double* xyz) {
   if (!ctx) return SIPG_ERR_INVALID;
-  if (ctx->mapped) return ctx->fail(SIPG_ERR_INVALID, "boundary faces of box grids only");
   const Level& L = ctx->hier[SIPG_OP_VISCOUS].L[0];
   const LevelGeom& g = L.g;
   const int nb = n_wall_faces(g);
@@ -162,7 +180,10 @@ extern "C" int sipg_boundary_faces(sipg_ctx* ctx, int* nbf, int* cell_face_id, d
     }
   }
   if (xyz) {
-    CK(launch_boundary_points(L.n, g, ctx->stabs[L.n], xyz, ctx->st));
+    if (ctx->mapped)
+      CK(launch_mapped_boundary_points(L.n, g, ctx->stabs[L.n], L.verts, xyz, ctx->st));
+    else
+      CK(launch_boundary_points(L.n, g, ctx->stabs[L.n], xyz, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
   return SIPG_OK;
@@ -246,6 +267,10 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
     return ctx->fail(SIPG_ERR_INVALID, "unknown convective mode");
   if (so.convective_mode == SIPG_CONV_LINEAR_IMPLICIT && so.viscosity_mode != SIPG_VISC_LINEAR_IMPLICIT)
     return ctx->fail(SIPG_ERR_INVALID, "the linearly implicit convective step takes the linear-implicit viscosity");
+  if (ctx->mapped && (so.convective_mode != SIPG_CONV_EXPLICIT || so.penalty))
+    return ctx->fail(SIPG_ERR_INVALID,
+                     "trilinear cells: explicit convective term, no penalty step (the linearised convective "
+                     "form and the penalty forms are built for affine cells)");
   RheologyDev law;
   const double* u0 = S.u[0];
   int rc = ctx->parse_rheology(rh, u0, &law);
@@ -269,8 +294,8 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   // ---- 1 convective step: C(u^n) (C(u^{n-1}) kept from the previous step)
   std::swap(S.conv[0], S.conv[1]);
   S.conv1 = S.steps > 0;
-  CK(launch_convective(Lu.n, Lu.g, tab, wall_n, S.u[0], S.conv[0], st));
-  if (m == 2 && !S.conv1) CK(launch_convective(Lu.n, Lu.g, tab, wall_n, S.u[1], S.conv[1], st));
+  CK(form_convective(ctx, wall_n, S.u[0], S.conv[0]));
+  if (m == 2 && !S.conv1) CK(form_convective(ctx, wall_n, S.u[1], S.conv[1]));
   // tmp = sum_i alpha_i/dt u^{n-i} + b ; bv = M tmp - sum_i beta_i C_i ; uhat = (gamma0/dt M)^-1 bv
   CK(launch_scale(nu, alpha[0] / dt, S.u[0], S.tmp, st));
   if (m == 2) CK(launch_add_scaled_f64(nu, alpha[1] / dt, S.u[1], S.tmp, st));
@@ -291,8 +316,14 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   pa.betabar[0] = betabar[0];
   pa.betabar[1] = betabar[1];
   pa.gn_coef = -gamma0 / dt;
-  CK(launch_ppe_boundary(Lu.n, Lu.g, tab, wall, pa, law, S.u[0], m == 2 ? S.u[1] : S.u[0], S.sb, st));
-  CK(launch_ppe_rhs(Lu.n, Lu.g, tab, gamma0 / dt, S.uhat, S.sb, S.prhs, st));
+  if (ctx->mapped) {
+    CK(launch_mapped_ppe_boundary(Lu.n, Lu.g, tab, Lu.verts, wall, pa, law, S.u[0], m == 2 ? S.u[1] : S.u[0], S.sb,
+                                  st));
+    CK(launch_mapped_ppe_rhs(Lu.n, Lu.g, tab, Lu.verts, gamma0 / dt, S.uhat, S.sb, S.prhs, st));
+  } else {
+    CK(launch_ppe_boundary(Lu.n, Lu.g, tab, wall, pa, law, S.u[0], m == 2 ? S.u[1] : S.u[0], S.sb, st));
+    CK(launch_ppe_rhs(Lu.n, Lu.g, tab, gamma0 / dt, S.uhat, S.sb, S.prhs, st));
+  }
   sipg_solve_opts ps{so.ppe_rtol, 0.0, so.maxit, SIPG_PRECOND_MG, 0.0};
   sipg_solve_stats pst{};
   rc = ctx->solve(SIPG_OP_POISSON, S.prhs, S.p, &ps, &pst);
@@ -300,7 +331,7 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   const auto t2 = Clock::now();
 
   // ---- 3 projection step: uhh = uhat + (gamma0/dt M)^-1 [(div v, p) - (v, {{p}} n)]
-  CK(launch_projection_rhs(Lu.n, Lu.g, tab, S.p, S.tmp, st));
+  CK(form_projection(ctx, S.p, S.tmp));
   if ((rc = ctx->mass_apply(SIPG_OP_VISCOUS, SIPG_F64_FF, S.tmp, S.uhh, gamma0 / dt, true))) return rc;
   CK(launch_add_scaled_f64(nu, 1.0, S.uhat, S.uhh, st));
   CK(cudaStreamSynchronize(st));
@@ -318,7 +349,7 @@ extern "C" int sipg_step(sipg_ctx* ctx, const sipg_rheology* rh, const sipg_step
   if (so.viscosity_mode == SIPG_VISC_LINEAR_IMPLICIT) {
     if ((rc = ctx->eval_viscosity(law, S.usharp))) return rc;
     if (wall_moving) {
-      CK(launch_viscous_wall_rhs(Lu.n, Lu.g, tab, wall, Lu.nu_face64, S.tmp, st));
+      CK(form_viscous_wall(ctx, wall, S.tmp));
       CK(launch_add_scaled_f64(nu, 1.0, S.tmp, S.bv, st));
     }
     sipg_solve_opts vs{so.visc_rtol, 0.0, so.maxit, SIPG_PRECOND_MG, mc};

@@ -12,8 +12,8 @@ constexpr int kSplitThreads = 128;
 
 // out = A along DIR applied to the tensor in (extents EX, EY, EZ, x fastest);
 // A row-major [NO][E_DIR] (TR = false) or [E_DIR][NO] (TR = true), leading dim lda
-template <int EX, int EY, int EZ, int DIR, int NO, bool TR>
-__device__ __forceinline__ void sweep(const double* A, int lda, const double* in, double* out) {
+template <int EX, int EY, int EZ, int DIR, int NO, bool TR, typename R>
+__device__ __forceinline__ void sweep(const R* A, int lda, const R* in, R* out) {
   constexpr int OX = DIR == 0 ? NO : EX, OY = DIR == 1 ? NO : EY, OZ = DIR == 2 ? NO : EZ;
   constexpr int EIN = DIR == 0 ? EX : (DIR == 1 ? EY : EZ);
   constexpr int SIN = DIR == 0 ? 1 : (DIR == 1 ? EX : EX * EY);
@@ -21,7 +21,7 @@ __device__ __forceinline__ void sweep(const double* A, int lda, const double* in
     const int x = t % OX, y = (t / OX) % OY, z = t / (OX * OY);
     const int o = DIR == 0 ? x : (DIR == 1 ? y : z);
     const int base = (DIR == 0 ? 0 : x) + (DIR == 1 ? 0 : y) * EX + (DIR == 2 ? 0 : z) * EX * EY;
-    double acc = 0.0;
+    R acc = R(0);
 #pragma unroll
     for (int m = 0; m < EIN; ++m) acc += (TR ? A[m * lda + o] : A[o * lda + m]) * in[base + m * SIN];
     out[t] = acc;
@@ -29,9 +29,8 @@ __device__ __forceinline__ void sweep(const double* A, int lda, const double* in
 }
 
 // three sweeps with the same matrix (N -> NO per direction); tmp: two buffers of N^3
-template <int N, int NO, bool TR>
-__device__ __forceinline__ void sweep3(const double* A, int lda, const double* in, double* t0, double* t1,
-                                       double* out) {
+template <int N, int NO, bool TR, typename R>
+__device__ __forceinline__ void sweep3(const R* A, int lda, const R* in, R* t0, R* t1, R* out) {
   sweep<N, N, N, 0, NO, TR>(A, lda, in, t0);
   __syncthreads();
   sweep<NO, N, N, 1, NO, TR>(A, lda, t0, t1);
@@ -41,8 +40,8 @@ __device__ __forceinline__ void sweep3(const double* A, int lda, const double* i
 }
 
 // single sweep along a runtime direction (n^3 -> n^3)
-template <int N, bool TR>
-__device__ __forceinline__ void sweep_dir(int dir, const double* A, const double* in, double* out) {
+template <int N, bool TR, typename R>
+__device__ __forceinline__ void sweep_dir(int dir, const R* A, const R* in, R* out) {
   if (dir == 0) sweep<N, N, N, 0, N, TR>(A, N, in, out);
   else if (dir == 1) sweep<N, N, N, 1, N, TR>(A, N, in, out);
   else sweep<N, N, N, 2, N, TR>(A, N, in, out);
@@ -117,12 +116,15 @@ __device__ __forceinline__ double wall_val(const Wall& w, const LevelGeom& g, in
   return w.g[boundary_id(g, e, f)][c];
 }
 
-// load the split tables into shared memory
-struct STabSm {
-  double S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN], Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
-  double dS[2][kMaxN], lg[2][kMaxN], dlg[2][kMaxN], gw[kMaxN];
+// load the split tables into shared memory (in the arithmetic type R of the kernel)
+template <typename R>
+struct STabSmT {
+  R S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN], Sp[kMaxN * kMaxN], DSp[kMaxN * kMaxN];
+  R dS[2][kMaxN], lg[2][kMaxN], dlg[2][kMaxN], gw[kMaxN];
 };
-__device__ __forceinline__ void load_tab(const SplitTab& t, STabSm& s) {
+using STabSm = STabSmT<double>;
+template <typename R>
+__device__ __forceinline__ void load_tab(const SplitTab& t, STabSmT<R>& s) {
   for (int i = threadIdx.x; i < kMaxN * kMaxN; i += blockDim.x) {
     s.S[i] = t.S[i];
     s.DS[i] = t.DS[i];
@@ -147,15 +149,15 @@ __device__ __forceinline__ double cell_weight(const STabSm& t, int q, int n, dou
 
 // trace on face (d, s) of a field F given at the n^3 Gauss points, with the 1D
 // vector L over the normal index (values lg or derivatives dlg at 0 / 1)
-template <int N>
-__device__ __forceinline__ void trace(const double* F, const double* L, int d, double* out) {
+template <int N, typename R>
+__device__ __forceinline__ void trace(const R* F, const R* L, int d, R* out) {
   int t1, t2;
   face_dirs(d, &t1, &t2);
   const int str[3] = {1, N, N * N};
   for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
     const int a = p % N, b = p / N;
     const int base = a * str[t1] + b * str[t2];
-    double acc = 0.0;
+    R acc = R(0);
 #pragma unroll
     for (int q = 0; q < N; ++q) acc += L[q] * F[base + q * str[d]];
     out[p] = acc;
@@ -163,4 +165,7 @@ __device__ __forceinline__ void trace(const double* F, const double* L, int d, d
 }
 
 }  // namespace sweeps
+
+// device copy of the wall data of the form launchers (split.cu)
+sweeps::Wall make_wall(const WallArg& a);
 }  // namespace sipg

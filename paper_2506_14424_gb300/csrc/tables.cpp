@@ -186,6 +186,10 @@ SplitTab make_split_tab(int n) {
     T.gw[j] = gw[j];
     T.gp[j] = gp[j];
   }
+  for (int j = 0; j < n; ++j) {
+    const auto lj = lagrange_values(gp, gll[j]);
+    for (int q = 0; q < n; ++q) T.Sinv[j * n + q] = lj[q];
+  }
   return T;
 }
 

@@ -321,3 +321,57 @@ def test_jittered_channel_multigrid_solve():
     assert _rel(xs.cpu().numpy(), ref) <= 1e-9
     assert st["iterations"] <= 60, st
     ctx.close()
+
+
+def _jittered(c):
+    from oracle.mapped import MappedMesh
+    V = inputs.bfs_vertices(c)
+    return V, MappedMesh(*c["dims"], V, bc=tuple(VEL) + ('D',), active=c["active"], periodic=c["periodic"])
+
+
+def test_jittered_channel_forms_match_oracle():
+    """Trilinear cells: the cell mass matrix and its inverse (w det J per point), the
+    convective vector with the inflow data, the projection right-hand side and the CFL
+    time step equal the oracle's on the jittered channel."""
+    from oracle import mass as omass
+    from oracle.mapped import MappedSIPG
+    c = _channel(2)
+    V, mesh = _jittered(c)
+    k = 3
+    S = MappedSIPG(mesh, k, 3)
+    ctx = _mapped_ctx(c, V, k)
+    u = S.interpolate(lambda p: inputs.fourier_field(p, inputs.fourier_modes(2)))
+    du = _dev(u)
+    assert _rel(ctx.mass("viscous", du, coeff=2.5).cpu().numpy(), omass.apply_mass(S, u, 2.5)) <= TOL64
+    assert _rel(ctx.mass("viscous", du, coeff=2.5, inverse=True).cpu().numpy(),
+                omass.apply_inverse_mass(S, u, 2.5)) <= 1e-11
+    assert _rel(ctx.convective(du).cpu().numpy(), osp.convective_vector(S, u, [np.zeros(3)] * 7)) <= TOL64
+    Sp = MappedSIPG(mesh, k - 1, 1, n_quad=k + 1)
+    p = inputs.uniform_vector(Sp.n_dofs, seed=5)
+    assert _rel(ctx.projection_rhs(_dev(p)).cpu().numpy(), osp.projection_rhs(S, Sp, p)) <= TOL64
+    assert abs(ctx.cfl_dt(du, 0.3) - osp.cfl_dt(S, u, 0.3)) <= 1e-12 * osp.cfl_dt(S, u, 0.3)
+    ctx.close()
+
+
+def test_jittered_channel_steps_match_oracle():
+    """The splitting step on trilinear cells (5 % jitter inside the fluid): ramped parabolic
+    inflow, outflow, no-slip walls and step, z periodic, Carreau-Yasuda; BDF1 then BDF2 steps
+    equal the oracle's exactly-solved steps."""
+    c = _channel(2)
+    V, mesh = _jittered(c)
+    k = 2
+    ref = osp.Splitting(mesh, k, CARREAU, g_faces=[_inflow] + [np.zeros(3)] * 6, ramp=_ramp)
+    ref.set_initial(np.zeros(ref.Su.n_dofs))
+    ctx = _mapped_ctx(c, V, k)
+    ctx.step_init(torch.zeros(ref.Su.n_dofs, dtype=torch.float64, device="cuda"))
+    dt, t = 0.02, 0.0
+    for n in range(3):
+        r = ref.step(dt)
+        st = ctx.step(CARREAU, dt, wall_points=_wall_points(ctx, t + dt), wall_points_prev=_wall_points(ctx, t),
+                      ppe_rtol=1e-13, visc_rtol=1e-13, maxit=3000)
+        t += dt
+        assert st["order"] == r["order"]
+        assert _rel(ctx.step_field("uhat").cpu().numpy(), r["uhat"]) <= 1e-10
+        assert _rel(ctx.step_field("p").cpu().numpy(), r["p"]) <= 1e-8
+        assert _rel(ctx.step_field("u").cpu().numpy(), r["u"]) <= 1e-8
+    ctx.close()

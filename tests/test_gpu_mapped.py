@@ -170,14 +170,22 @@ def test_multigrid_cuts_iterations_at_8cubed():
 
 
 def test_box_only_calls_refuse_trilinear_cells():
+    """Float-float applies and the affine-only step options are refused on trilinear cells;
+    the FP32 level apply (mixed-precision multigrid) matches the oracle to FP32 accuracy."""
     dims = (2, 2, 2)
-    ctx = Context(*dims, 2, vertices=jittered_vertices(*dims, amp=0.1))
+    V = jittered_vertices(*dims, amp=0.1)
+    ctx = Context(*dims, 2, vertices=V)
     x = torch.zeros(ctx.n_dofs("viscous"), dtype=torch.float64, device="cuda")
     ctx.set_viscosity({'law': 'constant', 'nu': 1.0})
-    for call in (lambda: ctx.apply("viscous", x, arith="f64ff"),
-                 lambda: ctx.apply("viscous", x.float()),
-                 lambda: ctx.mass("viscous", x),
-                 lambda: ctx.step_init(x)):
+    with pytest.raises(SipgError):
+        ctx.apply("viscous", x, arith="f64ff")
+    ctx.step_init(x)
+    for kw in ({"penalty": True}, {"convective_mode": "linear_implicit"}):
         with pytest.raises(SipgError):
-            call()
+            ctx.step({'law': 'constant', 'nu': 1.0}, 0.01, **kw)
+    S = MappedSIPG(MappedMesh(*dims, V), 2, 3)
+    xr = inputs.uniform_vector(S.n_dofs, seed=3)
+    y32 = ctx.apply("viscous", torch.tensor(xr, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    ref = S.apply(xr, *S.viscosity_at_points({'law': 'constant', 'nu': 1.0}))
+    assert np.abs(y32 - ref).max() <= 2e-5 * np.abs(ref).max()
     ctx.close()
