@@ -40,13 +40,14 @@ def parse():
     p.add_argument("--arith", default="f64ff", choices=["f64", "f64ff"],
                    help="arithmetic of the timed apply: native FP64 or float-float (FP64-accurate)")
     p.add_argument("--channel-steps", type=int, default=10, help="timed steps of the channel extras")
+    p.add_argument("--setup-lag", type=int, default=1, help="mg_setup_lag of the channel extras")
     p.add_argument("--extra", default=None,
                    choices=["mass", "picard", "step", "trilinear", "channel", "jchannel", "f32apply", "serve"],
                    help="run one extra workload alone and print its JSON (profiling runs)")
     return p.parse_args()
 
 
-def run_extra(name, steps=10):
+def run_extra(name, steps=10, lag=1):
     """One extra workload on its own (the commands of the ncu summaries in profiles/)."""
     import torch
 
@@ -57,9 +58,9 @@ def run_extra(name, steps=10):
     elif name == "trilinear":
         out = trilinear_extras()
     elif name == "channel":
-        out = channel_extras(steps=steps)
+        out = channel_extras(steps=steps, setup_lag=lag)
     elif name == "jchannel":
-        out = channel_extras(steps=steps, jitter=True)
+        out = channel_extras(steps=steps, jitter=True, setup_lag=lag)
     elif name == "f32apply":
         out = f32_apply_extra()
     elif name == "serve":
@@ -443,7 +444,7 @@ def gpu_extras(ctx, xs, ys, stream):
                     ("splitting_step_32cubed_k3", step_extras),
                     ("trilinear_cells_32cubed_k3", trilinear_extras),
                     ("bfs_channel_steps", channel_extras),
-                    ("bfs_jittered_channel_steps", lambda: channel_extras(jitter=True)),
+                    ("bfs_jittered_channel_steps", lambda: channel_extras(jitter=True, steps=3)),
                     ("components_16cubed_k4", lambda: component_timings(stream)),
                     ("serving", serving_extras)):
         try:
@@ -582,7 +583,7 @@ def step_extras(n_cells=32, k=3, courant=0.3, warm=2, steps=5):
     return out
 
 
-def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=1.0, jitter=False):
+def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=1.0, jitter=False, setup_lag=1):
     """Projection-scheme steps on the backward-facing-step channel (inlet [-5, 0] x [1, 2],
     outlet [0, 30] x [0, 2], z in [0, 4] periodic, step height 1, expansion ratio 2), cubes
     of side 1/8: 133,120 hexes, k = 3 velocity / k = 2 pressure; with jitter the vertices
@@ -592,7 +593,9 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
     walls and step, Carreau-Yasuda viscosity linear implicit, fluid at rest at t = 0,
     dt from the CFL rule (Cr = 0.3) at the full inflow velocity, CG to 1e-8 with the FP32
     hp-multigrid (p: 3 -> 2 -> 1, then h down to cubes of side 1). The wall data of every
-    step are evaluated before the timed steps. Host-clock step times (the step synchronises)."""
+    step are evaluated before the timed steps. Host-clock step times (the step synchronises).
+    setup_lag > 1 rebuilds the multigrid eigenvalue estimates and coarse inverse at every
+    setup_lag-th viscosity update only (sipg_opts.mg_setup_lag)."""
     import numpy as np
     import torch
 
@@ -602,7 +605,7 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
     ctx = Context(*c["dims"], k, extent=c["extent"], origin=c["lo"], active=c["active"], periodic=c["periodic"],
                   bc_velocity="DNDDDD", bc_pressure="NDNNNN", bc_removed="DN",
                   krylov_arith="f64" if jitter else "f64ff", coarse_max_dofs=8000, mg_precision="f32",
-                  vertices=inputs.bfs_vertices(c) if jitter else None)
+                  vertices=inputs.bfs_vertices(c) if jitter else None, mg_setup_lag=setup_lag)
     t_create = time.perf_counter() - t0
     rh = inputs.carreau_blood_like()
     n = ctx.n_dofs("viscous")
@@ -626,7 +629,8 @@ def channel_extras(cells_per_unit=8, k=3, courant=0.3, warm=2, steps=10, t_ramp=
               for l in range(ctx.num_levels("viscous"))]
     out = {"geometry": ("trilinear cells (5 % vertex jitter inside the fluid, seed 4)" if jitter
                         else "affine cells (no vertex jitter)"),
-           "multigrid": "FP32 V-cycle, FP64 CG", "cells": ctx.n_cells, "n_dofs_velocity": n,
+           "multigrid": "FP32 V-cycle, FP64 CG", "mg_setup_lag": setup_lag, "cells": ctx.n_cells,
+           "n_dofs_velocity": n,
            "n_dofs_pressure": ctx.n_dofs("poisson"), "dt": dt,
            "steps_timed": steps, "create_seconds": t_create, "viscous_levels": levels,
            "mean_seconds": float(np.mean([r["seconds"] for r in rows])),
@@ -926,7 +930,7 @@ def run_reference(args):
 if __name__ == "__main__":
     a = parse()
     if a.extra:
-        run_extra(a.extra, steps=a.channel_steps)
+        run_extra(a.extra, steps=a.channel_steps, lag=a.setup_lag)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -137,6 +137,14 @@ typedef struct {
                         continuous space of the same degree, then lower degrees and
                         coarser meshes in the continuous space (Galerkin operators
                         P^T A_DG P); 0: DG on every level [0]; box meshes only */
+  int mg_setup_lag;  /* multigrid setup after a viscosity update: the level diagonals
+                        are rebuilt at every update, the Chebyshev eigenvalue
+                        estimates and the coarse-level inverse at every mg_setup_lag-th
+                        update (and whenever the mass coefficient changes); between
+                        full rebuilds the preconditioner keeps the earlier ones - a
+                        fixed SPD preconditioner per solve, so the CG solution is
+                        unchanged, only its iteration count may grow [1 = rebuild at
+                        every update; 0 is read as 1] */
 } sipg_opts;
 
 /* Viscosity field (Eq. viscosity_general and Sec. 2).

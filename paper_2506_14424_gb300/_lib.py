@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("mg_precision", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_range", ctypes.c_double),
                 ("cheb_lmax_factor", ctypes.c_double), ("lanczos_steps", ctypes.c_int),
                 ("coarse_max_dofs", ctypes.c_int), ("seed", ctypes.c_uint64), ("krylov_arith", ctypes.c_int),
-                ("mg_cph", ctypes.c_int)]
+                ("mg_cph", ctypes.c_int), ("mg_setup_lag", ctypes.c_int)]
 
 
 class Rheology(ctypes.Structure):

@@ -55,7 +55,7 @@ class Context:
     def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
                  penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
                  cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, krylov_arith="f64",
-                 stream=None, vertices=None, mg_cph=False, active=None, periodic=(False, False, False),
+                 stream=None, vertices=None, mg_cph=False, active=None, periodic=(False, False, False), mg_setup_lag=1,
                  origin=(0.0, 0.0, 0.0), bc_removed="DN"):
         """vertices: optional (nz+1, ny+1, nx+1, 3) host array of vertex positions
         (trilinear cells; fine level only, see include/sipg.h).
@@ -100,6 +100,7 @@ class Context:
         o.seed = int(seed)
         o.krylov_arith = L.PREC[krylov_arith]
         o.mg_cph = int(bool(mg_cph))
+        o.mg_setup_lag = int(mg_setup_lag)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = self._lib.sipg_create(ctypes.byref(m), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),

@@ -443,6 +443,7 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (o.krylov_arith != SIPG_F64 && o.krylov_arith != SIPG_F64_FF) return SIPG_ERR_INVALID;
   if (mesh->vertices && o.krylov_arith != SIPG_F64) return SIPG_ERR_INVALID;  // FP64 applies only
   if (o.mg_cph != 0 && o.mg_cph != 1) return SIPG_ERR_INVALID;
+  if (o.mg_setup_lag < 0) return SIPG_ERR_INVALID;
   if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
   const bool topo = mesh_topology(mesh);
   if (topo) {
@@ -724,7 +725,7 @@ static double tridiag_lmax(const std::vector<double>& a, const std::vector<doubl
   return hi;
 }
 
-int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
+int sipg_ctx::setup_level_smoother(int op, int l, double mass, bool estimate) {
   sipg_ctx* ctx = this;
   Hier& H = hier[op];
   Level& L = H.L[l];
@@ -741,7 +742,7 @@ int sipg_ctx::setup_level_smoother(int op, int l, double mass) {
   }
   CK(launch_reciprocal(L.ndofs, L.diag64, L.dinv64, st));
   CK((launch_cast<double, float>(L.ndofs, L.dinv64, L.dinv32, st)));
-  if (l + 1 == (int)H.L.size()) return SIPG_OK;
+  if (l + 1 == (int)H.L.size() || !estimate) return SIPG_OK;
   // Lanczos on D^-1/2 A D^-1/2 with level applies in the multigrid's arithmetic:
   // the Chebyshev smoother applies that operator, and the estimate needs a few
   // digits only (FP32 applies are 8x cheaper than FP64 ones on this GPU)
@@ -809,6 +810,61 @@ void sipg_ctx::sqrt_inplace(int64_t n, double* v) {
   launch_sqrt(n, v, st);
 }
 
+// Colouring of the cells of a (coarse) level for the column assembly of its DG
+// operator: colour = (i mod c_x) + c_x ((j mod c_y) + c_y (k mod c_z)) with
+// c_d = 3, or the extent n_d where n_d < 3 or where a periodic direction's extent
+// is not a multiple of 3; two cells of one colour are then at least three cells
+// apart along some direction, so their closed face neighbourhoods are disjoint.
+// owner[colour * C + c'] = the cell of that colour in {c'} u N(c'), or -1.
+int sipg_ctx::coarse_colouring(const LevelGeom& g, std::vector<int>* colour, std::vector<int>* owner, int* ncolours) {
+  sipg_ctx* ctx = this;
+  const int C = g.ncells;
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  int cd[3];
+  for (int d = 0; d < 3; ++d) {
+    const bool per = g.nbr && mesh.periodic[d];
+    cd[d] = dims[d] < 3 ? dims[d] : ((per && dims[d] % 3 != 0) ? dims[d] : 3);
+  }
+  std::vector<int> nbr((size_t)C * 6), cgrid;
+  if (g.nbr) {
+    cgrid.resize(C);
+    CK(cudaMemcpy(nbr.data(), g.nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cgrid.data(), g.cgrid, sizeof(int) * C, cudaMemcpyDeviceToHost));
+  }
+  colour->assign(C, 0);
+  for (int e = 0; e < C; ++e) {
+    const int gi = g.nbr ? cgrid[e] : e;
+    const int i = gi % g.nx, j = (gi / g.nx) % g.ny, k = gi / (g.nx * g.ny);
+    (*colour)[e] = (i % cd[0]) + cd[0] * ((j % cd[1]) + cd[1] * (k % cd[2]));
+    if (!g.nbr)
+      for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1, s = f & 1;
+        int ijk[3] = {i, j, k};
+        ijk[d] += s ? 1 : -1;
+        nbr[(size_t)e * 6 + f] = (ijk[d] < 0 || ijk[d] >= dims[d]) ? -1 : (ijk[2] * g.ny + ijk[1]) * g.nx + ijk[0];
+      }
+  }
+  *ncolours = cd[0] * cd[1] * cd[2];
+  if (*ncolours > C) {  // a grid with many removed cells: one colour per cell (the unit columns)
+    for (int e = 0; e < C; ++e) (*colour)[e] = e;
+    *ncolours = C;
+  }
+  owner->assign((size_t)*ncolours * C, -1);
+  for (int e = 0; e < C; ++e) {
+    const int col = (*colour)[e];
+    (*owner)[(size_t)col * C + e] = e;
+    for (int f = 0; f < 6; ++f) {
+      const int nb = nbr[(size_t)e * 6 + f];
+      if (nb >= 0) {
+        int& o = (*owner)[(size_t)col * C + nb];
+        if (o >= 0 && o != e) return fail(SIPG_ERR_STATE, "coarse colouring: overlapping neighbourhoods");
+        o = e;
+      }
+    }
+  }
+  return SIPG_OK;
+}
+
 int sipg_ctx::setup_coarse(int op, double mass) {
   sipg_ctx* ctx = this;
   Hier& H = hier[op];
@@ -816,15 +872,38 @@ int sipg_ctx::setup_coarse(int op, double mass) {
   const int N = C.N;
   const int l = (int)H.L.size() - 1;
   if (H.singular && op == SIPG_OP_VISCOUS && mass == 0.0) return SIPG_OK;  // rigid modes: no inverse
-  // columns of the operator: apply to all unit vectors in one batched launch
-  CK(launch_unit_columns(N, 0, N, C.Atmp, st));
   const double* nc = op == SIPG_OP_VISCOUS ? C.nu_cell64 : nullptr;
   const double* nf = op == SIPG_OP_VISCOUS ? C.nu_face64 : nullptr;
-  if (mapped) {
-    CK(launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.verts, C.lam, nc, nf, mass, C.Atmp, C.Ainv, N, st));
-  } else if (C.cg) {
+  if (!C.cg) {
+    // columns of the DG operator by colouring (see coarse_colouring): one batched
+    // apply of ncolours x (DoFs per cell) probe vectors instead of N unit vectors
+    std::vector<int> colour, owner;
+    int ncol = 0;
+    int rc = coarse_colouring(C.g, &colour, &owner, &ncol);
+    if (rc) return rc;
+    const int dpc = H.ncomp * C.n * C.n * C.n;
+    const int nb = ncol * dpc;
+    int *dcol = nullptr, *down = nullptr;
+    CK(cudaMalloc(&dcol, sizeof(int) * colour.size()));
+    cudaError_t ce = cudaMalloc(&down, sizeof(int) * owner.size());
+    if (!ce) ce = cudaMemcpyAsync(dcol, colour.data(), sizeof(int) * colour.size(), cudaMemcpyHostToDevice, st);
+    if (!ce) ce = cudaMemcpyAsync(down, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, st);
+    if (!ce) ce = launch_colour_probes(N, dpc, nb, dcol, C.Atmp, st);
+    if (!ce)
+      ce = mapped ? launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.verts, C.lam, nc, nf, mass, C.Atmp, C.Ainv,
+                                        nb, st)
+                  : launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, nb, st);
+    if (!ce) ce = cudaMemsetAsync(C.Atmp, 0, sizeof(double) * (size_t)N * N, st);
+    if (!ce) ce = launch_colour_scatter(N, C.g.ncells, dpc, nb, down, C.Ainv, C.Atmp, st);
+    if (!ce) ce = cudaMemcpyAsync(C.Ainv, C.Atmp, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, st);
+    if (!ce) ce = cudaStreamSynchronize(st);
+    cudaFree(dcol);
+    cudaFree(down);
+    CK(ce);
+  } else {
     // continuous coarse level: columns P^T A_DG P e_j in chunks of columns (gather,
     // batched DG apply, batched sum over copies)
+    CK(launch_unit_columns(N, 0, N, C.Atmp, st));
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)(64 << 20) / (16 * C.ndg)));
     double *ga = nullptr, *gb = nullptr;
     CK(cudaMalloc(&ga, sizeof(double) * (size_t)C.ndg * chunk));
@@ -841,8 +920,6 @@ int sipg_ctx::setup_coarse(int op, double mass) {
     cudaFree(ga);
     cudaFree(gb);
     CK(ce);
-  } else {
-    CK((launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, N, st)));
   }
   (void)l;
   // column j of A is stored contiguously: that is A^T row-major = A (symmetric)
@@ -883,15 +960,22 @@ int sipg_ctx::ensure_setup(int op) {
 int sipg_ctx::setup_operator(int op, double mass) {
   sipg_ctx* ctx = this;
   Hier& H = hier[op];
+  const int lag = opts.mg_setup_lag > 1 ? opts.mg_setup_lag : 1;
+  const bool full = !H.have_full || H.full_mass != mass || H.updates_since_full + 1 >= lag;
   for (size_t l = 0; l < H.L.size(); ++l) {
-    int rc = setup_level_smoother(op, (int)l, mass);
+    int rc = setup_level_smoother(op, (int)l, mass, full);
     if (rc) return rc;
   }
-  int rc = setup_coarse(op, mass);
-  if (rc) return rc;
+  if (full) {
+    int rc = setup_coarse(op, mass);
+    if (rc) return rc;
+  }
   CK(cudaStreamSynchronize(st));
   H.setup_mass = mass;
   H.ready = true;
+  H.updates_since_full = full ? 0 : H.updates_since_full + 1;
+  H.have_full = true;
+  H.full_mass = mass;
   return SIPG_OK;
 }
 

@@ -52,6 +52,11 @@ struct Hier {
   bool singular = false;
   bool ready = false;
   double setup_mass = 0.0;
+  // lagged setup (opts.mg_setup_lag): viscosity updates since the last full setup
+  // (eigenvalue estimates and coarse inverse), and the mass coefficient it used
+  int updates_since_full = 0;
+  bool have_full = false;
+  double full_mass = 0.0;
   std::vector<Level> L;
   double* cg[5] = {nullptr};  // r, z, p, q, tmp (level 0, FP64)
 };
@@ -118,8 +123,9 @@ struct sipg_ctx {
   template <typename T>
   T* alloc(int64_t n, cudaError_t* e);
   int build_hierarchy(int op);
-  int setup_level_smoother(int op, int l, double mass);
+  int setup_level_smoother(int op, int l, double mass, bool estimate = true);
   int setup_coarse(int op, double mass);
+  int coarse_colouring(const sipg::LevelGeom& g, std::vector<int>* colour, std::vector<int>* owner, int* ncolours);
   int setup_operator(int op, double mass);
   int ensure_setup(int op);
   template <typename T>

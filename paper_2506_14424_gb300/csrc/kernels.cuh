@@ -172,6 +172,11 @@ cudaError_t launch_sum(int64_t n, const double* a, double* partials, double* dev
 cudaError_t launch_add_const(int64_t n, const double* dev_c, double scale, double* y, cudaStream_t st);
 cudaError_t launch_check_finite(int64_t n, const double* a, int* flag, cudaStream_t st);
 // dense FP64 helpers for the coarse level
+// probe vectors of the coloured column assembly of the coarse operator and the
+// scatter of the probed products into the dense matrix (columns contiguous)
+cudaError_t launch_colour_probes(int N, int dpc, int nb, const int* colour, double* out, cudaStream_t st);
+cudaError_t launch_colour_scatter(int N, int C, int dpc, int nb, const int* owner, const double* Y, double* A,
+                                  cudaStream_t st);
 cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStream_t st);
 // blocked step: pivots k0 .. k0+b-1 (b <= 16); Pinv: b*b, R: b*N float-float scratch
 cudaError_t launch_gj_block(int N, int k0, int b, const float2* A, float2* B, float2* Pinv, float2* R,

@@ -564,6 +564,41 @@ cudaError_t launch_unit_columns(int N, int j0, int ncols, double* out, cudaStrea
   return cudaGetLastError();
 }
 
+// Columns of a DG operator by colouring: probe vector b = (colour, local DoF l)
+// is 1 at DoF l of every cell of that colour; since the closed face
+// neighbourhoods of the cells of one colour are disjoint, row r of A probe_b
+// belongs to the column of the unique cell of that colour in the neighbourhood
+// of r's cell (owner table), or is zero.
+__global__ void colour_probe_kernel(int N, int dpc, int nb, const int* __restrict__ colour, double* __restrict__ out) {
+  const int64_t total = (int64_t)N * nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / N), r = (int)(i - (int64_t)b * N);
+    out[i] = (colour[r / dpc] == b / dpc && r % dpc == b % dpc) ? 1.0 : 0.0;
+  }
+}
+__global__ void colour_scatter_kernel(int N, int C, int dpc, int nb, const int* __restrict__ owner,
+                                      const double* __restrict__ Y, double* __restrict__ A) {
+  const int64_t total = (int64_t)N * nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / N), r = (int)(i - (int64_t)b * N);
+    const int c = owner[(size_t)(b / dpc) * C + r / dpc];
+    if (c >= 0) A[((size_t)c * dpc + b % dpc) * N + r] = Y[i];
+  }
+}
+cudaError_t launch_colour_probes(int N, int dpc, int nb, const int* colour, double* out, cudaStream_t st) {
+  const int64_t total = (int64_t)N * nb;
+  colour_probe_kernel<<<(int)std::min<int64_t>((total + kBS - 1) / kBS, 152 * 32), kBS, 0, st>>>(N, dpc, nb, colour,
+                                                                                                out);
+  return cudaGetLastError();
+}
+cudaError_t launch_colour_scatter(int N, int C, int dpc, int nb, const int* owner, const double* Y, double* A,
+                                  cudaStream_t st) {
+  const int64_t total = (int64_t)N * nb;
+  colour_scatter_kernel<<<(int)std::min<int64_t>((total + kBS - 1) / kBS, 152 * 32), kBS, 0, st>>>(N, C, dpc, nb,
+                                                                                                  owner, Y, A);
+  return cudaGetLastError();
+}
+
 // Gauss-Jordan inverse of the dense coarse matrix (no pivoting: the coarse
 // operator is SPD, or SPD after the rank-one term of the singular Poisson
 // case), entries in float-float (float2 = (hi, lo)) for the FP32 pipe.

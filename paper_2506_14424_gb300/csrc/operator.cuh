@@ -115,11 +115,13 @@ __device__ __forceinline__ int face_node(int d, int layer, int a, int b) {
 template <int N>
 __device__ __forceinline__ int dir_stride(int d) { return d == 0 ? 1 : (d == 1 ? N : N * N); }
 
-// Cells per CTA and threads per CTA of the operator kernels: about 100 1D
-// lines per sweep (one thread each), so that a CTA is a few warps and many
-// independent CTAs share an SM (their barriers overlap).
+// Cells per CTA and threads per CTA of the operator kernels (one thread per 1D
+// line of a sweep). Measured at 32^3, k = 3 with the float-float arithmetic
+// (1.086 / 0.964 / 0.849 / 0.838 ms for 2 / 4 / 6 / 8 cells; FP64 unchanged at
+// 2.776 ms): larger CTAs amortise the barriers of the cooperative sweeps and
+// keep more independent lines per warp in flight.
 template <int N, int NC> struct OpCfg {
-  static constexpr int CPB = NC == 3 ? (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : (N == 5 ? 2 : 1))))
+  static constexpr int CPB = NC == 3 ? (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 8 : (N == 5 ? 2 : 1))))
                                      : (N == 2 ? 32 : (N == 3 ? 12 : (N == 4 ? 8 : (N == 5 ? 4 : 3))));
   static constexpr int LINES = CPB * NC * N * N;
   static constexpr int NT = ((LINES + 31) / 32) * 32;
@@ -129,8 +131,9 @@ template <int N, int NC> struct OpCfg {
 // budget per thread: the float-float and FP32 kernels are issue and latency
 // bound, and more resident warps hide more of it. Measured at 32^3, k = 3:
 // float-float 72 -> 56 registers 1.347 -> 1.266 ms (36 bytes of spills),
-// FP32 59 -> 48 registers 0.398 -> 0.361 ms; lower budgets spill more and run
-// slower. The native FP64 kernel is bound by the FP64 pipe and keeps MIN = 1.
+// FP32 59 -> 48 registers 0.398 -> 0.361 ms; with 8 cells per CTA a 64-register
+// budget is 8 % slower than 56 (0.907 vs 0.838 ms) and 48 equal. The native FP64
+// kernel is bound by the FP64 pipe and keeps MIN = 1.
 #ifndef SIPG_FF_REG
 #define SIPG_FF_REG 56
 #endif

@@ -194,6 +194,25 @@ def test_mg_cg_solve_matches_oracle(prec, contrast):
     assert st["iterations"] < 40, st
 
 
+def test_lagged_multigrid_setup_keeps_the_solution():
+    """mg_setup_lag = 3: after a second viscosity update the eigenvalue estimates and the
+    coarse inverse of the first are kept (the diagonals follow); the preconditioner is
+    still fixed and SPD, so CG reaches the oracle's solution of the new system."""
+    dims, k = (4, 4, 2), 3
+    ctx = Context(*dims, k, coarse_max_dofs=300, mg_setup_lag=3)
+    S = SIPG(BoxMesh(*dims), k, 3)
+    its = []
+    for contrast in (1e2, 3e2, 1e3):
+        rheo = inputs.sinker(seed=2, count=8, radius=0.2, nu_max=contrast)
+        ctx.set_viscosity(rheo)
+        A = S.assemble(*S.viscosity_at_points(rheo))
+        b = A @ inputs.uniform_vector(S.n_dofs, seed=84)
+        x, st = ctx.solve("viscous", _dev(b), rtol=1e-8, precond="mg", maxit=300)
+        assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-8 * (1 + 1e-6) * np.linalg.norm(b)
+        its.append(st["iterations"])
+    assert max(its) < 60, its
+
+
 def test_poisson_mg_solve_singular():
     dims, kp = (4, 4, 4), 2
     ctx = Context(*dims, kp + 1, coarse_max_dofs=200)
