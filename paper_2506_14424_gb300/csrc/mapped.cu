@@ -18,105 +18,122 @@
 #include "mapped_geom.cuh"
 #include "sweeps.cuh"
 
-// Resident CTAs per SM requested from the compiler for the trilinear apply: the
-// kernel is latency bound (barriers between sweeps, one CTA of 128 threads per
-// cell) and at its natural 204 registers only 2 CTAs fit. Measured at 32^3, k = 3:
-// 2 CTAs 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers, ~1 KB of spills) 11.1 ms.
-// Shared memory caps the count at higher degree (n = 6: 48 KB per CTA).
-template <int N> struct MappedMinBlocks { static constexpr int value = N <= 4 ? 8 : (N == 5 ? 6 : 4); };
+// Cells per CTA of the trilinear apply (128 threads): at low degree one cell
+// leaves most lanes idle between the barriers of its sweeps (n^3 = 8 or 27
+// points), so several cells share a CTA and every phase runs over all of them.
+// Resident CTAs per SM requested from the compiler: the kernel is latency bound
+// (barriers between sweeps); one cell per CTA measured at 32^3, k = 3: 2 CTAs
+// 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers) 11.1 ms.
+template <int N> struct MappedCfg {
+  static constexpr int CB = N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1));
+  static constexpr int MIN_BLOCKS = N <= 4 ? 4 : (N == 5 ? 6 : 4);
+};
 
 namespace sipg {
 namespace {
 using namespace sweeps;
 using namespace mgeo;
 template <int N, int NC, typename R>
-__global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+__global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
                                                                      const double* __restrict__ verts,
                                                                      const double* __restrict__ lam,
                                                                      const R* __restrict__ nu_cell,
                                                                      const R* __restrict__ nu_face, double mass_d,
                                                                      const R* __restrict__ x,
                                                                      R* __restrict__ y, int64_t batch_stride) {
-  constexpr int N3 = N * N * N, N2 = N * N;
+  constexpr int N3 = N * N * N, N2 = N * N, CB = MappedCfg<N>::CB, NT = CB * NC;
   __shared__ STabSmT<R> T;
-  __shared__ R X[8][3], XN[8][3];
+  __shared__ R X[CB][8][3], XN[CB][8][3];
+  __shared__ R U[NT][N3], Q[NT][N3], G[3][NT][N3], T0[NT][N3], T1[NT][N3], OUT[NT][N3];
+  __shared__ R FM[NT][4 * N2], FP[NT][4 * N2], CF[NT][4 * N2], SC[8 * NT * N2];
+  __shared__ int NB[CB];
   const R mass = (R)mass_d;
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
-  __shared__ R U[NC][N3], Q[NC][N3], G[NC][3][N3], T0[N3], T1[N3], OUT[NC][N3];
-  __shared__ R FM[NC][4 * N2], FP[NC][4 * N2], CF[NC][4 * N2], SC[5 * N2];
-  const int e = blockIdx.x;
+  const int e0 = blockIdx.x * CB, last = g.ncells - 1;
   load_tab(tab, T);
-  load_cell_vertices(g, verts, e, X);
-  for (int i = threadIdx.x; i < NC * N3; i += blockDim.x) U[i / N3][i % N3] = x[(size_t)e * NC * N3 + i];
+  for (int c = 0; c < CB; ++c) load_cell_vertices(g, verts, min(e0 + c, last), X[c]);
+  for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) {
+    const int b = i / N3, c = b / NC;
+    U[b][i - b * N3] = x[(size_t)min(e0 + c, last) * NC * N3 + (b - c * NC) * N3 + (i - b * N3)];
+  }
   __syncthreads();
   // ---- cell term
-  for (int c = 0; c < NC; ++c) sweep3<N, N, false>(T.S, N, U[c], T0, T1, Q[c]);
-  for (int c = 0; c < NC; ++c)
-    for (int m = 0; m < 3; ++m) sweep_dir<N, false>(m, T.Dg, Q[c], G[c][m]);
+  sweep3b<N, N, false>(T.S, N, U[0], T0[0], T1[0], Q[0], NT);
+  for (int m = 0; m < 3; ++m) sweep_dirb<N, false>(m, T.Dg, Q[0], G[m][0], NT);
   __syncthreads();
-  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+  for (int i = threadIdx.x; i < CB * N3; i += blockDim.x) {
+    const int c = i / N3, q = i - c * N3;
+    const int e = min(e0 + c, last);
     const int qx = q % N, qy = (q / N) % N, qz = q / N2;
     R J[3][3], Ji[3][3];
-    trilinear_jac<R>(X, (R)tab.gp[qx], (R)tab.gp[qy], (R)tab.gp[qz], J);
+    trilinear_jac<R>(X[c], (R)tab.gp[qx], (R)tab.gp[qy], (R)tab.gp[qz], J);
     const R det = inverse3(J, Ji);
     const R W = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
     R Gp[NC][3];
-    for (int c = 0; c < NC; ++c)
-      for (int l = 0; l < 3; ++l) Gp[c][l] = G[c][0][q] * Ji[0][l] + G[c][1][q] * Ji[1][l] + G[c][2][q] * Ji[2][l];
+    for (int k = 0; k < NC; ++k) {
+      const int b = c * NC + k;
+      for (int l = 0; l < 3; ++l) Gp[k][l] = G[0][b][q] * Ji[0][l] + G[1][b][q] * Ji[1][l] + G[2][b][q] * Ji[2][l];
+    }
     R Tf[NC][3];
     if (NC == 3) {
       const R nu = nu_cell[(size_t)e * N3 + q];
-      for (int c = 0; c < 3; ++c)
-        for (int l = 0; l < 3; ++l) Tf[c][l] = nu * (Gp[c][l] + Gp[l][c]);  // 2 nu eps(u)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) Tf[k][l] = nu * (Gp[k][l] + Gp[l][k]);  // 2 nu eps(u)
     } else {
       for (int l = 0; l < 3; ++l) Tf[0][l] = Gp[0][l];
     }
-    for (int c = 0; c < NC; ++c) {
-      for (int m = 0; m < 3; ++m) G[c][m][q] = W * (Tf[c][0] * Ji[m][0] + Tf[c][1] * Ji[m][1] + Tf[c][2] * Ji[m][2]);
-      Q[c][q] = mass * W * Q[c][q];
+    for (int k = 0; k < NC; ++k) {
+      const int b = c * NC + k;
+      for (int m = 0; m < 3; ++m) G[m][b][q] = W * (Tf[k][0] * Ji[m][0] + Tf[k][1] * Ji[m][1] + Tf[k][2] * Ji[m][2]);
+      Q[b][q] = mass * W * Q[b][q];
     }
   }
   __syncthreads();
-  for (int c = 0; c < NC; ++c) {
-    for (int m = 0; m < 3; ++m) {
-      sweep_dir<N, true>(m, T.Dg, G[c][m], T0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < N3; q += blockDim.x) Q[c][q] += T0[q];
-      __syncthreads();
-    }
-    sweep3<N, N, true>(T.S, N, Q[c], T0, T1, OUT[c]);
+  for (int m = 0; m < 3; ++m) {
+    sweep_dirb<N, true>(m, T.Dg, G[m][0], T0[0], NT);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) Q[0][i] += T0[0][i];
+    __syncthreads();
   }
+  sweep3b<N, N, true>(T.S, N, Q[0], T0[0], T1[0], OUT[0], NT);
   // ---- faces
-  const R lam_e = (R)lam[e];
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
     int t1, t2;
     face_dirs(d, &t1, &t2);
-    const int nb = cell_neighbor(g, e, f);
-    if (nb < 0 && face_bc(g, e, f) == 1) continue;  // homogeneous Neumann: no term
     const int fo = 2 * d + (1 - s);
-    for (int c = 0; c < NC; ++c) face_eval<N>(U[c], d, s, T, FM[c], SC);
-    if (nb >= 0) {
-      load_cell_vertices(g, verts, nb, XN);
-      for (int c = 0; c < NC; ++c) face_eval<N>(x + (size_t)nb * NC * N3 + c * N3, d, 1 - s, T, FP[c], SC);
-    }
+    for (int c = threadIdx.x; c < CB; c += blockDim.x) NB[c] = cell_neighbor(g, min(e0 + c, last), f);
     __syncthreads();
+    for (int c = 0; c < CB; ++c)
+      if (NB[c] >= 0) load_cell_vertices(g, verts, NB[c], XN[c]);
+    face_evalb<N>([&](int b, int i) { return U[b][i]; }, d, s, T, FM[0], SC, NT);
+    face_evalb<N>(
+        [&](int b, int i) {
+          const int nb = NB[b / NC];
+          return nb >= 0 ? x[(size_t)nb * NC * N3 + (b % NC) * N3 + i] : R(0);
+        },
+        d, 1 - s, T, FP[0], SC, NT);
     const R orient = R((2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0));
-    const R lam_p = nb >= 0 ? (R)lam[nb] : lam_e;
-    const R tau0 = R(g.cip * (double)(N * N)) * (lam_e > lam_p ? lam_e : lam_p);
-    for (int p = threadIdx.x; p < N2; p += blockDim.x) {
+    for (int i = threadIdx.x; i < CB * N2; i += blockDim.x) {
+      const int c = i / N2, p = i - c * N2;
+      const int e = min(e0 + c, last);
+      const int nb = NB[c];
+      const bool neumann = nb < 0 && face_bc(g, e, f) == 1;  // homogeneous Neumann: no term
+      const R lam_e = (R)lam[e];
+      const R lam_p = nb >= 0 ? (R)lam[nb] : lam_e;
+      const R tau0 = R(g.cip * (double)(N * N)) * (lam_e > lam_p ? lam_e : lam_p);
       R xi[3];
       xi[d] = s ? R(1) : R(0);
       xi[t1] = (R)tab.gp[p % N];
       xi[t2] = (R)tab.gp[p / N];
       R Jm[3][3], Jim[3][3], Jp[3][3], Jip[3][3];
-      trilinear_jac<R>(X, xi[0], xi[1], xi[2], Jm);
+      trilinear_jac<R>(X[c], xi[0], xi[1], xi[2], Jm);
       inverse3(Jm, Jim);
       if (nb >= 0) {
         R xo[3] = {xi[0], xi[1], xi[2]};
         xo[d] = s ? R(0) : R(1);
-        trilinear_jac<R>(XN, xo[0], xo[1], xo[2], Jp);
+        trilinear_jac<R>(XN[c], xo[0], xo[1], xo[2], Jp);
         inverse3(Jp, Jip);
       } else {
         for (int a = 0; a < 3; ++a)
@@ -129,22 +146,24 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
       const R W = T.gw[p % N] * T.gw[p / N] * area;
       // physical traces
       R um[NC], up[NC], Gm[NC][3], Gq[NC][3];
-      for (int c = 0; c < NC; ++c) {
+      for (int k = 0; k < NC; ++k) {
+        const R* fm = FM[c * NC + k];
+        const R* fp = FP[c * NC + k];
         R rm[3], rp[3];
-        rm[d] = FM[c][N2 + p];
-        rm[t1] = FM[c][2 * N2 + p];
-        rm[t2] = FM[c][3 * N2 + p];
-        um[c] = FM[c][p];
-        for (int l = 0; l < 3; ++l) Gm[c][l] = rm[0] * Jim[0][l] + rm[1] * Jim[1][l] + rm[2] * Jim[2][l];
+        rm[d] = fm[N2 + p];
+        rm[t1] = fm[2 * N2 + p];
+        rm[t2] = fm[3 * N2 + p];
+        um[k] = fm[p];
+        for (int l = 0; l < 3; ++l) Gm[k][l] = rm[0] * Jim[0][l] + rm[1] * Jim[1][l] + rm[2] * Jim[2][l];
         if (nb >= 0) {
-          rp[d] = FP[c][N2 + p];
-          rp[t1] = FP[c][2 * N2 + p];
-          rp[t2] = FP[c][3 * N2 + p];
-          up[c] = FP[c][p];
-          for (int l = 0; l < 3; ++l) Gq[c][l] = rp[0] * Jip[0][l] + rp[1] * Jip[1][l] + rp[2] * Jip[2][l];
+          rp[d] = fp[N2 + p];
+          rp[t1] = fp[2 * N2 + p];
+          rp[t2] = fp[3 * N2 + p];
+          up[k] = fp[p];
+          for (int l = 0; l < 3; ++l) Gq[k][l] = rp[0] * Jip[0][l] + rp[1] * Jip[1][l] + rp[2] * Jip[2][l];
         } else {  // Dirichlet mirror
-          up[c] = -um[c];
-          for (int l = 0; l < 3; ++l) Gq[c][l] = Gm[c][l];
+          up[k] = -um[k];
+          for (int l = 0; l < 3; ++l) Gq[k][l] = Gm[k][l];
         }
       }
       R cv[NC], S[NC][3];
@@ -156,17 +175,17 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
         if (g.face_nu == 2) nub = R(2) * num * nup / (num + nup);
         const R tau = tau0 * nub;
         R jm[3], jn = R(0);
-        for (int c = 0; c < 3; ++c) {
-          jm[c] = um[c] - up[c];
-          jn += jm[c] * n[c];
+        for (int k = 0; k < 3; ++k) {
+          jm[k] = um[k] - up[k];
+          jn += jm[k] * n[k];
         }
-        for (int c = 0; c < 3; ++c) {
+        for (int k = 0; k < 3; ++k) {
           // (A + A^T) n, A = (nu- Gm + nu+ Gp)/2
           R an = R(0);
           for (int l = 0; l < 3; ++l)
-            an += R(0.5) * (num * (Gm[c][l] + Gm[l][c]) + nup * (Gq[c][l] + Gq[l][c])) * n[l];
-          cv[c] = W * (-an + tau * (jm[c] + n[c] * jn));
-          for (int l = 0; l < 3; ++l) S[c][l] = -W * num * R(0.5) * (jm[c] * n[l] + jm[l] * n[c]);
+            an += R(0.5) * (num * (Gm[k][l] + Gm[l][k]) + nup * (Gq[k][l] + Gq[l][k])) * n[l];
+          cv[k] = W * (-an + tau * (jm[k] + n[k] * jn));
+          for (int l = 0; l < 3; ++l) S[k][l] = -W * num * R(0.5) * (jm[k] * n[l] + jm[l] * n[k]);
         }
       } else {
         const R tau = tau0;
@@ -176,19 +195,23 @@ __global__ void __launch_bounds__(kSplitThreads, MappedMinBlocks<N>::value) mapp
         cv[0] = W * (-gn + tau * jm);
         for (int l = 0; l < 3; ++l) S[0][l] = -W * R(0.5) * jm * n[l];
       }
-      for (int c = 0; c < NC; ++c) {
+      for (int k = 0; k < NC; ++k) {
+        R* cf = CF[c * NC + k];
         R Rv[3];
-        for (int m = 0; m < 3; ++m) Rv[m] = S[c][0] * Jim[m][0] + S[c][1] * Jim[m][1] + S[c][2] * Jim[m][2];
-        CF[c][p] = cv[c];
-        CF[c][N2 + p] = Rv[d];
-        CF[c][2 * N2 + p] = Rv[t1];
-        CF[c][3 * N2 + p] = Rv[t2];
+        for (int m = 0; m < 3; ++m) Rv[m] = S[k][0] * Jim[m][0] + S[k][1] * Jim[m][1] + S[k][2] * Jim[m][2];
+        cf[p] = neumann ? R(0) : cv[k];
+        cf[N2 + p] = neumann ? R(0) : Rv[d];
+        cf[2 * N2 + p] = neumann ? R(0) : Rv[t1];
+        cf[3 * N2 + p] = neumann ? R(0) : Rv[t2];
       }
     }
     __syncthreads();
-    for (int c = 0; c < NC; ++c) face_eval_t<N>(CF[c], d, s, T, OUT[c], SC);
+    face_eval_tb<N>(CF[0], d, s, T, OUT[0], SC, NT);
   }
-  for (int i = threadIdx.x; i < NC * N3; i += blockDim.x) y[(size_t)e * NC * N3 + i] = OUT[i / N3][i % N3];
+  for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) {
+    const int c = (i / N3) / NC;
+    if (e0 + c <= last) y[(size_t)e0 * NC * N3 + i] = OUT[0][i];
+  }
 }
 
 // Lambda_e = sum_f w_f |f| / |Omega_e| (w = 1/2 interior, 1 boundary), one thread per cell
@@ -361,7 +384,8 @@ cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const Spli
                                 const double* x, double* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
-  const dim3 grid(g.ncells, nbatch);
+  const int cb = n == 2 ? MappedCfg<2>::CB : (n == 3 ? MappedCfg<3>::CB : (n == 4 ? MappedCfg<4>::CB : 1));
+  const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, double><<<grid, kSplitThreads, 0, st>>>(
                                 g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
@@ -378,7 +402,8 @@ cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const 
                                     const float* x, float* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
-  const dim3 grid(g.ncells, nbatch);
+  const int cb = n == 2 ? MappedCfg<2>::CB : (n == 3 ? MappedCfg<3>::CB : (n == 4 ? MappedCfg<4>::CB : 1));
+  const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, float><<<grid, kSplitThreads, 0, st>>>(
                                 g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));

@@ -138,5 +138,89 @@ __device__ void face_eval_t(const R* cf, int d, int s, const STabSmT<R>& T, R* Y
 }
 
 
+// face_eval on ntens tensors at once: src(b, i) is node i of tensor b (shared or
+// global memory); out: ntens x 4 N^2 ([b][slot][p]); sc: 6 ntens N^2 scratch
+template <int N, typename R, typename Src>
+__device__ void face_evalb(Src src, int d, int s, const STabSmT<R>& T, R* out, R* sc, int ntens) {
+  constexpr int N2 = N * N;
+  const int M = ntens * N2;
+  R *L = sc, *D = sc + M, *A = sc + 2 * M, *B = sc + 3 * M, *C = sc + 4 * M, *E = sc + 5 * M;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    const int b = t / N2, p = t - b * N2;
+    const int a = p % N, c = p / N;
+    L[t] = src(b, lnode(d, s ? N - 1 : 0, a, c, N));
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc += T.dS[s][i] * src(b, lnode(d, i, a, c, N));
+    D[t] = acc;
+  }
+  __syncthreads();
+  // along a: A = S L, B = DS L, C = S D
+  sweepb<N, N, 1, 0, N, false>(T.S, N, L, A, ntens);
+  sweepb<N, N, 1, 0, N, false>(T.DS, N, L, B, ntens);
+  sweepb<N, N, 1, 0, N, false>(T.S, N, D, C, ntens);
+  __syncthreads();
+  // along b: values E = S A, d/dxi_d L = S C, d/dxi_t1 D = S B (inputs and outputs disjoint)
+  sweepb<N, N, 1, 1, N, false>(T.S, N, A, E, ntens);
+  sweepb<N, N, 1, 1, N, false>(T.S, N, C, L, ntens);
+  sweepb<N, N, 1, 1, N, false>(T.S, N, B, D, ntens);
+  __syncthreads();
+  sweepb<N, N, 1, 1, N, false>(T.DS, N, A, C, ntens);   // d/dxi_t2 = DS_b A
+  __syncthreads();
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    const int b = t / N2, p = t - b * N2;
+    R* o = out + b * 4 * N2 + p;
+    o[0] = E[t];
+    o[N2] = L[t];
+    o[2 * N2] = D[t];
+    o[3 * N2] = C[t];
+  }
+  __syncthreads();
+}
+
+// face_eval_t on ntens tensors: coefficients cf (ntens x 4 N^2, [b][slot][p]) added
+// to Y (ntens x N^3); sc: 8 ntens N^2 scratch
+template <int N, typename R>
+__device__ void face_eval_tb(const R* cf, int d, int s, const STabSmT<R>& T, R* Y, R* sc, int ntens) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int M = ntens * N2;
+  R *V0 = sc, *V1 = sc + M, *V2 = sc + 2 * M, *V3 = sc + 3 * M;
+  R *Pv = sc + 4 * M, *Pn = sc + 5 * M, *P1 = sc + 6 * M, *P2 = sc + 7 * M;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    const int b = t / N2, p = t - b * N2;
+    const R* c = cf + b * 4 * N2 + p;
+    V0[t] = c[0];
+    V1[t] = c[N2];
+    V2[t] = c[2 * N2];
+    V3[t] = c[3 * N2];
+  }
+  __syncthreads();
+  // along b (transposed): value S^T, normal S^T, t1 S^T, t2 DS^T
+  sweepb<N, N, 1, 1, N, true>(T.S, N, V0, Pv, ntens);
+  sweepb<N, N, 1, 1, N, true>(T.S, N, V1, Pn, ntens);
+  sweepb<N, N, 1, 1, N, true>(T.S, N, V2, P1, ntens);
+  sweepb<N, N, 1, 1, N, true>(T.DS, N, V3, P2, ntens);
+  __syncthreads();
+  for (int t = threadIdx.x; t < M; t += blockDim.x) Pv[t] += P2[t];  // value and t2 parts share S_a^T
+  __syncthreads();
+  // along a (transposed): (value + t2) S^T, normal S^T, t1 DS^T
+  sweepb<N, N, 1, 0, N, true>(T.S, N, Pv, V0, ntens);
+  sweepb<N, N, 1, 0, N, true>(T.S, N, Pn, V1, ntens);
+  sweepb<N, N, 1, 0, N, true>(T.DS, N, P1, V2, ntens);
+  __syncthreads();
+  // layer nodes: values and tangential parts; every node along the normal line: normal part
+  int t1, t2;
+  face_dirs(d, &t1, &t2);
+  for (int i = threadIdx.x; i < ntens * N3; i += blockDim.x) {
+    const int b = i / N3, r = i - b * N3;
+    const int idx[3] = {r % N, (r / N) % N, r / N2};
+    const int p = b * N2 + idx[t1] + N * idx[t2];
+    R v = T.dS[s][idx[d]] * V1[p];
+    if (idx[d] == (s ? N - 1 : 0)) v += V0[p] + V2[p];
+    Y[i] += v;
+  }
+  __syncthreads();
+}
+
 }  // namespace mgeo
 }  // namespace sipg

@@ -28,6 +28,41 @@ __device__ __forceinline__ void sweep(const R* A, int lda, const R* in, R* out) 
   }
 }
 
+// the same on ntens tensors stored one after another (inputs EX*EY*EZ apart,
+// outputs OX*OY*OZ apart): several cells of a CTA in one pass
+template <int EX, int EY, int EZ, int DIR, int NO, bool TR, typename R>
+__device__ __forceinline__ void sweepb(const R* A, int lda, const R* in, R* out, int ntens) {
+  constexpr int OX = DIR == 0 ? NO : EX, OY = DIR == 1 ? NO : EY, OZ = DIR == 2 ? NO : EZ;
+  constexpr int EIN = DIR == 0 ? EX : (DIR == 1 ? EY : EZ);
+  constexpr int SIN = DIR == 0 ? 1 : (DIR == 1 ? EX : EX * EY);
+  constexpr int SI = EX * EY * EZ, SO = OX * OY * OZ;
+  for (int t = threadIdx.x; t < ntens * SO; t += blockDim.x) {
+    const int b = t / SO, u = t - b * SO;
+    const int x = u % OX, y = (u / OX) % OY, z = u / (OX * OY);
+    const int o = DIR == 0 ? x : (DIR == 1 ? y : z);
+    const int base = b * SI + (DIR == 0 ? 0 : x) + (DIR == 1 ? 0 : y) * EX + (DIR == 2 ? 0 : z) * EX * EY;
+    R acc = R(0);
+#pragma unroll
+    for (int m = 0; m < EIN; ++m) acc += (TR ? A[m * lda + o] : A[o * lda + m]) * in[base + m * SIN];
+    out[t] = acc;
+  }
+}
+template <int N, int NO, bool TR, typename R>
+__device__ __forceinline__ void sweep3b(const R* A, int lda, const R* in, R* t0, R* t1, R* out, int ntens) {
+  sweepb<N, N, N, 0, NO, TR>(A, lda, in, t0, ntens);
+  __syncthreads();
+  sweepb<NO, N, N, 1, NO, TR>(A, lda, t0, t1, ntens);
+  __syncthreads();
+  sweepb<NO, NO, N, 2, NO, TR>(A, lda, t1, out, ntens);
+  __syncthreads();
+}
+template <int N, bool TR, typename R>
+__device__ __forceinline__ void sweep_dirb(int dir, const R* A, const R* in, R* out, int ntens) {
+  if (dir == 0) sweepb<N, N, N, 0, N, TR>(A, N, in, out, ntens);
+  else if (dir == 1) sweepb<N, N, N, 1, N, TR>(A, N, in, out, ntens);
+  else sweepb<N, N, N, 2, N, TR>(A, N, in, out, ntens);
+}
+
 // three sweeps with the same matrix (N -> NO per direction); tmp: two buffers of N^3
 template <int N, int NO, bool TR, typename R>
 __device__ __forceinline__ void sweep3(const R* A, int lda, const R* in, R* t0, R* t1, R* out) {
