@@ -58,6 +58,8 @@ enum { SIPG_F64 = 0, SIPG_F32 = 1, SIPG_F64_FF = 2 };
 enum { SIPG_FACE_NU_MAX = 0, SIPG_FACE_NU_ARITH = 1, SIPG_FACE_NU_HARMONIC = 2 };
 enum { SIPG_LAW_CONSTANT = 0, SIPG_LAW_ANALYTIC = 1, SIPG_LAW_SINKER = 2, SIPG_LAW_CARREAU = 3 };
 enum { SIPG_PRECOND_NONE = 0, SIPG_PRECOND_JACOBI = 1, SIPG_PRECOND_MG = 2 };
+/* multigrid hierarchy below the DG level (sipg_opts.mg_cph) */
+enum { SIPG_MG_AUTO = -1, SIPG_MG_DG = 0, SIPG_MG_CPH = 1 };
 
 typedef struct sipg_ctx sipg_ctx;
 
@@ -133,10 +135,14 @@ typedef struct {
   uint64_t seed;
   int krylov_arith;  /* arithmetic of the FP64 operator applies inside CG:
                         SIPG_F64 or SIPG_F64_FF [F64] */
-  int mg_cph;        /* 1: "cph" hierarchy of Sec. 5.4 - below the DG level, the
-                        continuous space of the same degree, then lower degrees and
+  int mg_cph;        /* SIPG_MG_CPH: "cph" hierarchy of Sec. 5.4 - below the DG level,
+                        the continuous space of the same degree, then lower degrees and
                         coarser meshes in the continuous space (Galerkin operators
-                        P^T A_DG P); 0: DG on every level [0]; box meshes only */
+                        P^T A_DG P); plain boxes only (no vertex array, no removed
+                        cells, no periodic direction: SIPG_ERR_INVALID otherwise).
+                        SIPG_MG_DG: DG on every level. SIPG_MG_AUTO: cph on a plain
+                        box, DG on any other mesh [AUTO from sipg_default_opts; a
+                        zero-filled struct reads as DG] */
   int mg_setup_lag;  /* multigrid setup after a viscosity update: the level diagonals
                         are rebuilt at every update, the Chebyshev eigenvalue
                         estimates and the coarse-level inverse at every mg_setup_lag-th

@@ -18,6 +18,7 @@ OP = {"viscous": 0, "poisson": 1}
 PREC = {"f64": 0, "f32": 1, "f64ff": 2}
 LAW = {"constant": 0, "analytic": 1, "sinker": 2, "carreau": 3}
 PRECOND = {"none": 0, "jacobi": 1, "mg": 2}
+MG_AUTO, MG_DG, MG_CPH = -1, 0, 1
 FACE_NU = {"max": 0, "arith": 1, "harmonic": 2}
 BC = {"D": 0, "N": 1}
 

@@ -55,14 +55,16 @@ class Context:
     def __init__(self, nx, ny, nz, k_u, extent=(1.0, 1.0, 1.0), bc_velocity="DDDDDD", bc_pressure="NNNNNN",
                  penalty_factor=1.0, face_nu="max", mg_precision="f32", cheb_degree=3, cheb_range=20.0,
                  cheb_lmax_factor=1.2, lanczos_steps=15, coarse_max_dofs=2000, seed=0, krylov_arith="f64",
-                 stream=None, vertices=None, mg_cph=False, active=None, periodic=(False, False, False), mg_setup_lag=1,
+                 stream=None, vertices=None, mg_cph="auto", active=None, periodic=(False, False, False), mg_setup_lag=1,
                  origin=(0.0, 0.0, 0.0), bc_removed="DN"):
         """vertices: optional (nz+1, ny+1, nx+1, 3) host array of vertex positions
         (trilinear cells; fine level only, see include/sipg.h).
         active: optional (nz, ny, nx) flags of the grid cells (False = removed, e.g. the
         block below a backward-facing step); periodic: per direction; origin: lower
         corner of the grid; bc_removed: velocity and pressure condition on faces
-        against removed cells (see sipg_mesh_desc)."""
+        against removed cells (see sipg_mesh_desc).
+        mg_cph: 'auto' (the cph hierarchy of Sec. 5.4 on a plain box, DG levels on any
+        other mesh), True (cph; plain boxes only) or False (DG on every level)."""
         self._lib = L.load()
         m = L.MeshDesc()
         m.nx, m.ny, m.nz = int(nx), int(ny), int(nz)
@@ -99,7 +101,9 @@ class Context:
         o.coarse_max_dofs = int(coarse_max_dofs)
         o.seed = int(seed)
         o.krylov_arith = L.PREC[krylov_arith]
-        o.mg_cph = int(bool(mg_cph))
+        if mg_cph not in ("auto", True, False):
+            raise ValueError("mg_cph: 'auto', True or False")
+        o.mg_cph = L.MG_AUTO if mg_cph == "auto" else int(bool(mg_cph))
         o.mg_setup_lag = int(mg_setup_lag)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()

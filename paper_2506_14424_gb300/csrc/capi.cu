@@ -109,6 +109,12 @@ bool mesh_topology(const sipg_mesh_desc* m) {
   return m->active != nullptr || m->periodic[0] || m->periodic[1] || m->periodic[2];
 }
 
+// SIPG_MG_AUTO: the continuous (cph) levels on a plain box, the DG levels on any other mesh
+int resolved_mg_cph(int mg_cph, const sipg_mesh_desc* m) {
+  if (mg_cph != SIPG_MG_AUTO) return mg_cph;
+  return (m->vertices || mesh_topology(m)) ? SIPG_MG_DG : SIPG_MG_CPH;
+}
+
 // Active flags of the once-coarsened grid; false if a 2x2x2 block mixes active
 // and removed cells (the mesh cannot be coarsened).
 bool coarsen_mask(int nx, int ny, int nz, const std::vector<unsigned char>& fine, std::vector<unsigned char>* coarse) {
@@ -414,6 +420,7 @@ extern "C" void sipg_default_opts(sipg_opts* o) {
   o->lanczos_steps = 15;
   o->coarse_max_dofs = 2000;
   o->seed = 0;
+  o->mg_cph = SIPG_MG_AUTO;
 }
 
 extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in, void* stream, sipg_ctx** out) {
@@ -442,10 +449,11 @@ extern "C" int sipg_create(const sipg_mesh_desc* mesh, const sipg_opts* opts_in,
   if (o.face_nu < 0 || o.face_nu > 2 || o.cheb_degree < 1 || o.lanczos_steps < 2) return SIPG_ERR_INVALID;
   if (o.krylov_arith != SIPG_F64 && o.krylov_arith != SIPG_F64_FF) return SIPG_ERR_INVALID;
   if (mesh->vertices && o.krylov_arith != SIPG_F64) return SIPG_ERR_INVALID;  // FP64 applies only
-  if (o.mg_cph != 0 && o.mg_cph != 1) return SIPG_ERR_INVALID;
+  if (o.mg_cph != SIPG_MG_AUTO && o.mg_cph != SIPG_MG_DG && o.mg_cph != SIPG_MG_CPH) return SIPG_ERR_INVALID;
   if (o.mg_setup_lag < 0) return SIPG_ERR_INVALID;
-  if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
   const bool topo = mesh_topology(mesh);
+  o.mg_cph = resolved_mg_cph(o.mg_cph, mesh);
+  if (o.mg_cph && mesh->vertices) return SIPG_ERR_INVALID;  // continuous levels: box meshes only
   if (topo) {
     if (o.mg_cph) return SIPG_ERR_INVALID;  // continuous levels: plain boxes only
     const int dims[3] = {mesh->nx, mesh->ny, mesh->nz};
@@ -530,6 +538,8 @@ extern "C" int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* 
     if (o.k_u == 0) o.k_u = d.k_u;
   }
   if (o.k_u < 2 || o.k_u > 5 || mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return SIPG_ERR_INVALID;
+  if (o.mg_cph != SIPG_MG_AUTO && o.mg_cph != SIPG_MG_DG && o.mg_cph != SIPG_MG_CPH) return SIPG_ERR_INVALID;
+  o.mg_cph = resolved_mg_cph(o.mg_cph, mesh);
   sipg_ctx probe;
   probe.dry = true;
   probe.mesh = *mesh;
@@ -563,6 +573,8 @@ extern "C" int sipg_level_plan(const sipg_mesh_desc* mesh, const sipg_opts* opts
     if (o.k_u == 0) o.k_u = d.k_u;
   }
   if (o.k_u < 2 || o.k_u > 5 || mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return SIPG_ERR_INVALID;
+  if (o.mg_cph != SIPG_MG_AUTO && o.mg_cph != SIPG_MG_DG && o.mg_cph != SIPG_MG_CPH) return SIPG_ERR_INVALID;
+  o.mg_cph = resolved_mg_cph(o.mg_cph, mesh);
   sipg_ctx probe;
   probe.dry = true;
   probe.mesh = *mesh;

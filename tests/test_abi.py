@@ -34,6 +34,7 @@ def test_default_opts(lib):
     lib.sipg_default_opts(ctypes.byref(o))
     assert o.k_u == 3 and o.cheb_degree == 3 and o.cheb_range == 20.0 and o.coarse_max_dofs == 2000
     assert abs(o.cheb_lmax_factor - 1.2) < 1e-15 and o.mg_precision == 1
+    assert o.mg_cph == _lib.MG_AUTO and o.mg_setup_lag == 0
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("k_u", 1), ("k_u", 6), ("bc", 7)])

@@ -88,7 +88,7 @@ def test_f32_level_applies_close_to_oracle(op, dims, k_u):
     (42, 22, 45) leave ragged warps of 10 and 32 cells."""
     extent = (1.3, 0.7, 2.1)
     bcv, bcp = "DNDDND", "NDNNDN"
-    ctx = Context(*dims, k_u, extent=extent, bc_velocity=bcv, bc_pressure=bcp)
+    ctx = Context(*dims, k_u, extent=extent, bc_velocity=bcv, bc_pressure=bcp, mg_cph=False)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     nc = 3 if op == "viscous" else 1
@@ -200,7 +200,7 @@ def test_full_size_32cubed_sampled_rows():
 
 @pytest.mark.parametrize("op,dims,k", [("viscous", (4, 2, 2), 3), ("poisson", (4, 4, 2), 3)])
 def test_inverse_diagonal_matches_oracle(op, dims, k):
-    ctx = Context(*dims, k, bc_velocity="DDNDDD", bc_pressure="NNDNNN")
+    ctx = Context(*dims, k, bc_velocity="DDNDDD", bc_pressure="NNDNNN", mg_cph=False)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     nlev = ctx.num_levels(op)

@@ -60,7 +60,7 @@ def _oracle_hierarchy(ctx, op, rheo, bc, mass=0.0, u=None):
 
 @pytest.mark.parametrize("op", ["viscous", "poisson"])
 def test_transfers_match_oracle(op):
-    ctx = Context(4, 2, 2, 4, coarse_max_dofs=100)
+    ctx = Context(4, 2, 2, 4, coarse_max_dofs=100, mg_cph=False)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     _, Ps, _ = _oracle_hierarchy(ctx, op, rheo, "DDDDDD" if op == "viscous" else "NNNNNN")
@@ -75,7 +75,7 @@ def test_transfers_match_oracle(op):
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-5)])
 def test_smoother_matches_oracle_chebyshev(prec, tol):
-    ctx = Context(3, 3, 2, 3, mg_precision=prec)
+    ctx = Context(3, 3, 2, 3, mg_precision=prec, mg_cph=False)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     mats, _, _ = _oracle_hierarchy(ctx, "viscous", rheo, "DDDDDD")
@@ -94,7 +94,7 @@ def test_smoother_matches_oracle_chebyshev(prec, tol):
 def test_lanczos_estimate_bounded_by_exact(prec, tol):
     # the estimate is of the operator the smoother applies: FP32 multigrid
     # estimates the FP32-rounded operator (relative perturbation ~ 1e-7)
-    ctx = Context(2, 2, 2, 3, mg_precision=prec)
+    ctx = Context(2, 2, 2, 3, mg_precision=prec, mg_cph=False)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     mats, _, _ = _oracle_hierarchy(ctx, "viscous", rheo, "DDDDDD")
@@ -109,7 +109,7 @@ def test_lanczos_estimate_bounded_by_exact(prec, tol):
 @pytest.mark.parametrize("op,bc", [("viscous", "DDDDDD"), ("poisson", "NNNNNN")])
 def test_vcycle_f64_matches_oracle_vcycle(op, bc):
     kw = {"bc_velocity": bc} if op == "viscous" else {"bc_pressure": bc}
-    ctx = Context(4, 4, 4, 3, mg_precision="f64", coarse_max_dofs=300, **kw)
+    ctx = Context(4, 4, 4, 3, mg_precision="f64", coarse_max_dofs=300, mg_cph=False, **kw)
     rheo = {'law': 'analytic'}
     ctx.set_viscosity(rheo)
     mats, Ps, _ = _oracle_hierarchy(ctx, op, rheo, bc)
@@ -164,7 +164,7 @@ def test_level_viscosity_matches_oracle(rheo_name):
         rheo = inputs.carreau_blood_like()
         modes = inputs.fourier_modes(1)
         u = S.interpolate(lambda p: inputs.fourier_field(p, modes))
-    ctx = Context(*dims, k, coarse_max_dofs=100)
+    ctx = Context(*dims, k, coarse_max_dofs=100, mg_cph=False)
     ctx.set_viscosity(rheo, None if u is None else _dev(u))
     levels = []
     for level in range(ctx.num_levels("viscous")):
@@ -177,12 +177,13 @@ def test_level_viscosity_matches_oracle(rheo_name):
         assert _rel(nf.cpu().numpy(), rf) <= 1e-13, level
 
 
+@pytest.mark.parametrize("hier", ["auto", False])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("contrast", [1.0, 1e4, 1e6])
-def test_mg_cg_solve_matches_oracle(prec, contrast):
+def test_mg_cg_solve_matches_oracle(prec, contrast, hier):
     dims, k = (4, 4, 2), 3
     rheo = inputs.sinker(seed=2, count=8, radius=0.2, nu_max=contrast)
-    ctx = Context(*dims, k, mg_precision=prec, coarse_max_dofs=300)
+    ctx = Context(*dims, k, mg_precision=prec, coarse_max_dofs=300, mg_cph=hier)
     ctx.set_viscosity(rheo)
     S = SIPG(BoxMesh(*dims), k, 3)
     A = S.assemble(*S.viscosity_at_points(rheo))

@@ -10,7 +10,10 @@ hierarchy, computed by the C library's host code, equal the oracle's mesh.
   133,120-cell channel grid;
 * the multigrid level sequence of a dry hierarchy build (sipg_level_plan) equals
   the oracle's level sequence (p-levels, masked h-coarsening, periodic minimum,
-  coarse-size threshold) for the channel, a box and a periodic grid.
+  coarse-size threshold) for the channel, a box and a periodic grid;
+* the default hierarchy choice (SIPG_MG_AUTO): the cph levels (the DG level, then the
+  continuous twin of every DG level) on a plain box, the DG levels on a grid with
+  removed cells or a periodic direction.
 """
 import ctypes
 
@@ -114,7 +117,7 @@ def test_estimate_bytes_of_the_channel(lib):
     assert 10 * 8 * n_vel < nbytes.value < 60e9
 
 
-def _plan(lib, c, k, op, bc_v="DNDDDD", bc_p="NDNNNN", coarse=2000):
+def _plan(lib, c, k, op, bc_v="DNDDDD", bc_p="NDNNNN", coarse=2000, mg_cph=0):
     from paper_2506_14424_gb300 import _lib
     m = _lib.MeshDesc()
     m.nx, m.ny, m.nz = c["dims"]
@@ -134,6 +137,7 @@ def _plan(lib, c, k, op, bc_v="DNDDDD", bc_p="NDNNNN", coarse=2000):
     lib.sipg_default_opts(ctypes.byref(o))
     o.k_u = k
     o.coarse_max_dofs = coarse
+    o.mg_cph = mg_cph
     nl = ctypes.c_int()
     info = np.zeros(6 * 16, dtype=np.int32)
     assert lib.sipg_level_plan(ctypes.byref(m), ctypes.byref(o), 0 if op == "viscous" else 1, 16,
@@ -161,3 +165,33 @@ def test_level_plan_matches_oracle_sequence(lib, name, make, k, coarse, op):
     for row, (m, kl) in zip(plan, ref):
         assert tuple(row[:3]) == m.n_cells_dir and row[3] == kl and row[4] == m.n_cells
         assert row[5] == m.n_cells * ncomp * (kl + 1) ** 3
+
+
+def _box(dims, periodic=(False, False, False)):
+    return {"dims": dims, "extent": (1.0, 1.0, 1.0), "lo": (0.0, 0.0, 0.0), "active": None, "periodic": periodic}
+
+
+@pytest.mark.parametrize("op", ["viscous", "poisson"])
+def test_default_hierarchy_is_cph_on_plain_boxes(lib, op):
+    from paper_2506_14424_gb300 import _lib
+    k, coarse = 4, 2000
+    ncomp, kk = (3, k) if op == "viscous" else (1, k - 1)
+    box = _box((8, 8, 8))
+    dg = _plan(lib, box, k, op, coarse=coarse, mg_cph=_lib.MG_DG)
+    auto = _plan(lib, box, k, op, coarse=coarse, mg_cph=_lib.MG_AUTO)
+    assert np.array_equal(auto, _plan(lib, box, k, op, coarse=coarse, mg_cph=_lib.MG_CPH))
+    # [DG level 0, continuous twin of every DG level]: same cells and degree, shared nodes
+    assert len(auto) == len(dg) + 1
+    assert np.array_equal(auto[0], dg[0])
+    for row, d in zip(auto[1:], dg):
+        assert np.array_equal(row[:5], d[:5])
+        nx, ny, nz, kl = d[0], d[1], d[2], d[3]
+        assert row[5] == ncomp * (nx * kl + 1) * (ny * kl + 1) * (nz * kl + 1)
+    assert kk == dg[0][3]
+    # the continuous levels are built for plain boxes only: auto keeps DG elsewhere
+    per = _box((8, 4, 8), periodic=(True, False, True))
+    assert np.array_equal(_plan(lib, per, 3, op, coarse=300, mg_cph=_lib.MG_AUTO),
+                          _plan(lib, per, 3, op, coarse=300, mg_cph=_lib.MG_DG))
+    chan = inputs.bfs_channel(4, inlet_length=1.0, outlet_length=3.0, depth=1.0)
+    assert np.array_equal(_plan(lib, chan, 2, op, coarse=500, mg_cph=_lib.MG_AUTO),
+                          _plan(lib, chan, 2, op, coarse=500, mg_cph=_lib.MG_DG))
