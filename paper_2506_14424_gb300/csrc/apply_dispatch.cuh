@@ -7,16 +7,6 @@
 
 namespace sipg {
 
-// Host conversion of the FP64 tables to the kernel's arithmetic type (the
-// float-float split is exact: hi = RN(d), lo = RN(d - hi)).
-template <typename T>
-inline T host_from_double(double d) { return T(d); }
-template <>
-inline ff host_from_double<ff>(double d) {
-  const float h = (float)d;
-  return ff(h, (float)(d - (double)h));
-}
-
 template <typename T>
 CTab<T> make_ctab(const Tab& t) {
   CTab<T> c{};
@@ -48,7 +38,7 @@ cudaError_t launch_apply_g(const LevelGeom& g, const Tab& tab, const TX* x, TS* 
   if (grid == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
   apply_kernel<N, NC, TX, TS, TN, TC, TOPO><<<dim3(grid, nbatch), Cfg::NT, smem, st>>>(
-      g, make_ctab<TC>(tab), x, y, nu_cell, nu_face, mass, stride);
+      g, make_ctab<TC>(tab), level_consts<TC>(g, N, mass), x, y, nu_cell, nu_face, stride);
   return cudaGetLastError();
 }
 

@@ -36,8 +36,8 @@ cudaError_t launch_tpc_g(const LevelGeom& g, const Tab& tab, const float* x, flo
   const int grid = (g.ncells + CW - 1) / CW;
   if (grid == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
-  apply_tpc_kernel<N, NC, TOPO><<<dim3(grid, nbatch), 32, smem, st>>>(g, make_tpc_tab(tab), x, y, nu_cell, nu_face,
-                                                                      mass, stride);
+  apply_tpc_kernel<N, NC, TOPO><<<dim3(grid, nbatch), 32, smem, st>>>(
+      g, make_tpc_tab(tab), level_consts<float>(g, N, mass), x, y, nu_cell, nu_face, stride);
   return cudaGetLastError();
 }
 

@@ -342,7 +342,11 @@ int sipg_ctx::build_hierarchy(int op) {
     Cl.gjw = alloc<double>(256 + 16 * (int64_t)Cl.N, &e); if (e) return fail(SIPG_ERR_NOMEM, "alloc coarse", e);
   }
   // trilinear cells: vertices of every level (p-levels share the finer level's, h-levels
-  // take every other vertex) and the penalty factors with each level's Gauss rule
+  // take every other vertex), the penalty factors with each level's Gauss rule and the
+  // metric terms of the operator kernels (counted in the estimate)
+  if (mapped)
+    for (const Level& L : H.L)
+      bytes += (int64_t)(12 * (mapped_cell_metric_len(L.n, L.g.ncells) + mapped_face_metric_len(L.n, L.g.ncells)));
   if (mapped && !dry) {
     for (size_t l = 0; l < H.L.size(); ++l) {
       Level& L = H.L[l];
@@ -360,6 +364,13 @@ int sipg_ctx::build_hierarchy(int op) {
       e = cudaMalloc(&L.lam, sizeof(double) * (size_t)L.g.ncells);
       if (!e) e = launch_mapped_lambda(L.n, L.g, stabs[L.n], L.verts, L.lam, st);
       if (e) return fail(SIPG_ERR_NOMEM, "level penalty factors", e);
+      const size_t lc = mapped_cell_metric_len(L.n, L.g.ncells), lf = mapped_face_metric_len(L.n, L.g.ncells);
+      e = cudaMalloc(&L.cmet64, sizeof(double) * lc);
+      if (!e) e = cudaMalloc(&L.cmet32, sizeof(float) * lc);
+      if (!e) e = cudaMalloc(&L.fmet64, sizeof(double) * lf);
+      if (!e) e = cudaMalloc(&L.fmet32, sizeof(float) * lf);
+      if (!e) e = launch_mapped_metric(L.n, L.g, stabs[L.n], L.verts, L.cmet64, L.cmet32, L.fmet64, L.fmet32, st);
+      if (e) return fail(SIPG_ERR_NOMEM, "level metric terms", e);
     }
   }
   // CG vectors on level 0
@@ -388,6 +399,7 @@ sipg_ctx::~sipg_ctx() {
       cudaFree(L.nu_cellff); cudaFree(L.nu_faceff); cudaFree(L.xff);
       cudaFree(L.ulin); cudaFree(L.diag64); cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.gjw);
       cudaFree(L.lam);
+      cudaFree(L.cmet64); cudaFree(L.cmet32); cudaFree(L.fmet64); cudaFree(L.fmet32);
       if (L.own_verts) cudaFree(L.verts);
       for (int p = 0; p < 2; ++p) for (int v = 0; v < 4; ++v) cudaFree(L.w[p][v]);
       cudaFree(L.Ainv); cudaFree(L.Atmp);
@@ -544,9 +556,11 @@ extern "C" int sipg_estimate_bytes(const sipg_mesh_desc* mesh, const sipg_opts* 
   probe.dry = true;
   probe.mesh = *mesh;
   probe.opts = o;
+  probe.mapped = mesh->vertices != nullptr;
   probe.topo = mesh_topology(mesh);
   if (mesh->active) probe.mask.assign(mesh->active, mesh->active + (size_t)mesh->nx * mesh->ny * mesh->nz);
   probe.mesh.active = nullptr;
+  probe.mesh.vertices = nullptr;
   for (int op = 0; op < 2; ++op) {
     int rc = probe.build_hierarchy(op);
     if (rc) return rc;
@@ -653,11 +667,12 @@ int sipg_ctx::level_apply(int op, int l, const T* x, T* y, double mass) {
   }
   if (mapped) {
     if constexpr (sizeof(T) == 8) {
-      CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam, op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
+      CK(launch_mapped_apply(L.n, H.ncomp, L.g, stabs[L.n], L.cmet64, L.fmet64, L.lam,
+                             op == SIPG_OP_VISCOUS ? L.nu_cell64 : nullptr,
                              op == SIPG_OP_VISCOUS ? L.nu_face64 : nullptr, mass, (const double*)x, (double*)y, 1, st));
       return SIPG_OK;
     } else {
-      CK(launch_mapped_apply_f32(L.n, H.ncomp, L.g, stabs[L.n], L.verts, L.lam,
+      CK(launch_mapped_apply_f32(L.n, H.ncomp, L.g, stabs[L.n], L.cmet32, L.fmet32, L.lam,
                                  op == SIPG_OP_VISCOUS ? L.nu_cell32 : nullptr,
                                  op == SIPG_OP_VISCOUS ? L.nu_face32 : nullptr, mass, (const float*)x, (float*)y, 1,
                                  st));
@@ -902,8 +917,8 @@ int sipg_ctx::setup_coarse(int op, double mass) {
     if (!ce) ce = cudaMemcpyAsync(down, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, st);
     if (!ce) ce = launch_colour_probes(N, dpc, nb, dcol, C.Atmp, st);
     if (!ce)
-      ce = mapped ? launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.verts, C.lam, nc, nf, mass, C.Atmp, C.Ainv,
-                                        nb, st)
+      ce = mapped ? launch_mapped_apply(C.n, H.ncomp, C.g, stabs[C.n], C.cmet64, C.fmet64, C.lam, nc, nf, mass,
+                                        C.Atmp, C.Ainv, nb, st)
                   : launch_apply<double>(C.n, H.ncomp, C.g, tabs[C.n], C.Atmp, C.Ainv, nc, nf, mass, nb, st);
     if (!ce) ce = cudaMemsetAsync(C.Atmp, 0, sizeof(double) * (size_t)N * N, st);
     if (!ce) ce = launch_colour_scatter(N, C.g.ncells, dpc, nb, down, C.Ainv, C.Atmp, st);

@@ -35,6 +35,10 @@ struct Level {
   double* verts = nullptr;   // trilinear cells: this level's vertices (device)
   bool own_verts = false;    //   allocated for this level (h-levels); p-levels share the finer one's
   double* lam = nullptr;     // trilinear cells: Lambda_e per cell with this level's Gauss rule
+  double* cmet64 = nullptr;  // trilinear cells: metric terms of the cell points [C][10][n^3]
+  float* cmet32 = nullptr;   //   (J^-1, w det J) and of the face points [C][6][13][n^2]
+  double* fmet64 = nullptr;  //   (J^-1, unit normal, surface weight), FP64 and FP32
+  float* fmet32 = nullptr;
   // continuous (cph) levels: values on the global node grid; the operator is
   // P^T A_DG P with the DG data (viscosity) of the twin level of the same mesh/degree
   bool cg = false;

@@ -107,12 +107,17 @@ cudaError_t launch_mapped_mass(int n, int ncomp, const LevelGeom& g, const Split
                                double coeff, bool inverse, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_mapped_boundary_points(int n, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                           double* xyz, cudaStream_t st);
-cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
-                                    const double* lam, const float* nu_cell, const float* nu_face, double mass,
-                                    const float* x, float* y, int nbatch, cudaStream_t st);
-cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
-                                const double* lam, const double* nu_cell, const double* nu_face, double mass,
-                                const double* x, double* y, int nbatch, cudaStream_t st);
+// metric terms of a trilinear level: cmet [C][10][n^3], fmet [C][6][13][n^2] (mapped.cu)
+inline size_t mapped_cell_metric_len(int n, int ncells) { return (size_t)ncells * 10 * n * n * n; }
+inline size_t mapped_face_metric_len(int n, int ncells) { return (size_t)ncells * 6 * 13 * n * n; }
+cudaError_t launch_mapped_metric(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double* cmet64,
+                                 float* cmet32, double* fmet64, float* fmet32, cudaStream_t st);
+cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const float* cmet,
+                                    const float* fmet, const double* lam, const float* nu_cell, const float* nu_face,
+                                    double mass, const float* x, float* y, int nbatch, cudaStream_t st);
+cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* cmet,
+                                const double* fmet, const double* lam, const double* nu_cell, const double* nu_face,
+                                double mass, const double* x, double* y, int nbatch, cudaStream_t st);
 cudaError_t launch_mapped_diagonal(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
                                    const double* lam, const double* nu_cell, const double* nu_face, double mass,
                                    double* diag, cudaStream_t st);

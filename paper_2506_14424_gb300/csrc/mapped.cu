@@ -10,10 +10,19 @@
 // The topology is structured (cells (i, j, k), neighbours across the faces),
 // vertex (i, j, k) at verts[((k (ny+1) + j)(nx+1) + i) * 3 + c].
 //
-// FP64, one CTA per cell, one thread per tensor entry of each sweep (the
-// split.cu style). The Jacobian is recomputed in the thread that owns a point
-// instead of being stored: per point, reference gradients -> physical ->
-// flux -> back to reference coefficients in one pass.
+// The operator kernels read the geometry of every quadrature point from
+// per-level metric arrays built once per mesh (mapped_metric_kernel, FP64 with
+// an FP32 copy), the scheme of matrix-free codes on general cells:
+//   cell point q:      J^-1 (9 entries), W = w_q det J             [cell][10][n^3]
+//   face f, point p:   J^-1 of the own side (9), the unit normal n (3, outward
+//                      of the own cell), W = w_a w_b |t1 x t2|      [cell][6][13][n^2]
+// and the neighbour's J^-1 at the same face point from the neighbour's entry of
+// its opposite face (same tangential coordinates on the structured grid).
+// Without them every point re-evaluated the trilinear Jacobian from the 8
+// vertices (about 100 flops per point, twice per face point), which made the
+// FP64 apply twice as expensive as the affine one and the FP32 applies
+// latency bound. The other trilinear forms (mass, diagonal, step forms) still
+// evaluate the geometry from the vertices: they run once per setup or step.
 #include "kernels.cuh"
 #include "mapped_geom.cuh"
 #include "sweeps.cuh"
@@ -24,26 +33,90 @@
 // Resident CTAs per SM requested from the compiler: the kernel is latency bound
 // (barriers between sweeps); one cell per CTA measured at 32^3, k = 3: 2 CTAs
 // 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers) 11.1 ms.
-template <int N> struct MappedCfg {
-  static constexpr int CB = N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1));
-  static constexpr int MIN_BLOCKS = N <= 4 ? 4 : (N == 5 ? 6 : 4);
+#ifndef SIPG_MAPPED_CBX
+#define SIPG_MAPPED_CBX 1
+#endif
+#ifndef SIPG_MAPPED_MINB
+#define SIPG_MAPPED_MINB 4
+#endif
+template <int N, typename R = double> struct MappedCfg {
+  static constexpr int CB = (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1))) * (sizeof(R) == 4 && N <= 4 ? SIPG_MAPPED_CBX : 1);
+  static constexpr int MIN_BLOCKS = sizeof(R) == 4 && N <= 4 ? SIPG_MAPPED_MINB : (N <= 4 ? 4 : (N == 5 ? 6 : 4));
 };
 
 namespace sipg {
 namespace {
 using namespace sweeps;
 using namespace mgeo;
+// Metric terms of one level (see the header): one CTA per cell, FP64, stored in
+// FP64 and rounded to FP32.
+template <int N>
+__global__ void __launch_bounds__(kSplitThreads) mapped_metric_kernel(LevelGeom g, SplitTab tab,
+                                                                      const double* __restrict__ verts,
+                                                                      double* __restrict__ cmet64,
+                                                                      float* __restrict__ cmet32,
+                                                                      double* __restrict__ fmet64,
+                                                                      float* __restrict__ fmet32) {
+  constexpr int N3 = N * N * N, N2 = N * N;
+  __shared__ double X[8][3];
+  const int e = blockIdx.x;
+  load_cell_vertices(g, verts, e, X);
+  __syncthreads();
+  const size_t cb = (size_t)e * 10 * N3;
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
+    double J[3][3], Ji[3][3];
+    trilinear_jac<double>(X, tab.gp[qx], tab.gp[qy], tab.gp[qz], J);
+    const double det = inverse3(J, Ji);
+    double v[10];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) v[3 * a + b] = Ji[a][b];
+    v[9] = tab.gw[qx] * tab.gw[qy] * tab.gw[qz] * det;
+    for (int k = 0; k < 10; ++k) {
+      cmet64[cb + (size_t)k * N3 + q] = v[k];
+      cmet32[cb + (size_t)k * N3 + q] = (float)v[k];
+    }
+  }
+  for (int i = threadIdx.x; i < 6 * N2; i += blockDim.x) {
+    const int f = i / N2, p = i - f * N2;
+    const int d = f >> 1, s = f & 1;
+    int t1, t2;
+    face_dirs(d, &t1, &t2);
+    double xi[3];
+    xi[d] = s ? 1.0 : 0.0;
+    xi[t1] = tab.gp[p % N];
+    xi[t2] = tab.gp[p / N];
+    double J[3][3], Ji[3][3];
+    trilinear_jac<double>(X, xi[0], xi[1], xi[2], J);
+    inverse3(J, Ji);
+    const double ta[3] = {J[0][t1], J[1][t1], J[2][t1]}, tb[3] = {J[0][t2], J[1][t2], J[2][t2]};
+    double n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
+    const double area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const double orient = (2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0);
+    double v[13];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) v[3 * a + b] = Ji[a][b];
+    for (int k = 0; k < 3; ++k) v[9 + k] = n[k] * (orient / area);
+    v[12] = tab.gw[p % N] * tab.gw[p / N] * area;
+    const size_t fb = ((size_t)e * 6 + f) * 13 * N2;
+    for (int k = 0; k < 13; ++k) {
+      fmet64[fb + (size_t)k * N2 + p] = v[k];
+      fmet32[fb + (size_t)k * N2 + p] = (float)v[k];
+    }
+  }
+}
+
 template <int N, int NC, typename R>
-__global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
-                                                                     const double* __restrict__ verts,
+__global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+                                                                     const R* __restrict__ cmet,
+                                                                     const R* __restrict__ fmet,
                                                                      const double* __restrict__ lam,
                                                                      const R* __restrict__ nu_cell,
                                                                      const R* __restrict__ nu_face, double mass_d,
                                                                      const R* __restrict__ x,
                                                                      R* __restrict__ y, int64_t batch_stride) {
-  constexpr int N3 = N * N * N, N2 = N * N, CB = MappedCfg<N>::CB, NT = CB * NC;
+  constexpr int N3 = N * N * N, N2 = N * N, CB = MappedCfg<N, R>::CB, NT = CB * NC;
   __shared__ STabSmT<R> T;
-  __shared__ R X[CB][8][3], XN[CB][8][3];
   __shared__ R U[NT][N3], Q[NT][N3], G[3][NT][N3], T0[NT][N3], T1[NT][N3], OUT[NT][N3];
   __shared__ R FM[NT][4 * N2], FP[NT][4 * N2], CF[NT][4 * N2], SC[8 * NT * N2];
   __shared__ int NB[CB];
@@ -52,7 +125,6 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mappe
   y += (int64_t)blockIdx.y * batch_stride;
   const int e0 = blockIdx.x * CB, last = g.ncells - 1;
   load_tab(tab, T);
-  for (int c = 0; c < CB; ++c) load_cell_vertices(g, verts, min(e0 + c, last), X[c]);
   for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) {
     const int b = i / N3, c = b / NC;
     U[b][i - b * N3] = x[(size_t)min(e0 + c, last) * NC * N3 + (b - c * NC) * N3 + (i - b * N3)];
@@ -65,11 +137,13 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mappe
   for (int i = threadIdx.x; i < CB * N3; i += blockDim.x) {
     const int c = i / N3, q = i - c * N3;
     const int e = min(e0 + c, last);
-    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
-    R J[3][3], Ji[3][3];
-    trilinear_jac<R>(X[c], (R)tab.gp[qx], (R)tab.gp[qy], (R)tab.gp[qz], J);
-    const R det = inverse3(J, Ji);
-    const R W = T.gw[qx] * T.gw[qy] * T.gw[qz] * det;
+    const R* cm = cmet + (size_t)e * 10 * N3 + q;
+    R Ji[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Ji[a][b] = cm[(3 * a + b) * N3];
+    const R W = cm[9 * N3];
     R Gp[NC][3];
     for (int k = 0; k < NC; ++k) {
       const int b = c * NC + k;
@@ -105,8 +179,6 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mappe
     const int fo = 2 * d + (1 - s);
     for (int c = threadIdx.x; c < CB; c += blockDim.x) NB[c] = cell_neighbor(g, min(e0 + c, last), f);
     __syncthreads();
-    for (int c = 0; c < CB; ++c)
-      if (NB[c] >= 0) load_cell_vertices(g, verts, NB[c], XN[c]);
     face_evalb<N>([&](int b, int i) { return U[b][i]; }, d, s, T, FM[0], SC, NT);
     face_evalb<N>(
         [&](int b, int i) {
@@ -114,7 +186,6 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mappe
           return nb >= 0 ? x[(size_t)nb * NC * N3 + (b % NC) * N3 + i] : R(0);
         },
         d, 1 - s, T, FP[0], SC, NT);
-    const R orient = R((2.0 * s - 1.0) * (d == 1 ? -1.0 : 1.0));
     for (int i = threadIdx.x; i < CB * N2; i += blockDim.x) {
       const int c = i / N2, p = i - c * N2;
       const int e = min(e0 + c, last);
@@ -123,27 +194,19 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N>::MIN_BLOCKS) mappe
       const R lam_e = (R)lam[e];
       const R lam_p = nb >= 0 ? (R)lam[nb] : lam_e;
       const R tau0 = R(g.cip * (double)(N * N)) * (lam_e > lam_p ? lam_e : lam_p);
-      R xi[3];
-      xi[d] = s ? R(1) : R(0);
-      xi[t1] = (R)tab.gp[p % N];
-      xi[t2] = (R)tab.gp[p / N];
-      R Jm[3][3], Jim[3][3], Jp[3][3], Jip[3][3];
-      trilinear_jac<R>(X[c], xi[0], xi[1], xi[2], Jm);
-      inverse3(Jm, Jim);
-      if (nb >= 0) {
-        R xo[3] = {xi[0], xi[1], xi[2]};
-        xo[d] = s ? R(0) : R(1);
-        trilinear_jac<R>(XN[c], xo[0], xo[1], xo[2], Jp);
-        inverse3(Jp, Jip);
-      } else {
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) Jip[a][b] = Jim[a][b];
-      }
-      const R ta[3] = {Jm[0][t1], Jm[1][t1], Jm[2][t1]}, tb[3] = {Jm[0][t2], Jm[1][t2], Jm[2][t2]};
-      R n[3] = {ta[1] * tb[2] - ta[2] * tb[1], ta[2] * tb[0] - ta[0] * tb[2], ta[0] * tb[1] - ta[1] * tb[0]};
-      const R area = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-      for (int k = 0; k < 3; ++k) n[k] *= orient / area;
-      const R W = T.gw[p % N] * T.gw[p / N] * area;
+      const R* fm = fmet + ((size_t)e * 6 + f) * 13 * N2 + p;
+      const R* fq = fmet + ((size_t)(nb >= 0 ? nb : e) * 6 + (nb >= 0 ? fo : f)) * 13 * N2 + p;
+      R Jim[3][3], Jip[3][3], n[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          Jim[a][b] = fm[(3 * a + b) * N2];
+          Jip[a][b] = fq[(3 * a + b) * N2];
+        }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) n[k] = fm[(9 + k) * N2];
+      const R W = fm[12 * N2];
       // physical traces
       R um[NC], up[NC], Gm[NC][3], Gq[NC][3];
       for (int k = 0; k < NC; ++k) {
@@ -379,37 +442,48 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_viscosity_kernel(LevelGe
     default: return cudaErrorInvalidValue;          \
   }
 
-cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
-                                const double* lam, const double* nu_cell, const double* nu_face, double mass,
-                                const double* x, double* y, int nbatch, cudaStream_t st) {
+cudaError_t launch_mapped_metric(int n, const LevelGeom& g, const SplitTab& tab, const double* verts, double* cmet64,
+                                 float* cmet32, double* fmet64, float* fmet32, cudaStream_t st) {
+  if (g.ncells == 0) return cudaSuccess;
+  SIPG_MAPPED_DISPATCH(n, (mapped_metric_kernel<N><<<g.ncells, kSplitThreads, 0, st>>>(g, tab, verts, cmet64, cmet32,
+                                                                                       fmet64, fmet32)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* cmet,
+                                const double* fmet, const double* lam, const double* nu_cell, const double* nu_face,
+                                double mass, const double* x, double* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
   const int cb = n == 2 ? MappedCfg<2>::CB : (n == 3 ? MappedCfg<3>::CB : (n == 4 ? MappedCfg<4>::CB : 1));
   const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, double><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
   } else {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, double><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
   }
   return cudaGetLastError();
 }
 
-// the same operator in FP32 (multigrid levels: geometry, sweeps and flux in binary32)
-cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* verts,
-                                    const double* lam, const float* nu_cell, const float* nu_face, double mass,
-                                    const float* x, float* y, int nbatch, cudaStream_t st) {
+// the same operator in FP32 (multigrid levels: metric, sweeps and flux in binary32)
+cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const float* cmet,
+                                    const float* fmet, const double* lam, const float* nu_cell, const float* nu_face,
+                                    double mass, const float* x, float* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
   const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
-  const int cb = n == 2 ? MappedCfg<2>::CB : (n == 3 ? MappedCfg<3>::CB : (n == 4 ? MappedCfg<4>::CB : 1));
+  const int cb = n == 2 ? MappedCfg<2, float>::CB
+                         : (n == 3 ? MappedCfg<3, float>::CB
+                                   : (n == 4 ? MappedCfg<4, float>::CB : (n == 5 ? MappedCfg<5, float>::CB
+                                                                                 : MappedCfg<6, float>::CB)));
   const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, float><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
   } else {
     SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, float><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, verts, lam, nu_cell, nu_face, mass, x, y, stride)));
+                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
   }
   return cudaGetLastError();
 }

@@ -37,6 +37,8 @@
 #include "common.cuh"
 #include "ff.cuh"
 
+#include <type_traits>
+
 namespace sipg {
 
 // 1D tables in the arithmetic type of a kernel (kernel parameter: compile-time
@@ -48,6 +50,48 @@ struct CTab {
   T dS0[kMaxN], dS1[kMaxN], gw[kMaxN];
 };
 
+// Host conversion of a binary64 value to the kernel's arithmetic type (the
+// float-float split is exact: hi = RN(d), lo = RN(d - hi)).
+template <typename T>
+inline T host_from_double(double d) { return T(d); }
+template <>
+inline ff host_from_double<ff>(double d) {
+  const float h = (float)d;
+  return ff(h, (float)(d - (double)h));
+}
+
+// Per-level constants of one apply in the arithmetic type, converted on the
+// host, so that the float-float and FP32 kernels issue no FP64 instruction
+// (this GPU's FP64 pipe runs about 1/70 of the FP32 rate): 1/h per direction,
+// the face area h_t1 h_t2 per normal direction, the cell volume, the mass
+// coefficient and C_IP N^2 of the penalty.
+template <typename T>
+struct LevelConsts {
+  T ih[3], area[3], detJ, mass, cipn2;
+};
+template <typename T>
+inline LevelConsts<T> level_consts(const LevelGeom& g, int n, double mass) {
+  LevelConsts<T> c;
+  for (int d = 0; d < 3; ++d) c.ih[d] = host_from_double<T>(g.ih[d]);
+  c.area[0] = host_from_double<T>(g.h[1] * g.h[2]);
+  c.area[1] = host_from_double<T>(g.h[0] * g.h[2]);
+  c.area[2] = host_from_double<T>(g.h[0] * g.h[1]);
+  c.detJ = host_from_double<T>(g.h[0] * g.h[1] * g.h[2]);
+  c.mass = host_from_double<T>(mass);
+  c.cipn2 = host_from_double<T>(g.cip * double(n * n));
+  return c;
+}
+
+// Penalty length scale of a cell in the arithmetic type: sum over its faces of
+// w / h_d, w = 1/2 on interior faces and 1 on boundary faces.
+template <bool TOPO, typename T>
+__device__ __forceinline__ T penalty_lambda_c(const LevelGeom& g, int e, const T* ih) {
+  T lam = T(0);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) lam = lam + (cell_neighbor_t<TOPO>(g, e, f) >= 0 ? T(0.5f) : T(1)) * ih[f >> 1];
+  return lam;
+}
+
 template <typename T>
 __device__ __forceinline__ T nubar_of(int mode, T a, T b) {
   if (mode == 1) return T(0.5f) * (a + b);
@@ -55,11 +99,29 @@ __device__ __forceinline__ T nubar_of(int mode, T a, T b) {
   return a > b ? a : b;
 }
 
+// Shared-memory swizzle of the degree-3 tensors of the binary64 kernel: inside
+// each 128-byte row of 16 doubles the element index is XORed with r + 4r, r =
+// row index mod 4 (the z layer of a cell tensor, the component-cell index of a
+// face slot). The threads of a warp then touch every bank pair at most twice in
+// the x-, y- and z-line sweeps and in the line phases of the face slots, instead
+// of up to eight times (row strides of 4 and 16 elements). Every access to a
+// tensor uses the same map of its index relative to the region's base (Xs, Y,
+// W0..W2, the face slots F), and the bases are multiples of 16 elements.
+// Measured at 32^3, k = 3: binary64 2.62 -> 2.56 ms; the float-float kernel
+// (issue bound) lost more to the index arithmetic than it gained (0.787 ->
+// 0.885 ms) and keeps the plain layout.
+template <int N, typename T>
+__device__ __forceinline__ int swz(int i) {
+  if constexpr (N == 4 && std::is_same<T, double>::value) return i ^ (((i >> 4) & 3) * 5);
+  else return i;
+}
+
 // out[t][.. o ..] (+)= sum_j M(o, j) in[t][.. j ..] along direction DIR of
 // N^3 tensors (x fastest); M(o, j) = M[o*N + j], or M[j*N + o] if TR.
 // One thread per 1D line: the N inputs are loaded once into registers, the
 // N x N matrix comes from the kernel-parameter bank, N outputs are stored.
-template <int N, int DIR, bool TR, bool ACC, typename T>
+// SW: the tensors are stored with the swizzle swz (the operator kernel).
+template <int N, int DIR, bool TR, bool ACC, bool SW = false, typename T>
 __device__ __forceinline__ void sweep3(const T* __restrict__ in, T* __restrict__ out, const T* M, int ntens) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int STR = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
@@ -69,13 +131,13 @@ __device__ __forceinline__ void sweep3(const T* __restrict__ in, T* __restrict__
     const int off = t * N3 + (DIR == 0 ? r * N : (DIR == 1 ? (r % N) + (r / N) * N2 : r));
     T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = in[off + j * STR];
+    for (int j = 0; j < N; ++j) v[j] = in[SW ? swz<N, T>(off + j * STR) : off + j * STR];
 #pragma unroll
     for (int o = 0; o < N; ++o) {
       Acc<T> acc;
 #pragma unroll
       for (int j = 0; j < N; ++j) acc.add(TR ? M[j * N + o] : M[o * N + j], v[j]);
-      T* dst = out + off + o * STR;
+      T* dst = out + (SW ? swz<N, T>(off + o * STR) : off + o * STR);
       *dst = ACC ? *dst + acc.get() : acc.get();
     }
   }
@@ -150,16 +212,18 @@ template <int N, int NC> struct OccCfg<N, NC, ff> {
   static constexpr int MIN = 65536 / (OpCfg<N, NC>::NT * REG) > 0 ? 65536 / (OpCfg<N, NC>::NT * REG) : 1;
 };
 
-// Shared-memory layout per cell (elements of T): staged x, the y accumulator,
-// and a work region used by the cell phase (3 tensors) and then by the face
-// phase (16 face slots: 8 per side of one direction).
+// Shared-memory layout (elements of T): the 1D tables, the face penalties, the
+// quadrature weights times det J of the N^3 cell points, and per cell the staged
+// x, the y accumulator and a work region used by the cell phase (3 tensors) and
+// then by the face phase (16 face slots: 8 per side of one direction).
 template <int N, int NC>
 __host__ __device__ constexpr int op_work_elems() {
   return (3 * NC * N * N * N > 16 * NC * N * N) ? 3 * NC * N * N * N : 16 * NC * N * N;
 }
 template <int N, int NC>
 __host__ __device__ constexpr int op_smem_elems() {
-  return 2 * N * N + 4 * N + 6 * OpCfg<N, NC>::CPB + OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
+  return 2 * N * N + 4 * N + 6 * OpCfg<N, NC>::CPB + N * N * N +
+         OpCfg<N, NC>::CPB * (2 * NC * N * N * N + op_work_elems<N, NC>());
 }
 // bytes: the T region above, then the per-CTA face table (int, 6 per cell):
 // the neighbour across each face, or kBndDirichlet / kBndNeumann
@@ -191,12 +255,11 @@ __device__ __forceinline__ T sel3(const T* v, int i) { return i == 0 ? v[0] : (i
 
 template <int N, int NC, typename TN, typename T>
 __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int cell0, int FS, const T* ih,
-                                               const T* gw, const T* pen, const int* nbt,
+                                               const T area, const T* gw, const T* pen, const int* nbt,
                                                const TN* __restrict__ nu_face, T* F) {
   constexpr int N2 = N * N, CPB = OpCfg<N, NC>::CPB;
   const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
   const T ihd = sel3(ih, D), iht1 = sel3(ih, T1), iht2 = sel3(ih, T2);
-  const T area = from_double<T>(g.h[T1] * g.h[T2]);
   const int last = g.ncells - 1;
   for (int i = threadIdx.x; i < 2 * CPB * N2; i += blockDim.x) {
     const int s = i / (CPB * N2);
@@ -206,23 +269,17 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
     const int e = min(cell0 + c, last);
     const int f = 2 * D + s;
     const int nb = nbt[c * 6 + f];
-    T* gV = F + (s * 8 + 0) * FS;
-    T* gN = F + (s * 8 + 1) * FS;
-    const T* gVp = F + (s * 8 + 2) * FS;
-    const T* gNp = F + (s * 8 + 3) * FS;
-    T* gT2 = F + (s * 8 + 4) * FS;
-    T* gT1 = F + (s * 8 + 5) * FS;
-    const T* gT2p = F + (s * 8 + 6) * FS;
-    const T* gT1p = F + (s * 8 + 7) * FS;
+    // slot q of side s, entry j
+    auto at = [&](int q, int j) -> T& { return F[swz<N, T>((s * 8 + q) * FS + j)]; };
     if (nb == kBndNeumann) {  // homogeneous Neumann: no face term
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const int j = (c * NC + k) * N2 + p;
-        gV[j] = T(0); gN[j] = T(0);
+        at(0, j) = T(0); at(1, j) = T(0);
       }
       if (NC == 3) {
         const int jd = (c * 3 + D) * N2 + p;
-        gT1[jd] = T(0); gT2[jd] = T(0);
+        at(5, jd) = T(0); at(4, jd) = T(0);
       }
       continue;
     }
@@ -244,20 +301,20 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int j = (c * 3 + k) * N2 + p;
-        um[k] = gV[j];
-        nm[k] = gN[j];
+        um[k] = at(0, j);
+        nm[k] = at(1, j);
         if (inner) {
-          up[k] = gVp[j];
-          npd[k] = gNp[j];
+          up[k] = at(2, j);
+          npd[k] = at(3, j);
         } else {  // Dirichlet mirror: u+ = -u-, grad u+ = grad u-
           up[k] = -um[k];
           npd[k] = nm[k];
         }
       }
       const int jd = (c * 3 + D) * N2 + p;
-      const T t1m = gT1[jd], t2m = gT2[jd];
-      const T t1p = inner ? gT1p[jd] : t1m;
-      const T t2p = inner ? gT2p[jd] : t2m;
+      const T t1m = at(5, jd), t2m = at(4, jd);
+      const T t1p = inner ? at(7, jd) : t1m;
+      const T t2p = inner ? at(6, jd) : t2m;
       T jmp[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) jmp[k] = um[k] - up[k];
@@ -265,34 +322,34 @@ __device__ __forceinline__ void face_flux_pair(int D, const LevelGeom& g, int ce
       for (int k = 0; k < 3; ++k) {
         const int j = (c * 3 + k) * N2 + p;
         if (k == D) {
-          gV[j] = T(2) * (tW * jmp[k] - (am * nm[k] + ap * npd[k]) * ihd);
-          gN[j] = T(2) * cq * jmp[k] * ihd;
+          at(0, j) = T(2) * (tW * jmp[k] - (am * nm[k] + ap * npd[k]) * ihd);
+          at(1, j) = T(2) * cq * jmp[k] * ihd;
         } else {
           const T tm = k == T1 ? t1m * iht1 : t2m * iht2;
           const T tp = k == T1 ? t1p * iht1 : t2p * iht2;
-          gV[j] = tW * jmp[k] - (am * (nm[k] * ihd + tm) + ap * (npd[k] * ihd + tp));
-          gN[j] = cq * jmp[k] * ihd;
+          at(0, j) = tW * jmp[k] - (am * (nm[k] * ihd + tm) + ap * (npd[k] * ihd + tp));
+          at(1, j) = cq * jmp[k] * ihd;
         }
       }
-      gT1[jd] = cq * sel3(jmp, T1) * iht1;
-      gT2[jd] = cq * sel3(jmp, T2) * iht2;
+      at(5, jd) = cq * sel3(jmp, T1) * iht1;
+      at(4, jd) = cq * sel3(jmp, T2) * iht2;
     } else {
       const T tau = pe;
       const int j = c * N2 + p;
-      const T pm = gV[j];
-      const T dnm = gN[j] * ihd;
+      const T pm = at(0, j);
+      const T dnm = at(1, j) * ihd;
       T pp, dnp;
       if (inner) {
-        pp = gVp[j];
-        dnp = gNp[j] * ihd;
+        pp = at(2, j);
+        dnp = at(3, j) * ihd;
       } else {
         pp = -pm;
         dnp = dnm;
       }
       const T jmp = pm - pp;
       // -grad q . n jump/2 - q ({{dp/dx_d}} n_d - tau jump)
-      gV[j] = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
-      gN[j] = -W * T(0.5f) * jmp * nsign * ihd;
+      at(0, j) = -W * (T(0.5f) * (dnm + dnp) * nsign - tau * jmp);
+      at(1, j) = -W * T(0.5f) * jmp * nsign * ihd;
     }
   }
 }
@@ -314,8 +371,8 @@ __device__ __forceinline__ T line_dot(const T* M, const T* v, int o) {
 template <int N, int NC, typename TX, typename TN, typename T>
 __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, const T* Dg, int cell0,
                                        const TX* __restrict__ x, const TN* __restrict__ nu_face, const T* Xs, T* Y,
-                                       T* F, const T* pen, const int* nbt, const T* ih, const T* gw, const T* dS0,
-                                       const T* dS1) {
+                                       T* F, const T* pen, const int* nbt, const T* ih, const T area, const T* gw,
+                                       const T* dS0, const T* dS1) {
   constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
   constexpr int nt = CPB * NC;
   constexpr int FS = CPB * NC * N2;
@@ -330,13 +387,13 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     const int off0 = face_node<N>(D, 0, p % N, p / N);
     const T* dS = s ? dS1 : dS0;
     const T* dSn = s ? dS0 : dS1;
-    const T* xs = Xs + t * N3 + off0;
+    const int xb = t * N3 + off0;
     Acc<T> dn;
 #pragma unroll
-    for (int j = 0; j < N; ++j) dn.add(dS[j], xs[j * STD]);
-    T* Fs = F + s * 8 * FS;
-    Fs[rem] = xs[(s ? N - 1 : 0) * STD];
-    Fs[FS + rem] = dn.get();
+    for (int j = 0; j < N; ++j) dn.add(dS[j], Xs[swz<N, T>(xb + j * STD)]);
+    const int fb = s * 8 * FS + rem;
+    F[swz<N, T>(fb)] = Xs[swz<N, T>(xb + (s ? N - 1 : 0) * STD)];
+    F[swz<N, T>(fb + FS)] = dn.get();
     const int nb = nbt[c * 6 + 2 * D + s];
     if (nb >= 0) {
       const TX* xn = x + ((size_t)nb * NC + comp) * N3 + off0;
@@ -346,11 +403,11 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
       Acc<T> dnn;
 #pragma unroll
       for (int j = 0; j < N; ++j) dnn.add(dSn[j], v[j]);
-      Fs[2 * FS + rem] = v[s ? 0 : N - 1];
-      Fs[3 * FS + rem] = dnn.get();
+      F[swz<N, T>(fb + 2 * FS)] = v[s ? 0 : N - 1];
+      F[swz<N, T>(fb + 3 * FS)] = dnn.get();
     } else {
-      Fs[2 * FS + rem] = T(0);
-      Fs[3 * FS + rem] = T(0);
+      F[swz<N, T>(fb + 2 * FS)] = T(0);
+      F[swz<N, T>(fb + 3 * FS)] = T(0);
     }
   }
   __syncthreads();
@@ -360,46 +417,41 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     const int rem = line - s * 4 * nt * N;
     const int q = rem / (nt * N), lt = rem - q * nt * N;
     const int t = lt / N, r = lt - t * N;
-    const T* in = F + (s * 8 + q) * FS + t * N2 + r * N;
-    T* out = F + (s * 8 + 4 + q) * FS + t * N2 + r * N;
+    const int ib = (s * 8 + q) * FS + t * N2 + r * N;
+    const int ob = ib + 4 * FS;
     T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = in[j];
+    for (int j = 0; j < N; ++j) v[j] = F[swz<N, T>(ib + j)];
 #pragma unroll
-    for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(S, v, o);
+    for (int o = 0; o < N; ++o) F[swz<N, T>(ob + o)] = line_dot<N, false>(S, v, o);
   }
   __syncthreads();
-  // (C) along b: values at the face Gauss points; the b-derivative of the
-  // traces is needed only for the normal component D of the velocity
-  for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
-    const int s = line / (nt * N);
-    const int lt = line - s * nt * N;
+  // (C) along b: values at the face Gauss points, one thread per (side, own /
+  // neighbour, line): trace and normal derivative, slots 4, 5 -> 0, 1 (own) and
+  // 6, 7 -> 2, 3 (neighbour); the b-derivative of the trace (slot 4 / 6) is
+  // needed only for the normal component D of the velocity
+  for (int line = threadIdx.x; line < 2 * 2 * nt * N; line += blockDim.x) {
+    const int s = line / (2 * nt * N);
+    const int rem = line - s * 2 * nt * N;
+    const int q = rem / (nt * N), lt = rem - q * nt * N;
     const int t = lt / N, r = lt - t * N;
-    T* Fs = F + s * 8 * FS + t * N2 + r;
-    T v4[N], v5[N], v6[N], v7[N];
+    const int fb = s * 8 * FS + t * N2 + r;
+    T va[N], vb[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      v4[j] = Fs[4 * FS + j * N];
-      v5[j] = Fs[5 * FS + j * N];
-      v6[j] = Fs[6 * FS + j * N];
-      v7[j] = Fs[7 * FS + j * N];
+      va[j] = F[swz<N, T>(fb + (4 + 2 * q) * FS + j * N)];
+      vb[j] = F[swz<N, T>(fb + (5 + 2 * q) * FS + j * N)];
     }
-    T gv[N], gvp[N];
+    T gv[N];
 #pragma unroll
     for (int o = 0; o < N; ++o) {
-      gv[o] = line_dot<N, false>(S, v4, o);
-      gvp[o] = line_dot<N, false>(S, v6, o);
-      Fs[0 * FS + o * N] = gv[o];
-      Fs[1 * FS + o * N] = line_dot<N, false>(S, v5, o);
-      Fs[2 * FS + o * N] = gvp[o];
-      Fs[3 * FS + o * N] = line_dot<N, false>(S, v7, o);
+      gv[o] = line_dot<N, false>(S, va, o);
+      F[swz<N, T>(fb + (2 * q) * FS + o * N)] = gv[o];
+      F[swz<N, T>(fb + (2 * q + 1) * FS + o * N)] = line_dot<N, false>(S, vb, o);
     }
     if (NC == 3 && t % 3 == D) {
 #pragma unroll
-      for (int o = 0; o < N; ++o) {
-        Fs[4 * FS + o * N] = line_dot<N, false>(Dg, gv, o);
-        Fs[6 * FS + o * N] = line_dot<N, false>(Dg, gvp, o);
-      }
+      for (int o = 0; o < N; ++o) F[swz<N, T>(fb + (4 + 2 * q) * FS + o * N)] = line_dot<N, false>(Dg, gv, o);
     }
   }
   __syncthreads();
@@ -412,60 +464,61 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
       const int q = rem / (CPB * N), lc = rem - q * CPB * N;  // q = 0 own, 1 neighbour
       const int c = lc / N, r = lc - c * N;
       const int t = c * 3 + D;
-      const T* in = F + (s * 8 + 2 * q) * FS + t * N2 + r * N;
-      T* out = F + (s * 8 + 5 + 2 * q) * FS + t * N2 + r * N;
+      const int ib = (s * 8 + 2 * q) * FS + t * N2 + r * N;
+      const int ob = ib + 5 * FS;
       T v[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) v[j] = in[j];
+      for (int j = 0; j < N; ++j) v[j] = F[swz<N, T>(ib + j)];
 #pragma unroll
-      for (int o = 0; o < N; ++o) out[o] = line_dot<N, false>(Dg, v, o);
+      for (int o = 0; o < N; ++o) F[swz<N, T>(ob + o)] = line_dot<N, false>(Dg, v, o);
     }
     __syncthreads();
   }
   // (E) numerical flux
-  face_flux_pair<N, NC, TN, T>(D, g, cell0, FS, ih, gw, pen, nbt, nu_face, F);
+  face_flux_pair<N, NC, TN, T>(D, g, cell0, FS, ih, area, gw, pen, nbt, nu_face, F);
   __syncthreads();
   // (F) test side, along a: slot 2 = gV + Dg_a^T gT1
   for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
     const int s = line / (nt * N);
     const int lt = line - s * nt * N;
     const int t = lt / N, r = lt - t * N;
-    T* Fs = F + s * 8 * FS + t * N2 + r * N;
+    const int fb = s * 8 * FS + t * N2 + r * N;
     if (NC == 3 && t % 3 == D) {
       T g5[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) g5[j] = Fs[5 * FS + j];
+      for (int j = 0; j < N; ++j) g5[j] = F[swz<N, T>(fb + 5 * FS + j)];
 #pragma unroll
-      for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o] + line_dot<N, true>(Dg, g5, o);
+      for (int o = 0; o < N; ++o) F[swz<N, T>(fb + 2 * FS + o)] = F[swz<N, T>(fb + o)] + line_dot<N, true>(Dg, g5, o);
     } else {
 #pragma unroll
-      for (int o = 0; o < N; ++o) Fs[2 * FS + o] = Fs[o];
+      for (int o = 0; o < N; ++o) F[swz<N, T>(fb + 2 * FS + o)] = F[swz<N, T>(fb + o)];
     }
   }
   __syncthreads();
-  // (G) along b: slot 6 = S_b^T (slot 2 + Dg_b^T gT2), slot 7 = S_b^T gN
-  for (int line = threadIdx.x; line < 2 * nt * N; line += blockDim.x) {
-    const int s = line / (nt * N);
-    const int lt = line - s * nt * N;
+  // (G) along b, one thread per (side, output, line):
+  // slot 6 = S_b^T (slot 2 + Dg_b^T gT2), slot 7 = S_b^T gN
+  for (int line = threadIdx.x; line < 2 * 2 * nt * N; line += blockDim.x) {
+    const int s = line / (2 * nt * N);
+    const int rem = line - s * 2 * nt * N;
+    const int q = rem / (nt * N), lt = rem - q * nt * N;
     const int t = lt / N, r = lt - t * N;
-    T* Fs = F + s * 8 * FS + t * N2 + r;
-    T w[N], g4[N], g1[N];
+    const int fb = s * 8 * FS + t * N2 + r;
+    T w[N];
+    if (q == 1) {
 #pragma unroll
-    for (int j = 0; j < N; ++j) g1[j] = Fs[1 * FS + j * N];
-    if (NC == 3 && t % 3 == D) {
+      for (int j = 0; j < N; ++j) w[j] = F[swz<N, T>(fb + 1 * FS + j * N)];
+    } else if (NC == 3 && t % 3 == D) {
+      T g4[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) g4[j] = Fs[4 * FS + j * N];
+      for (int j = 0; j < N; ++j) g4[j] = F[swz<N, T>(fb + 4 * FS + j * N)];
 #pragma unroll
-      for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N] + line_dot<N, true>(Dg, g4, o);
+      for (int o = 0; o < N; ++o) w[o] = F[swz<N, T>(fb + 2 * FS + o * N)] + line_dot<N, true>(Dg, g4, o);
     } else {
 #pragma unroll
-      for (int o = 0; o < N; ++o) w[o] = Fs[2 * FS + o * N];
+      for (int o = 0; o < N; ++o) w[o] = F[swz<N, T>(fb + 2 * FS + o * N)];
     }
 #pragma unroll
-    for (int o = 0; o < N; ++o) {
-      Fs[6 * FS + o * N] = line_dot<N, true>(S, w, o);
-      Fs[7 * FS + o * N] = line_dot<N, true>(S, g1, o);
-    }
+    for (int o = 0; o < N; ++o) F[swz<N, T>(fb + (6 + q) * FS + o * N)] = line_dot<N, true>(S, w, o);
   }
   __syncthreads();
   // (H) along a: node coefficients, slot 0 (value) and slot 1 (normal)
@@ -474,13 +527,13 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     const int rem = line - s * 2 * nt * N;
     const int q = rem / (nt * N), lt = rem - q * nt * N;
     const int t = lt / N, r = lt - t * N;
-    const T* in = F + (s * 8 + 6 + q) * FS + t * N2 + r * N;
-    T* out = F + (s * 8 + q) * FS + t * N2 + r * N;
+    const int ob = (s * 8 + q) * FS + t * N2 + r * N;
+    const int ib = ob + 6 * FS;
     T v[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = in[j];
+    for (int j = 0; j < N; ++j) v[j] = F[swz<N, T>(ib + j)];
 #pragma unroll
-    for (int o = 0; o < N; ++o) out[o] = line_dot<N, true>(S, v, o);
+    for (int o = 0; o < N; ++o) F[swz<N, T>(ob + o)] = line_dot<N, true>(S, v, o);
   }
   __syncthreads();
   // (I) scatter onto the cell nodes: value on the face layer, normal
@@ -490,10 +543,10 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
     const int ix = r % N, iy = (r / N) % N, iz = r / N2;
     const int id = D == 0 ? ix : (D == 1 ? iy : iz);
     const int fp = t * N2 + (D == 0 ? iy : ix) + N * (D == 2 ? iy : iz);
-    T v = dS0[id] * F[1 * FS + fp] + dS1[id] * F[9 * FS + fp];
-    if (id == 0) v += F[fp];
-    if (id == N - 1) v += F[8 * FS + fp];
-    Y[i] += v;
+    T v = dS0[id] * F[swz<N, T>(1 * FS + fp)] + dS1[id] * F[swz<N, T>(9 * FS + fp)];
+    if (id == 0) v += F[swz<N, T>(fp)];
+    if (id == N - 1) v += F[swz<N, T>(8 * FS + fp)];
+    Y[swz<N, T>(i)] += v;
   }
   __syncthreads();
 }
@@ -506,10 +559,10 @@ __device__ __noinline__ void face_pair(int D, const LevelGeom& g, const T* S, co
 // type (double, float, or ff = float-float: x and nu pre-split into (hi, lo)
 // pairs, y stored as binary64).
 template <int N, int NC, typename TX, typename TS, typename TN, typename T, bool TOPO>
-__device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const TX* __restrict__ x,
-                                            TS* __restrict__ y, const TN* __restrict__ nu_cell,
-                                            const TN* __restrict__ nu_face, double mass_d, int cell0,
-                                            unsigned char* smraw) {
+__device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& ct, const LevelConsts<T>& lc,
+                                            const TX* __restrict__ x, TS* __restrict__ y,
+                                            const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face,
+                                            int cell0, unsigned char* smraw) {
   constexpr int N2 = N * N, N3 = N2 * N, CPB = OpCfg<N, NC>::CPB;
   constexpr int nt = CPB * NC;
   T* sm = reinterpret_cast<T*>(smraw);
@@ -520,7 +573,9 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
   T* dS1 = dS0 + N;
   T* gw = dS1 + N;
   T* pen = gw + 2 * N;             // 6 * CPB: C_IP N^2 max(Lambda-, Lambda+) per face
-  T* Xs = pen + 6 * CPB;           // CPB * NC * N3
+  T* Wq = pen + 6 * CPB;           // N3: w_x w_y w_z det J of the cell points
+  T* Xs = Wq + N3;                 // CPB * NC * N3
+  static_assert((2 * N2 + 4 * N + 6 * CPB + N3) % 16 == 0 || N != 4, "swizzled tensors start on 128-byte rows");
   T* Y = Xs + CPB * NC * N3;       // CPB * NC * N3
   T* Wk = Y + CPB * NC * N3;       // CPB * op_work_elems
   T* W0 = Wk;
@@ -535,104 +590,123 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
     Dsh[i] = ct.Dg[i];
   }
   const int last = g.ncells - 1;
+  const T ih[3] = {lc.ih[0], lc.ih[1], lc.ih[2]};
   // face tables: neighbour (or boundary kind) and penalty of each face
   for (int i = threadIdx.x; i < 6 * CPB; i += blockDim.x) {
     const int c = i / 6, f = i - 6 * c;
     const int e = min(cell0 + c, last);
     const int nb = cell_neighbor_t<TOPO>(g, e, f);
     nbt[i] = nb >= 0 ? nb : (face_bc_t<TOPO>(g, e, f) == 1 ? kBndNeumann : kBndDirichlet);
-    const double lm = penalty_lambda_t<TOPO>(g, e);
-    const double lp = nb >= 0 ? penalty_lambda_t<TOPO>(g, nb) : lm;
-    pen[i] = from_double<T>(g.cip * double(N * N) * (lm > lp ? lm : lp));
+    const T lm = penalty_lambda_c<TOPO, T>(g, e, ih);
+    const T lp = nb >= 0 ? penalty_lambda_c<TOPO, T>(g, nb, ih) : lm;
+    pen[i] = lc.cipn2 * (lm > lp ? lm : lp);
   }
-  const T mass = from_double<T>(mass_d);
+  const T mass = lc.mass;
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) Wq[q] = ct.gw[q % N] * ct.gw[(q / N) % N] * ct.gw[q / N2] * lc.detJ;
   const int ncell = min(CPB, g.ncells - cell0);  // cells stored by this CTA
   for (int i = threadIdx.x; i < nt * N3; i += blockDim.x) {
     const int c = i / (NC * N3);
     const int e = min(cell0 + c, last);
-    Xs[i] = load_as<T>(x[(size_t)e * NC * N3 + (i - c * NC * N3)]);
+    Xs[swz<N, T>(i)] = load_as<T>(x[(size_t)e * NC * N3 + (i - c * NC * N3)]);
   }
   __syncthreads();
 
   // ---- cell term: nodes -> Gauss points along x, y; the z pass also forms
   // the collocation z-derivative
-  sweep3<N, 0, false, false>(Xs, W1, S, nt);
+  sweep3<N, 0, false, false, true>(Xs, W1, S, nt);
   __syncthreads();
-  sweep3<N, 1, false, false>(W1, W2, S, nt);
+  sweep3<N, 1, false, false, true>(W1, W2, S, nt);
   __syncthreads();
   for (int line = threadIdx.x; line < nt * N2; line += blockDim.x) {
     const int t = line / N2, r = line - t * N2;
     const int off = t * N3 + r;
     T v[N], u[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = W2[off + j * N2];
+    for (int j = 0; j < N; ++j) v[j] = W2[swz<N, T>(off + j * N2)];
 #pragma unroll
     for (int o = 0; o < N; ++o) {
       u[o] = line_dot<N, false>(S, v, o);
-      W0[off + o * N2] = u[o];
+      W0[swz<N, T>(off + o * N2)] = u[o];
     }
 #pragma unroll
-    for (int o = 0; o < N; ++o) Y[off + o * N2] = line_dot<N, false>(Dg, u, o);  // d/dz (Y free until the end)
+    for (int o = 0; o < N; ++o) Y[swz<N, T>(off + o * N2)] = line_dot<N, false>(Dg, u, o);  // d/dz (Y free until the end)
   }
   __syncthreads();
-  sweep3<N, 0, false, false>(W0, W1, Dg, nt);
-  sweep3<N, 1, false, false>(W0, W2, Dg, nt);
+  sweep3<N, 0, false, false, true>(W0, W1, Dg, nt);
+  sweep3<N, 1, false, false, true>(W0, W2, Dg, nt);
   __syncthreads();
-  const T ih[3] = {from_double<T>(g.ih[0]), from_double<T>(g.ih[1]), from_double<T>(g.ih[2])};
-  const T detJ = from_double<T>(g.h[0] * g.h[1] * g.h[2]);
-  for (int i = threadIdx.x; i < CPB * N3; i += blockDim.x) {
-    const int c = i / N3, q = i - c * N3;
-    const int qx = q % N, qy = (q / N) % N, qz = q / N2;
-    const T W = gw[qx] * gw[qy] * gw[qz] * detJ;
-    T* Bl[3] = {W1, W2, Y};
-    if constexpr (NC == 3) {
-      T G[3][3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) G[k][l] = Bl[l][(c * 3 + k) * N3 + q] * ih[l];
-      const T nu2W = T(2) * load_as<T>(nu_cell[(size_t)min(cell0 + c, last) * N3 + q]) * W;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          Bl[l][(c * 3 + k) * N3 + q] = nu2W * T(0.5f) * (G[k][l] + G[l][k]) * ih[l];
-        W0[(c * 3 + k) * N3 + q] *= mass * W;
+  if constexpr (NC == 3) {
+    // 2 nu eps(u) W at the points, one thread per (cell, item, point): items
+    // 0..5 the symmetric pairs (k, l), k <= l, of the gradient (each reads and
+    // writes only its own two entries), items 6..8 the mass term of component
+    // k - an even split of the point work over the CTA's threads
+    for (int i = threadIdx.x; i < CPB * 9 * N3; i += blockDim.x) {
+      const int c = i / (9 * N3), rem = i - c * 9 * N3;
+      const int it = rem / N3, q = rem - it * N3;
+      const T W = Wq[q];
+      if (it >= 6) {
+        W0[swz<N, T>((c * 3 + it - 6) * N3 + q)] *= mass * W;
+        continue;
       }
-    } else {
+      const int k = it < 3 ? it : (it == 5 ? 1 : 0);
+      const int l = it < 3 ? it : (it == 3 ? 1 : 2);
+      const T nuW = load_as<T>(nu_cell[(size_t)min(cell0 + c, last) * N3 + q]) * W;
+      T* Bk = k == 0 ? W1 : (k == 1 ? W2 : Y);
+      T* Bl = l == 0 ? W1 : (l == 1 ? W2 : Y);
+      const T ihk = sel3(ih, k), ihl = sel3(ih, l);
+      if (k == l) {
+        // 2 nu W d_k u_k / h_k^2
+        T& g = Bk[swz<N, T>((c * 3 + k) * N3 + q)];
+        g = T(2) * nuW * g * ihk * ihk;
+      } else {
+        // e_kl = nu W (d_l u_k / h_l + d_k u_l / h_k), the same for both entries
+        T& gkl = Bl[swz<N, T>((c * 3 + k) * N3 + q)];
+        T& glk = Bk[swz<N, T>((c * 3 + l) * N3 + q)];
+        const T e = nuW * (gkl * ihl + glk * ihk);
+        gkl = e * ihl;
+        glk = e * ihk;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < CPB * N3; i += blockDim.x) {
+      const int c = i / N3, q = i - c * N3;
+      const T W = Wq[q];
+      T* Bl[3] = {W1, W2, Y};
+      const int j = swz<N, T>(c * N3 + q);
 #pragma unroll
-      for (int l = 0; l < 3; ++l) Bl[l][c * N3 + q] = Bl[l][c * N3 + q] * ih[l] * W * ih[l];
-      W0[c * N3 + q] *= mass * W;
+      for (int l = 0; l < 3; ++l) Bl[l][j] = Bl[l][j] * ih[l] * W * ih[l];
+      W0[j] *= mass * W;
     }
   }
   __syncthreads();
   // transposed: W0 += Dx^T W1 + Dy^T W2 + Dz^T Y, then S^T in z (fused), y, x
-  sweep3<N, 0, true, true>(W1, W0, Dg, nt);
+  sweep3<N, 0, true, true, true>(W1, W0, Dg, nt);
   __syncthreads();
-  sweep3<N, 1, true, true>(W2, W0, Dg, nt);
+  sweep3<N, 1, true, true, true>(W2, W0, Dg, nt);
   __syncthreads();
   for (int line = threadIdx.x; line < nt * N2; line += blockDim.x) {
     const int t = line / N2, r = line - t * N2;
     const int off = t * N3 + r;
     T v[N], z[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) z[j] = Y[off + j * N2];
+    for (int j = 0; j < N; ++j) z[j] = Y[swz<N, T>(off + j * N2)];
 #pragma unroll
-    for (int o = 0; o < N; ++o) v[o] = W0[off + o * N2] + line_dot<N, true>(Dg, z, o);
+    for (int o = 0; o < N; ++o) v[o] = W0[swz<N, T>(off + o * N2)] + line_dot<N, true>(Dg, z, o);
 #pragma unroll
-    for (int o = 0; o < N; ++o) W1[off + o * N2] = line_dot<N, true>(S, v, o);
+    for (int o = 0; o < N; ++o) W1[swz<N, T>(off + o * N2)] = line_dot<N, true>(S, v, o);
   }
   __syncthreads();
-  sweep3<N, 1, true, false>(W1, W2, S, nt);
+  sweep3<N, 1, true, false, true>(W1, W2, S, nt);
   __syncthreads();
-  sweep3<N, 0, true, false>(W2, Y, S, nt);  // Y = cell contribution to y
+  sweep3<N, 0, true, false, true>(W2, Y, S, nt);  // Y = cell contribution to y
   __syncthreads();
 
   // ---- face terms, both faces of one direction at a time (work region reused)
   for (int d = 0; d < 3; ++d)
-    face_pair<N, NC, TX, TN, T>(d, g, Ssh, Dsh, cell0, x, nu_face, Xs, Y, Wk, pen, nbt, ih, gw, dS0, dS1);
+    face_pair<N, NC, TX, TN, T>(d, g, Ssh, Dsh, cell0, x, nu_face, Xs, Y, Wk, pen, nbt, ih, lc.area[d], gw, dS0,
+                                dS1);
   const size_t base0 = (size_t)cell0 * NC * N3;
-  for (int i = threadIdx.x; i < ncell * NC * N3; i += blockDim.x) y[base0 + i] = stream_store<TS>(Y[i]);
+  for (int i = threadIdx.x; i < ncell * NC * N3; i += blockDim.x) y[base0 + i] = stream_store<TS>(Y[swz<N, T>(i)]);
 }
 
 // One CTA per CPB consecutive cells of one level; blockIdx.y selects one of
@@ -640,12 +714,12 @@ __device__ __forceinline__ void apply_cells(const LevelGeom& g, const CTab<T>& c
 // level has topology tables (removed cells or periodic directions).
 template <int N, int NC, typename TX, typename TS, typename TN, typename T, bool TOPO>
 __global__ void __launch_bounds__(OpCfg<N, NC>::NT, (OccCfg<N, NC, T>::MIN))
-apply_kernel(LevelGeom g, CTab<T> ct, const TX* __restrict__ x, TS* __restrict__ y,
-             const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, double mass_d, int64_t batch_stride) {
+apply_kernel(LevelGeom g, CTab<T> ct, LevelConsts<T> lc, const TX* __restrict__ x, TS* __restrict__ y,
+             const TN* __restrict__ nu_cell, const TN* __restrict__ nu_face, int64_t batch_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
-  apply_cells<N, NC, TX, TS, TN, T, TOPO>(g, ct, x, y, nu_cell, nu_face, mass_d, blockIdx.x * OpCfg<N, NC>::CPB,
+  apply_cells<N, NC, TX, TS, TN, T, TOPO>(g, ct, lc, x, y, nu_cell, nu_face, blockIdx.x * OpCfg<N, NC>::CPB,
                                           smem_raw);
 }
 
@@ -657,11 +731,11 @@ apply_kernel(LevelGeom g, CTab<T> ct, const TX* __restrict__ x, TS* __restrict__
 template <typename TS, typename TN>
 struct ApplyDesc {
   LevelGeom g;
+  LevelConsts<TN> lc;  // in the arithmetic type, which is that of nu
   const TS* x;
   TS* y;
   const TN* nu_cell;
   const TN* nu_face;
-  double mass;
 };
 
 template <int N, int NC, typename TS, typename TN, typename T>
@@ -671,8 +745,9 @@ apply_multi_kernel(const ApplyDesc<TS, TN>* __restrict__ descs, const int2* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int2 tl = tiles[tile];
+    static_assert(std::is_same<TN, T>::value, "served applies compute in the type of nu");
     const ApplyDesc<TS, TN> d = descs[tl.x];
-    apply_cells<N, NC, TS, TS, TN, T, false>(d.g, ct, d.x, d.y, d.nu_cell, d.nu_face, d.mass, tl.y, smem_raw);
+    apply_cells<N, NC, TS, TS, TN, T, false>(d.g, ct, d.lc, d.x, d.y, d.nu_cell, d.nu_face, tl.y, smem_raw);
     __syncthreads();  // the next tile reuses the shared memory
   }
 }

@@ -22,6 +22,7 @@
 #pragma once
 #include "common.cuh"
 #include "ff.cuh"
+#include "operator.cuh"
 
 namespace sipg {
 
@@ -213,12 +214,12 @@ template <int N, int NC, bool TOPO, int D>
 __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, const float* __restrict__ x,
                                           const float* __restrict__ xe, const float* __restrict__ nu_face, int e,
                                           int kk, int cw, bool active, const int* ijk, const float* ihf, float lam_e,
-                                          float (&t)[N * N * N], float* tsm) {
+                                          const LevelConsts<float>& lc, float (&t)[N * N * N], float* tsm) {
   constexpr int N2 = N * N, N3 = N2 * N;
   (void)N3;
   const int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
   const float ihd = ihf[D], iht1 = ihf[T1], iht2 = ihf[T2];
-  const float area = (float)(g.h[T1] * g.h[T2]);
+  const float area = lc.area[D];
 #pragma unroll 1
   for (int s = 0; s < 2; ++s) {
     const int f = 2 * D + s;
@@ -274,7 +275,7 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
         if (!TOPO) nijk[D] += s ? 1 : -1;
         lam_n = lambda_f<TOPO>(g, nb, nijk, ihf);
       }
-      pe = (float)g.cip * float(N * N) * fmaxf(lam_e, lam_n);
+      pe = lc.cipn2 * fmaxf(lam_e, lam_n);
     }
     const float nsign = s ? 1.f : -1.f;
     float gV[N2], gN[N2];
@@ -386,8 +387,8 @@ __device__ __forceinline__ void tpc_faces(const LevelGeom& g, const TpcTab& tb, 
 
 template <int N, int NC, bool TOPO>
 __global__ void __launch_bounds__(32, 8)
-apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __restrict__ y,
-                 const float* __restrict__ nu_cell, const float* __restrict__ nu_face, float mass,
+apply_tpc_kernel(LevelGeom g, TpcTab tb, LevelConsts<float> lc, const float* __restrict__ x,
+                 float* __restrict__ y, const float* __restrict__ nu_cell, const float* __restrict__ nu_face,
                  int64_t batch_stride) {
   constexpr int N2 = N * N, N3 = N2 * N, CW = TpcCfg<NC>::CW;
   extern __shared__ __align__(16) float tsm[];
@@ -401,8 +402,9 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
   const bool store = active && cell_raw < g.ncells;
   const int e = min(cell_raw, g.ncells - 1);
   const int kk = active ? k : 0;
-  const float ihf[3] = {(float)g.ih[0], (float)g.ih[1], (float)g.ih[2]};
-  const float detJ = (float)(g.h[0] * g.h[1] * g.h[2]);
+  const float ihf[3] = {lc.ih[0], lc.ih[1], lc.ih[2]};
+  const float detJ = lc.detJ;
+  const float mass = lc.mass;
   int ijk[3] = {0, 0, 0};
   if (!TOPO) {
     ijk[0] = e % g.nx;
@@ -522,9 +524,9 @@ apply_tpc_kernel(LevelGeom g, TpcTab tb, const float* __restrict__ x, float* __r
   {
     lam_e = lambda_f<TOPO>(g, e, ijk, ihf);
   }
-  tpc_faces<N, NC, TOPO, 0>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, t, tsm);
-  tpc_faces<N, NC, TOPO, 1>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, t, tsm);
-  tpc_faces<N, NC, TOPO, 2>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, t, tsm);
+  tpc_faces<N, NC, TOPO, 0>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, lc, t, tsm);
+  tpc_faces<N, NC, TOPO, 1>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, lc, t, tsm);
+  tpc_faces<N, NC, TOPO, 2>(g, tb, x, xe, nu_face, e, kk, cw, active, ijk, ihf, lam_e, lc, t, tsm);
   if (store) {
     float* ye = y + ((size_t)e * NC + kk) * N3;
     if constexpr (N3 % 4 == 0) {

@@ -422,7 +422,7 @@ int sipg_server::batched_apply(const std::map<int, std::vector<Request*>>& by_k)
         d.nu_cell = L.nu_cell64;
         d.nu_face = L.nu_face64;
       }
-      d.mass = 0.0;
+      d.lc = level_consts<TN>(L.g, kv.first + 1, 0.0);
       const int di = (int)descs.size();
       descs.push_back(d);
       const int cpb = op_cells_per_cta(kv.first + 1, 3);
