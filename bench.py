@@ -781,7 +781,7 @@ def component_timings(stream, contrast=1e2):
 
 
 def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5, sizes=(8, 12, 16), degrees=(2, 3, 4),
-                   contrasts=(1.0, 1e2, 1e4), rhs="buoyancy", budget_gib=96, slots=8):
+                   contrasts=(1.0, 1e2, 1e4), rhs="buoyancy", budget_gib=96, slots=8, progress=False):
     """Served stream: Poisson arrivals, uneven sizes/degrees/contrasts, rtol 1e-8.
 
     Each request solves the viscous system on the n^3 unit cube (Dirichlet walls) with
@@ -839,6 +839,8 @@ def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5, sizes=(8, 12, 16), deg
         service.append(time.perf_counter() - t0 - t_rhs)
     out["one_at_a_time_service_s"] = {"total": float(sum(service)), "mean": float(np.mean(service)),
                                       "max": float(max(service))}
+    if progress:
+        print(json.dumps({"serving_one_at_a_time": out["one_at_a_time_service_s"]}), file=sys.stderr, flush=True)
     runs = []
     for rate in rates:
         arr = np.cumsum(np.random.default_rng(seed + int(rate)).exponential(1.0 / rate, n_req))
@@ -866,8 +868,10 @@ def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5, sizes=(8, 12, 16), deg
                      "max_rel_residual": max(r["rel_residual"] for r in res),
                      "makespan_s": t_end - t0,
                      "one_at_a_time": {"solves_per_s": n_req / max(fin, arr[-1]),
-                                            "p50_s": float(np.percentile(lat_seq, 50)),
-                                            "p99_s": float(np.percentile(lat_seq, 99))}})
+                                       "p50_s": float(np.percentile(lat_seq, 50)),
+                                       "p99_s": float(np.percentile(lat_seq, 99))}})
+        if progress:  # one line per finished rate on stderr (long runs)
+            print(json.dumps({"serving_rate_done": runs[-1]}), file=sys.stderr, flush=True)
     out["runs"] = runs
     return out
 
@@ -877,7 +881,7 @@ def serving_full():
     in {1, 1e2, 1e4}, sphere-buoyancy right-hand sides, Poisson arrivals at 10, 20, 50, 100
     and 200 per second."""
     return serving_extras(n_req=256, rates=(10.0, 20.0, 50.0, 100.0, 200.0), sizes=(8, 16, 24, 32, 40, 48),
-                          degrees=(2, 3, 4, 5), budget_gib=160, slots=12)
+                          degrees=(2, 3, 4, 5), budget_gib=160, slots=12, progress=True)
 
 
 # ------------------------------------------------------------- CPU oracle

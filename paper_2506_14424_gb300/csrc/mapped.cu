@@ -29,20 +29,25 @@
 
 // Cells per CTA of the trilinear apply (128 threads): at low degree one cell
 // leaves most lanes idle between the barriers of its sweeps (n^3 = 8 or 27
-// points), so several cells share a CTA and every phase runs over all of them.
-// Resident CTAs per SM requested from the compiler: the kernel is latency bound
-// (barriers between sweeps); one cell per CTA measured at 32^3, k = 3: 2 CTAs
-// 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers) 11.1 ms.
-#ifndef SIPG_MAPPED_CBX
-#define SIPG_MAPPED_CBX 1
-#endif
-#ifndef SIPG_MAPPED_MINB
-#define SIPG_MAPPED_MINB 4
-#endif
+// points), so several cells share a CTA and every phase runs over all of them;
+// the tensors live in dynamic shared memory. Measured at 32^3, 5 % jitter (FP32
+// level applies k = 3 / 2 / 1 viscous and k = 2 pressure, ms): 2 / 4 / 8 cells
+// 1.17 / 0.58 / 0.24 / 0.36, twice that 0.84 / 0.52 / 0.16 / 0.27, three times
+// 0.82 / 0.49 / 0.14 / 0.22, four times 0.93 / 0.71 / 0.14 / 0.29; the FP64
+// apply (bound by the FP64 pipe) is slower with more cells (3.88 -> 4.44 ms).
+// Resident CTAs per SM requested from the compiler: one cell per CTA measured at
+// 32^3, k = 3: 2 CTAs 22.5 ms, 4 (128 registers) 12.7 ms, 8 (64 registers)
+// 11.1 ms; with the stored metric the budget of 4 keeps every instance unspilled.
 template <int N, typename R = double> struct MappedCfg {
-  static constexpr int CB = (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1))) * (sizeof(R) == 4 && N <= 4 ? SIPG_MAPPED_CBX : 1);
-  static constexpr int MIN_BLOCKS = sizeof(R) == 4 && N <= 4 ? SIPG_MAPPED_MINB : (N <= 4 ? 4 : (N == 5 ? 6 : 4));
+  static constexpr int CB = (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1))) * (sizeof(R) == 4 && N <= 4 ? 3 : 1);
+  static constexpr int MIN_BLOCKS = N <= 4 ? 4 : (N == 5 ? 6 : 4);
 };
+// dynamic shared memory of the apply (elements of R): U, Q, G[3], T0, T1, OUT
+// (n^3 per tensor) and FM, FP, CF (4 n^2), SC (8 n^2) per tensor of the CTA
+template <int N, int NC, typename R>
+constexpr size_t mapped_apply_smem() {
+  return sizeof(R) * (size_t)MappedCfg<N, R>::CB * NC * (8 * N * N * N + 20 * N * N);
+}
 
 namespace sipg {
 namespace {
@@ -108,6 +113,7 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_metric_kernel(LevelGeom 
 
 template <int N, int NC, typename R>
 __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+                                                                     mgeo::MTab<R> mt,
                                                                      const R* __restrict__ cmet,
                                                                      const R* __restrict__ fmet,
                                                                      const double* __restrict__ lam,
@@ -117,9 +123,20 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) ma
                                                                      R* __restrict__ y, int64_t batch_stride) {
   constexpr int N3 = N * N * N, N2 = N * N, CB = MappedCfg<N, R>::CB, NT = CB * NC;
   __shared__ STabSmT<R> T;
-  __shared__ R U[NT][N3], Q[NT][N3], G[3][NT][N3], T0[NT][N3], T1[NT][N3], OUT[NT][N3];
-  __shared__ R FM[NT][4 * N2], FP[NT][4 * N2], CF[NT][4 * N2], SC[8 * NT * N2];
   __shared__ int NB[CB];
+  extern __shared__ __align__(16) unsigned char msm_raw[];
+  R* msm = reinterpret_cast<R*>(msm_raw);
+  R(*U)[N3] = reinterpret_cast<R(*)[N3]>(msm);
+  R(*Q)[N3] = reinterpret_cast<R(*)[N3]>(msm + 1 * NT * N3);
+  R(*G)[NT][N3] = reinterpret_cast<R(*)[NT][N3]>(msm + 2 * NT * N3);
+  R(*T0)[N3] = reinterpret_cast<R(*)[N3]>(msm + 5 * NT * N3);
+  R(*T1)[N3] = reinterpret_cast<R(*)[N3]>(msm + 6 * NT * N3);
+  R(*OUT)[N3] = reinterpret_cast<R(*)[N3]>(msm + 7 * NT * N3);
+  R* fbase = msm + 8 * NT * N3;
+  R(*FM)[4 * N2] = reinterpret_cast<R(*)[4 * N2]>(fbase);
+  R(*FP)[4 * N2] = reinterpret_cast<R(*)[4 * N2]>(fbase + 4 * NT * N2);
+  R(*CF)[4 * N2] = reinterpret_cast<R(*)[4 * N2]>(fbase + 8 * NT * N2);
+  R* SC = fbase + 12 * NT * N2;
   const R mass = (R)mass_d;
   x += (int64_t)blockIdx.y * batch_stride;
   y += (int64_t)blockIdx.y * batch_stride;
@@ -131,8 +148,20 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) ma
   }
   __syncthreads();
   // ---- cell term
-  sweep3b<N, N, false>(T.S, N, U[0], T0[0], T1[0], Q[0], NT);
-  for (int m = 0; m < 3; ++m) sweep_dirb<N, false>(m, T.Dg, Q[0], G[m][0], NT);
+  if constexpr (mapped_line_sweeps<N>()) {
+    lsweep<N, 0, false, false>(mt.S, U[0], T0[0], NT);
+    __syncthreads();
+    lsweep<N, 1, false, false>(mt.S, T0[0], T1[0], NT);
+    __syncthreads();
+    lsweep<N, 2, false, false>(mt.S, T1[0], Q[0], NT);
+    __syncthreads();
+    lsweep<N, 0, false, false>(mt.Dg, Q[0], G[0][0], NT);
+    lsweep<N, 1, false, false>(mt.Dg, Q[0], G[1][0], NT);
+    lsweep<N, 2, false, false>(mt.Dg, Q[0], G[2][0], NT);
+  } else {
+    sweep3b<N, N, false>(T.S, N, U[0], T0[0], T1[0], Q[0], NT);
+    for (int m = 0; m < 3; ++m) sweep_dirb<N, false>(m, T.Dg, Q[0], G[m][0], NT);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < CB * N3; i += blockDim.x) {
     const int c = i / N3, q = i - c * N3;
@@ -164,13 +193,29 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) ma
     }
   }
   __syncthreads();
-  for (int m = 0; m < 3; ++m) {
-    sweep_dirb<N, true>(m, T.Dg, G[m][0], T0[0], NT);
+  // Q += Dx^T Gx + Dy^T Gy + Dz^T Gz, then S^T along x, y, z
+  if constexpr (mapped_line_sweeps<N>()) {
+    lsweep<N, 0, true, true>(mt.Dg, G[0][0], Q[0], NT);
     __syncthreads();
-    for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) Q[0][i] += T0[0][i];
+    lsweep<N, 1, true, true>(mt.Dg, G[1][0], Q[0], NT);
     __syncthreads();
+    lsweep<N, 2, true, true>(mt.Dg, G[2][0], Q[0], NT);
+    __syncthreads();
+    lsweep<N, 0, true, false>(mt.S, Q[0], T0[0], NT);
+    __syncthreads();
+    lsweep<N, 1, true, false>(mt.S, T0[0], T1[0], NT);
+    __syncthreads();
+    lsweep<N, 2, true, false>(mt.S, T1[0], OUT[0], NT);
+    __syncthreads();
+  } else {
+    for (int m = 0; m < 3; ++m) {
+      sweep_dirb<N, true>(m, T.Dg, G[m][0], T0[0], NT);
+      __syncthreads();
+      for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) Q[0][i] += T0[0][i];
+      __syncthreads();
+    }
+    sweep3b<N, N, true>(T.S, N, Q[0], T0[0], T1[0], OUT[0], NT);
   }
-  sweep3b<N, N, true>(T.S, N, Q[0], T0[0], T1[0], OUT[0], NT);
   // ---- faces
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, s = f & 1;
@@ -179,13 +224,13 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) ma
     const int fo = 2 * d + (1 - s);
     for (int c = threadIdx.x; c < CB; c += blockDim.x) NB[c] = cell_neighbor(g, min(e0 + c, last), f);
     __syncthreads();
-    face_evalb<N>([&](int b, int i) { return U[b][i]; }, d, s, T, FM[0], SC, NT);
+    face_evalb<N>([&](int b, int i) { return U[b][i]; }, d, s, T, mt, FM[0], SC, NT);
     face_evalb<N>(
         [&](int b, int i) {
           const int nb = NB[b / NC];
           return nb >= 0 ? x[(size_t)nb * NC * N3 + (b % NC) * N3 + i] : R(0);
         },
-        d, 1 - s, T, FP[0], SC, NT);
+        d, 1 - s, T, mt, FP[0], SC, NT);
     for (int i = threadIdx.x; i < CB * N2; i += blockDim.x) {
       const int c = i / N2, p = i - c * N2;
       const int e = min(e0 + c, last);
@@ -269,7 +314,7 @@ __global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) ma
       }
     }
     __syncthreads();
-    face_eval_tb<N>(CF[0], d, s, T, OUT[0], SC, NT);
+    face_eval_tb<N>(CF[0], d, s, T, mt, OUT[0], SC, NT);
   }
   for (int i = threadIdx.x; i < NT * N3; i += blockDim.x) {
     const int c = (i / N3) / NC;
@@ -450,21 +495,39 @@ cudaError_t launch_mapped_metric(int n, const LevelGeom& g, const SplitTab& tab,
   return cudaGetLastError();
 }
 
+// one launch of the trilinear apply: shared-memory opt-in once per instantiation
+template <int N, int NC, typename R>
+cudaError_t launch_mapped_apply_n(const LevelGeom& g, const SplitTab& tab, const R* cmet, const R* fmet,
+                                  const double* lam, const R* nu_cell, const R* nu_face, double mass, const R* x, R* y,
+                                  int nbatch, cudaStream_t st) {
+  constexpr size_t smem = mapped_apply_smem<N, NC, R>();
+  static bool attr_set = false;  // per instantiation, per process (single device)
+  if (!attr_set) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(mapped_apply_kernel<N, NC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  constexpr int cb = MappedCfg<N, R>::CB;
+  const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
+  const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
+  mapped_apply_kernel<N, NC, R><<<grid, kSplitThreads, smem, st>>>(g, tab, mgeo::make_mtab<R>(tab), cmet, fmet, lam,
+                                                                     nu_cell, nu_face, mass, x, y, stride);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mapped_apply(int n, int ncomp, const LevelGeom& g, const SplitTab& tab, const double* cmet,
                                 const double* fmet, const double* lam, const double* nu_cell, const double* nu_face,
                                 double mass, const double* x, double* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
-  const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
-  const int cb = n == 2 ? MappedCfg<2>::CB : (n == 3 ? MappedCfg<3>::CB : (n == 4 ? MappedCfg<4>::CB : 1));
-  const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, double><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
+    SIPG_MAPPED_DISPATCH(n, return (launch_mapped_apply_n<N, 3, double>(g, tab, cmet, fmet, lam, nu_cell, nu_face,
+                                                                        mass, x, y, nbatch, st)));
   } else {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, double><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
+    SIPG_MAPPED_DISPATCH(n, return (launch_mapped_apply_n<N, 1, double>(g, tab, cmet, fmet, lam, nu_cell, nu_face,
+                                                                        mass, x, y, nbatch, st)));
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 // the same operator in FP32 (multigrid levels: metric, sweeps and flux in binary32)
@@ -472,20 +535,14 @@ cudaError_t launch_mapped_apply_f32(int n, int ncomp, const LevelGeom& g, const 
                                     const float* fmet, const double* lam, const float* nu_cell, const float* nu_face,
                                     double mass, const float* x, float* y, int nbatch, cudaStream_t st) {
   if (g.ncells == 0 || nbatch == 0) return cudaSuccess;
-  const int64_t stride = (int64_t)g.ncells * ncomp * n * n * n;
-  const int cb = n == 2 ? MappedCfg<2, float>::CB
-                         : (n == 3 ? MappedCfg<3, float>::CB
-                                   : (n == 4 ? MappedCfg<4, float>::CB : (n == 5 ? MappedCfg<5, float>::CB
-                                                                                 : MappedCfg<6, float>::CB)));
-  const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
   if (ncomp == 3) {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 3, float><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
+    SIPG_MAPPED_DISPATCH(n, return (launch_mapped_apply_n<N, 3, float>(g, tab, cmet, fmet, lam, nu_cell, nu_face,
+                                                                       mass, x, y, nbatch, st)));
   } else {
-    SIPG_MAPPED_DISPATCH(n, (mapped_apply_kernel<N, 1, float><<<grid, kSplitThreads, 0, st>>>(
-                                g, tab, cmet, fmet, lam, nu_cell, nu_face, mass, x, y, stride)));
+    SIPG_MAPPED_DISPATCH(n, return (launch_mapped_apply_n<N, 1, float>(g, tab, cmet, fmet, lam, nu_cell, nu_face,
+                                                                       mass, x, y, nbatch, st)));
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 // Vertices of a coarser level of the same structured mesh: every (stride)-th vertex.
@@ -523,7 +580,7 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_diagonal_kernel(LevelGeo
                                                                         double mass, double* __restrict__ diag) {
   constexpr int N3 = N * N * N, N2 = N * N;
   __shared__ STabSm T;
-  __shared__ double X[8][3], XN[8][3];
+  __shared__ double X[8][3];
   __shared__ double JI[9][N3], WQ[N3], NU[N3];
   __shared__ double FJ[9][N2], FNm[3][N2], FW[N2], FT[N2], FNU[N2];
   __shared__ double ACC[NC][N3];

@@ -138,10 +138,84 @@ __device__ void face_eval_t(const R* cf, int d, int s, const STabSmT<R>& T, R* Y
 }
 
 
+// 1D matrices of the trilinear apply as a kernel parameter: in the line sweeps
+// below every matrix index is a compile-time constant, so S, DS and Dg are
+// constant-bank operands of the multiply-adds (no shared-memory loads of the
+// matrices, one thread per line instead of one per output entry)
+template <typename R>
+struct MTab {
+  R S[kMaxN * kMaxN], DS[kMaxN * kMaxN], Dg[kMaxN * kMaxN];
+};
+template <typename R>
+inline MTab<R> make_mtab(const SplitTab& t) {
+  MTab<R> m{};
+  for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    m.S[i] = (R)t.S[i];
+    m.DS[i] = (R)t.DS[i];
+    m.Dg[i] = (R)t.Dg[i];
+  }
+  return m;
+}
+
+// out (+)= M along DIR on ntens consecutive N^3 tensors (x fastest), one thread
+// per 1D line: its N inputs in registers, N outputs; M(o, j) = M[o N + j], or
+// M[j N + o] if TR
+template <int N, int DIR, bool TR, bool ACC, typename R>
+__device__ __forceinline__ void lsweep(const R* M, const R* __restrict__ in, R* __restrict__ out, int ntens) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int STR = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
+  for (int line = threadIdx.x; line < ntens * N2; line += blockDim.x) {
+    const int t = line / N2, r = line - t * N2;
+    const int off = t * N3 + (DIR == 0 ? r * N : (DIR == 1 ? (r % N) + (r / N) * N2 : r));
+    R v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = in[off + j * STR];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      R acc = R(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc += (TR ? M[j * N + o] : M[o * N + j]) * v[j];
+      R* dst = out + off + o * STR;
+      *dst = ACC ? *dst + acc : acc;
+    }
+  }
+}
+
+// the same on ntens consecutive N^2 face tensors (a fastest): DIR 0 along a, 1 along b
+template <int N, int DIR, bool TR, typename R>
+__device__ __forceinline__ void lsweep2(const R* M, const R* __restrict__ in, R* __restrict__ out, int ntens) {
+  constexpr int N2 = N * N;
+  constexpr int STR = DIR == 0 ? 1 : N;
+  for (int line = threadIdx.x; line < ntens * N; line += blockDim.x) {
+    const int t = line / N, r = line - t * N;
+    const int off = t * N2 + (DIR == 0 ? r * N : r);
+    R v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = in[off + j * STR];
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      R acc = R(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc += (TR ? M[j * N + o] : M[o * N + j]) * v[j];
+      out[off + o * STR] = acc;
+    }
+  }
+}
+
+// Line sweeps (one thread per line, matrices in the kernel parameter) or entry
+// sweeps (one thread per output entry, matrices in shared memory): lines of an
+// even degree count N >= 4 are 4-way bank-conflicted (stride N), so they keep the
+// entry form. Measured at 32^3, 5 % jitter (FP32 level applies): n = 3 viscous
+// 0.49 -> 0.39 ms, n = 3 pressure 0.22 -> 0.21 ms, n = 2 0.143 -> 0.136 ms with
+// lines; n = 4 0.83 -> 1.22 ms (FP32) and 3.9 -> 5.0 ms (FP64) with lines.
+template <int N>
+__host__ __device__ constexpr bool mapped_line_sweeps() { return N == 2 || N % 2 == 1; }
+
 // face_eval on ntens tensors at once: src(b, i) is node i of tensor b (shared or
 // global memory); out: ntens x 4 N^2 ([b][slot][p]); sc: 6 ntens N^2 scratch
 template <int N, typename R, typename Src>
-__device__ void face_evalb(Src src, int d, int s, const STabSmT<R>& T, R* out, R* sc, int ntens) {
+__device__ __forceinline__ void face_evalb(Src src, int d, int s, const STabSmT<R>& T, const MTab<R>& mt, R* out,
+                                           R* sc, int ntens) {
   constexpr int N2 = N * N;
   const int M = ntens * N2;
   R *L = sc, *D = sc + M, *A = sc + 2 * M, *B = sc + 3 * M, *C = sc + 4 * M, *E = sc + 5 * M;
@@ -155,18 +229,31 @@ __device__ void face_evalb(Src src, int d, int s, const STabSmT<R>& T, R* out, R
     D[t] = acc;
   }
   __syncthreads();
-  // along a: A = S L, B = DS L, C = S D
-  sweepb<N, N, 1, 0, N, false>(T.S, N, L, A, ntens);
-  sweepb<N, N, 1, 0, N, false>(T.DS, N, L, B, ntens);
-  sweepb<N, N, 1, 0, N, false>(T.S, N, D, C, ntens);
-  __syncthreads();
-  // along b: values E = S A, d/dxi_d L = S C, d/dxi_t1 D = S B (inputs and outputs disjoint)
-  sweepb<N, N, 1, 1, N, false>(T.S, N, A, E, ntens);
-  sweepb<N, N, 1, 1, N, false>(T.S, N, C, L, ntens);
-  sweepb<N, N, 1, 1, N, false>(T.S, N, B, D, ntens);
-  __syncthreads();
-  sweepb<N, N, 1, 1, N, false>(T.DS, N, A, C, ntens);   // d/dxi_t2 = DS_b A
-  __syncthreads();
+  if constexpr (mapped_line_sweeps<N>()) {
+    // along a: A = S L, B = DS L, C = S D
+    lsweep2<N, 0, false>(mt.S, L, A, ntens);
+    lsweep2<N, 0, false>(mt.DS, L, B, ntens);
+    lsweep2<N, 0, false>(mt.S, D, C, ntens);
+    __syncthreads();
+    // along b: values E = S A, d/dxi_d L = S C, d/dxi_t1 D = S B (inputs and outputs disjoint)
+    lsweep2<N, 1, false>(mt.S, A, E, ntens);
+    lsweep2<N, 1, false>(mt.S, C, L, ntens);
+    lsweep2<N, 1, false>(mt.S, B, D, ntens);
+    __syncthreads();
+    lsweep2<N, 1, false>(mt.DS, A, C, ntens);  // d/dxi_t2 = DS_b A
+    __syncthreads();
+  } else {
+    sweepb<N, N, 1, 0, N, false>(T.S, N, L, A, ntens);
+    sweepb<N, N, 1, 0, N, false>(T.DS, N, L, B, ntens);
+    sweepb<N, N, 1, 0, N, false>(T.S, N, D, C, ntens);
+    __syncthreads();
+    sweepb<N, N, 1, 1, N, false>(T.S, N, A, E, ntens);
+    sweepb<N, N, 1, 1, N, false>(T.S, N, C, L, ntens);
+    sweepb<N, N, 1, 1, N, false>(T.S, N, B, D, ntens);
+    __syncthreads();
+    sweepb<N, N, 1, 1, N, false>(T.DS, N, A, C, ntens);
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < M; t += blockDim.x) {
     const int b = t / N2, p = t - b * N2;
     R* o = out + b * 4 * N2 + p;
@@ -181,7 +268,8 @@ __device__ void face_evalb(Src src, int d, int s, const STabSmT<R>& T, R* out, R
 // face_eval_t on ntens tensors: coefficients cf (ntens x 4 N^2, [b][slot][p]) added
 // to Y (ntens x N^3); sc: 8 ntens N^2 scratch
 template <int N, typename R>
-__device__ void face_eval_tb(const R* cf, int d, int s, const STabSmT<R>& T, R* Y, R* sc, int ntens) {
+__device__ __forceinline__ void face_eval_tb(const R* cf, int d, int s, const STabSmT<R>& T, const MTab<R>& mt, R* Y,
+                                             R* sc, int ntens) {
   constexpr int N2 = N * N, N3 = N2 * N;
   const int M = ntens * N2;
   R *V0 = sc, *V1 = sc + M, *V2 = sc + 2 * M, *V3 = sc + 3 * M;
@@ -196,17 +284,30 @@ __device__ void face_eval_tb(const R* cf, int d, int s, const STabSmT<R>& T, R* 
   }
   __syncthreads();
   // along b (transposed): value S^T, normal S^T, t1 S^T, t2 DS^T
-  sweepb<N, N, 1, 1, N, true>(T.S, N, V0, Pv, ntens);
-  sweepb<N, N, 1, 1, N, true>(T.S, N, V1, Pn, ntens);
-  sweepb<N, N, 1, 1, N, true>(T.S, N, V2, P1, ntens);
-  sweepb<N, N, 1, 1, N, true>(T.DS, N, V3, P2, ntens);
+  if constexpr (mapped_line_sweeps<N>()) {
+    lsweep2<N, 1, true>(mt.S, V0, Pv, ntens);
+    lsweep2<N, 1, true>(mt.S, V1, Pn, ntens);
+    lsweep2<N, 1, true>(mt.S, V2, P1, ntens);
+    lsweep2<N, 1, true>(mt.DS, V3, P2, ntens);
+  } else {
+    sweepb<N, N, 1, 1, N, true>(T.S, N, V0, Pv, ntens);
+    sweepb<N, N, 1, 1, N, true>(T.S, N, V1, Pn, ntens);
+    sweepb<N, N, 1, 1, N, true>(T.S, N, V2, P1, ntens);
+    sweepb<N, N, 1, 1, N, true>(T.DS, N, V3, P2, ntens);
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < M; t += blockDim.x) Pv[t] += P2[t];  // value and t2 parts share S_a^T
   __syncthreads();
   // along a (transposed): (value + t2) S^T, normal S^T, t1 DS^T
-  sweepb<N, N, 1, 0, N, true>(T.S, N, Pv, V0, ntens);
-  sweepb<N, N, 1, 0, N, true>(T.S, N, Pn, V1, ntens);
-  sweepb<N, N, 1, 0, N, true>(T.DS, N, P1, V2, ntens);
+  if constexpr (mapped_line_sweeps<N>()) {
+    lsweep2<N, 0, true>(mt.S, Pv, V0, ntens);
+    lsweep2<N, 0, true>(mt.S, Pn, V1, ntens);
+    lsweep2<N, 0, true>(mt.DS, P1, V2, ntens);
+  } else {
+    sweepb<N, N, 1, 0, N, true>(T.S, N, Pv, V0, ntens);
+    sweepb<N, N, 1, 0, N, true>(T.S, N, Pn, V1, ntens);
+    sweepb<N, N, 1, 0, N, true>(T.DS, N, P1, V2, ntens);
+  }
   __syncthreads();
   // layer nodes: values and tangential parts; every node along the normal line: normal part
   int t1, t2;
