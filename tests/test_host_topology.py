@@ -13,7 +13,8 @@ hierarchy, computed by the C library's host code, equal the oracle's mesh.
   coarse-size threshold) for the channel, a box and a periodic grid;
 * the default hierarchy choice (SIPG_MG_AUTO): the cph levels (the DG level, then the
   continuous twin of every DG level) on a plain box, the DG levels on a grid with
-  removed cells or a periodic direction.
+  removed cells or a periodic direction;
+* the estimate of trilinear cells counts the stored metric of every level.
 """
 import ctypes
 
@@ -195,3 +196,41 @@ def test_default_hierarchy_is_cph_on_plain_boxes(lib, op):
     chan = inputs.bfs_channel(4, inlet_length=1.0, outlet_length=3.0, depth=1.0)
     assert np.array_equal(_plan(lib, chan, 2, op, coarse=500, mg_cph=_lib.MG_AUTO),
                           _plan(lib, chan, 2, op, coarse=500, mg_cph=_lib.MG_DG))
+
+
+def test_estimate_counts_the_trilinear_metric(lib):
+    """Trilinear cells add the stored metric of every level of both hierarchies to the
+    estimate: 12 bytes (FP64 + FP32) per value, 10 n^3 cell values (J^-1, w det J) and
+    6 x 13 n^2 face values (J^-1, unit normal, surface weight) per cell; they drop the
+    float-float split buffer of level 0 (8 bytes per DoF), which only the affine
+    float-float operator uses."""
+    from oracle.mapped import jittered_vertices
+    from paper_2506_14424_gb300 import _lib
+    dims, k = (6, 4, 4), 3
+    V = np.ascontiguousarray(jittered_vertices(*dims, amp=0.05, seed=1), dtype=np.float64)
+    est = []
+    for verts in (None, V):
+        m = _lib.MeshDesc()
+        m.nx, m.ny, m.nz = dims
+        m.lx = m.ly = m.lz = 1.0
+        for i in range(6):
+            m.bc_velocity[i] = _lib.BC["D"]
+            m.bc_pressure[i] = _lib.BC["N"]
+        if verts is not None:
+            m.vertices = verts.ctypes.data
+        o = _lib.Opts()
+        lib.sipg_default_opts(ctypes.byref(o))
+        o.k_u = k
+        o.mg_cph = _lib.MG_DG
+        nbytes = ctypes.c_int64()
+        assert lib.sipg_estimate_bytes(ctypes.byref(m), ctypes.byref(o), ctypes.byref(nbytes)) == 0
+        est.append(nbytes.value)
+    box = _box(dims)
+    metric = split = 0
+    for op in ("viscous", "poisson"):
+        plan = _plan(lib, box, k, op, bc_v="DDDDDD", bc_p="NNNNNN", coarse=2000, mg_cph=_lib.MG_DG)
+        for row in plan:
+            n = int(row[3]) + 1
+            metric += 12 * int(row[4]) * (10 * n ** 3 + 78 * n ** 2)
+        split += 8 * int(plan[0][5])
+    assert est[1] - est[0] == metric - split
