@@ -863,8 +863,11 @@ def serving_extras(n_req=32, rates=(20.0, 100.0), seed=5, sizes=(8, 12, 16), deg
         srv.close()
         lat = np.array([r["latency_s"] for r in res])
         ok = sum(1 for r in res if r["status"] == 0 and r["rel_residual"] <= 1e-8)
+        status_counts = {}
+        for r in res:
+            status_counts[str(r["status"])] = status_counts.get(str(r["status"]), 0) + 1
         runs.append({"rate_per_s": rate, "solves_per_s": n_req / (t_end - t0), "p50_s": float(np.percentile(lat, 50)),
-                     "p99_s": float(np.percentile(lat, 99)), "converged": ok,
+                     "p99_s": float(np.percentile(lat, 99)), "converged": ok, "status_counts": status_counts,
                      "max_rel_residual": max(r["rel_residual"] for r in res),
                      "makespan_s": t_end - t0,
                      "one_at_a_time": {"solves_per_s": n_req / max(fin, arr[-1]),
