@@ -27,7 +27,7 @@
 #include "mapped_geom.cuh"
 #include "sweeps.cuh"
 
-// Cells per CTA of the trilinear apply (128 threads): at low degree one cell
+// Cells per CTA of the trilinear apply: at low degree one cell
 // leaves most lanes idle between the barriers of its sweeps (n^3 = 8 or 27
 // points), so several cells share a CTA and every phase runs over all of them;
 // the tensors live in dynamic shared memory. Measured at 32^3, 5 % jitter (FP32
@@ -40,7 +40,16 @@
 // 11.1 ms; with the stored metric the budget of 4 keeps every instance unspilled.
 template <int N, typename R = double> struct MappedCfg {
   static constexpr int CB = (N == 2 ? 8 : (N == 3 ? 4 : (N == 4 ? 2 : 1))) * (sizeof(R) == 4 && N <= 4 ? 3 : 1);
-  static constexpr int MIN_BLOCKS = N <= 4 ? 4 : (N == 5 ? 6 : 4);
+};
+// Threads per CTA and resident CTAs requested from the compiler: the FP32
+// instances are latency bound at 12 resident warps per SM (three 4-warp CTAs by
+// shared memory); measured FP32 level applies at 32^3 (ms, 128 / 192 / 256
+// threads): n = 4 viscous 0.83 / 0.80 / 0.78, n = 3 viscous 0.39 / 0.37 / 0.41,
+// n = 3 pressure 0.21 / 0.24 / 0.25, n = 2 viscous 0.14 / 0.16 / 0.16.
+template <int N, int NC, typename R> struct MappedLaunch {
+  static constexpr bool F32 = sizeof(R) == 4;
+  static constexpr int THREADS = F32 && N == 4 ? 256 : (F32 && N == 3 && NC == 3 ? 192 : sipg::sweeps::kSplitThreads);
+  static constexpr int MIN_BLOCKS = THREADS > sipg::sweeps::kSplitThreads ? 3 : (N <= 4 ? 4 : (N == 5 ? 6 : 4));
 };
 // dynamic shared memory of the apply (elements of R): U, Q, G[3], T0, T1, OUT
 // (n^3 per tensor) and FM, FP, CF (4 n^2), SC (8 n^2) per tensor of the CTA
@@ -112,7 +121,7 @@ __global__ void __launch_bounds__(kSplitThreads) mapped_metric_kernel(LevelGeom 
 }
 
 template <int N, int NC, typename R>
-__global__ void __launch_bounds__(kSplitThreads, MappedCfg<N, R>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
+__global__ void __launch_bounds__(MappedLaunch<N, NC, R>::THREADS, MappedLaunch<N, NC, R>::MIN_BLOCKS) mapped_apply_kernel(LevelGeom g, SplitTab tab,
                                                                      mgeo::MTab<R> mt,
                                                                      const R* __restrict__ cmet,
                                                                      const R* __restrict__ fmet,
@@ -511,7 +520,7 @@ cudaError_t launch_mapped_apply_n(const LevelGeom& g, const SplitTab& tab, const
   constexpr int cb = MappedCfg<N, R>::CB;
   const int64_t stride = (int64_t)g.ncells * NC * N * N * N;
   const dim3 grid((g.ncells + cb - 1) / cb, nbatch);
-  mapped_apply_kernel<N, NC, R><<<grid, kSplitThreads, smem, st>>>(g, tab, mgeo::make_mtab<R>(tab), cmet, fmet, lam,
+  mapped_apply_kernel<N, NC, R><<<grid, MappedLaunch<N, NC, R>::THREADS, smem, st>>>(g, tab, mgeo::make_mtab<R>(tab), cmet, fmet, lam,
                                                                      nu_cell, nu_face, mass, x, y, stride);
   return cudaGetLastError();
 }
