@@ -88,6 +88,7 @@ struct Request {
   double* hsc = nullptr;  // pinned: rr, flag
   cudaEvent_t ev_ready = nullptr, ev_rr = nullptr;
   int iters = 0;
+  int replacements = 0;  // restarts from the true residual (see confirm_or_restart)
   double bnorm = 0.0;
   Clock::time_point t_submit, t_admit, t_done;
   sipg_result result{};
@@ -141,6 +142,7 @@ struct sipg_server {
   template <typename TN>
   int batched_apply(const std::map<int, std::vector<Request*>>& by_k);
   int finish(Request* r);
+  int confirm_or_restart(Request* r, bool* restarted);
   int acquire_context(int nc, int k, int64_t need, ContextEntry** out);
   void release_entry(ContextEntry& c);
   void set_error(const std::string& m) {
@@ -493,6 +495,15 @@ int sipg_server::round() {
     const double res = std::sqrt(std::max(r->hsc[0], 0.0));
     const bool broke = r->hsc[1] != 0.0 || !std::isfinite(res);
     const bool conv = res <= r->spec.rtol * r->bnorm;
+    if (conv && !broke) {
+      bool restarted = false;
+      int rc = confirm_or_restart(r, &restarted);
+      if (rc) return rc;
+      if (restarted) {
+        still.push_back(r);
+        continue;
+      }
+    }
     if (conv || broke || r->iters >= r->spec.maxit) {
       r->result.status = conv ? SIPG_OK : (broke ? SIPG_ERR_BREAKDOWN : SIPG_ERR_MAXIT);
       int rc = finish(r);
@@ -502,6 +513,35 @@ int sipg_server::round() {
     }
   }
   active.swap(still);
+  return SIPG_OK;
+}
+
+// The recursive residual met the tolerance: confirm it with the true residual
+// b - A x. On large, high-contrast systems rounding in the recursion can leave the
+// true residual a few times above the recursive one; then CG restarts from the
+// true residual (r = b - A x, z = M r, p = z), at most kMaxReplacements times and
+// within maxit, instead of returning a solution above the tolerance.
+constexpr int kMaxReplacements = 3;
+int sipg_server::confirm_or_restart(Request* r, bool* restarted) {
+  *restarted = false;
+  if (r->replacements >= kMaxReplacements || r->iters >= r->spec.maxit) return SIPG_OK;
+  sipg_ctx* ctx = r->ctx;
+  cudaStream_t st = ctx->st;
+  Hier& H = ctx->hier[SIPG_OP_VISCOUS];
+  double *rr = H.cg[0], *z = H.cg[1], *p = H.cg[2], *t = H.cg[3];
+  const int64_t n = r->n;
+  int rc = ctx->krylov_apply(SIPG_OP_VISCOUS, r->x, t, 0.0);
+  if (rc) return rc;
+  if (launch_sub<double>(n, r->b, t, rr, st)) return SIPG_ERR_CUDA;
+  double rr2 = 0.0;
+  if ((rc = ctx->dot(n, rr, rr, &rr2))) return rc;
+  if (std::sqrt(rr2) <= r->spec.rtol * r->bnorm) return SIPG_OK;
+  rc = ctx->precondition(SIPG_OP_VISCOUS, SIPG_PRECOND_MG, rr, z, 0.0);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st)) return SIPG_ERR_CUDA;
+  if (launch_dot(n, rr, z, ctx->partials, r->sc + 0, st)) return SIPG_ERR_CUDA;
+  r->replacements++;
+  *restarted = true;
   return SIPG_OK;
 }
 

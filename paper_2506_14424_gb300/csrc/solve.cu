@@ -194,7 +194,8 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
   if ((rc = dot(n, r, r, &rr))) return rc;
   const double bnorm = std::sqrt(bnorm2);
   const double target = std::max(so.rtol * bnorm, so.atol);
-  int status = SIPG_OK, it = 0;
+  int status = SIPG_OK, it = 0, replacements = 0;
+  constexpr int kMaxReplacements = 3;
   if (!std::isfinite(rr)) status = SIPG_ERR_NAN;
   if (status == SIPG_OK && std::sqrt(rr) > target) {
     if ((rc = precondition(op, so.precond, r, z, so.mass_coeff))) return rc;
@@ -215,7 +216,22 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
       ++it;
       if ((rc = dot(n, r, r, &rr))) return rc;
       if (!std::isfinite(rr)) { status = SIPG_ERR_NAN; break; }
-      if (std::sqrt(rr) <= target) break;
+      if (std::sqrt(rr) <= target) {
+        // confirm with the true residual b - A x: on large, high-contrast systems
+        // rounding in the recursion can leave it a few times above the recursive
+        // one; then restart from it (at most kMaxReplacements times, within maxit)
+        if (replacements >= kMaxReplacements || it >= so.maxit) break;
+        if ((rc = krylov_apply(op, x, q, so.mass_coeff))) return rc;
+        CK(launch_sub<double>(n, bb, q, r, st));
+        if (proj) { if ((rc = project_mean(n, r))) return rc; }
+        if ((rc = dot(n, r, r, &rr))) return rc;
+        if (std::sqrt(rr) <= target) break;
+        ++replacements;
+        if ((rc = precondition(op, so.precond, r, z, so.mass_coeff))) return rc;
+        CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        if ((rc = dot(n, r, z, &rz))) return rc;
+        continue;
+      }
       if ((rc = precondition(op, so.precond, r, z, so.mass_coeff))) return rc;
       double rz_new;
       if ((rc = dot(n, r, z, &rz_new))) return rc;
