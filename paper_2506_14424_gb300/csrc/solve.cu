@@ -196,6 +196,7 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
   const double target = std::max(so.rtol * bnorm, so.atol);
   int status = SIPG_OK, it = 0, replacements = 0;
   constexpr int kMaxReplacements = 3;
+  bool true_rr = false;  // r and rr hold the true residual of x
   if (!std::isfinite(rr)) status = SIPG_ERR_NAN;
   if (status == SIPG_OK && std::sqrt(rr) > target) {
     if ((rc = precondition(op, so.precond, r, z, so.mass_coeff))) return rc;
@@ -225,7 +226,9 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
         CK(launch_sub<double>(n, bb, q, r, st));
         if (proj) { if ((rc = project_mean(n, r))) return rc; }
         if ((rc = dot(n, r, r, &rr))) return rc;
+        true_rr = true;
         if (std::sqrt(rr) <= target) break;
+        true_rr = false;
         ++replacements;
         if ((rc = precondition(op, so.precond, r, z, so.mass_coeff))) return rc;
         CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -240,11 +243,13 @@ int sipg_ctx::solve(int op, const double* b, double* x, const sipg_solve_opts* s
       rz = rz_new;
     }
   }
-  // true residual of the returned iterate
-  if ((rc = krylov_apply(op, x, q, so.mass_coeff))) return rc;
-  CK(launch_sub<double>(n, bb, q, r, st));
-  if (proj) { if ((rc = project_mean(n, r))) return rc; }
-  if ((rc = dot(n, r, r, &rr))) return rc;
+  // true residual of the returned iterate (already at hand after a confirmed convergence)
+  if (!true_rr) {
+    if ((rc = krylov_apply(op, x, q, so.mass_coeff))) return rc;
+    CK(launch_sub<double>(n, bb, q, r, st));
+    if (proj) { if ((rc = project_mean(n, r))) return rc; }
+    if ((rc = dot(n, r, r, &rr))) return rc;
+  }
   CK(cudaStreamSynchronize(st));
   const auto t1 = std::chrono::steady_clock::now();
   if (stats) {
