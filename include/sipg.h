@@ -246,7 +246,10 @@ int sipg_level_apply(sipg_ctx* ctx, int op, int level, int prec, const void* x, 
  * arithmetic is opts.mg_precision. b, x: DEVICE double*; x holds the initial
  * guess on entry and the solution on return. For the all-Neumann Poisson
  * operator, b and the iterates are kept mean-free (Sec. 3.2: the pressure is
- * fixed up to a constant). (sync) */
+ * fixed up to a constant). Convergence of the recursive residual is confirmed
+ * with the true residual b - A x; when that is still above the tolerance, CG
+ * restarts from it (at most three times, within maxit). stats->rel_residual is
+ * the true relative residual of the returned x. (sync) */
 int sipg_solve(sipg_ctx* ctx, int op, const double* b, double* x, const sipg_solve_opts* so,
                sipg_solve_stats* stats);
 
@@ -567,7 +570,10 @@ typedef struct {
                                 SIPG_LAW_CONSTANT, ANALYTIC or SINKER */
   int rhs;                   /* SIPG_RHS_* */
   const double* b;           /* HOST or DEVICE right-hand side (rhs HOST / DEVICE) */
-  double rtol;               /* relative residual target ||b - A x|| <= rtol ||b|| */
+  double rtol;               /* relative residual target ||b - A x|| <= rtol ||b||: met by the
+                                recursive CG residual, then confirmed with the true one (CG
+                                restarts from the true residual, at most three times, when
+                                it is still above the target) */
   int maxit;
   uint64_t seed;             /* of u* (rhs MANUFACTURED) */
   int keep_solution;         /* keep x for sipg_server_poll */
